@@ -1,0 +1,290 @@
+"""Benchmark: direction-optimised BFS on R-MAT scale 22 (edge factor 16,
+a=.57 b=.19 c=.19 d=.05, symmetrised, duplicates and self-loops removed,
+seed 2) from 64 seeded random non-isolated sources, one GB300.
+
+A step = one BFS from each of the 64 sources (the Graph500-style batch);
+value = 64 * m_stored / step time in GTEPS (TEPS counts stored nonzeros as
+the paper's Table 9 does), which equals the harmonic mean of the per-BFS
+TEPS. The graph (0.5 GB of column indices) is larger than the 129 MB L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the oracle (plain single-threaded C queue BFS) on
+the host cores over a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SCALE, EF, SEED, NSRC, SRC_SEED = 22, 16, 2, 64, 1
+METRIC = "BFS GTEPS (R-MAT s22 ef16, 64 sources, direction-optimised)"
+WORKLOAD = "rmat_s22_e16_seed2_bfs64"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device=0):
+        self.device = device
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for k, nm in enumerate(names):
+                if s[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_inputs():
+    import gen
+    t = gen.rmat(SCALE, EF, seed=SEED)
+    srcs = gen.sources(t, NSRC, seed=SRC_SEED)
+    return t, srcs
+
+
+def run_reference(args):
+    """The oracle, as it stands, timed on the host cores."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    t, srcs = make_inputs()
+    g = oracle.csr_from_tuples(t)
+    m = g.m
+    per_step = max(1, args.ref_sources)
+    step_times = []
+    k = 0
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for _ in range(per_step):
+            oracle.bfs(g, int(srcs[k % len(srcs)]))
+            k += 1
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            step_times.append(dt)
+    tot = sum(step_times)
+    value = per_step * args.steps * m / tot / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{per_step} BFS per step of the 64 sources", "m_stored": m,
+                   "n": g.n},
+        "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} single-thread queue BFS per step (sources in bench order)"},
+        "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(t, srcs, budget_s):
+    """Oracle BFS on the host over as many of the sources as fit the budget."""
+    import oracle
+    g = oracle.csr_from_tuples(t)
+    done, t0 = 0, time.perf_counter()
+    while done < len(srcs) and (time.perf_counter() - t0) < budget_s:
+        oracle.bfs(g, int(srcs[done]))
+        done += 1
+    dt = time.perf_counter() - t0
+    return {"value": done * g.m / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"{done} of the 64 BFS sources, single-thread queue BFS, {dt:.1f} s"}
+
+
+def run_gbx(args):
+    import torch
+    import paper_1908_01407_gb300 as gb
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = f"cuda:{local}"
+
+    t, srcs = make_inputs()
+    ctx = gb.Context(local)
+    stream = torch.cuda.Stream(device=dev)
+    ctx.set_stream(stream)
+    A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, flags=gb.SYMMETRIC)
+    n, m = A.nrows, A.nvals
+    desc = gb.Descriptor(beta=args.beta) if args.beta else None
+    levels = torch.empty(n, dtype=torch.int32, device=dev)
+    parents = torch.empty(n, dtype=torch.int32, device=dev)
+
+    # untimed pass with statistics: algorithmic bytes and levels per source
+    alg, depth, pushes, pulls = [], [], [], []
+    for s in srcs:
+        _, _, st = gb.bfs(ctx, A, int(s), levels, parents, desc=desc, stats=True)
+        alg.append(st["alg_bytes"]); depth.append(st["depth"])
+        pushes.append(st["push_levels"]); pulls.append(st["pull_levels"])
+    alg_per_bfs = float(np.mean(alg))
+
+    def step():
+        for s in srcs:
+            gb.bfs(ctx, A, int(s), levels, parents, desc=desc, stats=False)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ctx.profile(True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    total_ms = ev0.elapsed_time(ev1)
+    k_ms, k_n = ctx.profile_get("bfs")
+    ctx.profile(False)
+    clk = clocks.stop()
+
+    if ws > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * NSRC * m / (ms_per_step / 1e3) / 1e9
+
+    # end to end through the C ABI with host buffers: outputs copied to pinned host memory
+    lv_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    pa_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    srcs_h = torch.from_numpy(srcs.astype(np.int64)).pin_memory()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(max(1, min(args.steps, 2))):
+        sl = srcs_h.tolist()
+        for s in sl:
+            gb.bfs(ctx, A, int(s), lv_h, pa_h, desc=desc, stats=False)
+    e_steps = max(1, min(args.steps, 2))
+    e2e_s = (time.perf_counter() - e0) / e_steps
+    e2e_val = NSRC * m / e2e_s / 1e9
+
+    hbm, peak_kind = peaks()
+    avg_kernel_ms = k_ms / max(k_n, 1)
+    achieved = alg_per_bfs / (avg_kernel_ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "m_stored": m, "sources": NSRC, "l2": "inputs_larger_than_l2",
+                   "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                   "beta": args.beta or 10},
+        "gpu_launches": int(args.steps * NSRC),
+        "roofline": {"bound": "hbm", "kernel": "k_bfs", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
+                     "alg_bytes_per_launch": alg_per_bfs, "avg_launch_ms": avg_kernel_ms},
+        "e2e": {"value": e2e_val, "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": int(NSRC * 2 * 4 * n)},
+        "clocks": clk,
+        "bfs": {"median_depth": float(np.median(depth)), "mean_push_levels": float(np.mean(pushes)),
+                "mean_pull_levels": float(np.mean(pulls)), "ms_per_bfs": ms_per_step / NSRC,
+                "gteps_graph500": value / 2},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(t, srcs, args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    A.free()
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbx", choices=["gbx", "reference"])
+    ap.add_argument("--beta", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-sources", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gbx(args)
+
+
+if __name__ == "__main__":
+    main()

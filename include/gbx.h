@@ -1,0 +1,361 @@
+/*
+ * gbx.h -- C ABI of a GB300 (sm_103a) library for the masked
+ * generalized-semiring graph operations of GraphBLAST (Yang, Buluc, Owens,
+ * "GraphBLAST: A High-Performance Linear Algebra-based Graph Framework on
+ * the GPU", ACM TOMS 2021, arXiv 1908.01407).
+ *
+ * Conventions (apply to every call):
+ *  - Every call returns gb_info. No call aborts the process; on failure
+ *    gb_last_error() gives a message (per host thread).
+ *  - Objects (context, matrix, vector, descriptor, server) are opaque
+ *    handles owned by the library until the matching *_free / destroy.
+ *  - Input arrays are BORROWED: the call reads them before returning (or,
+ *    for device pointers, in stream order before any later work on the
+ *    context stream) and keeps no reference. A gb_mem argument says whether
+ *    a pointer is host memory (GB_HOST) or device memory of the context's
+ *    GPU (GB_DEVICE).
+ *  - Outputs go into caller-provided buffers of the stated length.
+ *  - All device work is ordered on the context stream (gb_context_set_stream).
+ *    Calls that write to GB_HOST buffers synchronise that stream before
+ *    returning; calls that write to GB_DEVICE buffers do not.
+ *  - Indices are uint32: n, ncols and stored-entry counts must be < 2^32
+ *    (GB_INVALID_VALUE otherwise).
+ */
+#ifndef GBX_H
+#define GBX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes, modelled on the GraphBLAS C API's GrB_Info (Section 3.3,
+ * "Info is an error type ... according to the C API specification"). */
+typedef enum {
+    GB_SUCCESS = 0,
+    GB_NO_VALUE = 1,            /* extract_element on a position with no value */
+    GB_NULL_POINTER = 2,
+    GB_INVALID_VALUE = 3,       /* bad enum, size >= 2^32, object not built */
+    GB_INVALID_INDEX = 4,       /* an index outside the dimension */
+    GB_DOMAIN_MISMATCH = 5,     /* unsupported (semiring, type) combination */
+    GB_DIMENSION_MISMATCH = 6,
+    GB_OUT_OF_MEMORY = 7,
+    GB_NOT_IMPLEMENTED = 8,
+    GB_TIMEOUT = 9,             /* a bounded device wait ran out, or server wait */
+    GB_PANIC = 10,              /* a CUDA error; the message names it */
+    GB_INSUFFICIENT_SPACE = 11  /* an output buffer is too small */
+} gb_info;
+
+typedef enum { GB_HOST = 0, GB_DEVICE = 1 } gb_mem;
+
+/* Element types (the paper's Matrix<T>/Vector<T> template types, Section 3.4). */
+typedef enum { GB_BOOL = 0, GB_INT32 = 1, GB_UINT32 = 2, GB_UINT64 = 3, GB_FP32 = 4, GB_FP64 = 5 } gb_type;
+
+/* Binary operators: accumulators, dup operators and eWise operators. */
+typedef enum {
+    GB_NOP = 0,       /* "no accumulator" (accum argument only) */
+    GB_PLUS = 1, GB_TIMES = 2, GB_MIN = 3, GB_MAX = 4, GB_LOR = 5, GB_LAND = 6,
+    GB_FIRST = 7, GB_SECOND = 8, GB_PAIR = 9, GB_MINUS = 10
+} gb_binop;
+
+/* Monoids of Table 4 (operator and identity). */
+typedef enum {
+    GB_MONOID_PLUS = 0, GB_MONOID_TIMES = 1, GB_MONOID_MIN = 2, GB_MONOID_MAX = 3,
+    GB_MONOID_LOR = 4, GB_MONOID_LAND = 5
+} gb_monoid;
+
+/* Semirings (add monoid, multiply operator): the five of Table 4, plus
+ * min.second used by the connected-components listing (Appendix A.4) and
+ * plus.pair used for triangle counting (Section 6.5). For integer types the
+ * "plus" of MIN_PLUS/MAX_PLUS saturates at the type's max/min, so the
+ * identity behaves as infinity. Supported (semiring, type) pairs:
+ *   PLUS_TIMES, MIN_PLUS, MIN_TIMES: INT32 UINT32 FP32 FP64
+ *   MAX_PLUS: INT32 FP32 FP64     LOR_LAND: BOOL
+ *   MIN_SECOND: INT32 UINT32 FP32 FP64     PLUS_PAIR: INT32 UINT32 UINT64 FP32 */
+typedef enum {
+    GB_PLUS_TIMES = 0, GB_LOR_LAND = 1, GB_MIN_PLUS = 2, GB_MAX_PLUS = 3,
+    GB_MIN_TIMES = 4, GB_MIN_SECOND = 5, GB_PLUS_PAIR = 6
+} gb_semiring;
+
+/* Descriptor fields and values (Table 5; Descriptor::toggle, Section 3.4). */
+typedef enum {
+    GB_MASK = 0,        /* value: GB_DEFAULT, or a bitwise OR of GB_SCMP and GB_STRUCTURE */
+    GB_OUTP = 1,        /* GB_DEFAULT or GB_REPLACE */
+    GB_INP0 = 2,        /* GB_DEFAULT or GB_TRAN */
+    GB_INP1 = 3,        /* GB_DEFAULT or GB_TRAN */
+    GB_DIRECTION = 4,   /* GB_AUTO (default), GB_PUSH or GB_PULL */
+    GB_SWITCH_BETA = 5  /* integer beta of the push/pull rule |E_f| > |E| / beta; 0 = tuned default */
+} gb_field;
+
+enum {
+    GB_DEFAULT = 0,
+    GB_SCMP = 1, GB_STRUCTURE = 2,   /* GB_MASK bits */
+    GB_REPLACE = 1,                  /* GB_OUTP */
+    GB_TRAN = 1,                     /* GB_INP0 / GB_INP1 */
+    GB_AUTO = 0, GB_PUSH = 1, GB_PULL = 2
+};
+
+/* Matrix build flags. */
+enum {
+    GB_BUILD_DEFAULT = 0,
+    GB_SYMMETRIC = 1,   /* caller asserts A == A^T: the CSC copy aliases the CSR copy */
+    GB_CSR_ONLY = 2     /* store CSR only (Section 4.3: users may drop one copy); push over columns is then unavailable */
+};
+
+typedef struct gb_context_t gb_context;
+typedef struct gb_matrix_t gb_matrix;
+typedef struct gb_vector_t gb_vector;
+typedef struct gb_desc_t gb_desc;
+typedef struct gb_server_t gb_server;
+
+/* ---------------------------------------------------------------- context */
+
+/* Creates a context on CUDA device `device`, owning a device memory pool
+ * (Section 5.1 keeps a pool of device memory for temporaries) and a stream
+ * (default: a new non-blocking stream). */
+gb_info gb_init(int device, gb_context **ctx);
+/* Orders all later work on `stream` (a cudaStream_t, e.g. torch's current
+ * stream); NULL selects the legacy default stream. The stream is borrowed. */
+gb_info gb_context_set_stream(gb_context *ctx, void *stream);
+gb_info gb_context_synchronize(gb_context *ctx);
+/* Bytes held by the context's pool and its high-water mark. */
+gb_info gb_context_pool_stats(gb_context *ctx, uint64_t *held_bytes, uint64_t *peak_bytes);
+/* Fault injection for tests: the next `count` pool allocations fail with
+ * GB_OUT_OF_MEMORY (host-side; no GPU fault). */
+gb_info gb_context_inject_alloc_failures(gb_context *ctx, uint32_t count);
+/* Kernel timing: while enabled, each operation records a pair of CUDA
+ * events on the context stream around its main kernel launch. Enabling or
+ * disabling clears earlier records. profile_get sums the recorded spans of
+ * the kernel named `kernel` (e.g. "bfs", "bfs_multi", "sssp", "pagerank_spmv",
+ * "cc", "tc") into *total_ms over *launches spans; it synchronises. */
+gb_info gb_context_profile(gb_context *ctx, int enable);
+gb_info gb_context_profile_get(gb_context *ctx, const char *kernel, double *total_ms, uint64_t *launches);
+gb_info gb_finalize(gb_context *ctx);
+/* Copies the calling thread's last error message (NUL-terminated). */
+gb_info gb_last_error(char *buf, size_t len);
+/* Library version string, e.g. "gbx 0.1 sm_103a". */
+const char *gb_version(void);
+
+/* ----------------------------------------------------------------- matrix */
+
+/* Table 2 "Matrix": an nrows x ncols matrix of `type`, initially empty. */
+gb_info gb_matrix_new(gb_matrix **A, gb_context *ctx, gb_type type, uint64_t nrows, uint64_t ncols);
+/* Table 2 "build" (Section 4.3 storage): builds CSR and CSC from nvals
+ * (row, col[, val]) tuples. vals == NULL builds a structural matrix whose
+ * stored values are all 1 (Section 6.1 "structure-only"). Tuples with equal
+ * (row, col) are combined with `dup` (PLUS/MIN/MAX/FIRST/SECOND/LOR/LAND;
+ * FIRST/SECOND by tuple order). Columns within a row come out sorted.
+ * rows/cols/vals live in `mem`. Index >= dimension: GB_INVALID_INDEX.
+ * Rebuilding a built matrix replaces its contents. */
+gb_info gb_matrix_build(gb_matrix *A, const uint32_t *rows, const uint32_t *cols, const void *vals,
+                        uint64_t nvals, gb_binop dup, gb_mem mem, uint32_t flags);
+gb_info gb_matrix_nrows(const gb_matrix *A, uint64_t *n);
+gb_info gb_matrix_ncols(const gb_matrix *A, uint64_t *n);
+gb_info gb_matrix_nvals(const gb_matrix *A, uint64_t *n);
+/* Table 2 "extractTuples": stored entries in CSR (row-major, sorted) order.
+ * *n_inout: capacity in, count out. vals may be NULL. */
+gb_info gb_matrix_extract_tuples(const gb_matrix *A, uint32_t *rows, uint32_t *cols, void *vals,
+                                 uint64_t *n_inout, gb_mem mem);
+/* Copies the CSR arrays: rowptr[nrows+1], colidx[nvals], vals[nvals] (may be NULL). */
+gb_info gb_matrix_export_csr(const gb_matrix *A, uint32_t *rowptr, uint32_t *colidx, void *vals, gb_mem mem);
+/* Copies the CSC arrays: colptr[ncols+1], rowidx[nvals], vals[nvals] (may be NULL). */
+gb_info gb_matrix_export_csc(const gb_matrix *A, uint32_t *colptr, uint32_t *rowidx, void *vals, gb_mem mem);
+/* L = strictly lower triangle of A (entries with col < row), CSR + CSC (Section 6.5). */
+gb_info gb_matrix_tril(gb_matrix *L, const gb_matrix *A);
+/* B = A with vertex v renamed new_id[v], where the order is decreasing
+ * degree, ties by lower old id (Section 6.5 sorts rows by nonzero count).
+ * A must be square; new_id (nrows entries, may be NULL) receives the map. */
+gb_info gb_matrix_degree_order(gb_matrix *B, const gb_matrix *A, uint32_t *new_id, gb_mem mem);
+gb_info gb_matrix_free(gb_matrix **A);
+
+/* ----------------------------------------------------------------- vector */
+
+/* Table 2 "Vector": size n, no stored values. Storage holds a dense value
+ * array, a presence bitmap, and a sparse index list kept alongside
+ * (Section 4.3: the backend switches dense/sparse; operand reuse). */
+gb_info gb_vector_new(gb_vector **v, gb_context *ctx, gb_type type, uint64_t n);
+/* Table 2 "build": stores vals[k] at idx[k] (vals == NULL stores 1);
+ * duplicates combined with dup. Previous contents are cleared. */
+gb_info gb_vector_build(gb_vector *v, const uint32_t *idx, const void *vals, uint64_t nvals,
+                        gb_binop dup, gb_mem mem);
+/* Table 2 "buildDense": every position present with vals[i] (n entries). */
+gb_info gb_vector_build_dense(gb_vector *v, const void *vals, gb_mem mem);
+/* Table 2 "fill": every position present with *scalar (host pointer). */
+gb_info gb_vector_fill(gb_vector *v, const void *scalar);
+gb_info gb_vector_set_element(gb_vector *v, uint32_t idx, const void *scalar);
+/* GB_NO_VALUE if position idx holds no value. *out is a host pointer. */
+gb_info gb_vector_extract_element(const gb_vector *v, uint32_t idx, void *out);
+/* Stored (index, value) pairs in increasing index order; *n_inout capacity
+ * in, count out; vals may be NULL. */
+gb_info gb_vector_extract_tuples(const gb_vector *v, uint32_t *idx, void *vals, uint64_t *n_inout, gb_mem mem);
+/* Dense view: vals[n] (absent positions get `absent_value`, host scalar)
+ * and optionally present[n] bytes (1 = stored). */
+gb_info gb_vector_extract_dense(const gb_vector *v, void *vals, uint8_t *present, const void *absent_value,
+                                gb_mem mem);
+gb_info gb_vector_size(const gb_vector *v, uint64_t *n);
+gb_info gb_vector_nvals(const gb_vector *v, uint64_t *n);
+/* Table 2 "dup": *out becomes a new vector equal to v. */
+gb_info gb_vector_dup(gb_vector **out, const gb_vector *v);
+/* Table 2 "clear": no stored values. */
+gb_info gb_vector_clear(gb_vector *v);
+gb_info gb_vector_free(gb_vector **v);
+
+/* ------------------------------------------------------------- descriptor */
+
+gb_info gb_desc_new(gb_desc **d);
+gb_info gb_desc_set(gb_desc *d, gb_field field, int value);
+gb_info gb_desc_get(const gb_desc *d, gb_field field, int *value);
+/* Descriptor::toggle (Section 3.4): GB_MASK flips GB_SCMP, GB_OUTP flips
+ * GB_REPLACE, GB_INP0/GB_INP1 flip GB_TRAN. */
+gb_info gb_desc_toggle(gb_desc *d, gb_field field);
+gb_info gb_desc_free(gb_desc **d);
+
+/* ------------------------------------------------------------- operations */
+/*
+ * Table 6 operations with the semantics of Section 3.2 (mask), Table 5
+ * (descriptor) and the GraphBLAS C API for accum/replace (Section 3.4 notes
+ * the paper itself ignores accum and omits REPLACE; this library honours
+ * both): with t the product,
+ *   z = accum == GB_NOP ? t : accum(w, t)   (union of w and t)
+ *   w(i) = z(i) where the mask allows i; elsewhere w(i) is kept, or
+ *   removed under GB_REPLACE.
+ * mask == NULL allows every position. A value mask allows i when it stores
+ * a nonzero at i; GB_STRUCTURE allows stored positions; GB_SCMP inverts.
+ * desc == NULL means all defaults. All operands of one call share a type,
+ * except that a structural matrix (built without values) acts as all-ones.
+ */
+
+/* Table 6 mxv: w<mask> = accum(w, A (+).(x) u); GB_INP0 = GB_TRAN uses A^T.
+ * Direction optimisation (Section 4): push = SpMSpV over the columns of A
+ * (CSC) selected by u's stored entries; pull = SpMV over the rows of A
+ * (CSR) the mask allows (Section 5.3 mask-first). GB_AUTO picks push when
+ * the frontier's edge count |E_f| <= |E| / beta (Table 8). */
+gb_info gb_mxv(gb_vector *w, const gb_vector *mask, gb_binop accum, gb_semiring s, const gb_matrix *A,
+               const gb_vector *u, const gb_desc *desc);
+/* Table 6 vxm: w<mask> = accum(w, u (+).(x) A), i.e. w(j) = (+)_i u(i) (x) A(i,j);
+ * identical to mxv with A transposed (Figure 4 caption). */
+gb_info gb_vxm(gb_vector *w, const gb_vector *mask, gb_binop accum, gb_semiring s, const gb_vector *u,
+               const gb_matrix *A, const gb_desc *desc);
+/* Table 6 mxm with a mask (Section 5.4 masked SpGEMM, Section 6.5):
+ * C<M> = accum(C, A (+).(x) B); GB_INP0/GB_INP1 = GB_TRAN transpose A/B.
+ * Only the positions stored in M are computed (mask first): for each
+ * M(i,j) the row A(i,:) is intersected with the column B(:,j). The mask must
+ * not be complemented (GB_SCMP on mxm: GB_NOT_IMPLEMENTED). C must be
+ * empty or have M's structure. */
+gb_info gb_mxm(gb_matrix *C, const gb_matrix *M, gb_binop accum, gb_semiring s, const gb_matrix *A,
+               const gb_matrix *B, const gb_desc *desc);
+/* Table 6 eWiseAdd (union) and eWiseMult (intersection) of vectors with a
+ * binary operator. */
+gb_info gb_ewise_add(gb_vector *w, const gb_vector *mask, gb_binop accum, gb_binop op, const gb_vector *u,
+                     const gb_vector *v, const gb_desc *desc);
+gb_info gb_ewise_mult(gb_vector *w, const gb_vector *mask, gb_binop accum, gb_binop op, const gb_vector *u,
+                      const gb_vector *v, const gb_desc *desc);
+/* Table 6 reduce to scalar: monoid over the stored values (identity if none).
+ * *out (host) has the vector's type; accum combines with the prior *out. */
+gb_info gb_reduce_vector(void *out, gb_binop accum, gb_monoid m, const gb_vector *u);
+gb_info gb_reduce_matrix(void *out, gb_binop accum, gb_monoid m, const gb_matrix *A);
+/* Table 6 reduce to vector: w(i) = (+)_j A(i,j) (GB_INP0 = GB_TRAN: over columns). */
+gb_info gb_reduce_rows(gb_vector *w, const gb_vector *mask, gb_binop accum, gb_monoid m, const gb_matrix *A,
+                       const gb_desc *desc);
+
+/* ------------------------------------------------------------- algorithms */
+
+typedef struct {
+    uint32_t depth;              /* number of BFS levels expanded */
+    uint32_t push_levels;
+    uint32_t pull_levels;
+    uint32_t status;             /* 0, or GB_TIMEOUT if a bounded device wait ran out */
+    uint64_t vertices_reached;
+    uint64_t edges_examined;     /* adjacency entries read (push and pull) */
+    uint64_t frontier_edges;     /* sum of degrees of all frontiers */
+    uint64_t alg_bytes;          /* algorithmic bytes moved (see the design notes) */
+} gb_bfs_stats;
+
+/* Direction-optimised BFS (Algorithm 1, Section 6.1): levels[v] = hop count
+ * from src (src 0, unreachable -1; the paper's depth minus one), and, if
+ * parents != NULL, a BFS-tree parent (parents[src] = src, unreachable -1).
+ * A must be square and symmetric-or-CSC-built. levels/parents have nrows
+ * entries in `mem`. stats may be NULL. desc: GB_DIRECTION, GB_SWITCH_BETA. */
+gb_info gb_bfs(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *levels, int32_t *parents,
+               gb_mem mem, const gb_desc *desc, gb_bfs_stats *stats);
+/* Multi-source BFS as Boolean SpMM over 64-bit bit-packed frontiers
+ * (Section 3.3 multi-nodeset traversal; Section 8 matrix direction
+ * optimisation): k <= 64 sources, levels is k x nrows (row q = source q). */
+gb_info gb_bfs_multi(gb_context *ctx, const gb_matrix *A, const uint32_t *srcs, uint32_t k, int32_t *levels,
+                     gb_mem mem, const gb_desc *desc, gb_bfs_stats *stats);
+/* SSSP (Section 6.2): adaptive Bellman-Ford by min.plus mxv restricted to
+ * the vertices whose distance changed. A holds uint32 weights. dist[v] =
+ * shortest distance (UINT32_MAX unreachable). iterations may be NULL. */
+gb_info gb_sssp(gb_context *ctx, const gb_matrix *A, uint32_t src, uint32_t *dist, gb_mem mem,
+                const gb_desc *desc, uint32_t *iterations);
+/* PageRank (Section 6.3), pull SpMV in FP32 with FP32 accumulation:
+ * p0 = 1/n; p' = (1-damping)/n + damping * (sum_{j in N(i)} p(j)/deg(j)
+ * + dangling/n), exactly `iters` iterations; the per-iteration L1 residual
+ * sum|p'-p| and the final normalisation are reduced in FP64.
+ * rank[n] in `mem`; residuals[iters] (host, may be NULL). */
+gb_info gb_pagerank(gb_context *ctx, const gb_matrix *A, float damping, uint32_t iters, float *rank,
+                    double *residuals, gb_mem mem);
+/* Connected components (Section 6.4) by min-label propagation
+ * (min.second mxv to a fixed point): labels[v] = smallest vertex id in v's
+ * component. iterations may be NULL. */
+gb_info gb_cc(gb_context *ctx, const gb_matrix *A, uint32_t *labels, gb_mem mem, uint32_t *iterations);
+/* Triangle counting (Section 6.5) as the masked SpGEMM C<L> = L (+).(x) L
+ * over plus.pair, reduced on the fly: L is a strictly lower-triangular
+ * matrix with CSR and CSC (gb_matrix_tril). *count (host) = number of
+ * triangles. If C != NULL it also receives C's values in L's structure. */
+gb_info gb_tc(gb_context *ctx, const gb_matrix *L, uint64_t *count, gb_matrix *C);
+
+/* ---------------------------------------------------------------- serving */
+
+typedef enum { GB_REQ_BFS = 0, GB_REQ_SSSP = 1, GB_REQ_PAGERANK = 2 } gb_request_kind;
+
+typedef struct {
+    uint32_t max_inflight;       /* requests running at once (default 8) */
+    uint32_t batch_window_us;    /* how long a BFS waits for batch partners (default 200) */
+    uint64_t hbm_budget_bytes;   /* admission limit on working memory (0 = 80% of free) */
+    uint32_t pagerank_iters;     /* default 50 */
+    float pagerank_damping;      /* default 0.85 */
+} gb_server_cfg;
+
+typedef struct {
+    gb_request_kind kind;
+    uint32_t graph_id;
+    uint32_t src;                /* BFS/SSSP source */
+} gb_request;
+
+typedef struct {
+    gb_info status;
+    uint32_t n;                  /* result length (vertices) */
+    double latency_us;           /* submit -> completion visible on the host */
+    uint32_t batch_size;         /* BFS requests served by the same launch */
+} gb_result;
+
+typedef struct {
+    uint64_t submitted, completed, batches, batched_bfs;
+    double p50_us, p99_us, mean_us, qps;
+    uint64_t hbm_in_use, hbm_peak;
+} gb_server_stats;
+
+/* A request loop on the context's GPU: graphs stay resident; requests are
+ * admitted while slots (max_inflight) and working memory (HBM budget) are
+ * free; concurrent BFS requests on one graph are packed (up to 64) into one
+ * multi-source bit-frontier BFS; running requests overlap on separate
+ * streams. Results stay on the device until fetched. */
+gb_info gb_server_create(gb_server **s, gb_context *ctx, const gb_server_cfg *cfg);
+/* The graph must outlive the server; it needs uint32 weights for SSSP. */
+gb_info gb_server_add_graph(gb_server *s, const gb_matrix *A, uint32_t *graph_id);
+gb_info gb_server_submit(gb_server *s, const gb_request *req, uint64_t *ticket);
+/* Waits up to timeout_ms for the ticket (GB_TIMEOUT if not done). */
+gb_info gb_server_wait(gb_server *s, uint64_t ticket, uint32_t timeout_ms, gb_result *res);
+/* Copies a finished ticket's result (int32 levels, uint32 distances or
+ * float ranks; res.n entries) into out and releases it. */
+gb_info gb_server_fetch(gb_server *s, uint64_t ticket, void *out, gb_mem mem);
+gb_info gb_server_stats_get(gb_server *s, gb_server_stats *st);
+gb_info gb_server_destroy(gb_server **s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBX_H */

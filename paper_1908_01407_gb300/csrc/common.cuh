@@ -1,0 +1,230 @@
+// Internal definitions shared by the library's translation units: object
+// layouts, error plumbing, the device memory pool, and small device helpers
+// (warp/block primitives, a bounded grid barrier).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda/atomic>
+#include <stdint.h>
+#include <stdio.h>
+#include <string>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/gbx.h"
+
+#define GBX_MAX_LEVEL_LOG 64
+
+// ------------------------------------------------------------------ errors
+namespace gbx {
+
+void set_error(const char *fmt, ...);
+gb_info fail(gb_info code, const char *fmt, ...);
+gb_info cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+}  // namespace gbx
+
+#define GB_CUDA(call)                                                              \
+    do {                                                                           \
+        cudaError_t _e = (call);                                                   \
+        if (_e != cudaSuccess) return gbx::cuda_fail(_e, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define GB_CHECK(call)                           \
+    do {                                         \
+        gb_info _r = (call);                     \
+        if (_r != GB_SUCCESS) return _r;         \
+    } while (0)
+
+#define GB_LAUNCH_CHECK() GB_CUDA(cudaGetLastError())
+
+// ------------------------------------------------------------------ objects
+struct gb_context_t {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    int l2_bytes = 0;
+    std::mutex mu;
+    uint64_t held = 0, peak = 0;
+    uint32_t inject_failures = 0;
+    std::unordered_map<void *, size_t> live;
+    // kernel timing (gb_context_profile): event pairs recorded around the
+    // main kernel launch of each operation, on the context stream
+    bool profiling = false;
+    struct Span { std::string name; cudaEvent_t a, b; };
+    std::vector<Span> spans;
+};
+
+struct gb_matrix_t {
+    gb_context *ctx = nullptr;
+    gb_type type = GB_UINT32;
+    uint32_t nrows = 0, ncols = 0;
+    uint64_t nvals = 0;
+    bool built = false;
+    bool has_vals = false;        // false: structural (every stored value is 1)
+    bool has_csc = false;
+    bool csc_alias = false;       // CSC arrays are the CSR arrays (symmetric)
+    uint32_t *rowptr = nullptr;   // [nrows + 1]
+    uint32_t *colidx = nullptr;   // [nvals]
+    void *vals = nullptr;         // [nvals] of type (nullptr if structural)
+    uint32_t *colptr = nullptr;   // [ncols + 1]
+    uint32_t *rowidx = nullptr;   // [nvals]
+    void *cvals = nullptr;        // [nvals]
+};
+
+struct gb_vector_t {
+    gb_context *ctx = nullptr;
+    gb_type type = GB_FP32;
+    uint32_t n = 0;
+    uint32_t nwords = 0;
+    void *vals = nullptr;          // [n] dense value array
+    uint32_t *bitmap = nullptr;    // [nwords] presence
+    // sparse index list, valid when list_valid (ascending order)
+    uint32_t *list = nullptr;      // [n]
+    bool list_valid = false;
+    uint64_t list_len = 0;
+};
+
+struct gb_desc_t {
+    int mask = GB_DEFAULT;
+    int outp = GB_DEFAULT;
+    int inp0 = GB_DEFAULT;
+    int inp1 = GB_DEFAULT;
+    int direction = GB_AUTO;
+    int beta = 0;
+};
+
+// ------------------------------------------------------------------ memory
+namespace gbx {
+
+size_t type_size(gb_type t);
+bool valid_type(int t);
+
+// Stream-ordered pool allocations on the context stream (Section 5.1 keeps
+// a pool of device memory; here the CUDA stream-ordered pool backs it).
+gb_info dalloc(gb_context *ctx, void **p, size_t bytes);
+void dfree(gb_context *ctx, void *p);
+
+template <typename T>
+gb_info dalloc_t(gb_context *ctx, T **p, size_t count) {
+    return dalloc(ctx, (void **)p, count * sizeof(T) + 16);
+}
+
+// RAII scratch buffer freed on scope exit (stream-ordered).
+struct Scratch {
+    gb_context *ctx;
+    void *p = nullptr;
+    explicit Scratch(gb_context *c) : ctx(c) {}
+    ~Scratch() { if (p) dfree(ctx, p); }
+    gb_info alloc(size_t bytes) { return dalloc(ctx, &p, bytes); }
+    template <typename T> T *as() const { return (T *)p; }
+};
+
+// Device-side helpers implemented in primitives.cu.
+gb_info memset_async(gb_context *ctx, void *p, int v, size_t bytes);
+gb_info copy_in(gb_context *ctx, void *dst_dev, const void *src, size_t bytes, gb_mem mem);
+gb_info copy_out(gb_context *ctx, void *dst, const void *src_dev, size_t bytes, gb_mem mem);
+gb_info sync(gb_context *ctx);
+
+// Exclusive prefix sum of n uint32 values (in may equal out); if total is
+// non-null the device total is written there (a device pointer).
+gb_info scan_exclusive_u32(gb_context *ctx, const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *total);
+// Stable LSD radix sort of (key, value) pairs by the low `key_bits` bits.
+// Results end in keys/vals (the buffers are ping-ponged with the scratch).
+gb_info radix_sort_pairs(gb_context *ctx, uint64_t *keys, uint32_t *vals, uint64_t n, int key_bits);
+
+// Builds CSR arrays from tuples already on the device.
+gb_info build_csr_from_device_tuples(gb_context *ctx, uint32_t nrows, uint32_t ncols, uint64_t ntup,
+                                     const uint32_t *rows, const uint32_t *cols, const void *vals,
+                                     gb_type vtype, gb_binop dup, uint32_t **rowptr, uint32_t **colidx,
+                                     void **ovals, uint64_t *nnz);
+
+int bits_for(uint64_t x);  // number of bits needed to represent values < x
+
+// Profiling spans: prof_begin records a start event when profiling is on
+// and returns its slot (or -1); prof_end records the matching end event.
+int prof_begin(gb_context *ctx, const char *name);
+void prof_end(gb_context *ctx, int slot);
+
+}  // namespace gbx
+
+// ------------------------------------------------------------------ device helpers
+namespace gbx {
+namespace dev {
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_exclusive_sum(T x, T *total) {
+    const int lane = threadIdx.x & 31;
+    T v = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    *total = __shfl_sync(0xffffffffu, v, 31);
+    return v - x;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Grid-wide barrier for cooperative launches, with a wall-clock bound: a
+// block that waits longer than `limit_ns` sets *err = GB_TIMEOUT and leaves.
+// Once *err is set every later barrier returns immediately.
+struct GridBarrier {
+    unsigned int count;
+    unsigned int generation;
+};
+
+__device__ __forceinline__ bool grid_sync(GridBarrier *bar, unsigned int nblocks, int *err, uint64_t limit_ns) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cuda::atomic_ref<unsigned int, cuda::thread_scope_device> gen(bar->generation);
+        cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(bar->count);
+        cuda::atomic_ref<int, cuda::thread_scope_device> e(*err);
+        __threadfence();
+        if (e.load(cuda::memory_order_relaxed) == 0) {
+            unsigned int my_gen = gen.load(cuda::memory_order_acquire);
+            unsigned int arrived = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
+            if (arrived == nblocks - 1) {
+                cnt.store(0u, cuda::memory_order_relaxed);
+                gen.fetch_add(1u, cuda::memory_order_release);
+            } else {
+                uint64_t t0 = globaltimer_ns();
+                unsigned int spins = 0;
+                while (gen.load(cuda::memory_order_acquire) == my_gen) {
+                    if (e.load(cuda::memory_order_relaxed) != 0) break;
+                    if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > limit_ns) {
+                        e.store((int)GB_TIMEOUT, cuda::memory_order_relaxed);
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return cuda::atomic_ref<int, cuda::thread_scope_device>(*err).load(cuda::memory_order_relaxed) == 0;
+}
+
+}  // namespace dev
+}  // namespace gbx

@@ -24,3 +24,16 @@ def read_golden(name):
             k, v = line.split(":", 1)
             out[k.strip()] = v.strip()
     return out
+
+
+@pytest.fixture(scope="session")
+def ctx():
+    """A gbx context on cuda:0 (GPU tests only)."""
+    import torch
+    import paper_1908_01407_gb300 as gb
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    c = gb.Context(0)
+    yield c
+    c.close()

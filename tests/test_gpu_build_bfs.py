@@ -1,0 +1,186 @@
+"""GPU parity: matrix build (CSR/CSC) and direction-optimised BFS against
+the oracle, element by element, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+import paper_1908_01407_gb300 as gb
+
+pytestmark = pytest.mark.gpu
+
+
+def make(ctx, t, weights=False, flags=gb.SYMMETRIC):
+    g = oracle.csr_from_tuples(t)
+    A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, t.w if weights else None, type_=gb.UINT32, flags=flags)
+    return g, A
+
+
+# ------------------------------------------------------------------ build
+@pytest.mark.parametrize("scale,ef", [(10, 8), (14, 16)])
+def test_build_csr_matches_oracle(ctx, scale, ef):
+    t = gen.rmat(scale, ef, seed=scale, wmax=255)
+    g, A = make(ctx, t, weights=True, flags=gb.BUILD_DEFAULT)
+    rp, ci, v = A.export_csr(with_vals=True)
+    assert A.nvals == g.m
+    assert np.array_equal(rp.astype(np.uint64), g.rowptr)
+    assert np.array_equal(ci, g.colidx)
+    assert np.array_equal(v, g.vals)
+    cp, ri, cv = A.export_csc(with_vals=True)
+    rows = np.repeat(np.arange(g.n, dtype=np.uint32), np.diff(g.rowptr).astype(np.int64))
+    gt = oracle.csr_build(g.n, g.colidx, rows, g.vals)
+    assert np.array_equal(cp.astype(np.uint64), gt.rowptr)
+    assert np.array_equal(ri, gt.colidx)
+    assert np.array_equal(cv, gt.vals)
+    A.free()
+
+
+@pytest.mark.parametrize("dup,odup", [(gb.PLUS, oracle.DUP_PLUS), (gb.MIN, oracle.DUP_MIN), (gb.MAX, oracle.DUP_MAX),
+                                      (gb.FIRST, oracle.DUP_FIRST), (gb.SECOND, oracle.DUP_SECOND)])
+def test_build_dup_operators_and_rectangular(ctx, dup, odup):
+    rng = np.random.default_rng(3)
+    nr, nc, nt = 777, 1234, 60000      # ragged sizes, many duplicates
+    r = rng.integers(0, nr, nt).astype(np.uint32)
+    c = rng.integers(0, nc, nt).astype(np.uint32)
+    v = rng.integers(0, 1 << 20, nt).astype(np.uint32)
+    A = gb.Matrix(ctx, gb.UINT32, nr, nc)
+    A.build(torch.from_numpy(r).cuda(), torch.from_numpy(c).cuda(), torch.from_numpy(v).cuda(), dup=dup)
+    g = oracle.csr_build(nr, r, c, v, odup, ncols=nc)
+    rp, ci, vv = A.export_csr(with_vals=True)
+    assert np.array_equal(rp.astype(np.uint64), g.rowptr)
+    assert np.array_equal(ci, g.colidx)
+    assert np.array_equal(vv, g.vals)
+    A.free()
+
+
+def test_build_errors_and_empty(ctx):
+    A = gb.Matrix(ctx, gb.UINT32, 10, 10)
+    with pytest.raises(gb.GBError) as e:
+        A.build(np.array([1, 10], np.uint32), np.array([0, 0], np.uint32))
+    assert e.value.code == gb.INVALID_INDEX
+    A.build(np.zeros(0, np.uint32), np.zeros(0, np.uint32))
+    assert A.nvals == 0
+    rp, ci = A.export_csr()
+    assert np.all(rp == 0)
+    A.free()
+
+
+# -------------------------------------------------------------------- BFS
+def check_bfs(ctx, g, A, src, desc=None):
+    lv, par, st = gb.bfs(ctx, A, src, desc=desc)
+    torch.cuda.synchronize()
+    lv, par = lv.cpu().numpy(), par.cpu().numpy()
+    want = oracle.bfs(g, src)
+    assert np.array_equal(lv, want)
+    assert oracle.bfs_parent_violations(g, src, lv, par) == 0
+    assert st["status"] == 0
+    assert st["vertices_reached"] == int((want >= 0).sum())
+    assert st["depth"] == int(want.max()) + 1
+    return st
+
+
+def test_bfs_rmat_s14_max_degree_source(ctx):
+    """R-MAT scale 14, edge factor 16, seed 1, source = max-degree vertex."""
+    t = gen.rmat(14, 16, seed=1)
+    g, A = make(ctx, t)
+    deg = g.degrees()
+    src = int(np.flatnonzero(deg == deg.max())[0])
+    st = check_bfs(ctx, g, A, src)
+    assert st["push_levels"] >= 1
+    for s in gen.sources(t, 8, seed=1):
+        check_bfs(ctx, g, A, int(s))
+    A.free()
+
+
+@pytest.mark.parametrize("direction", [gb.PUSH, gb.PULL, gb.AUTO])
+def test_bfs_directions_agree(ctx, direction):
+    t = gen.rmat(13, 16, seed=7)
+    g, A = make(ctx, t)
+    d = gb.Descriptor(direction=direction)
+    for s in gen.sources(t, 4, seed=3):
+        st = check_bfs(ctx, g, A, int(s), d)
+        if direction == gb.PUSH:
+            assert st["pull_levels"] == 0
+        if direction == gb.PULL:
+            assert st["push_levels"] == 0
+    d.free()
+    A.free()
+
+
+@pytest.mark.parametrize("beta", [1, 4, 10, 40, 1000])
+def test_bfs_switch_threshold_does_not_change_levels(ctx, beta):
+    t = gen.rmat(12, 16, seed=11)
+    g, A = make(ctx, t)
+    d = gb.Descriptor(beta=beta)
+    check_bfs(ctx, g, A, int(gen.sources(t, 1, seed=2)[0]), d)
+    A.free()
+
+
+def test_bfs_closed_form_graphs_and_edge_cases(ctx):
+    cases = [
+        gen.from_edges(37, [(i, i + 1) for i in range(36)]),                 # path, ragged n
+        gen.from_edges(70, [(0, i) for i in range(1, 70)]),                  # star
+        gen.from_edges(6, [(0, 1), (1, 2), (3, 4), (4, 5)]),                # two components
+        gen.grid(33, 31, 0.0, seed=1),                                       # full grid
+        gen.grid(64, 64, 0.1, seed=3),                                       # grid with deletions
+        gen.from_edges(1, []),                                               # a single vertex
+        gen.from_edges(5, [(1, 2)]),                                         # isolated source
+    ]
+    for t in cases:
+        g, A = make(ctx, t)
+        for src in sorted({0, t.n // 2, t.n - 1}):
+            for direction in (gb.AUTO, gb.PUSH, gb.PULL):
+                d = gb.Descriptor(direction=direction)
+                check_bfs(ctx, g, A, src, d)
+                d.free()
+        A.free()
+
+
+def test_bfs_csr_only_and_host_buffers(ctx):
+    t = gen.rmat(11, 8, seed=5)
+    g = oracle.csr_from_tuples(t)
+    A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, flags=gb.CSR_ONLY)
+    src = int(gen.sources(t, 1, seed=9)[0])
+    lv = np.empty(t.n, np.int32)
+    par = np.empty(t.n, np.int32)
+    _, _, st = gb.bfs(ctx, A, src, lv, par)          # push only (no CSC)
+    assert st["pull_levels"] == 0
+    assert np.array_equal(lv, oracle.bfs(g, src))
+    assert oracle.bfs_parent_violations(g, src, lv, par) == 0
+    with pytest.raises(gb.GBError) as e:
+        gb.bfs(ctx, A, t.n, lv, par)
+    assert e.value.code == gb.INVALID_INDEX
+    A.free()
+
+
+def test_bfs_directed_matrix_uses_csr_and_csc(ctx):
+    """A non-symmetric matrix: BFS follows edges i -> j (f' = f A)."""
+    rng = np.random.default_rng(5)
+    n = 3000
+    r = rng.integers(0, n, 20000).astype(np.uint32)
+    c = rng.integers(0, n, 20000).astype(np.uint32)
+    A = gb.Matrix.from_tuples(ctx, n, r, c)
+    g = oracle.csr_build(n, r, c)
+    for direction in (gb.AUTO, gb.PUSH, gb.PULL):
+        d = gb.Descriptor(direction=direction)
+        lv, par, st = gb.bfs(ctx, A, 7, desc=d)
+        lv = lv.cpu().numpy()
+        assert np.array_equal(lv, oracle.bfs(g, 7))
+        d.free()
+    A.free()
+
+
+@pytest.mark.slow
+def test_bfs_rmat_s22_full_size_sampled_sources(ctx):
+    """R-MAT scale 22, edge factor 16, seed 2: the benchmark graph, in the
+    benchmark's launch configuration, three of its 64 sources."""
+    t = gen.rmat(22, 16, seed=2)
+    A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, flags=gb.SYMMETRIC)
+    g = oracle.csr_from_tuples(t)
+    assert A.nvals == g.m
+    srcs = gen.sources(t, 64, seed=1)
+    for s in srcs[:3]:
+        st = check_bfs(ctx, g, A, int(s))
+        assert st["pull_levels"] >= 1
+    A.free()
