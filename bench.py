@@ -269,6 +269,25 @@ def run_gbx(args):
         dist.destroy_process_group()
 
 
+def run_profile_bfs(args):
+    """A short fixed run for profilers: build the s22 graph, then a few
+    BFS launches from the first sources (no timing, no CPU baseline)."""
+    import torch
+    import paper_1908_01407_gb300 as gb
+    t, srcs = make_inputs()
+    ctx = gb.Context(0)
+    A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, flags=gb.SYMMETRIC)
+    desc = gb.Descriptor(beta=args.beta) if args.beta else None
+    lv = torch.empty(t.n, dtype=torch.int32, device="cuda")
+    pa = torch.empty(t.n, dtype=torch.int32, device="cuda")
+    for s in srcs[:args.profile_launches]:
+        gb.bfs(ctx, A, int(s), lv, pa, desc=desc, stats=True)
+    torch.cuda.synchronize()
+    A.free()
+    ctx.close()
+    print("profile run done")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -279,8 +298,12 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-sources", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-bfs", action="store_true", help="short fixed BFS run for ncu")
+    ap.add_argument("--profile-launches", type=int, default=3)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_bfs:
+        run_profile_bfs(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gbx(args)

@@ -262,6 +262,8 @@ gb_info gb_reduce_rows(gb_vector *w, const gb_vector *mask, gb_binop accum, gb_m
 
 /* ------------------------------------------------------------- algorithms */
 
+#define GB_TRACE_LEVELS 32
+
 typedef struct {
     uint32_t depth;              /* number of BFS levels expanded */
     uint32_t push_levels;
@@ -271,6 +273,13 @@ typedef struct {
     uint64_t edges_examined;     /* adjacency entries read (push and pull) */
     uint64_t frontier_edges;     /* sum of degrees of all frontiers */
     uint64_t alg_bytes;          /* algorithmic bytes moved (see the design notes) */
+    /* per-level trace of the first GB_TRACE_LEVELS levels (single-source BFS) */
+    uint32_t trace_len;
+    uint32_t trace_dir[GB_TRACE_LEVELS];        /* 1 = push, 2 = pull */
+    uint32_t trace_vertices[GB_TRACE_LEVELS];   /* frontier size */
+    uint64_t trace_edges[GB_TRACE_LEVELS];      /* frontier out-edges */
+    float trace_us[GB_TRACE_LEVELS];            /* level duration (device clock) */
+    float init_us;                              /* initialisation before level 0 */
 } gb_bfs_stats;
 
 /* Direction-optimised BFS (Algorithm 1, Section 6.1): levels[v] = hop count

@@ -52,10 +52,17 @@ class BfsStats(ctypes.Structure):
     _fields_ = [("depth", ctypes.c_uint32), ("push_levels", ctypes.c_uint32), ("pull_levels", ctypes.c_uint32),
                 ("status", ctypes.c_uint32), ("vertices_reached", ctypes.c_uint64),
                 ("edges_examined", ctypes.c_uint64), ("frontier_edges", ctypes.c_uint64),
-                ("alg_bytes", ctypes.c_uint64)]
+                ("alg_bytes", ctypes.c_uint64), ("trace_len", ctypes.c_uint32),
+                ("trace_dir", ctypes.c_uint32 * 32), ("trace_vertices", ctypes.c_uint32 * 32),
+                ("trace_edges", ctypes.c_uint64 * 32), ("trace_us", ctypes.c_float * 32),
+                ("init_us", ctypes.c_float)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("trace")}
+        n = self.trace_len
+        d["trace"] = [{"dir": "pull" if self.trace_dir[i] == 2 else "push", "vertices": self.trace_vertices[i],
+                       "edges": self.trace_edges[i], "us": round(self.trace_us[i], 2)} for i in range(n)]
+        return d
 
 
 class ServerCfg(ctypes.Structure):

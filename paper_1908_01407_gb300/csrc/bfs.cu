@@ -35,8 +35,7 @@ constexpr int PUSH_ITEMS = 4;
 constexpr int PUSH_TILE = BLOCK * PUSH_ITEMS;      // edges per block tile
 constexpr int PUSH_OWNERS = PUSH_TILE + 1;          // owner entries staged in smem
 constexpr int PULL_WPW = 4;                          // bitmap words per warp per tile
-constexpr int PULL_TILE_WORDS = WARPS * PULL_WPW;    // 32 words = 1024 vertices
-constexpr int PULL_LANE_LIMIT = 8;                   // neighbours a lane checks alone
+constexpr int PULL_ROUNDS = 2;                       // 16-byte chunks a lane checks alone
 
 struct SmemPush {
     uint32_t P[PUSH_OWNERS];
@@ -44,19 +43,26 @@ struct SmemPush {
     uint32_t R[PUSH_OWNERS];
     uint32_t k0, nk;
 };
-struct SmemPull {
-    uint32_t v[WARPS][PULL_WPW * 32];
-    uint32_t deg[WARPS][PULL_WPW * 32];
+// Per-tile staging of newly discovered vertices: each warp collects up to
+// STAGE_CAP (vertex, out-degree) pairs, then one atomicAdd per block tile
+// reserves list slots and edge-prefix space for all of them.
+constexpr int STAGE_CAP = 128;
+static_assert(PUSH_ITEMS * 32 <= STAGE_CAP && PULL_WPW * 32 <= STAGE_CAP, "staging capacity");
+struct Stage {
+    uint32_t v[WARPS][STAGE_CAP];
+    uint32_t deg[WARPS][STAGE_CAP];
     uint32_t wcnt[WARPS];
     uint32_t wdeg[WARPS];
     unsigned long long base;
 };
-union Smem {
+struct Smem {
     SmemPush push;
-    SmemPull pull;
+    Stage stage;
+    unsigned long long qs;
 };
 
 __device__ __forceinline__ uint32_t ldcg(const uint32_t *p) { return __ldcg(p); }
+__device__ __forceinline__ int ld_relaxed_gpu_int_(const int *p) { return dev::ld_relaxed_gpu_int(p); }
 
 // largest k in [0, cnt) with P[k] <= e (P[0] == 0 <= e)
 __device__ __forceinline__ uint32_t owner_search_global(const uint32_t *P, uint32_t cnt, uint64_t e) {
@@ -68,26 +74,65 @@ __device__ __forceinline__ uint32_t owner_search_global(const uint32_t *P, uint3
     return lo;
 }
 
-__device__ void append_warp(const BfsArgs &a, int slot_next, uint32_t *Qn, uint32_t *Pn, bool win, uint32_t v,
-                            uint32_t deg) {
+// warp-level: add this lane's discovery (if win) to the warp's staging row
+__device__ __forceinline__ void stage_add(Stage &sg, uint32_t &staged, uint32_t &wdeg, bool win, uint32_t v,
+                                          uint32_t deg) {
     const uint32_t full = 0xffffffffu;
-    uint32_t wmask = __ballot_sync(full, win);
-    if (!wmask) return;
-    uint32_t tot;
-    uint32_t ex = dev::warp_exclusive_sum<uint32_t>(win ? deg : 0u, &tot);
-    unsigned long long base = 0;
-    const int lane = threadIdx.x & 31;
-    if (lane == 0) {
-        unsigned long long add = ((unsigned long long)__popc(wmask) << a.ebits) | tot;
-        base = atomicAdd(&a.st->qstate[slot_next], add);
-    }
-    base = __shfl_sync(full, base, 0);
+    const int warp = threadIdx.x >> 5;
+    uint32_t wm = __ballot_sync(full, win);
+    if (!wm) return;
     if (win) {
-        uint32_t pos = (uint32_t)(base >> a.ebits) + __popc(wmask & dev::lanemask_lt());
-        uint32_t pre = (uint32_t)(base & a.emask) + ex;
-        Qn[pos] = v;
-        Pn[pos] = pre;
+        uint32_t idx = staged + __popc(wm & dev::lanemask_lt());
+        sg.v[warp][idx] = v;
+        sg.deg[warp][idx] = deg;
     }
+    staged += __popc(wm);
+    wdeg += dev::warp_sum<uint32_t>(win ? deg : 0u);
+}
+
+// block-level (every thread calls it): append all staged discoveries to the
+// next list with one atomicAdd on the packed (count, edge-sum) word
+__device__ void stage_flush(const BfsArgs &a, Stage &sg, int slot_next, uint32_t *Qn, uint32_t *Pn, uint32_t *Rn,
+                            uint32_t staged, uint32_t wdeg) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sg.wcnt[warp] = staged;
+        sg.wdeg[warp] = wdeg;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t cacc = 0, sacc = 0;
+        for (int w = 0; w < WARPS; ++w) {
+            uint32_t cw = sg.wcnt[w], sw = sg.wdeg[w];
+            sg.wcnt[w] = cacc;
+            sg.wdeg[w] = sacc;
+            cacc += cw;
+            sacc += sw;
+        }
+        unsigned long long base = 0;
+        if (cacc) base = atomicAdd(&a.st->qstate[slot_next], ((unsigned long long)cacc << a.ebits) | sacc);
+        sg.base = base;
+    }
+    __syncthreads();
+    if (staged) {
+        unsigned long long base = sg.base;
+        uint32_t pos = (uint32_t)(base >> a.ebits) + sg.wcnt[warp];
+        uint32_t pre = (uint32_t)(base & a.emask) + sg.wdeg[warp];
+        for (uint32_t c0 = 0; c0 < staged; c0 += 32) {
+            uint32_t idx = c0 + lane;
+            uint32_t dg = idx < staged ? sg.deg[warp][idx] : 0u;
+            uint32_t tot;
+            uint32_t ex = dev::warp_exclusive_sum<uint32_t>(dg, &tot);
+            if (idx < staged) {
+                uint32_t v = sg.v[warp][idx];
+                Qn[pos + idx] = v;
+                Pn[pos + idx] = pre + ex;
+                Rn[pos + idx] = __ldg(&a.rp_out[v]);
+            }
+            pre += tot;
+        }
+    }
+    __syncthreads();
 }
 
 __device__ __forceinline__ bool claim(const BfsArgs &a, uint32_t v, uint32_t parent, int d, uint32_t *Fn,
@@ -103,106 +148,196 @@ __device__ __forceinline__ bool claim(const BfsArgs &a, uint32_t v, uint32_t par
     return true;
 }
 
+// Cooperative search by the whole block: the largest k in [0, cnt) with
+// P[k] <= x (P is non-decreasing and P[0] = 0). Each round probes BLOCK
+// evenly spaced positions in parallel, so a list of 4M entries needs three
+// rounds of one load per thread instead of a 22-step dependent chain.
+__device__ uint32_t block_owner_search(const uint32_t *P, uint32_t cnt, uint64_t x) {
+    uint32_t lo = 0, hi = cnt;   // answer in [lo, hi)
+    while (hi - lo > 1) {
+        uint32_t span = hi - lo;
+        uint32_t step = (span + BLOCK - 1) / BLOCK;
+        uint32_t idx = lo + threadIdx.x * step;
+        int ok = (idx < hi) && (uint64_t)ldcg(&P[idx]) <= x;
+        int c = __syncthreads_count(ok);      // probes 0..c-1 satisfy (monotone)
+        uint32_t nlo = lo + (uint32_t)(c - 1) * step;
+        uint32_t nhi = nlo + step < hi ? nlo + step : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    return lo;
+}
+
+// Push: every block takes an equal, contiguous share of the frontier's
+// edges (merge-path split over the edge prefixes), stages the owning
+// vertices of a tile (prefix, id, row start) in shared memory and maps each
+// edge to its owner by binary search there.
 __device__ void push_level(const BfsArgs &a, Smem &sm, int d, uint32_t cnt, uint64_t fe) {
     const int cur = d & 1, nxt = (d + 1) & 1;
     const int slot_next = (d + 1) % 3;
     const uint32_t *Q = a.q[cur];
     const uint32_t *P = a.qp[cur];
+    const uint32_t *R = a.qr[cur];
     uint32_t *Qn = a.q[nxt];
     uint32_t *Pn = a.qp[nxt];
+    uint32_t *Rn = a.qr[nxt];
     uint32_t *Fn = a.front[(d + 1) % 3];
-    uint64_t ntiles = (fe + PUSH_TILE - 1) / PUSH_TILE;
-    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        uint64_t E0 = t * PUSH_TILE;
-        uint64_t E1 = E0 + PUSH_TILE < fe ? E0 + PUSH_TILE : fe;
-        if (threadIdx.x == 0) {
-            uint32_t k0 = owner_search_global(P, cnt, E0);
-            uint32_t k1 = owner_search_global(P, cnt, E1 - 1);
-            sm.push.k0 = k0;
-            sm.push.nk = k1 - k0 + 1;
-        }
-        __syncthreads();
-        const uint32_t k0 = sm.push.k0, nk = sm.push.nk;
-        const bool staged = nk <= PUSH_OWNERS;
-        if (staged) {
-            for (uint32_t j = threadIdx.x; j < nk; j += BLOCK) {
-                uint32_t u = ldcg(&Q[k0 + j]);
-                sm.push.Q[j] = u;
-                sm.push.P[j] = ldcg(&P[k0 + j]);
-                sm.push.R[j] = __ldg(&a.rp_out[u]);
+    const uint64_t Eb0 = fe * blockIdx.x / gridDim.x;
+    const uint64_t Eb1 = fe * (blockIdx.x + 1) / gridDim.x;
+    if (Eb0 >= Eb1) return;
+    uint32_t k = block_owner_search(P, cnt, Eb0);
+    uint64_t E = Eb0;
+    while (E < Eb1) {
+        const uint32_t W = cnt - k < (uint32_t)(PUSH_OWNERS - 1) ? cnt - k : (uint32_t)(PUSH_OWNERS - 1);
+        for (uint32_t j = threadIdx.x; j <= W; j += BLOCK) {
+            if (j < W) {
+                sm.push.Q[j] = ldcg(&Q[k + j]);
+                sm.push.P[j] = ldcg(&P[k + j]);
+                sm.push.R[j] = ldcg(&R[k + j]);
+            } else {
+                sm.push.P[j] = k + W < cnt ? ldcg(&P[k + W]) : (uint32_t)fe;   // end of the staged owners' edges
             }
         }
         __syncthreads();
+        uint64_t Eend = E + PUSH_TILE;
+        if (Eend > Eb1) Eend = Eb1;
+        if (Eend > sm.push.P[W]) Eend = sm.push.P[W];
+        if (Eend <= E) {          // every staged owner has no out-edges: skip them
+            __syncthreads();
+            k += W;
+            continue;
+        }
+        uint32_t staged = 0, wdeg = 0;
 #pragma unroll
         for (int it = 0; it < PUSH_ITEMS; ++it) {
-            uint64_t e = E0 + (uint64_t)it * BLOCK + threadIdx.x;
+            uint64_t e = E + (uint64_t)it * BLOCK + threadIdx.x;
             bool win = false;
             uint32_t v = 0, deg = 0;
-            if (e < E1) {
-                uint32_t u, p;
-                if (staged) {
-                    uint32_t lo = 0, hi = nk;
-                    while (hi - lo > 1) {
-                        uint32_t mid = (lo + hi) >> 1;
-                        if ((uint64_t)sm.push.P[mid] <= e) lo = mid; else hi = mid;
-                    }
-                    u = sm.push.Q[lo];
-                    p = sm.push.R[lo] + (uint32_t)(e - sm.push.P[lo]);
-                } else {
-                    uint32_t k = owner_search_global(P, cnt, e);
-                    u = ldcg(&Q[k]);
-                    p = __ldg(&a.rp_out[u]) + (uint32_t)(e - ldcg(&P[k]));
+            if (e < Eend) {
+                uint32_t lo = 0, hi = W;
+                while (hi - lo > 1) {
+                    uint32_t mid = (lo + hi) >> 1;
+                    if ((uint64_t)sm.push.P[mid] <= e) lo = mid; else hi = mid;
                 }
+                uint32_t u = sm.push.Q[lo];
+                uint32_t p = sm.push.R[lo] + (uint32_t)(e - sm.push.P[lo]);
                 v = __ldg(&a.ci_out[p]);
                 win = claim(a, v, u, d, Fn, &deg);
             }
-            append_warp(a, slot_next, Qn, Pn, win, v, deg);
+            stage_add(sm.stage, staged, wdeg, win, v, deg);
         }
-        __syncthreads();
+        // the owner of the next tile's first edge
+        uint32_t knext = k + W;
+        if (Eend < sm.push.P[W]) {
+            uint32_t lo = 0, hi = W;
+            while (hi - lo > 1) {
+                uint32_t mid = (lo + hi) >> 1;
+                if ((uint64_t)sm.push.P[mid] <= Eend) lo = mid; else hi = mid;
+            }
+            knext = k + lo;
+        }
+        stage_flush(a, sm.stage, slot_next, Qn, Pn, Rn, staged, wdeg);
+        k = knext;
+        E = Eend;
     }
 }
 
-__device__ void pull_level(const BfsArgs &a, Smem &sm, int d, unsigned long long *examined) {
-    const int nxt = (d + 1) & 1;
-    const int slot_next = (d + 1) % 3;
+// Pull: warps work independently over groups of PULL_WPW bitmap words
+// (PULL_WPW * 32 vertices), keeping each lane's PULL_WPW vertices in flight
+// together. A vertex checks its in-neighbours in aligned 16-byte chunks (up
+// to 4 per load) against the frontier bitmap, for PULL_ROUNDS chunks; the
+// rare longer scans continue warp-cooperatively, 32 neighbours per step,
+// with early exit. Pull writes the next frontier as a bitmap and only counts
+// it (vertices, out-edges); the list form is built when a push needs it.
+__device__ void pull_level(const BfsArgs &a, int d, unsigned long long *examined, uint32_t *cnt_out,
+                           uint32_t *deg_out) {
     const uint32_t *F = a.front[d % 3];
     uint32_t *Fn = a.front[(d + 1) % 3];
-    uint32_t *Qn = a.q[nxt];
-    uint32_t *Pn = a.qp[nxt];
     const uint32_t full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint64_t ntiles = (a.nwords + PULL_TILE_WORDS - 1) / PULL_TILE_WORDS;
+    const uint4 *ci4 = reinterpret_cast<const uint4 *>(a.ci_in);
+    const uint64_t ngroups = (a.nwords + PULL_WPW - 1) / PULL_WPW;
+    const uint64_t nwarps = (uint64_t)gridDim.x * WARPS;
     unsigned long long exam = 0;
-    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        uint32_t staged = 0;
-        uint32_t wdegsum = 0;
-#pragma unroll 1
+    uint32_t mycnt = 0, mydeg = 0;
+    for (uint64_t g = (uint64_t)blockIdx.x * WARPS + warp; g < ngroups; g += nwarps) {
+        const uint64_t w0 = g * PULL_WPW;
+        uint32_t vis[PULL_WPW], b[PULL_WPW], e[PULL_WPW], p[PULL_WPW], par[PULL_WPW];
+        bool act[PULL_WPW], found[PULL_WPW];
+#pragma unroll
         for (int j = 0; j < PULL_WPW; ++j) {
-            uint64_t word = t * PULL_TILE_WORDS + (uint64_t)warp * PULL_WPW + j;
-            if (word >= a.nwords) break;
-            uint32_t vis = ldcg(&a.visited[word]);
-            uint32_t cand = ~vis;
-            if (cand == 0) continue;
-            uint32_t v = (uint32_t)(word * 32 + lane);
-            bool active = (cand >> lane) & 1u;
-            bool found = false;
-            uint32_t par = 0, b = 0, e = 0, p = 0;
-            if (active) {
-                b = __ldg(&a.rp_in[v]);
-                e = __ldg(&a.rp_in[v + 1]);
-                uint32_t lim = e - b > PULL_LANE_LIMIT ? b + PULL_LANE_LIMIT : e;
-                for (p = b; p < lim; ++p) {
-                    uint32_t u = __ldg(&a.ci_in[p]);
-                    if ((ldcg(&F[u >> 5]) >> (u & 31)) & 1u) { found = true; par = u; ++p; break; }
-                }
-                exam += p - b;
+            vis[j] = (w0 + j < a.nwords) ? ldcg(&a.visited[w0 + j]) : full;
+            act[j] = !((vis[j] >> lane) & 1u);
+            found[j] = false;
+            par[j] = 0;
+            b[j] = e[j] = 0;
+        }
+        // row bounds are loaded for every vertex of the group, without
+        // waiting for the visited words, so the two loads overlap
+#pragma unroll
+        for (int j = 0; j < PULL_WPW; ++j) {
+            uint32_t v = (uint32_t)((w0 + j) * 32 + lane);
+            if (v < a.n) {
+                b[j] = __ldg(&a.rp_in[v]);
+                e[j] = __ldg(&a.rp_in[v + 1]);
             }
-            uint32_t coop = __ballot_sync(full, active && !found && p < e);
+        }
+#pragma unroll
+        for (int j = 0; j < PULL_WPW; ++j) {
+            if (!act[j]) e[j] = b[j];
+            p[j] = b[j];
+        }
+#pragma unroll 1
+        for (int r = 0; r < PULL_ROUNDS; ++r) {
+            uint4 c[PULL_WPW];
+            bool pend[PULL_WPW];
+#pragma unroll
+            for (int j = 0; j < PULL_WPW; ++j) {
+                pend[j] = act[j] && !found[j] && p[j] < e[j];
+                if (pend[j]) c[j] = __ldg(&ci4[p[j] >> 2]);
+            }
+            uint32_t fw[PULL_WPW][4];
+#pragma unroll
+            for (int j = 0; j < PULL_WPW; ++j) {
+                uint32_t q = p[j] & ~3u;
+                uint32_t cc[4] = {c[j].x, c[j].y, c[j].z, c[j].w};
+#pragma unroll
+                for (int k2 = 0; k2 < 4; ++k2) {
+                    bool in = pend[j] && q + k2 >= p[j] && q + k2 < e[j];
+                    fw[j][k2] = in ? ldcg(&F[cc[k2] >> 5]) : 0u;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < PULL_WPW; ++j) {
+                if (!pend[j]) continue;
+                uint32_t q = p[j] & ~3u;
+                uint32_t cc[4] = {c[j].x, c[j].y, c[j].z, c[j].w};
+                uint32_t stop = q + 4 < e[j] ? q + 4 : e[j];
+#pragma unroll
+                for (int k2 = 0; k2 < 4; ++k2) {
+                    uint32_t pos = q + k2;
+                    if (!found[j] && pos >= p[j] && pos < e[j] && ((fw[j][k2] >> (cc[k2] & 31)) & 1u)) {
+                        found[j] = true;
+                        par[j] = cc[k2];
+                        stop = pos + 1;
+                    }
+                }
+                exam += stop - p[j];
+                p[j] = found[j] ? stop : q + 4;
+            }
+            bool any = false;
+#pragma unroll
+            for (int j = 0; j < PULL_WPW; ++j) any |= act[j] && !found[j] && p[j] < e[j];
+            if (!__any_sync(full, any)) break;
+        }
+#pragma unroll
+        for (int j = 0; j < PULL_WPW; ++j) {
+            uint32_t coop = __ballot_sync(full, act[j] && !found[j] && p[j] < e[j]);
             while (coop) {
                 int l = __ffs(coop) - 1;
                 coop &= coop - 1;
-                uint32_t pb = __shfl_sync(full, p, l);
-                uint32_t pe = __shfl_sync(full, e, l);
+                uint32_t pb = __shfl_sync(full, p[j], l);
+                uint32_t pe = __shfl_sync(full, e[j], l);
                 bool got = false;
                 uint32_t gpar = 0;
                 for (uint32_t q0 = pb; q0 < pe; q0 += 32) {
@@ -223,65 +358,87 @@ __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, unsigned long long
                     }
                     if (lane == 0) exam += (pe - q0 < 32 ? pe - q0 : 32);
                 }
-                if (lane == l && got) { found = true; par = gpar; }
-            }
-            uint32_t fm = __ballot_sync(full, found);
-            if (fm) {
-                if (lane == 0) {
-                    a.visited[word] = vis | fm;
-                    Fn[word] = fm;
-                }
-                uint32_t deg = 0;
-                if (found) {
-                    a.levels[v] = d + 1;
-                    if (a.parents) a.parents[v] = (int32_t)par;
-                    deg = a.csr_is_csc ? e - b : __ldg(&a.rp_out[v + 1]) - __ldg(&a.rp_out[v]);
-                    uint32_t idx = staged + __popc(fm & dev::lanemask_lt());
-                    sm.pull.v[warp][idx] = v;
-                    sm.pull.deg[warp][idx] = deg;
-                }
-                staged += __popc(fm);
-                wdegsum += dev::warp_sum<uint32_t>(deg);
+                if (lane == l && got) { found[j] = true; par[j] = gpar; }
             }
         }
+#pragma unroll
+        for (int j = 0; j < PULL_WPW; ++j) {
+            uint32_t fm = __ballot_sync(full, found[j]);
+            if (!fm) continue;
+            const uint64_t word = w0 + j;
+            if (lane == 0) {
+                a.visited[word] = vis[j] | fm;
+                Fn[word] = fm;
+            }
+            if (found[j]) {
+                uint32_t v = (uint32_t)(word * 32 + lane);
+                a.levels[v] = d + 1;
+                if (a.parents) a.parents[v] = (int32_t)par[j];
+                mydeg += a.csr_is_csc ? e[j] - b[j] : __ldg(&a.rp_out[v + 1]) - __ldg(&a.rp_out[v]);
+                mycnt += 1;
+            }
+        }
+    }
+    *examined += exam;
+    *cnt_out += mycnt;
+    *deg_out += mydeg;
+}
+
+// Builds the frontier list (with out-degree prefixes) of level d from its
+// bitmap, for a push that follows a pull. Each block compacts a contiguous
+// range of words; one atomicAdd per 256-word chunk on the packed
+// (count, edge-sum) word places the chunk in the list.
+__device__ void compact_level(const BfsArgs &a, Smem &sm, int d) {
+    const uint32_t *F = a.front[d % 3];
+    uint32_t *Q = a.q[d & 1];
+    uint32_t *P = a.qp[d & 1];
+    uint32_t *R = a.qr[d & 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t wb0 = (uint64_t)a.nwords * blockIdx.x / gridDim.x;
+    const uint64_t wb1 = (uint64_t)a.nwords * (blockIdx.x + 1) / gridDim.x;
+    for (uint64_t c = wb0; c < wb1; c += BLOCK) {
+        const uint64_t word = c + threadIdx.x;
+        uint32_t bits = word < wb1 ? ldcg(&F[word]) : 0u;
+        uint32_t cntv = __popc(bits), degv = 0;
+        for (uint32_t bb = bits; bb; bb &= bb - 1) {
+            uint32_t v = (uint32_t)(word * 32 + (__ffs(bb) - 1));
+            degv += __ldg(&a.rp_out[v + 1]) - __ldg(&a.rp_out[v]);
+        }
+        uint32_t tc, td;
+        uint32_t ec = dev::warp_exclusive_sum<uint32_t>(cntv, &tc);
+        uint32_t ed = dev::warp_exclusive_sum<uint32_t>(degv, &td);
         if (lane == 0) {
-            sm.pull.wcnt[warp] = staged;
-            sm.pull.wdeg[warp] = wdegsum;
+            sm.stage.wcnt[warp] = tc;
+            sm.stage.wdeg[warp] = td;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            uint32_t c = 0, s = 0;
+            uint32_t cacc = 0, sacc = 0;
             for (int w = 0; w < WARPS; ++w) {
-                uint32_t cw = sm.pull.wcnt[w], sw = sm.pull.wdeg[w];
-                sm.pull.wcnt[w] = c;
-                sm.pull.wdeg[w] = s;
-                c += cw;
-                s += sw;
+                uint32_t cw = sm.stage.wcnt[w], sw = sm.stage.wdeg[w];
+                sm.stage.wcnt[w] = cacc;
+                sm.stage.wdeg[w] = sacc;
+                cacc += cw;
+                sacc += sw;
             }
             unsigned long long base = 0;
-            if (c) base = atomicAdd(&a.st->qstate[slot_next], ((unsigned long long)c << a.ebits) | s);
-            sm.pull.base = base;
+            if (cacc) base = atomicAdd(&a.st->cstate[d % 3], ((unsigned long long)cacc << a.ebits) | sacc);
+            sm.stage.base = base;
         }
         __syncthreads();
-        {
-            unsigned long long base = sm.pull.base;
-            uint32_t pos = (uint32_t)(base >> a.ebits) + sm.pull.wcnt[warp];
-            uint32_t pre = (uint32_t)(base & a.emask) + sm.pull.wdeg[warp];
-            for (uint32_t c0 = 0; c0 < staged; c0 += 32) {
-                uint32_t idx = c0 + lane;
-                uint32_t dg = idx < staged ? sm.pull.deg[warp][idx] : 0u;
-                uint32_t tot;
-                uint32_t ex = dev::warp_exclusive_sum<uint32_t>(dg, &tot);
-                if (idx < staged) {
-                    Qn[pos + idx] = sm.pull.v[warp][idx];
-                    Pn[pos + idx] = pre + ex;
-                }
-                pre += tot;
-            }
+        uint32_t pos = (uint32_t)(sm.stage.base >> a.ebits) + sm.stage.wcnt[warp] + ec;
+        uint32_t pre = (uint32_t)(sm.stage.base & a.emask) + sm.stage.wdeg[warp] + ed;
+        for (uint32_t bb = bits; bb; bb &= bb - 1) {
+            uint32_t v = (uint32_t)(word * 32 + (__ffs(bb) - 1));
+            uint32_t r0 = __ldg(&a.rp_out[v]);
+            Q[pos] = v;
+            P[pos] = pre;
+            R[pos] = r0;
+            pre += __ldg(&a.rp_out[v + 1]) - r0;
+            ++pos;
         }
         __syncthreads();
     }
-    *examined += exam;
 }
 
 __device__ __forceinline__ bool choose_pull(const BfsArgs &a, uint64_t fe) {
@@ -290,17 +447,16 @@ __device__ __forceinline__ bool choose_pull(const BfsArgs &a, uint64_t fe) {
     return fe * (uint64_t)a.beta > a.m;
 }
 
-__global__ void __launch_bounds__(BLOCK) k_bfs(BfsArgs a) {
+__global__ void __launch_bounds__(BLOCK, 3) k_bfs(BfsArgs a) {
     __shared__ Smem sm;
     __shared__ unsigned long long s_exam;
+    __shared__ uint32_t s_cnt, s_deg;
     const uint32_t nthreads = gridDim.x * BLOCK;
     const uint32_t tid = blockIdx.x * BLOCK + threadIdx.x;
     BfsState *st = a.st;
-    // ---- init: levels/parents, bitmaps, the level-0 list
-    for (uint64_t i = tid; i < a.n; i += nthreads) {
-        a.levels[i] = i == a.src ? 0 : -1;
-        if (a.parents) a.parents[i] = i == a.src ? (int32_t)a.src : -1;
-    }
+    BfsResult *res = &st->res;
+    // ---- init: bitmaps and the level-0 list (levels/parents of vertices
+    // that stay unreached are written at the end)
     const uint32_t sw = a.src >> 5, sbit = 1u << (a.src & 31);
     const uint32_t tail = (a.n & 31) ? ~((1u << (a.n & 31)) - 1u) : 0u;
     for (uint64_t w = tid; w < a.nwords; w += nthreads) {
@@ -312,25 +468,32 @@ __global__ void __launch_bounds__(BLOCK) k_bfs(BfsArgs a) {
         a.front[2][w] = 0u;
     }
     if (tid == 0) {
-        uint32_t deg = __ldg(&a.rp_out[a.src + 1]) - __ldg(&a.rp_out[a.src]);
+        uint32_t r0 = __ldg(&a.rp_out[a.src]);
+        uint32_t deg = __ldg(&a.rp_out[a.src + 1]) - r0;
+        a.levels[a.src] = 0;
+        if (a.parents) a.parents[a.src] = (int32_t)a.src;
         a.q[0][0] = a.src;
         a.qp[0][0] = 0;
+        a.qr[0][0] = r0;
         st->qstate[0] = (1ull << a.ebits) | deg;
-        st->qstate[1] = 0;
-        st->qstate[2] = 0;
-        st->exam[0] = st->exam[1] = st->exam[2] = 0;
+        memset(res, 0, sizeof(BfsResult));
     }
-    if (!dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns)) return;
-    const uint64_t t_start = a.t_start_hint ? a.t_start_hint : dev::globaltimer_ns();
+    bool ok = dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns);
+    const uint64_t t_start = dev::globaltimer_ns();
     uint64_t reached = 0;
     // previous level's numbers for the algorithmic byte count
     uint32_t prev_dir = 0, prev_cnt = 0;
     uint64_t prev_fe = 0, prev_unvisited = 0;
-    double alg = 8.0 * a.n;   // levels + parents initialisation writes
+    double alg = 8.0 * a.n;   // levels + parents writes
+    bool list_valid = true;    // the list form of the current frontier exists
     int d = 0;
-    for (;; ++d) {
-        unsigned long long qs = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>(st->qstate[d % 3])
-                                    .load(cuda::memory_order_relaxed);
+    for (; ok; ++d) {
+        if (threadIdx.x == 0)
+            sm.qs = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>(st->qstate[d % 3])
+                        .load(cuda::memory_order_relaxed);
+        __syncthreads();
+        const unsigned long long qs = sm.qs;
+        __syncthreads();
         uint32_t cnt = (uint32_t)(qs >> a.ebits);
         uint64_t fe = qs & a.emask;
         if (tid == 0 && d > 0) {
@@ -339,21 +502,26 @@ __global__ void __launch_bounds__(BLOCK) k_bfs(BfsArgs a) {
                 alg += 8.0 * prev_cnt + 4.0 * prev_fe + 12.0 * cnt;
             else
                 alg += a.n / 8.0 + 8.0 * prev_unvisited + 4.0 * ex + 12.0 * cnt;
-            st->edges_examined += prev_dir == 0 ? prev_fe : ex;
+            res->edges_examined += prev_dir == 0 ? prev_fe : ex;
         }
         if (cnt == 0) break;
-        // guards: no BFS has more than n levels; the whole kernel has a wall-clock budget
-        if (d > (int)a.n || dev::globaltimer_ns() - t_start > a.total_limit_ns) {
-            if (tid == 0) atomicCAS(&st->err, 0, (int)GB_TIMEOUT);
-            break;
+        // guard: no BFS has more than n levels; the traversal has a wall-clock budget
+        if (d > (int)a.n || (threadIdx.x == 0 && dev::globaltimer_ns() - t_start > a.total_limit_ns)) {
+            atomicCAS(&st->err, 0, (int)GB_TIMEOUT);
         }
         const bool pull = choose_pull(a, fe);
         if (tid == 0) {
-            if (d < GBX_MAX_LEVEL_LOG) st->dir_log[d] = pull ? 2 : 1;
-            if (pull) st->pull_levels++; else st->push_levels++;
+            if (d < GBX_MAX_LEVEL_LOG) {
+                res->dir_log[d] = pull ? 2 : 1;
+                res->lv_cnt[d] = cnt;
+                res->lv_fe[d] = fe;
+                res->lv_ns[d] = dev::globaltimer_ns();
+            }
+            if (pull) res->pull_levels++; else res->push_levels++;
             st->qstate[(d + 2) % 3] = 0;
             st->exam[(d + 2) % 3] = 0;
-            st->frontier_edges += fe;
+            st->cstate[(d + 2) % 3] = 0;
+            res->frontier_edges += fe;
             prev_unvisited = a.n - reached - cnt;
             prev_dir = pull ? 1u : 0u;
             prev_cnt = cnt;
@@ -363,23 +531,75 @@ __global__ void __launch_bounds__(BLOCK) k_bfs(BfsArgs a) {
         uint32_t *Fclr = a.front[(d + 2) % 3];
         for (uint64_t w = tid; w < a.nwords; w += nthreads) Fclr[w] = 0u;
         if (pull) {
-            if (threadIdx.x == 0) s_exam = 0;
+            if (threadIdx.x == 0) { s_exam = 0; s_cnt = 0; s_deg = 0; }
             __syncthreads();
             unsigned long long ex = 0;
-            pull_level(a, sm, d, &ex);
+            uint32_t c = 0, dg = 0;
+            pull_level(a, d, &ex, &c, &dg);
             ex = dev::warp_sum<unsigned long long>(ex);
-            if ((threadIdx.x & 31) == 0 && ex) atomicAdd(&s_exam, ex);
+            c = dev::warp_sum<uint32_t>(c);
+            dg = dev::warp_sum<uint32_t>(dg);
+            if ((threadIdx.x & 31) == 0) {
+                if (ex) atomicAdd(&s_exam, ex);
+                if (c) { atomicAdd(&s_cnt, c); atomicAdd(&s_deg, dg); }
+            }
             __syncthreads();
-            if (threadIdx.x == 0 && s_exam) atomicAdd(&st->exam[d % 3], s_exam);
+            if (threadIdx.x == 0) {
+                if (s_exam) atomicAdd(&st->exam[d % 3], s_exam);
+                if (s_cnt) atomicAdd(&st->qstate[(d + 1) % 3], ((unsigned long long)s_cnt << a.ebits) | s_deg);
+            }
+            list_valid = false;
         } else {
+            if (!list_valid) {
+                compact_level(a, sm, d);
+                if (!dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns)) { ok = false; break; }
+            }
             push_level(a, sm, d, cnt, fe);
+            list_valid = true;
         }
-        if (!dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns)) return;
+        ok = dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns);
+    }
+    // ---- vertices never reached get level and parent -1
+    // (a warp per bitmap word: one broadcast load, 32 coalesced stores)
+    if (ok) {
+        const int lane = threadIdx.x & 31;
+        const uint64_t nwarps = (uint64_t)gridDim.x * WARPS;
+        uint64_t w = (uint64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+        for (; w < a.nwords; w += 4 * nwarps) {
+            uint32_t bits[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) bits[k] = w + k * nwarps < a.nwords ? ldcg(&a.visited[w + k * nwarps]) : ~0u;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (!((bits[k] >> lane) & 1u)) {
+                    uint64_t v = (w + k * nwarps) * 32 + lane;
+                    a.levels[v] = -1;
+                    if (a.parents) a.parents[v] = -1;
+                }
+            }
+        }
     }
     if (tid == 0) {
-        st->depth = d;
-        st->reached = reached;
-        st->alg_bytes = alg;
+        res->depth = d;
+        res->reached = reached;
+        res->alg_bytes = alg;
+        if (d < GBX_MAX_LEVEL_LOG) res->lv_ns[d] = dev::globaltimer_ns();
+        res->t_begin = t_start;
+    }
+    // ---- leave: the last block out resets the working state for the next launch
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned int old = atomicAdd(&st->bar.exits, 1u);
+        if (old == gridDim.x - 1) {
+            __threadfence();
+            res->err = ld_relaxed_gpu_int_(&st->err);
+            st->err = 0;
+            st->bar.count = 0;
+            for (int k = 0; k < 3; ++k) { st->qstate[k] = 0; st->exam[k] = 0; st->cstate[k] = 0; }
+            __threadfence();
+            st->bar.exits = 0;
+        }
     }
 }
 
@@ -387,7 +607,7 @@ __global__ void __launch_bounds__(BLOCK) k_bfs(BfsArgs a) {
 
 struct BfsWorkspace {
     uint32_t n = 0;
-    uint32_t *visited = nullptr, *front = nullptr, *q = nullptr, *qp = nullptr;
+    uint32_t *visited = nullptr, *front = nullptr, *q = nullptr, *qp = nullptr, *qr = nullptr;
     BfsState *st = nullptr;
     int grid = 0;
 };
@@ -399,14 +619,18 @@ gb_info bfs_workspace(gb_context *ctx, uint32_t n, BfsWorkspace **out) {
     std::lock_guard<std::mutex> g(g_ws_mu);
     BfsWorkspace &w = g_ws[ctx];
     if (w.n < n || !w.st) {
-        dfree(ctx, w.visited); dfree(ctx, w.front); dfree(ctx, w.q); dfree(ctx, w.qp); dfree(ctx, w.st);
+        dfree(ctx, w.visited); dfree(ctx, w.front); dfree(ctx, w.q); dfree(ctx, w.qp); dfree(ctx, w.qr);
+        dfree(ctx, w.st);
         w = BfsWorkspace();
         uint32_t nw = (n + 31) / 32;
         GB_CHECK(dalloc_t(ctx, &w.visited, nw));
         GB_CHECK(dalloc_t(ctx, &w.front, 3ull * nw));
         GB_CHECK(dalloc_t(ctx, &w.q, 2ull * n + 2));
         GB_CHECK(dalloc_t(ctx, &w.qp, 2ull * n + 2));
+        GB_CHECK(dalloc_t(ctx, &w.qr, 2ull * n + 2));
         GB_CHECK(dalloc_t(ctx, &w.st, 1));
+        // the only reset of the working state: launches leave it zeroed
+        GB_CHECK(memset_async(ctx, w.st, 0, sizeof(BfsState)));
         w.n = n;
     }
     if (!w.grid) {
@@ -424,7 +648,8 @@ void bfs_workspace_release(gb_context *ctx) {
     auto it = g_ws.find(ctx);
     if (it == g_ws.end()) return;
     BfsWorkspace &w = it->second;
-    dfree(ctx, w.visited); dfree(ctx, w.front); dfree(ctx, w.q); dfree(ctx, w.qp); dfree(ctx, w.st);
+    dfree(ctx, w.visited); dfree(ctx, w.front); dfree(ctx, w.q); dfree(ctx, w.qp); dfree(ctx, w.qr);
+    dfree(ctx, w.st);
     g_ws.erase(it);
 }
 
@@ -446,6 +671,7 @@ gb_info bfs_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *l
     for (int k = 0; k < 3; ++k) a.front[k] = w->front + (size_t)k * a.nwords;
     a.q[0] = w->q; a.q[1] = w->q + A->nrows + 1;
     a.qp[0] = w->qp; a.qp[1] = w->qp + A->nrows + 1;
+    a.qr[0] = w->qr; a.qr[1] = w->qr + A->nrows + 1;
     a.ebits = 64 - bits_for((uint64_t)A->nrows + 1);
     a.emask = (a.ebits >= 64) ? ~0ull : ((1ull << a.ebits) - 1);
     a.mode = desc ? desc->direction : GB_AUTO;
@@ -453,8 +679,6 @@ gb_info bfs_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *l
     a.st = w->st;
     a.timeout_ns = 4000000000ull;
     a.total_limit_ns = 120000000000ull;
-    a.t_start_hint = 0;
-    GB_CUDA(cudaMemsetAsync(w->st, 0, sizeof(BfsState), ctx->stream));
     int grid = grid_override > 0 && grid_override < w->grid ? grid_override : w->grid;
     void *args[] = {&a};
     int span = prof_begin(ctx, "bfs");
@@ -491,8 +715,8 @@ extern "C" gb_info gb_bfs(gb_context *ctx, const gb_matrix *A, uint32_t src, int
         if (parents) GB_CUDA(cudaMemcpyAsync(parents, dp, (size_t)A->nrows * 4, cudaMemcpyDeviceToHost, ctx->stream));
     }
     if (stats || mem == GB_HOST) {
-        BfsState hs;
-        GB_CUDA(cudaMemcpyAsync(&hs, w->st, sizeof(BfsState), cudaMemcpyDeviceToHost, ctx->stream));
+        BfsResult hs;
+        GB_CUDA(cudaMemcpyAsync(&hs, &w->st->res, sizeof(BfsResult), cudaMemcpyDeviceToHost, ctx->stream));
         GB_CUDA(cudaStreamSynchronize(ctx->stream));
         if (stats) {
             stats->depth = hs.depth;
@@ -503,6 +727,16 @@ extern "C" gb_info gb_bfs(gb_context *ctx, const gb_matrix *A, uint32_t src, int
             stats->edges_examined = hs.edges_examined;
             stats->frontier_edges = hs.frontier_edges;
             stats->alg_bytes = (uint64_t)hs.alg_bytes;
+            uint32_t nl = hs.depth < GB_TRACE_LEVELS ? hs.depth : GB_TRACE_LEVELS;
+            stats->trace_len = nl;
+            for (uint32_t l = 0; l < nl; ++l) {
+                stats->trace_dir[l] = hs.dir_log[l];
+                stats->trace_vertices[l] = hs.lv_cnt[l];
+                stats->trace_edges[l] = hs.lv_fe[l];
+                uint64_t t1 = (l + 1 < GBX_MAX_LEVEL_LOG) ? hs.lv_ns[l + 1] : hs.lv_ns[l];
+                stats->trace_us[l] = (float)((t1 - hs.lv_ns[l]) * 1e-3);
+            }
+            stats->init_us = hs.depth ? (float)((hs.lv_ns[0] - hs.t_begin) * 1e-3) : 0.f;
         }
         if (hs.err) return fail(GB_TIMEOUT, "gb_bfs: a bounded grid barrier wait ran out");
     }

@@ -5,18 +5,32 @@
 
 namespace gbx {
 
+// What a launch reports; block 0 thread 0 writes it, the last block to
+// leave the kernel adds the error code.
+struct BfsResult {
+    int err;
+    unsigned int depth, push_levels, pull_levels;
+    unsigned long long edges_examined;
+    unsigned long long frontier_edges;
+    unsigned long long reached;
+    double alg_bytes;
+    unsigned long long t_begin;
+    unsigned int dir_log[GBX_MAX_LEVEL_LOG];        // 1 = push, 2 = pull
+    unsigned int lv_cnt[GBX_MAX_LEVEL_LOG];         // frontier vertices per level
+    unsigned long long lv_fe[GBX_MAX_LEVEL_LOG];    // frontier out-edges per level
+    unsigned long long lv_ns[GBX_MAX_LEVEL_LOG];    // %globaltimer at each level start
+};
+
+// Working state. It is all zero when a launch starts: the last block to
+// leave a launch zeroes it again (so no memset is needed between launches).
 struct BfsState {
     dev::GridBarrier bar;
     int err;
     int pad0;
     unsigned long long qstate[3];      // packed (list length << ebits | edge-prefix total), per level slot
     unsigned long long exam[3];        // adjacency entries read by pull, per level slot
-    unsigned long long edges_examined;
-    unsigned long long frontier_edges;
-    unsigned long long reached;
-    double alg_bytes;
-    unsigned int depth, push_levels, pull_levels, pad1;
-    unsigned int dir_log[GBX_MAX_LEVEL_LOG];   // 1 = push, 2 = pull
+    unsigned long long cstate[3];      // packed counter of the bitmap -> list compaction, per level slot
+    BfsResult res;
 };
 
 struct BfsArgs {
@@ -29,7 +43,7 @@ struct BfsArgs {
     int32_t *levels, *parents;
     uint32_t *visited;
     uint32_t *front[3];
-    uint32_t *q[2], *qp[2];
+    uint32_t *q[2], *qp[2], *qr[2];    // frontier list: vertex, out-edge prefix, row start
     int ebits;
     unsigned long long emask;
     int mode;
@@ -37,7 +51,6 @@ struct BfsArgs {
     BfsState *st;
     uint64_t timeout_ns;       // bound on one grid-barrier wait
     uint64_t total_limit_ns;   // bound on the whole traversal
-    uint64_t t_start_hint;     // 0: each block reads the clock itself
 };
 
 }  // namespace gbx

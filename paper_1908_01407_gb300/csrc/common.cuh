@@ -186,44 +186,66 @@ __device__ __forceinline__ T warp_sum(T x) {
     return x;
 }
 
-// Grid-wide barrier for cooperative launches, with a wall-clock bound: a
-// block that waits longer than `limit_ns` sets *err = GB_TIMEOUT and leaves.
-// Once *err is set every later barrier returns immediately.
+// Grid-wide barrier for cooperative launches. Arrival is one
+// atom.add.release.gpu on a counter that only grows during a launch (no
+// generation word, no reset between barriers): block k of the i-th barrier
+// waits until the counter reaches i * nblocks, polling with relaxed loads
+// and finishing with one acquire fence. The counter must be 0 (a multiple
+// of nblocks) when the launch starts. A block that waits longer than
+// limit_ns sets *err = GB_TIMEOUT and leaves; once *err is set every later
+// barrier returns false at once.
 struct GridBarrier {
     unsigned int count;
-    unsigned int generation;
+    unsigned int exits;    // blocks that have left the kernel (for end-of-launch resets)
 };
 
+__device__ __forceinline__ unsigned int atom_add_release_gpu(unsigned int *p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ unsigned int ld_relaxed_gpu(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed_gpu_int(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ bool grid_sync(GridBarrier *bar, unsigned int nblocks, int *err, uint64_t limit_ns) {
+    __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        cuda::atomic_ref<unsigned int, cuda::thread_scope_device> gen(bar->generation);
-        cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(bar->count);
-        cuda::atomic_ref<int, cuda::thread_scope_device> e(*err);
-        __threadfence();
-        if (e.load(cuda::memory_order_relaxed) == 0) {
-            unsigned int my_gen = gen.load(cuda::memory_order_acquire);
-            unsigned int arrived = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
-            if (arrived == nblocks - 1) {
-                cnt.store(0u, cuda::memory_order_relaxed);
-                gen.fetch_add(1u, cuda::memory_order_release);
-            } else {
-                uint64_t t0 = globaltimer_ns();
-                unsigned int spins = 0;
-                while (gen.load(cuda::memory_order_acquire) == my_gen) {
-                    if (e.load(cuda::memory_order_relaxed) != 0) break;
-                    if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > limit_ns) {
-                        e.store((int)GB_TIMEOUT, cuda::memory_order_relaxed);
+        int ok = ld_relaxed_gpu_int(err) == 0;
+        if (ok) {
+            unsigned int old = atom_add_release_gpu(&bar->count, 1u);
+            unsigned int target = old - old % nblocks + nblocks;
+            unsigned int spins = 0;
+            uint64_t t0 = 0;
+            while ((int)(ld_relaxed_gpu(&bar->count) - target) < 0) {
+                if ((++spins & 255u) == 0) {
+                    uint64_t t = globaltimer_ns();
+                    if (t0 == 0) {
+                        t0 = t;
+                    } else if (t - t0 > limit_ns) {
+                        atomicCAS(err, 0, (int)GB_TIMEOUT);
+                        ok = 0;
                         break;
                     }
-                    __nanosleep(32);
+                    if (ld_relaxed_gpu_int(err) != 0) { ok = 0; break; }
                 }
             }
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
         }
-        __threadfence();
+        s_ok = ok;
     }
     __syncthreads();
-    return cuda::atomic_ref<int, cuda::thread_scope_device>(*err).load(cuda::memory_order_relaxed) == 0;
+    return s_ok != 0;
 }
 
 }  // namespace dev
