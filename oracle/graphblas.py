@@ -11,6 +11,7 @@ Readings where the paper is silent (also listed in the design notes):
   positions the mask lets through, as the GraphBLAS C API defines it.
 * REPLACE: the paper leaves it out (Section 3.4); here positions outside the
   mask are cleared when it is set.
+* No mask allows every position; the complement of no mask allows none.
 * A matrix built without values is structural: every stored entry is 1.
 * MIN_PLUS / MAX_PLUS on integer types add with saturation, so the
   additive identity (type max / type min) absorbs like +-infinity.
@@ -140,9 +141,10 @@ class Mat:
 def mask_allows(mask_e, i, structural, scmp):
     """Section 3.2.1: a stored nonzero lets the output through; the
     structural complement inverts that. With `structural` only presence
-    counts. A missing mask allows everything."""
+    counts. A missing mask allows everything, and its complement nothing
+    (GraphBLAS C API reading of GrB_COMP with no mask)."""
     if mask_e is None:
-        return True
+        return not scmp
     if structural:
         m = i in mask_e
     else:

@@ -447,6 +447,8 @@ def test_mask_semantics_special_cases():
     assert gbo.mxv(w0, ones, None, "PLUS_TIMES", A, u).e == full.e
     empty = gbo.Vec(n, "bool")
     assert gbo.mxv(w0, empty, None, "PLUS_TIMES", A, u, scmp=True).e == full.e
+    assert gbo.mxv(w0, None, None, "PLUS_TIMES", A, u, scmp=True).e == w0.e
+    assert gbo.mxv(w0, None, None, "PLUS_TIMES", A, u, scmp=True, replace=True).e == {}
     assert gbo.mxv(w0, empty, None, "PLUS_TIMES", A, u).e == w0.e
     m = gbo.Vec(n, "int32", {i: (i % 2) for i in range(0, n, 2)})   # stored zeros
     val = gbo.mxv(w0, m, None, "PLUS_TIMES", A, u)
