@@ -270,16 +270,16 @@ def reduce_matrix(t, monoid, A: Mat):
 
 def reduce_rows(w: Vec, mask, accum, monoid, A: Mat, *, tran=False, structural=False,
                 scmp=False, replace=False) -> Vec:
-    """w(i) = (+)_j A(i, j) over stored entries; rows without entries give
-    no value (Table 6 reduce to vector)."""
+    """w(i) = (+)_j A(i, j) over stored entries, starting from the monoid's
+    identity; rows without entries give no value (Table 6 reduce to vector)."""
     if tran:
         A = A.T()
     t = w.t
-    op, _ = MONOIDS[monoid]
+    op, ident = MONOIDS[monoid]
     prod = {}
     for (i, j) in sorted(A.e):
         a = cast(t, A.e[(i, j)])
-        prod[i] = BINOPS[op](t, prod[i], a) if i in prod else a
+        prod[i] = BINOPS[op](t, prod[i] if i in prod else ident(t), a)
     me = mask.e if mask is not None else None
     return Vec(w.n, t, _finish(w.e, prod, lambda i: mask_allows(me, i, structural, scmp),
                                accum, t, replace, range(w.n)))
