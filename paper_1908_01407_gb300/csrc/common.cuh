@@ -55,6 +55,7 @@ struct gb_context_t {
     bool profiling = false;
     struct Span { std::string name; cudaEvent_t a, b; };
     std::vector<Span> spans;
+    std::vector<cudaEvent_t> event_pool;   // reused across enable/disable cycles
 };
 
 struct gb_matrix_t {
@@ -146,6 +147,7 @@ int bits_for(uint64_t x);  // number of bits needed to represent values < x
 // Profiling spans: prof_begin records a start event when profiling is on
 // and returns its slot (or -1); prof_end records the matching end event.
 int prof_begin(gb_context *ctx, const char *name);
+void bfs_workspace_release(gb_context *ctx);
 void prof_end(gb_context *ctx, int slot);
 
 }  // namespace gbx

@@ -111,12 +111,22 @@ gb_info sync(gb_context *ctx) {
     return GB_SUCCESS;
 }
 
+static bool pool_event(gb_context *ctx, cudaEvent_t *e) {
+    if (!ctx->event_pool.empty()) {
+        *e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return true;
+    }
+    if (cudaEventCreate(e) != cudaSuccess) { cudaGetLastError(); return false; }
+    return true;
+}
+
 int prof_begin(gb_context *ctx, const char *name) {
     if (!ctx->profiling) return -1;
     gb_context::Span sp;
     sp.name = name;
-    if (cudaEventCreate(&sp.a) != cudaSuccess) { cudaGetLastError(); return -1; }
-    if (cudaEventCreate(&sp.b) != cudaSuccess) { cudaGetLastError(); cudaEventDestroy(sp.a); return -1; }
+    if (!pool_event(ctx, &sp.a)) return -1;
+    if (!pool_event(ctx, &sp.b)) { ctx->event_pool.push_back(sp.a); return -1; }
     cudaEventRecord(sp.a, ctx->stream);
     ctx->spans.push_back(sp);
     return (int)ctx->spans.size() - 1;
@@ -128,8 +138,14 @@ void prof_end(gb_context *ctx, int slot) {
 }
 
 static void prof_clear(gb_context *ctx) {
-    for (auto &sp : ctx->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
+    for (auto &sp : ctx->spans) { ctx->event_pool.push_back(sp.a); ctx->event_pool.push_back(sp.b); }
     ctx->spans.clear();
+}
+
+static void prof_destroy(gb_context *ctx) {
+    prof_clear(ctx);
+    for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    ctx->event_pool.clear();
 }
 
 }  // namespace gbx
@@ -236,7 +252,8 @@ gb_info gb_finalize(gb_context *ctx) {
     if (!ctx) return fail(GB_NULL_POINTER, "gb_finalize: ctx is NULL");
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    prof_clear(ctx);
+    prof_destroy(ctx);
+    bfs_workspace_release(ctx);
     for (auto &kv : ctx->live) cudaFreeAsync(kv.first, ctx->stream);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);

@@ -1,0 +1,319 @@
+// Min-relaxation over a frontier of changed vertices, as one persistent
+// cooperative kernel (the loop of Section 6.2 run on the device):
+//  * SSSP, adaptive Bellman-Ford with sparsification (Section 6.2):
+//      dist(v) <- min(dist(v), min_{u in F, (u,v) in E} dist(u) + w(u,v))
+//    over the min.plus semiring (saturating add, UINT32_MAX = infinity);
+//  * connected components by min-label propagation (min.second):
+//      label(v) <- min(label(v), min_{u in F, (u,v) in E} label(u)),
+//    labels starting at the vertex ids, every vertex active at first.
+// The next frontier is exactly the set of vertices whose value decreased
+// (the sparsification step: Section 6.2 keeps only vertices that improved).
+// Each iteration is a push (merge-path over the frontier's out-edges,
+// atomicMin into the target) or a pull (every vertex scans its in-edges,
+// taking only frontier sources into account) by the rule of Table 8. The
+// loop ends when no value changes, which is the exact fixed point.
+#include "common.cuh"
+#include "bfs_common.cuh"
+#include "frontier.cuh"
+#include "types.cuh"
+
+using namespace gbx;
+
+namespace gbx {
+namespace rlx {
+using namespace fr;
+
+struct RelaxArgs {
+    const uint32_t *rp_out, *ci_out, *w_out;   // CSR (+ weights): out-edges, for push
+    const uint32_t *rp_in, *ci_in, *w_in;      // CSC (+ weights): in-edges, for pull
+    bool weighted;                             // SSSP (true) or components (false)
+    bool csr_is_csc;
+    uint32_t n, nwords;
+    uint64_t m;
+    uint32_t src;
+    bool all_active;
+    uint32_t *val;
+    uint32_t *front[3];
+    uint32_t *q[2], *qp[2], *qr[2];
+    int ebits;
+    unsigned long long emask;
+    int mode;
+    uint32_t beta;
+    BfsState *st;
+    uint64_t timeout_ns, total_limit_ns;
+};
+
+constexpr int RPULL_WPW = 4;
+
+__device__ __forceinline__ uint32_t relax_val(const RelaxArgs &a, uint32_t vu, uint32_t p, const uint32_t *w) {
+    return a.weighted ? sat_add<uint32_t>(vu, __ldg(&w[p])) : vu;
+}
+
+// pull: lane per vertex (RPULL_WPW vertices per lane in flight), scanning
+// all in-edges; rows longer than 32 are scanned by the whole warp
+__device__ void relax_pull(const RelaxArgs &a, int d, uint32_t *cnt_out, uint32_t *deg_out) {
+    const uint32_t *F = a.front[d % 3];
+    uint32_t *Fn = a.front[(d + 1) % 3];
+    const uint32_t full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t ngroups = (a.nwords + RPULL_WPW - 1) / RPULL_WPW;
+    const uint64_t nwarps = (uint64_t)gridDim.x * WARPS;
+    uint32_t mycnt = 0, mydeg = 0;
+    for (uint64_t g = (uint64_t)blockIdx.x * WARPS + warp; g < ngroups; g += nwarps) {
+        const uint64_t w0 = g * RPULL_WPW;
+        uint32_t b[RPULL_WPW], e[RPULL_WPW], best[RPULL_WPW], cur[RPULL_WPW];
+#pragma unroll
+        for (int j = 0; j < RPULL_WPW; ++j) {
+            uint32_t v = (uint32_t)((w0 + j) * 32 + lane);
+            b[j] = e[j] = 0;
+            cur[j] = best[j] = UINT32_MAX;
+            if (v < a.n) {
+                b[j] = __ldg(&a.rp_in[v]);
+                e[j] = __ldg(&a.rp_in[v + 1]);
+                cur[j] = ldcg(&a.val[v]);
+                best[j] = cur[j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < RPULL_WPW; ++j) {
+            if (e[j] - b[j] <= 32) {
+                for (uint32_t p = b[j]; p < e[j]; ++p) {
+                    uint32_t u = __ldg(&a.ci_in[p]);
+                    if ((ldcg(&F[u >> 5]) >> (u & 31)) & 1u) {
+                        uint32_t c = relax_val(a, ldcg(&a.val[u]), p, a.w_in);
+                        if (c < best[j]) best[j] = c;
+                    }
+                }
+            }
+            uint32_t coop = __ballot_sync(full, e[j] - b[j] > 32);
+            while (coop) {
+                int l = __ffs(coop) - 1;
+                coop &= coop - 1;
+                uint32_t pb = __shfl_sync(full, b[j], l), pe = __shfl_sync(full, e[j], l);
+                uint32_t mn = UINT32_MAX;
+                for (uint32_t p = pb + lane; p < pe; p += 32) {
+                    uint32_t u = __ldg(&a.ci_in[p]);
+                    if ((ldcg(&F[u >> 5]) >> (u & 31)) & 1u) {
+                        uint32_t c = relax_val(a, ldcg(&a.val[u]), p, a.w_in);
+                        if (c < mn) mn = c;
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    uint32_t y = __shfl_xor_sync(full, mn, o);
+                    mn = y < mn ? y : mn;
+                }
+                if (lane == l && mn < best[j]) best[j] = mn;
+            }
+            bool improved = best[j] < cur[j];
+            uint32_t fm = __ballot_sync(full, improved);
+            if (fm) {
+                const uint64_t word = w0 + j;
+                if (lane == 0) Fn[word] = fm;
+                if (improved) {
+                    uint32_t v = (uint32_t)(word * 32 + lane);
+                    a.val[v] = best[j];
+                    mydeg += a.csr_is_csc ? e[j] - b[j] : __ldg(&a.rp_out[v + 1]) - __ldg(&a.rp_out[v]);
+                    mycnt += 1;
+                }
+            }
+        }
+    }
+    *cnt_out += mycnt;
+    *deg_out += mydeg;
+}
+
+__global__ void __launch_bounds__(BLOCK, 3) k_relax(RelaxArgs a) {
+    __shared__ Smem sm;
+    __shared__ uint32_t s_cnt, s_deg;
+    const uint32_t nthreads = gridDim.x * BLOCK;
+    const uint32_t tid = blockIdx.x * BLOCK + threadIdx.x;
+    BfsState *st = a.st;
+    BfsResult *res = &st->res;
+    const uint32_t tail = (a.n & 31) ? ((1u << (a.n & 31)) - 1u) : ~0u;
+    for (uint64_t i = tid; i < a.n; i += nthreads)
+        a.val[i] = a.all_active ? (uint32_t)i : (i == a.src ? 0u : UINT32_MAX);
+    for (uint64_t w = tid; w < a.nwords; w += nthreads) {
+        uint32_t f;
+        if (a.all_active) f = (w == a.nwords - 1) ? tail : ~0u;
+        else f = (w == (a.src >> 5)) ? (1u << (a.src & 31)) : 0u;
+        a.front[0][w] = f;
+        a.front[1][w] = 0u;
+        a.front[2][w] = 0u;
+    }
+    if (tid == 0) {
+        memset(res, 0, sizeof(BfsResult));
+        if (a.all_active) {
+            st->qstate[0] = ((unsigned long long)a.n << a.ebits) | a.m;
+        } else {
+            uint32_t r0 = __ldg(&a.rp_out[a.src]);
+            a.q[0][0] = a.src;
+            a.qp[0][0] = 0;
+            a.qr[0][0] = r0;
+            st->qstate[0] = (1ull << a.ebits) | (__ldg(&a.rp_out[a.src + 1]) - r0);
+        }
+    }
+    bool ok = dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns);
+    const uint64_t t_start = dev::globaltimer_ns();
+    bool list_valid = !a.all_active;
+    int d = 0;
+    for (; ok; ++d) {
+        if (threadIdx.x == 0)
+            sm.qs = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>(st->qstate[d % 3])
+                        .load(cuda::memory_order_relaxed);
+        __syncthreads();
+        const unsigned long long qs = sm.qs;
+        __syncthreads();
+        const uint32_t cnt = (uint32_t)(qs >> a.ebits);
+        const uint64_t fe = qs & a.emask;
+        if (cnt == 0) break;
+        // guard: every value can decrease only finitely often; a wall-clock budget bounds the loop
+        if (threadIdx.x == 0 && dev::globaltimer_ns() - t_start > a.total_limit_ns) atomicCAS(&st->err, 0, (int)GB_TIMEOUT);
+        bool pull = a.rp_in && a.mode != GB_PUSH && (a.mode == GB_PULL || fe * (uint64_t)a.beta > a.m);
+        if (tid == 0) {
+            if (d < GBX_MAX_LEVEL_LOG) {
+                res->dir_log[d] = pull ? 2 : 1;
+                res->lv_cnt[d] = cnt;
+                res->lv_fe[d] = fe;
+                res->lv_ns[d] = dev::globaltimer_ns();
+            }
+            if (pull) res->pull_levels++; else res->push_levels++;
+            res->frontier_edges += fe;
+            st->qstate[(d + 2) % 3] = 0;
+            st->cstate[(d + 2) % 3] = 0;
+        }
+        uint32_t *Fclr = a.front[(d + 2) % 3];
+        for (uint64_t w = tid; w < a.nwords; w += nthreads) Fclr[w] = 0u;
+        if (pull) {
+            if (threadIdx.x == 0) { s_cnt = 0; s_deg = 0; }
+            __syncthreads();
+            uint32_t c = 0, dg = 0;
+            relax_pull(a, d, &c, &dg);
+            c = dev::warp_sum<uint32_t>(c);
+            dg = dev::warp_sum<uint32_t>(dg);
+            if ((threadIdx.x & 31) == 0 && c) { atomicAdd(&s_cnt, c); atomicAdd(&s_deg, dg); }
+            __syncthreads();
+            if (threadIdx.x == 0 && s_cnt)
+                atomicAdd(&st->qstate[(d + 1) % 3], ((unsigned long long)s_cnt << a.ebits) | s_deg);
+            list_valid = false;
+        } else {
+            if (!list_valid) {
+                compact_level(a, sm, d);
+                if (!dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns)) { ok = false; break; }
+            }
+            push_edges(a, sm, d, cnt, fe, [&](uint32_t u, uint32_t v, uint32_t p, uint32_t *Fn, uint32_t *deg) {
+                uint32_t c = relax_val(a, ldcg(&a.val[u]), p, a.w_out);
+                if (c >= ldcg(&a.val[v])) return false;
+                uint32_t old = atomicMin(&a.val[v], c);
+                if (c >= old) return false;
+                uint32_t bit = 1u << (v & 31);
+                uint32_t o = atomicOr(&Fn[v >> 5], bit);
+                if (o & bit) return false;
+                *deg = __ldg(&a.rp_out[v + 1]) - __ldg(&a.rp_out[v]);
+                return true;
+            });
+            list_valid = true;
+        }
+        ok = dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns);
+    }
+    if (tid == 0) {
+        res->depth = d;
+        if (d < GBX_MAX_LEVEL_LOG) res->lv_ns[d] = dev::globaltimer_ns();
+        res->t_begin = t_start;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned int old = atomicAdd(&st->bar.exits, 1u);
+        if (old == gridDim.x - 1) {
+            __threadfence();
+            res->err = ld_relaxed_gpu_int_(&st->err);
+            st->err = 0;
+            st->bar.count = 0;
+            for (int k = 0; k < 3; ++k) { st->qstate[k] = 0; st->exam[k] = 0; st->cstate[k] = 0; }
+            __threadfence();
+            st->bar.exits = 0;
+        }
+    }
+}
+
+}  // namespace rlx
+
+struct BfsWorkspace;
+gb_info bfs_workspace_raw(gb_context *ctx, uint32_t n, uint32_t **visited, uint32_t **front, uint32_t **q,
+                          uint32_t **qp, uint32_t **qr, BfsState **st);
+
+static gb_info relax_run(gb_context *ctx, const gb_matrix *A, bool weighted, uint32_t src, uint32_t *out, gb_mem mem,
+                         const gb_desc *desc, uint32_t *iterations, const char *who) {
+    if (!ctx || !A || !out) return fail(GB_NULL_POINTER, "%s: NULL argument", who);
+    if (!A->built) return fail(GB_INVALID_VALUE, "%s: matrix not built", who);
+    if (A->nrows != A->ncols) return fail(GB_DIMENSION_MISMATCH, "%s: matrix must be square", who);
+    if (A->nrows == 0) return GB_SUCCESS;
+    if (weighted) {
+        if (src >= A->nrows) return fail(GB_INVALID_INDEX, "%s: source %u out of range", who, src);
+        if (!A->has_vals || A->type != GB_UINT32) return fail(GB_DOMAIN_MISMATCH, "%s: needs uint32 edge weights", who);
+    }
+    GB_CUDA(cudaSetDevice(ctx->device));
+    uint32_t *visited, *front, *q, *qp, *qr;
+    BfsState *st;
+    GB_CHECK(bfs_workspace_raw(ctx, A->nrows, &visited, &front, &q, &qp, &qr, &st));
+    rlx::RelaxArgs a;
+    a.n = A->nrows;
+    a.nwords = (A->nrows + 31) / 32;
+    a.m = A->nvals;
+    a.rp_out = A->rowptr; a.ci_out = A->colidx; a.w_out = weighted ? (const uint32_t *)A->vals : nullptr;
+    a.rp_in = A->has_csc ? A->colptr : nullptr;
+    a.ci_in = A->has_csc ? A->rowidx : nullptr;
+    a.w_in = (weighted && A->has_csc) ? (const uint32_t *)A->cvals : nullptr;
+    a.csr_is_csc = A->csc_alias;
+    a.weighted = weighted;
+    a.src = src;
+    a.all_active = !weighted;
+    Scratch ob(ctx);
+    a.val = out;
+    if (mem == GB_HOST) {
+        GB_CHECK(ob.alloc((size_t)A->nrows * 4 + 16));
+        a.val = ob.as<uint32_t>();
+    }
+    for (int k = 0; k < 3; ++k) a.front[k] = front + (size_t)k * a.nwords;
+    a.q[0] = q; a.q[1] = q + A->nrows + 1;
+    a.qp[0] = qp; a.qp[1] = qp + A->nrows + 1;
+    a.qr[0] = qr; a.qr[1] = qr + A->nrows + 1;
+    a.ebits = 64 - bits_for((uint64_t)A->nrows + 1);
+    a.emask = (a.ebits >= 64) ? ~0ull : ((1ull << a.ebits) - 1);
+    a.mode = desc ? desc->direction : GB_AUTO;
+    a.beta = (desc && desc->beta > 0) ? (uint32_t)desc->beta : 10u;
+    a.st = st;
+    a.timeout_ns = 4000000000ull;
+    a.total_limit_ns = 300000000000ull;
+    int occ = 0;
+    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rlx::k_relax, rlx::BLOCK, 0));
+    if (occ < 1) return fail(GB_PANIC, "%s: kernel cannot be resident", who);
+    void *args[] = {&a};
+    int span = prof_begin(ctx, weighted ? "sssp" : "cc");
+    GB_CUDA(cudaLaunchCooperativeKernel((const void *)rlx::k_relax, dim3(occ * ctx->num_sms), dim3(rlx::BLOCK), args,
+                                        0, ctx->stream));
+    prof_end(ctx, span);
+    BfsResult hs;
+    GB_CUDA(cudaMemcpyAsync(&hs, &st->res, sizeof(BfsResult), cudaMemcpyDeviceToHost, ctx->stream));
+    if (mem == GB_HOST) GB_CUDA(cudaMemcpyAsync(out, a.val, (size_t)A->nrows * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    GB_CHECK(sync(ctx));
+    if (iterations) *iterations = hs.depth;
+    if (hs.err) return fail(GB_TIMEOUT, "%s: a bounded device wait or the time budget ran out", who);
+    return GB_SUCCESS;
+}
+
+}  // namespace gbx
+
+extern "C" {
+
+gb_info gb_sssp(gb_context *ctx, const gb_matrix *A, uint32_t src, uint32_t *dist, gb_mem mem, const gb_desc *desc,
+                uint32_t *iterations) {
+    return relax_run(ctx, A, true, src, dist, mem, desc, iterations, "gb_sssp");
+}
+
+gb_info gb_cc(gb_context *ctx, const gb_matrix *A, uint32_t *labels, gb_mem mem, uint32_t *iterations) {
+    return relax_run(ctx, A, false, 0, labels, mem, nullptr, iterations, "gb_cc");
+}
+
+}  // extern "C"

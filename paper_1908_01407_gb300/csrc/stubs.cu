@@ -3,32 +3,7 @@
 using namespace gbx;
 #define STUB(name, ...) gb_info name(__VA_ARGS__) { return fail(GB_NOT_IMPLEMENTED, #name " is not implemented"); }
 extern "C" {
-STUB(gb_vector_new, gb_vector **v, gb_context *ctx, gb_type type, uint64_t n)
-STUB(gb_vector_build, gb_vector *v, const uint32_t *idx, const void *vals, uint64_t nvals, gb_binop dup, gb_mem mem)
-STUB(gb_vector_build_dense, gb_vector *v, const void *vals, gb_mem mem)
-STUB(gb_vector_fill, gb_vector *v, const void *scalar)
-STUB(gb_vector_set_element, gb_vector *v, uint32_t idx, const void *scalar)
-STUB(gb_vector_extract_element, const gb_vector *v, uint32_t idx, void *out)
-STUB(gb_vector_extract_tuples, const gb_vector *v, uint32_t *idx, void *vals, uint64_t *n_inout, gb_mem mem)
-STUB(gb_vector_extract_dense, const gb_vector *v, void *vals, uint8_t *present, const void *absent_value, gb_mem mem)
-STUB(gb_vector_size, const gb_vector *v, uint64_t *n)
-STUB(gb_vector_nvals, const gb_vector *v, uint64_t *n)
-STUB(gb_vector_dup, gb_vector **out, const gb_vector *v)
-STUB(gb_vector_clear, gb_vector *v)
-STUB(gb_vector_free, gb_vector **v)
-STUB(gb_mxv, gb_vector *w, const gb_vector *mask, gb_binop accum, gb_semiring s, const gb_matrix *A, const gb_vector *u, const gb_desc *desc)
-STUB(gb_vxm, gb_vector *w, const gb_vector *mask, gb_binop accum, gb_semiring s, const gb_vector *u, const gb_matrix *A, const gb_desc *desc)
-STUB(gb_mxm, gb_matrix *C, const gb_matrix *M, gb_binop accum, gb_semiring s, const gb_matrix *A, const gb_matrix *B, const gb_desc *desc)
-STUB(gb_ewise_add, gb_vector *w, const gb_vector *mask, gb_binop accum, gb_binop op, const gb_vector *u, const gb_vector *v, const gb_desc *desc)
-STUB(gb_ewise_mult, gb_vector *w, const gb_vector *mask, gb_binop accum, gb_binop op, const gb_vector *u, const gb_vector *v, const gb_desc *desc)
-STUB(gb_reduce_vector, void *out, gb_binop accum, gb_monoid m, const gb_vector *u)
-STUB(gb_reduce_matrix, void *out, gb_binop accum, gb_monoid m, const gb_matrix *A)
-STUB(gb_reduce_rows, gb_vector *w, const gb_vector *mask, gb_binop accum, gb_monoid m, const gb_matrix *A, const gb_desc *desc)
 STUB(gb_bfs_multi, gb_context *ctx, const gb_matrix *A, const uint32_t *srcs, uint32_t k, int32_t *levels, gb_mem mem, const gb_desc *desc, gb_bfs_stats *stats)
-STUB(gb_sssp, gb_context *ctx, const gb_matrix *A, uint32_t src, uint32_t *dist, gb_mem mem, const gb_desc *desc, uint32_t *iterations)
-STUB(gb_pagerank, gb_context *ctx, const gb_matrix *A, float damping, uint32_t iters, float *rank, double *residuals, gb_mem mem)
-STUB(gb_cc, gb_context *ctx, const gb_matrix *A, uint32_t *labels, gb_mem mem, uint32_t *iterations)
-STUB(gb_tc, gb_context *ctx, const gb_matrix *L, uint64_t *count, gb_matrix *C)
 STUB(gb_server_create, gb_server **s, gb_context *ctx, const gb_server_cfg *cfg)
 STUB(gb_server_add_graph, gb_server *s, const gb_matrix *A, uint32_t *graph_id)
 STUB(gb_server_submit, gb_server *s, const gb_request *req, uint64_t *ticket)

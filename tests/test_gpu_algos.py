@@ -1,0 +1,225 @@
+"""GPU parity of the algorithms built on the library: SSSP (bit-exact
+distances), connected components (bit-exact canonical labels), PageRank
+(L1 <= 1e-5 against the FP64 oracle) and triangle counting (exact count and
+exact per-entry C of C<L> = L*L), through the C ABI."""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+import paper_1908_01407_gb300 as gb
+
+pytestmark = pytest.mark.gpu
+
+PR_L1_TOL = 1e-5
+
+
+def build(ctx, t, weights=True, flags=gb.SYMMETRIC):
+    g = oracle.csr_from_tuples(t)
+    A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, t.w if (weights and t.w is not None) else None,
+                              type_=gb.UINT32, flags=flags)
+    return g, A
+
+
+def sssp_gpu(ctx, A, src, direction=gb.AUTO):
+    d = gb.Descriptor(direction=direction)
+    dist = np.empty(A.nrows, np.uint32)
+    _, it = gb.sssp(ctx, A, src, dist, d)
+    d.free()
+    return dist, it
+
+
+# ------------------------------------------------------------------- SSSP
+def test_sssp_small_graphs_all_directions(ctx):
+    cases = [gen.from_edges(12, [(i, i + 1) for i in range(11)], [37] * 11),
+             gen.random_small(12, 0.35, 104, wmax=20),
+             gen.random_small(9, 0.2, 7, wmax=5),
+             gen.grid(33, 17, 0.15, seed=5, wmax=1000),
+             gen.from_edges(1, [], [])]
+    for t in cases:
+        if t.w is None:
+            t = gen.Tuples(t.n, t.src, t.dst, np.ones_like(t.src), t.name)
+        g, A = build(ctx, t)
+        for src in sorted({0, t.n // 2, t.n - 1}):
+            want = oracle.sssp(g, src)
+            for direction in (gb.AUTO, gb.PUSH, gb.PULL):
+                got, _ = sssp_gpu(ctx, A, src, direction)
+                assert np.array_equal(got, want), (t.name, src, direction)
+        A.free()
+
+
+@pytest.mark.parametrize("scale,seed", [(12, 21), (14, 2)])
+def test_sssp_rmat(ctx, scale, seed):
+    t = gen.rmat(scale, 16, seed=seed, wmax=255)
+    g, A = build(ctx, t)
+    for s in gen.sources(t, 4, seed=1):
+        want = oracle.sssp(g, int(s))
+        got, it = sssp_gpu(ctx, A, int(s))
+        assert np.array_equal(got, want)
+        assert it >= 1
+    # device output buffer
+    dist = torch.empty(t.n, dtype=torch.int32, device="cuda")
+    gb.sssp(ctx, A, int(gen.sources(t, 1, seed=1)[0]), dist)
+    assert np.array_equal(dist.cpu().numpy().view(np.uint32), oracle.sssp(g, int(gen.sources(t, 1, seed=1)[0])))
+    A.free()
+
+
+def test_sssp_errors(ctx):
+    t = gen.rmat(8, 4, seed=1)
+    A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, flags=gb.SYMMETRIC)    # structural: no weights
+    with pytest.raises(gb.GBError) as e:
+        gb.sssp(ctx, A, 0, np.empty(t.n, np.uint32))
+    assert e.value.code == gb.DOMAIN_MISMATCH
+    t = gen.rmat(8, 4, seed=1, wmax=9)
+    g, A = build(ctx, t)
+    with pytest.raises(gb.GBError) as e:
+        gb.sssp(ctx, A, t.n, np.empty(t.n, np.uint32))
+    assert e.value.code == gb.INVALID_INDEX
+
+
+# --------------------------------------------------------------------- CC
+@pytest.mark.parametrize("case", ["rmat14", "rmat_sparse", "grid", "small"])
+def test_cc(ctx, case):
+    t = {"rmat14": lambda: gen.rmat(14, 16, seed=1),
+         "rmat_sparse": lambda: gen.rmat(13, 1, seed=9),
+         "grid": lambda: gen.grid(96, 80, 0.45, seed=3),
+         "small": lambda: gen.random_small(12, 0.15, 205)}[case]()
+    g, A = build(ctx, t, weights=False)
+    want = oracle.cc(g)
+    lab = np.empty(t.n, np.uint32)
+    _, it = gb.cc(ctx, A, lab)
+    assert np.array_equal(lab, want)
+    assert it >= 1
+    A.free()
+
+
+# ---------------------------------------------------------------- PageRank
+@pytest.mark.parametrize("case", ["rmat14", "rmat12_e4", "grid", "star", "cycle"])
+def test_pagerank_l1_vs_fp64_oracle(ctx, case):
+    t = {"rmat14": lambda: gen.rmat(14, 16, seed=1),
+         "rmat12_e4": lambda: gen.rmat(12, 4, seed=3),
+         "grid": lambda: gen.grid(70, 50, 0.1, seed=3),
+         "star": lambda: gen.from_edges(300, [(0, i) for i in range(1, 300)]),
+         "cycle": lambda: gen.from_edges(1000, [(i, (i + 1) % 1000) for i in range(1000)])}[case]()
+    g, A = build(ctx, t, weights=False)
+    want, wres = oracle.pagerank(g, 0.85, 50)
+    rank = np.empty(t.n, np.float32)
+    _, res = gb.pagerank(ctx, A, 0.85, 50, rank)
+    l1 = np.abs(rank.astype(np.float64) - want).sum()
+    assert l1 <= PR_L1_TOL, l1
+    assert abs(rank.astype(np.float64).sum() - 1.0) < 1e-5
+    # residuals follow the oracle's (FP32 rounding allows small differences)
+    assert np.all(np.abs(res - wres) <= 1e-6 + 1e-3 * wres), (res[:5], wres[:5])
+    if case == "cycle":
+        assert np.max(np.abs(rank - 1.0 / t.n)) < 1e-9
+    A.free()
+
+
+def test_pagerank_is_bit_reproducible(ctx):
+    t = gen.rmat(13, 16, seed=5)
+    g, A = build(ctx, t, weights=False)
+    r1 = np.empty(t.n, np.float32)
+    r2 = np.empty(t.n, np.float32)
+    gb.pagerank(ctx, A, 0.85, 20, r1)
+    gb.pagerank(ctx, A, 0.85, 20, r2)
+    assert np.array_equal(r1.view(np.uint32), r2.view(np.uint32))
+    A.free()
+
+
+# --------------------------------------------------------------------- TC
+def tc_pipeline(ctx, t):
+    A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, flags=gb.SYMMETRIC)
+    B, new_id = A.degree_order()
+    L = B.tril()
+    return A, B, L, new_id
+
+
+@pytest.mark.parametrize("case", ["k12", "wheel", "tree", "rmat12", "rmat14", "grid"])
+def test_tc_count_and_entries(ctx, case):
+    t = {"k12": lambda: gen.from_edges(12, list(itertools.combinations(range(12), 2))),
+         "wheel": lambda: gen.from_edges(10, [(0, i) for i in range(1, 10)] + [(i, i % 9 + 1) for i in range(1, 10)]),
+         "tree": lambda: gen.from_edges(31, [(i, (i - 1) // 2) for i in range(1, 31)]),
+         "rmat12": lambda: gen.rmat(12, 16, seed=4),
+         "rmat14": lambda: gen.rmat(14, 16, seed=4),
+         "grid": lambda: gen.grid(40, 40, 0.0, seed=1)}[case]()
+    g = oracle.csr_from_tuples(t)
+    A, B, L, new_id = tc_pipeline(ctx, t)
+    want_new = oracle.degree_order(g)
+    assert np.array_equal(new_id, want_new)
+    h = oracle.relabel(g, want_new)
+    want_vals, want_total = oracle.masked_LL(h)
+    assert want_total == oracle.tc(g)
+    C = gb.Matrix(ctx, gb.UINT32, t.n, t.n)
+    assert gb.tc(ctx, L) == want_total
+    assert gb.tc(ctx, L, C) == want_total
+    r, c, v = C.extract_tuples(with_vals=True)
+    Lr, Lc = L.extract_tuples()
+    assert np.array_equal(r, Lr) and np.array_equal(c, Lc)
+    assert np.array_equal(v, want_vals)
+    for x in (A, B, L, C):
+        x.free()
+
+
+def test_tc_agrees_with_generic_masked_mxm(ctx):
+    t = gen.rmat(11, 16, seed=6)
+    A, B, L, _ = tc_pipeline(ctx, t)
+    C = gb.Matrix(ctx, gb.UINT32, t.n, t.n)
+    gb.mxm(C, L, gb.NOP, gb.PLUS_PAIR, L, L, gb.Descriptor(mask=gb.STRUCTURE))
+    total = gb.reduce_matrix(C, gb.MONOID_PLUS)
+    assert total == gb.tc(ctx, L) == oracle.tc(oracle.csr_from_tuples(t))
+    for x in (A, B, L, C):
+        x.free()
+
+
+# ----------------------------------------------------- full config sizes
+@pytest.mark.slow
+def test_sssp_pagerank_rmat_s22_full_size(ctx):
+    """R-MAT scale 22, edge factor 16, seed 2, weights uniform in [1, 255]:
+    SSSP from the first of the benchmark's sources and 50 PageRank
+    iterations, against the oracle."""
+    t = gen.rmat(22, 16, seed=2, wmax=255)
+    g, A = build(ctx, t)
+    s = int(gen.sources(t, 8, seed=1)[0])
+    got, _ = sssp_gpu(ctx, A, s)
+    assert np.array_equal(got, oracle.sssp(g, s))
+    rank = np.empty(t.n, np.float32)
+    gb.pagerank(ctx, A, 0.85, 50, rank)
+    want, _ = oracle.pagerank(g, 0.85, 50)
+    assert np.abs(rank.astype(np.float64) - want).sum() <= PR_L1_TOL
+    A.free()
+
+
+@pytest.mark.slow
+def test_grid_4096_bfs_sssp_cc_full_size(ctx):
+    """4096 x 4096 grid, 10% of edges deleted (seed 3), weights in [1, 1000]:
+    BFS, SSSP and connected components against the oracle."""
+    t = gen.grid(4096, 4096, 0.1, seed=3, wmax=1000)
+    g, A = build(ctx, t)
+    src = gen.first_nonisolated(t)
+    lv, par, st = gb.bfs(ctx, A, src)
+    lv = lv.cpu().numpy()
+    want = oracle.bfs(g, src)
+    assert np.array_equal(lv, want)
+    assert oracle.bfs_parent_violations(g, src, lv, par.cpu().numpy()) == 0
+    got, _ = sssp_gpu(ctx, A, src)
+    assert np.array_equal(got, oracle.sssp(g, src))
+    lab = np.empty(t.n, np.uint32)
+    gb.cc(ctx, A, lab)
+    assert np.array_equal(lab, oracle.cc(g))
+    A.free()
+
+
+@pytest.mark.slow
+def test_tc_rmat_s20_full_size(ctx):
+    """R-MAT scale 20, edge factor 16, seed 4, degree-ordered, L = tril."""
+    from tests.conftest import read_golden
+    f = read_golden("tc_rmat_s20.txt")     # the oracle's count (tests/golden/make_golden.py)
+    t = gen.rmat(20, 16, seed=4)
+    A, B, L, _ = tc_pipeline(ctx, t)
+    assert A.nvals == int(f["m_stored"])
+    assert gb.tc(ctx, L) == int(f["triangles"])
+    for x in (A, B, L):
+        x.free()
