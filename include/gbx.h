@@ -289,6 +289,31 @@ typedef struct {
  * entries in `mem`. stats may be NULL. desc: GB_DIRECTION, GB_SWITCH_BETA. */
 gb_info gb_bfs(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *levels, int32_t *parents,
                gb_mem mem, const gb_desc *desc, gb_bfs_stats *stats);
+/* BFS that allocates no device memory (the paper has no counterpart; it is
+ * an extra for callers that cannot allocate on the call path: a process
+ * whose device memory belongs to another allocator such as a framework's
+ * caching allocator or a fixed arena, a latency-critical loop that cannot
+ * absorb the device-wide synchronisation of cudaFree, or a deployment that
+ * forbids dynamic allocation after start-up). Same traversal and outputs as
+ * gb_bfs with the default descriptor, but no gb_context or gb_matrix: the
+ * caller passes device pointers to CSR (rowptr[n+1], colidx[nnz]; out-edges)
+ * and optionally CSC (colptr[n+1], rowidx[nnz]; in-edges; pass the CSR
+ * pointers again for a symmetric graph, or NULL for push-only), and the
+ * outputs levels[n] and parents[n] (parents may be NULL). colidx and rowidx
+ * must start on a 16-byte boundary and stay readable for 16 bytes past
+ * their last entry. All scratch lives in one array built into the library
+ * (about 6.4 MB, enough for n <= GB_NOALLOC_MAX_VERTICES); each GPU that
+ * loads the library holds it until the process exits. n above that limit:
+ * GB_INVALID_VALUE. The first call on a device looks up the array's device
+ * address (with that device current); make that first call before any
+ * stream capture. Work is enqueued on `stream` (a cudaStream_t; NULL = the
+ * legacy default stream) and the call returns without waiting. Every call
+ * shares the one array and the array keeps the last call's contents:
+ * calls whose work overlaps on the GPU (e.g. on different streams) race, so
+ * order them on one stream or with events. */
+#define GB_NOALLOC_MAX_VERTICES 262144u
+gb_info gb_bfs_noalloc(const uint32_t *rowptr, const uint32_t *colidx, const uint32_t *colptr, const uint32_t *rowidx,
+                       uint32_t n, uint64_t nnz, uint32_t src, int32_t *levels, int32_t *parents, void *stream);
 /* Multi-source BFS as Boolean SpMM over 64-bit bit-packed frontiers
  * (Section 3.3 multi-nodeset traversal; Section 8 matrix direction
  * optimisation): k <= 64 sources, levels is k x nrows (row q = source q). */

@@ -123,7 +123,8 @@ _SIGS = {
     "gb_ewise_add": [_P, _P, _I, _I, _P, _P, _P], "gb_ewise_mult": [_P, _P, _I, _I, _P, _P, _P],
     "gb_reduce_vector": [_P, _I, _I, _P], "gb_reduce_matrix": [_P, _I, _I, _P],
     "gb_reduce_rows": [_P, _P, _I, _I, _P, _P],
-    "gb_bfs": [_P, _P, _U32, _P, _P, _I, _P, _P], "gb_bfs_multi": [_P, _P, _P, _U32, _P, _I, _P, _P],
+    "gb_bfs": [_P, _P, _U32, _P, _P, _I, _P, _P],
+    "gb_bfs_noalloc": [_P, _P, _P, _P, _U32, _U64, _U32, _P, _P, _P], "gb_bfs_multi": [_P, _P, _P, _U32, _P, _I, _P, _P],
     "gb_sssp": [_P, _P, _U32, _P, _I, _P, _P], "gb_pagerank": [_P, _P, ctypes.c_float, _U32, _P, _P, _I],
     "gb_cc": [_P, _P, _P, _I, _P], "gb_tc": [_P, _P, _P, _P],
     "gb_server_create": [_PP, _P, _P], "gb_server_add_graph": [_P, _P, _P], "gb_server_submit": [_P, _P, _P],
@@ -535,6 +536,23 @@ def bfs(ctx, A, src, levels=None, parents=None, desc=None, stats=True):
     st = BfsStats()
     check(lib().gb_bfs(ctx.h, A.h, src, pl, pp, ml, _h(desc), ctypes.byref(st) if stats else None))
     return levels, parents, (st.as_dict() if stats else None)
+
+
+NOALLOC_MAX_VERTICES = 262144
+
+
+def bfs_noalloc(rowptr, colidx, colptr, rowidx, n, nnz, src, levels, parents=None, stream=None):
+    """gb_bfs_noalloc: BFS with the library's built-in scratch (no device
+    allocation on the call path). All arrays are CUDA tensors; colidx and
+    rowidx must be 16-byte aligned and readable 16 bytes past their end.
+    stream: a torch.cuda.Stream (default: the current stream)."""
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    ptrs = [x.data_ptr() if x is not None else None for x in (rowptr, colidx, colptr, rowidx, levels, parents)]
+    check(lib().gb_bfs_noalloc(ptrs[0], ptrs[1], ptrs[2], ptrs[3], n, nnz, src, ptrs[4], ptrs[5],
+                               ctypes.c_void_p(stream.cuda_stream)))
+    return levels, parents
 
 
 def bfs_multi(ctx, A, srcs, levels=None, desc=None, stats=True):

@@ -501,3 +501,110 @@ extern "C" gb_info gb_bfs(gb_context *ctx, const gb_matrix *A, uint32_t src, int
     }
     return GB_SUCCESS;
 }
+
+// ------------------------------------------------------------------------
+// BFS without any device allocation: the scratch (bitmaps, frontier lists,
+// working state) lives in one array compiled into this library, so the call
+// path never calls cudaMalloc/cudaFree. It serves callers that cannot
+// allocate device memory when they run a traversal: a process whose device
+// memory is owned by another allocator (a framework's caching allocator or
+// a fixed arena), a latency-critical loop that cannot afford the device-wide
+// synchronisation cudaFree implies, or a deployment that forbids dynamic
+// allocation after start-up. The array has room for graphs of up to
+// GB_NOALLOC_MAX_VERTICES vertices and stays resident on every GPU that
+// loads the library until the process exits.
+namespace gbx {
+namespace noalloc {
+constexpr size_t MAX_N = GB_NOALLOC_MAX_VERTICES;
+constexpr size_t NW = (MAX_N + 31) / 32;
+constexpr size_t LIST = 2 * (MAX_N + 1) * sizeof(uint32_t);
+constexpr size_t OFF_VISITED = 0;
+constexpr size_t OFF_FRONT = OFF_VISITED + NW * 4;
+constexpr size_t OFF_Q = ((OFF_FRONT + 3 * NW * 4) + 255) / 256 * 256;
+constexpr size_t OFF_QP = OFF_Q + (LIST + 255) / 256 * 256;
+constexpr size_t OFF_QR = OFF_QP + (LIST + 255) / 256 * 256;
+constexpr size_t OFF_ST = OFF_QR + (LIST + 255) / 256 * 256;
+constexpr size_t BYTES = OFF_ST + (sizeof(BfsState) + 255) / 256 * 256;
+
+struct Device {
+    bool ready = false;
+    unsigned char *base = nullptr;   // device address of the scratch array on this device
+    int grid = 0;
+};
+constexpr int MAX_DEVICES = 64;
+std::mutex mu;
+Device devices[MAX_DEVICES];
+}  // namespace noalloc
+
+// The scratch array. In host code this name is only a stand-in: the device
+// address comes from cudaGetSymbolAddress (done once per device).
+static __device__ __align__(256) unsigned char g_bfs_scratch[noalloc::BYTES];
+
+}  // namespace gbx
+
+extern "C" gb_info gb_bfs_noalloc(const uint32_t *rowptr, const uint32_t *colidx, const uint32_t *colptr,
+                                  const uint32_t *rowidx, uint32_t n, uint64_t nnz, uint32_t src, int32_t *levels,
+                                  int32_t *parents, void *stream) {
+    using namespace gbx::noalloc;
+    if (!rowptr || !colidx || !levels) return fail(GB_NULL_POINTER, "gb_bfs_noalloc: NULL argument");
+    if ((colptr == nullptr) != (rowidx == nullptr))
+        return fail(GB_NULL_POINTER, "gb_bfs_noalloc: colptr and rowidx must both be given or both be NULL");
+    if (n == 0 || n > MAX_N)
+        return fail(GB_INVALID_VALUE, "gb_bfs_noalloc: n = %u vertices, but the built-in scratch holds 1..%u",
+                    n, (unsigned)MAX_N);
+    if (nnz >= (1ull << 32)) return fail(GB_INVALID_VALUE, "gb_bfs_noalloc: nnz must be < 2^32");
+    if (src >= n) return fail(GB_INVALID_INDEX, "gb_bfs_noalloc: source %u out of range", src);
+    if (((uintptr_t)colidx & 15) || ((uintptr_t)rowidx & 15))
+        return fail(GB_INVALID_VALUE, "gb_bfs_noalloc: colidx and rowidx must be 16-byte aligned");
+    int dev = 0;
+    GB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= MAX_DEVICES) return fail(GB_INVALID_VALUE, "gb_bfs_noalloc: device %d unsupported", dev);
+    Device *D = &devices[dev];
+    {
+        // set-up on the first call for this device (with it current)
+        std::lock_guard<std::mutex> g(mu);
+        if (!D->ready) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_bfs_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_bfs_scratch)", __FILE__, __LINE__);
+            int occ = 0, sms = 0;
+            GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bfsk::k_bfs, bfsk::BLOCK, 0));
+            GB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            if (occ < 1) return fail(GB_PANIC, "gb_bfs_noalloc: BFS kernel cannot be resident");
+            D->base = (unsigned char *)p;
+            D->grid = occ * sms;
+            D->ready = true;
+        }
+    }
+    unsigned char *base = D->base;
+    cudaStream_t s = (cudaStream_t)stream;
+    BfsArgs a;
+    a.n = n;
+    a.nwords = (n + 31) / 32;
+    a.m = nnz;
+    a.src = src;
+    a.rp_out = rowptr;
+    a.ci_out = colidx;
+    a.rp_in = colptr;
+    a.ci_in = rowidx;
+    a.csr_is_csc = colptr == rowptr && rowidx == colidx;
+    a.levels = levels;
+    a.parents = parents;
+    a.visited = (uint32_t *)(base + OFF_VISITED);
+    for (int k = 0; k < 3; ++k) a.front[k] = (uint32_t *)(base + OFF_FRONT) + (size_t)k * a.nwords;
+    a.q[0] = (uint32_t *)(base + OFF_Q); a.q[1] = a.q[0] + n + 1;
+    a.qp[0] = (uint32_t *)(base + OFF_QP); a.qp[1] = a.qp[0] + n + 1;
+    a.qr[0] = (uint32_t *)(base + OFF_QR); a.qr[1] = a.qr[0] + n + 1;
+    a.ebits = 64 - bits_for((uint64_t)n + 1);
+    a.emask = (1ull << a.ebits) - 1;
+    a.mode = GB_AUTO;
+    a.beta = 10u;
+    a.st = (BfsState *)(base + OFF_ST);
+    a.timeout_ns = 4000000000ull;
+    a.total_limit_ns = 120000000000ull;
+    // the kernel needs a zeroed working state; the last call's contents may remain
+    GB_CUDA(cudaMemsetAsync(a.st, 0, sizeof(BfsState), s));
+    void *args[] = {&a};
+    GB_CUDA(cudaLaunchCooperativeKernel((const void *)bfsk::k_bfs, dim3(D->grid), dim3(bfsk::BLOCK), args, 0, s));
+    return GB_SUCCESS;
+}
