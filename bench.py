@@ -259,6 +259,10 @@ def run_gbx(args):
                 "mean_pull_levels": float(np.mean(pulls)), "ms_per_bfs": ms_per_step / NSRC,
                 "gteps_graph500": value / 2},
     }
+    if rank == 0 and not args.no_rows:
+        line["rows"] = extra_rows(args, hbm)
+    if rank == 0 and not args.no_serving:
+        line["serving"] = serving_bench(args)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(t, srcs, args.cpu_budget)
     if rank == 0:
@@ -267,6 +271,174 @@ def run_gbx(args):
     ctx.close()
     if ws > 1:
         dist.destroy_process_group()
+
+
+def cuda_time_ms(fn, stream):
+    """Device time of fn() on `stream` (CUDA events, synchronised both sides)."""
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def extra_rows(args, hbm):
+    """GPU measurements of the other hot-path rows on their workloads."""
+    import torch
+    import gen
+    import paper_1908_01407_gb300 as gb
+    out = {}
+    stream = torch.cuda.Stream()
+    ctx = gb.Context(0)
+    ctx.set_stream(stream)
+    # --- SSSP and PageRank on R-MAT s22 (weights uniform in [1, 255])
+    t = gen.rmat(SCALE, EF, seed=SEED, wmax=255)
+    A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, t.w, type_=gb.UINT32, flags=gb.SYMMETRIC)
+    n, m = A.nrows, A.nvals
+    srcs = gen.sources(t, 8, seed=SRC_SEED)
+    dist = torch.empty(n, dtype=torch.int32, device="cuda")
+    for s in srcs[:2]:
+        gb.sssp(ctx, A, int(s), dist)
+    iters = []
+    def sssp_all():
+        for s in srcs:
+            _, it = gb.sssp(ctx, A, int(s), dist)
+            iters.append(it)
+    ms = cuda_time_ms(sssp_all, stream)
+    out["sssp_s22"] = {"sources": len(srcs), "ms_per_sssp": ms / len(srcs), "gteps": len(srcs) * m / (ms / 1e3) / 1e9,
+                       "mean_iterations": float(np.mean(iters)), "cpu_baseline": None}
+    rank = torch.empty(n, dtype=torch.float32, device="cuda")
+    gb.pagerank(ctx, A, 0.85, 50, rank, residuals=False)
+    ctx.profile(True)
+    ms = cuda_time_ms(lambda: gb.pagerank(ctx, A, 0.85, 50, rank, residuals=False), stream)
+    k_ms, k_n = ctx.profile_get("pagerank_spmv")
+    ctx.profile(False)
+    it_ms = k_ms / max(k_n, 1)
+    bytes_iter = 4.0 * m + 20.0 * n
+    out["pagerank_s22"] = {"iterations": 50, "ms_total": ms, "ms_per_iteration": it_ms,
+                           "gteps_per_iteration": m / (it_ms / 1e3) / 1e9,
+                           "roofline": {"bound": "hbm", "kernel": "k_pr_spmv", "alg_bytes_per_launch": bytes_iter,
+                                        "achieved": bytes_iter / (it_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                                        "frac": bytes_iter / (it_ms / 1e3) / 1e9 / hbm}}
+    # --- multi-source BFS: the 64 benchmark sources in one bit-frontier launch
+    bsrcs = gen.sources(t, NSRC, seed=SRC_SEED)
+    lv = torch.empty((NSRC, n), dtype=torch.int32, device="cuda")
+    gb.bfs_multi(ctx, A, bsrcs, lv, stats=False)
+    ms = cuda_time_ms(lambda: gb.bfs_multi(ctx, A, bsrcs, lv, stats=False), stream)
+    out["bfs_multi64_s22"] = {"ms_per_batch": ms, "gteps": NSRC * m / (ms / 1e3) / 1e9}
+    A.free()
+    del t
+    # --- triangle counting on R-MAT s20 (degree ordered, L = tril)
+    t = gen.rmat(20, 16, seed=4)
+    A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, flags=gb.SYMMETRIC)
+    B, _ = A.degree_order()
+    L = B.tril()
+    cnt = gb.tc(ctx, L)
+    ms = cuda_time_ms(lambda: gb.tc(ctx, L), stream)
+    out["tc_s20"] = {"triangles": cnt, "ms": ms, "nnz_L": L.nvals, "mteps": A.nvals / (ms / 1e3) / 1e6}
+    for x in (A, B, L):
+        x.free()
+    del t
+    # --- 4096 x 4096 grid, 10% of edges deleted, weights in [1, 1000]
+    t = gen.grid(4096, 4096, 0.1, seed=3, wmax=1000)
+    A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, t.w, type_=gb.UINT32, flags=gb.SYMMETRIC)
+    src = gen.first_nonisolated(t)
+    lvg = torch.empty(t.n, dtype=torch.int32, device="cuda")
+    pag = torch.empty(t.n, dtype=torch.int32, device="cuda")
+    _, _, st = gb.bfs(ctx, A, src, lvg, pag)
+    ms = cuda_time_ms(lambda: gb.bfs(ctx, A, src, lvg, pag, stats=False), stream)
+    g_out = {"bfs_ms": ms, "bfs_levels": st["depth"], "bfs_us_per_level": 1e3 * ms / max(st["depth"], 1)}
+    d = torch.empty(t.n, dtype=torch.int32, device="cuda")
+    its = []
+    ms = cuda_time_ms(lambda: its.append(gb.sssp(ctx, A, src, d)[1]), stream)
+    g_out.update({"sssp_ms": ms, "sssp_iterations": its[0]})
+    its = []
+    ms = cuda_time_ms(lambda: its.append(gb.cc(ctx, A, d)[1]), stream)
+    g_out.update({"cc_ms": ms, "cc_iterations": its[0]})
+    out["grid_4096"] = g_out
+    A.free()
+    ctx.close()
+    return out
+
+
+def serving_bench(args):
+    """Poisson stream of BFS/SSSP/PageRank (60/30/10) requests over 64
+    R-MAT graphs of scales 12..20 (log-uniform, edge factor 16, weights in
+    [1, 255], graph g seeded 1000 + g), served with continuous batching,
+    against the same requests run one at a time on the same GPU."""
+    import torch
+    import gen
+    import paper_1908_01407_gb300 as gb
+    ctx = gb.Context(0)
+    graphs = []
+    for g in range(args.serve_graphs):
+        scale = 12 + gen.draw(1000 + g, 0x5343414c, 0) % 9
+        t = gen.rmat(int(scale), 16, seed=1000 + g, wmax=255)
+        A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, t.w, type_=gb.UINT32, flags=gb.SYMMETRIC)
+        graphs.append((A, gen.sources(t, 64, seed=1000 + g), int(scale)))
+        del t
+    rng = np.random.default_rng(5)
+    N = args.serve_requests
+    kinds = rng.choice([gb.REQ_BFS, gb.REQ_SSSP, gb.REQ_PAGERANK], size=N, p=[0.6, 0.3, 0.1])
+    gids = rng.integers(0, len(graphs), N)
+    srcs = [int(graphs[g][1][rng.integers(len(graphs[g][1]))]) for g in gids]
+    maxn = max(A.nrows for A, _, _ in graphs)
+    outb = torch.empty(64 * maxn, dtype=torch.int32, device="cuda")
+    # serial baseline: one request at a time, FIFO, whole GPU
+    def run_one(i):
+        A = graphs[gids[i]][0]
+        if kinds[i] == gb.REQ_BFS:
+            gb.bfs(ctx, A, srcs[i], outb[:A.nrows], False, stats=False)
+        elif kinds[i] == gb.REQ_SSSP:
+            gb.sssp(ctx, A, srcs[i], outb[:A.nrows])
+        else:
+            gb.pagerank(ctx, A, 0.85, 50, outb[:A.nrows].view(torch.float32), residuals=False)
+        ctx.synchronize()
+    for i in range(min(N, 50)):
+        run_one(i)
+    t0 = time.perf_counter()
+    lat = []
+    for i in range(N):
+        a = time.perf_counter()
+        run_one(i)
+        lat.append((time.perf_counter() - a) * 1e6)
+    serial_s = time.perf_counter() - t0
+    serial = {"qps": N / serial_s, "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99))}
+    # served: Poisson arrivals at lam = load * serial capacity
+    lam = args.serve_load * serial["qps"]
+    S = gb.Server(ctx, max_inflight=args.serve_slots, batch_window_us=args.serve_window_us)
+    ids = [S.add_graph(A) for A, _, _ in graphs]
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, N))
+    tickets = [None] * N
+    import threading
+    def fetcher():
+        for i in range(N):
+            while tickets[i] is None:
+                time.sleep(0.0002)
+            r = S.wait(tickets[i], 600000)
+            S.fetch_into(tickets[i], outb[:r.n])
+    th = threading.Thread(target=fetcher)
+    th.start()
+    t0 = time.perf_counter()
+    for i in range(N):
+        while time.perf_counter() - t0 < arrivals[i]:
+            pass
+        tickets[i] = S.submit(int(kinds[i]), ids[gids[i]], srcs[i])
+    th.join()
+    st = S.stats()
+    S.destroy()
+    for A, _, _ in graphs:
+        A.free()
+    ctx.close()
+    return {"requests": N, "graphs": len(graphs), "mix": "60% BFS / 30% SSSP / 10% PageRank(50 it)",
+            "offered_qps": lam, "served": {"qps": st["qps"], "p50_us": st["p50_us"], "p99_us": st["p99_us"],
+                                           "batches": st["batches"], "bfs_batched": st["batched_bfs"],
+                                           "slots": args.serve_slots},
+            "serial": serial, "speedup_qps": st["qps"] / serial["qps"]}
 
 
 def run_profile_bfs(args):
@@ -298,6 +470,13 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-sources", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-rows", action="store_true", help="skip the SSSP/PageRank/TC/grid/multi-BFS rows")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-graphs", type=int, default=64)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-load", type=float, default=2.0, help="offered load as a multiple of serial capacity")
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-window-us", type=int, default=300)
     ap.add_argument("--profile-bfs", action="store_true", help="short fixed BFS run for ncu")
     ap.add_argument("--profile-launches", type=int, default=3)
     args = ap.parse_args()

@@ -373,10 +373,13 @@ typedef struct {
 } gb_server_stats;
 
 /* A request loop on the context's GPU: graphs stay resident; requests are
- * admitted while slots (max_inflight) and working memory (HBM budget) are
- * free; concurrent BFS requests on one graph are packed (up to 64) into one
+ * admitted while slots (max_inflight) and memory (HBM budget) are free;
+ * concurrent BFS requests on one graph are packed (up to 64) into one
  * multi-source bit-frontier BFS; running requests overlap on separate
- * streams. Results stay on the device until fetched. */
+ * streams, each slot's persistent kernels sized so all slots fit on the GPU
+ * at once. Results stay on the device until fetched and count against the
+ * budget until then; a job that cannot fit even with nothing running or
+ * held fails with GB_OUT_OF_MEMORY. Latency is from submit to completion. */
 gb_info gb_server_create(gb_server **s, gb_context *ctx, const gb_server_cfg *cfg);
 /* The graph must outlive the server; it needs uint32 weights for SSSP. */
 gb_info gb_server_add_graph(gb_server *s, const gb_matrix *A, uint32_t *graph_id);

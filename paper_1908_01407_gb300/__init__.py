@@ -641,6 +641,12 @@ class Server:
         check(lib().gb_server_fetch(self.h, ticket, out.ctypes.data, HOST))
         return out[:n]
 
+    def fetch_into(self, ticket, out):
+        """Copy a finished result into a caller buffer (torch tensor or numpy array)."""
+        p, mem = _out_mem(out)
+        check(lib().gb_server_fetch(self.h, ticket, p, mem))
+        return out
+
     def stats(self):
         s = ServerStats()
         check(lib().gb_server_stats_get(self.h, ctypes.byref(s)))

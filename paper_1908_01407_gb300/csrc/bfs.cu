@@ -438,7 +438,9 @@ gb_info bfs_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *l
     a.st = w->st;
     a.timeout_ns = 4000000000ull;
     a.total_limit_ns = 120000000000ull;
-    int grid = grid_override > 0 && grid_override < w->grid ? grid_override : w->grid;
+    int grid = w->grid;
+    if (ctx->grid_limit > 0 && ctx->grid_limit < grid) grid = ctx->grid_limit;
+    if (grid_override > 0 && grid_override < grid) grid = grid_override;
     void *args[] = {&a};
     int span = prof_begin(ctx, "bfs");
     GB_CUDA(cudaLaunchCooperativeKernel((const void *)bfsk::k_bfs, dim3(grid), dim3(bfsk::BLOCK), args, 0,

@@ -56,6 +56,9 @@ struct gb_context_t {
     struct Span { std::string name; cudaEvent_t a, b; };
     std::vector<Span> spans;
     std::vector<cudaEvent_t> event_pool;   // reused across enable/disable cycles
+    // upper bound on the blocks of a persistent (cooperative) launch; 0 = the
+    // whole GPU. Contexts that share a GPU concurrently split it this way.
+    int grid_limit = 0;
 };
 
 struct gb_matrix_t {
@@ -148,6 +151,7 @@ int bits_for(uint64_t x);  // number of bits needed to represent values < x
 // and returns its slot (or -1); prof_end records the matching end event.
 int prof_begin(gb_context *ctx, const char *name);
 void bfs_workspace_release(gb_context *ctx);
+void ms_workspace_release(gb_context *ctx);
 void prof_end(gb_context *ctx, int slot);
 
 }  // namespace gbx

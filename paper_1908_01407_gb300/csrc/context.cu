@@ -254,6 +254,7 @@ gb_info gb_finalize(gb_context *ctx) {
     cudaStreamSynchronize(ctx->stream);
     prof_destroy(ctx);
     bfs_workspace_release(ctx);
+    ms_workspace_release(ctx);
     for (auto &kv : ctx->live) cudaFreeAsync(kv.first, ctx->stream);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);

@@ -1,0 +1,429 @@
+// Multi-source BFS as a Boolean SpMM over 64-bit bit-packed frontiers
+// (Section 3.3: mxm is a traversal from several independent sets of active
+// vertices at once; Section 8 proposes direction optimisation for it). Up to
+// 64 BFS share one launch: bit q of F[v] says that v is on source q's
+// frontier. Per level, either
+//   push: every vertex u on some frontier ORs F[u] into the next-frontier
+//         word of each out-neighbour v, minus the bits v already has
+//         (merge-path over the frontier list's out-edges), or
+//   pull: every vertex v that some live source has not reached ORs the
+//         frontier words of its in-neighbours, stopping as soon as all live
+//         sources are covered (the Boolean early exit, per 64 searches),
+// chosen by the rule of Table 8 on the union frontier's edge count. The
+// visited words are merged one level late (V | F is the visited set), so a
+// level needs a single grid barrier.
+#include "common.cuh"
+#include "bfs_common.cuh"
+#include "frontier.cuh"
+
+using namespace gbx;
+
+namespace gbx {
+namespace msk {
+using namespace fr;
+
+struct MsArgs {
+    const uint32_t *rp_out, *ci_out;
+    const uint32_t *rp_in, *ci_in;
+    bool csr_is_csc;
+    uint32_t n, nwords;
+    uint64_t m;
+    uint32_t k;
+    unsigned long long live;          // bits of the k sources
+    const uint32_t *srcs;
+    int32_t *levels;                   // k x n
+    unsigned long long *V;             // visited, merged one level late
+    unsigned long long *F[3];          // frontier words, rotating
+    uint32_t *front[3];                // unused by this kernel (frontier helpers' interface)
+    uint32_t *q[2], *qp[2], *qr[2];
+    int ebits;
+    unsigned long long emask;
+    int mode;
+    uint32_t beta;
+    BfsState *st;
+    uint64_t timeout_ns, total_limit_ns;
+};
+
+__device__ __forceinline__ unsigned long long ldcg64(const unsigned long long *p) { return __ldcg(p); }
+
+// levels[q][v] = d for the bits q of f (lane per vertex; the warp loops over
+// the union of its lanes' bits so each store instruction is coalesced)
+__device__ __forceinline__ void write_levels(const MsArgs &a, uint64_t v, bool valid, unsigned long long f, int d) {
+    unsigned long long u = valid ? f : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) u |= __shfl_xor_sync(0xffffffffu, u, o);
+    while (u) {
+        int q = __ffsll((long long)u) - 1;
+        u &= u - 1;
+        if (valid && ((f >> q) & 1ull)) a.levels[(uint64_t)q * a.n + v] = d;
+    }
+}
+
+// Builds the list form (vertex, out-degree prefix, row start) of the
+// frontier F_d from its words; one atomicAdd per 256 vertices.
+__device__ void ms_compact(const MsArgs &a, Smem &sm, int d) {
+    const unsigned long long *F = a.F[d % 3];
+    uint32_t *Q = a.q[d & 1], *P = a.qp[d & 1], *R = a.qr[d & 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t vb0 = (uint64_t)a.n * blockIdx.x / gridDim.x;
+    const uint64_t vb1 = (uint64_t)a.n * (blockIdx.x + 1) / gridDim.x;
+    for (uint64_t c = vb0; c < vb1; c += BLOCK) {
+        const uint64_t v = c + threadIdx.x;
+        bool on = v < vb1 && ldcg64(&F[v]) != 0ull;
+        uint32_t r0 = 0, deg = 0;
+        if (on) { r0 = __ldg(&a.rp_out[v]); deg = __ldg(&a.rp_out[v + 1]) - r0; }
+        uint32_t tc, td;
+        uint32_t ec = dev::warp_exclusive_sum<uint32_t>(on ? 1u : 0u, &tc);
+        uint32_t ed = dev::warp_exclusive_sum<uint32_t>(deg, &td);
+        if (lane == 0) { sm.stage.wcnt[warp] = tc; sm.stage.wdeg[warp] = td; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t cacc = 0, sacc = 0;
+            for (int w = 0; w < WARPS; ++w) {
+                uint32_t cw = sm.stage.wcnt[w], sw = sm.stage.wdeg[w];
+                sm.stage.wcnt[w] = cacc;
+                sm.stage.wdeg[w] = sacc;
+                cacc += cw;
+                sacc += sw;
+            }
+            unsigned long long base = 0;
+            if (cacc) base = atomicAdd(&a.st->cstate[d % 3], ((unsigned long long)cacc << a.ebits) | sacc);
+            sm.stage.base = base;
+        }
+        __syncthreads();
+        if (on) {
+            uint32_t pos = (uint32_t)(sm.stage.base >> a.ebits) + sm.stage.wcnt[warp] + ec;
+            Q[pos] = (uint32_t)v;
+            P[pos] = (uint32_t)(sm.stage.base & a.emask) + sm.stage.wdeg[warp] + ed;
+            R[pos] = r0;
+        }
+        __syncthreads();
+    }
+}
+
+// pull: lane per vertex, 2 vertices per lane in flight; long rows continue
+// warp-cooperatively; every vertex also merges its frontier bits here
+__device__ void ms_pull(const MsArgs &a, int d, uint32_t *cnt_out, uint32_t *deg_out) {
+    const unsigned long long *F = a.F[d % 3];
+    unsigned long long *Fn = a.F[(d + 1) % 3];
+    const uint32_t full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t nwarps = (uint64_t)gridDim.x * WARPS;
+    const uint64_t ngroups = (a.n + 63) / 64;
+    uint32_t mycnt = 0, mydeg = 0;
+    for (uint64_t g = (uint64_t)blockIdx.x * WARPS + warp; g < ngroups; g += nwarps) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const uint64_t v = g * 64 + j * 32 + lane;
+            const bool valid = v < a.n;
+            unsigned long long f = 0, vis = a.live;
+            uint32_t b = 0, e = 0;
+            if (valid) {
+                f = ldcg64(&F[v]);
+                unsigned long long old = ldcg64(&a.V[v]);
+                vis = old | f;
+                if (f) a.V[v] = vis;
+                b = __ldg(&a.rp_in[v]);
+                e = __ldg(&a.rp_in[v + 1]);
+            }
+            write_levels(a, v, valid, f, d);
+            unsigned long long acc = 0;
+            bool need = valid && vis != a.live;
+            uint32_t p = b;
+            if (need) {
+                uint32_t lim = e - b > 32 ? b + 32 : e;
+                for (; p < lim; ++p) {
+                    acc |= ldcg64(&F[__ldg(&a.ci_in[p])]);
+                    if ((acc | vis) == a.live) { p = e; break; }
+                }
+            }
+            uint32_t coop = __ballot_sync(full, need && p < e);
+            while (coop) {
+                int l = __ffs(coop) - 1;
+                coop &= coop - 1;
+                uint32_t pb = __shfl_sync(full, p, l), pe = __shfl_sync(full, e, l);
+                unsigned long long lv = __shfl_sync(full, vis, l);
+                unsigned long long la = __shfl_sync(full, acc, l);
+                for (uint32_t q0 = pb; q0 < pe; q0 += 32) {
+                    unsigned long long x = 0;
+                    if (q0 + lane < pe) x = ldcg64(&F[__ldg(&a.ci_in[q0 + lane])]);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) x |= __shfl_xor_sync(full, x, o);
+                    la |= x;
+                    if ((la | lv) == a.live) break;
+                }
+                if (lane == l) acc = la;
+            }
+            unsigned long long nb = acc & ~vis;
+            if (nb) {
+                Fn[v] = nb;
+                mycnt += 1;
+                mydeg += a.csr_is_csc ? e - b : __ldg(&a.rp_out[v + 1]) - __ldg(&a.rp_out[v]);
+            }
+        }
+    }
+    *cnt_out += mycnt;
+    *deg_out += mydeg;
+}
+
+__global__ void __launch_bounds__(BLOCK, 3) k_msbfs(MsArgs a) {
+    __shared__ Smem sm;
+    __shared__ uint32_t s_cnt, s_deg;
+    const uint32_t nthreads = gridDim.x * BLOCK;
+    const uint32_t tid = blockIdx.x * BLOCK + threadIdx.x;
+    BfsState *st = a.st;
+    BfsResult *res = &st->res;
+    for (uint64_t v = tid; v < a.n; v += nthreads) {
+        a.V[v] = 0ull;
+        a.F[0][v] = 0ull;
+        a.F[1][v] = 0ull;
+        a.F[2][v] = 0ull;
+    }
+    bool ok = dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns);
+    if (ok && tid == 0) {
+        memset(res, 0, sizeof(BfsResult));
+        uint32_t cnt = 0, deg = 0;
+        for (uint32_t q = 0; q < a.k; ++q) {
+            uint32_t v = a.srcs[q];
+            unsigned long long old = a.F[0][v];
+            a.F[0][v] = old | (1ull << q);
+            if (!old) {
+                uint32_t r0 = __ldg(&a.rp_out[v]);
+                a.q[0][cnt] = v;
+                a.qp[0][cnt] = deg;
+                a.qr[0][cnt] = r0;
+                deg += __ldg(&a.rp_out[v + 1]) - r0;
+                ++cnt;
+            }
+        }
+        st->qstate[0] = ((unsigned long long)cnt << a.ebits) | deg;
+    }
+    if (ok) ok = dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns);
+    const uint64_t t_start = dev::globaltimer_ns();
+    bool list_valid = true;
+    int d = 0;
+    for (; ok; ++d) {
+        if (threadIdx.x == 0)
+            sm.qs = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>(st->qstate[d % 3])
+                        .load(cuda::memory_order_relaxed);
+        __syncthreads();
+        const unsigned long long qs = sm.qs;
+        __syncthreads();
+        const uint32_t cnt = (uint32_t)(qs >> a.ebits);
+        const uint64_t fe = qs & a.emask;
+        if (cnt == 0) break;
+        if (d > (int)a.n || (threadIdx.x == 0 && dev::globaltimer_ns() - t_start > a.total_limit_ns))
+            atomicCAS(&st->err, 0, (int)GB_TIMEOUT);
+        const bool pull = a.rp_in && a.mode != GB_PUSH && (a.mode == GB_PULL || fe * (uint64_t)a.beta > a.m);
+        if (tid == 0) {
+            if (d < GBX_MAX_LEVEL_LOG) {
+                res->dir_log[d] = pull ? 2 : 1;
+                res->lv_cnt[d] = cnt;
+                res->lv_fe[d] = fe;
+                res->lv_ns[d] = dev::globaltimer_ns();
+            }
+            if (pull) res->pull_levels++; else res->push_levels++;
+            res->frontier_edges += fe;
+            res->reached += cnt;
+            st->qstate[(d + 2) % 3] = 0;
+            st->cstate[(d + 2) % 3] = 0;
+        }
+        unsigned long long *Fclr = a.F[(d + 2) % 3];
+        for (uint64_t v = tid; v < a.n; v += nthreads) Fclr[v] = 0ull;
+        if (pull) {
+            if (threadIdx.x == 0) { s_cnt = 0; s_deg = 0; }
+            __syncthreads();
+            uint32_t c = 0, dg = 0;
+            ms_pull(a, d, &c, &dg);
+            c = dev::warp_sum<uint32_t>(c);
+            dg = dev::warp_sum<uint32_t>(dg);
+            if ((threadIdx.x & 31) == 0 && c) { atomicAdd(&s_cnt, c); atomicAdd(&s_deg, dg); }
+            __syncthreads();
+            if (threadIdx.x == 0 && s_cnt)
+                atomicAdd(&st->qstate[(d + 1) % 3], ((unsigned long long)s_cnt << a.ebits) | s_deg);
+            list_valid = false;
+        } else {
+            if (!list_valid) {
+                ms_compact(a, sm, d);
+                if (!dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns)) { ok = false; break; }
+            }
+            // merge this level's frontier into the visited words and write its levels
+            {
+                const uint32_t *Q = a.q[d & 1];
+                const uint64_t nw = ((uint64_t)cnt + 31) / 32;
+                for (uint64_t wi = (uint64_t)blockIdx.x * WARPS + (threadIdx.x >> 5); wi < nw;
+                     wi += (uint64_t)gridDim.x * WARPS) {
+                    uint64_t x = wi * 32 + (threadIdx.x & 31);
+                    bool valid = x < cnt;
+                    uint32_t v = valid ? ldcg(&Q[x]) : 0u;
+                    unsigned long long f = valid ? ldcg64(&a.F[d % 3][v]) : 0ull;
+                    if (valid) atomicOr(&a.V[v], f);
+                    // levels[q][v]: per-vertex stores (list order is not vertex order)
+                    if (valid)
+                        for (unsigned long long u = f; u; u &= u - 1)
+                            a.levels[(uint64_t)(__ffsll((long long)u) - 1) * a.n + v] = d;
+                }
+            }
+            const unsigned long long *F = a.F[d % 3];
+            unsigned long long *Fn = a.F[(d + 1) % 3];
+            push_edges(a, sm, d, cnt, fe, [&](uint32_t u, uint32_t v, uint32_t, uint32_t *, uint32_t *deg) {
+                unsigned long long nb = ldcg64(&F[u]) & ~(ldcg64(&a.V[v]) | ldcg64(&F[v]));
+                if (!nb) return false;
+                if ((ldcg64(&Fn[v]) | nb) == ldcg64(&Fn[v])) return false;
+                unsigned long long old = atomicOr(&Fn[v], nb);
+                if (old) return false;
+                *deg = __ldg(&a.rp_out[v + 1]) - __ldg(&a.rp_out[v]);
+                return true;
+            });
+            list_valid = true;
+        }
+        ok = dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns);
+    }
+    // ---- (source, vertex) pairs never reached get -1
+    if (ok) {
+        const int lane = threadIdx.x & 31;
+        const uint64_t nwarps = (uint64_t)gridDim.x * WARPS;
+        for (uint64_t g = (uint64_t)blockIdx.x * WARPS + (threadIdx.x >> 5); g * 32 < a.n; g += nwarps) {
+            uint64_t v = g * 32 + lane;
+            bool valid = v < a.n;
+            unsigned long long unv = valid ? (a.live & ~ldcg64(&a.V[v])) : 0ull;
+            write_levels(a, v, valid, unv, -1);
+        }
+    }
+    if (tid == 0) {
+        res->depth = d;
+        if (d < GBX_MAX_LEVEL_LOG) res->lv_ns[d] = dev::globaltimer_ns();
+        res->t_begin = t_start;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned int old = atomicAdd(&st->bar.exits, 1u);
+        if (old == gridDim.x - 1) {
+            __threadfence();
+            res->err = ld_relaxed_gpu_int_(&st->err);
+            st->err = 0;
+            st->bar.count = 0;
+            for (int k2 = 0; k2 < 3; ++k2) { st->qstate[k2] = 0; st->exam[k2] = 0; st->cstate[k2] = 0; }
+            __threadfence();
+            st->bar.exits = 0;
+        }
+    }
+}
+
+}  // namespace msk
+
+struct MsWorkspace {
+    uint32_t n = 0;
+    unsigned long long *V = nullptr, *F = nullptr;
+    uint32_t *q = nullptr, *qp = nullptr, *qr = nullptr;
+    BfsState *st = nullptr;
+};
+static std::mutex g_ms_mu;
+static std::unordered_map<gb_context *, MsWorkspace> g_ms;
+
+static gb_info ms_workspace(gb_context *ctx, uint32_t n, MsWorkspace **out) {
+    std::lock_guard<std::mutex> g(g_ms_mu);
+    MsWorkspace &w = g_ms[ctx];
+    if (w.n < n || !w.st) {
+        dfree(ctx, w.V); dfree(ctx, w.F); dfree(ctx, w.q); dfree(ctx, w.qp); dfree(ctx, w.qr); dfree(ctx, w.st);
+        w = MsWorkspace();
+        GB_CHECK(dalloc_t(ctx, &w.V, (size_t)n + 1));
+        GB_CHECK(dalloc_t(ctx, &w.F, 3ull * n + 3));
+        GB_CHECK(dalloc_t(ctx, &w.q, 2ull * n + 2));
+        GB_CHECK(dalloc_t(ctx, &w.qp, 2ull * n + 2));
+        GB_CHECK(dalloc_t(ctx, &w.qr, 2ull * n + 2));
+        GB_CHECK(dalloc_t(ctx, &w.st, 1));
+        GB_CHECK(memset_async(ctx, w.st, 0, sizeof(BfsState)));
+        w.n = n;
+    }
+    *out = &w;
+    return GB_SUCCESS;
+}
+
+void ms_workspace_release(gb_context *ctx) {
+    std::lock_guard<std::mutex> g(g_ms_mu);
+    auto it = g_ms.find(ctx);
+    if (it == g_ms.end()) return;
+    MsWorkspace &w = it->second;
+    dfree(ctx, w.V); dfree(ctx, w.F); dfree(ctx, w.q); dfree(ctx, w.qp); dfree(ctx, w.qr); dfree(ctx, w.st);
+    g_ms.erase(it);
+}
+
+// Launches a multi-source BFS (sources on the device) into levels (device).
+gb_info msbfs_launch(gb_context *ctx, const gb_matrix *A, const uint32_t *d_srcs, uint32_t k, int32_t *levels,
+                     const gb_desc *desc, BfsResult *res_out) {
+    MsWorkspace *w = nullptr;
+    GB_CHECK(ms_workspace(ctx, A->nrows, &w));
+    msk::MsArgs a;
+    a.n = A->nrows;
+    a.nwords = (A->nrows + 31) / 32;
+    a.m = A->nvals;
+    a.k = k;
+    a.live = k >= 64 ? ~0ull : ((1ull << k) - 1);
+    a.srcs = d_srcs;
+    a.levels = levels;
+    a.rp_out = A->rowptr;
+    a.ci_out = A->colidx;
+    a.rp_in = A->has_csc ? A->colptr : nullptr;
+    a.ci_in = A->has_csc ? A->rowidx : nullptr;
+    a.csr_is_csc = A->csc_alias;
+    a.V = w->V;
+    for (int j = 0; j < 3; ++j) { a.F[j] = w->F + (size_t)j * A->nrows; a.front[j] = nullptr; }
+    a.q[0] = w->q; a.q[1] = w->q + A->nrows + 1;
+    a.qp[0] = w->qp; a.qp[1] = w->qp + A->nrows + 1;
+    a.qr[0] = w->qr; a.qr[1] = w->qr + A->nrows + 1;
+    a.ebits = 64 - bits_for((uint64_t)A->nrows + 1);
+    a.emask = (1ull << a.ebits) - 1;
+    a.mode = desc ? desc->direction : GB_AUTO;
+    a.beta = (desc && desc->beta > 0) ? (uint32_t)desc->beta : 10u;
+    a.st = w->st;
+    a.timeout_ns = 4000000000ull;
+    a.total_limit_ns = 120000000000ull;
+    int occ = 0;
+    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, msk::k_msbfs, msk::BLOCK, 0));
+    if (occ < 1) return fail(GB_PANIC, "multi-source BFS kernel cannot be resident");
+    void *args[] = {&a};
+    int span = prof_begin(ctx, "bfs_multi");
+    int grid = occ * ctx->num_sms;
+    if (ctx->grid_limit > 0 && ctx->grid_limit < grid) grid = ctx->grid_limit;
+    GB_CUDA(cudaLaunchCooperativeKernel((const void *)msk::k_msbfs, dim3(grid), dim3(msk::BLOCK), args, 0,
+                                        ctx->stream));
+    prof_end(ctx, span);
+    if (res_out) GB_CUDA(cudaMemcpyAsync(res_out, &w->st->res, sizeof(BfsResult), cudaMemcpyDeviceToHost, ctx->stream));
+    return GB_SUCCESS;
+}
+
+}  // namespace gbx
+
+extern "C" gb_info gb_bfs_multi(gb_context *ctx, const gb_matrix *A, const uint32_t *srcs, uint32_t k, int32_t *levels,
+                                gb_mem mem, const gb_desc *desc, gb_bfs_stats *stats) {
+    if (!ctx || !A || !srcs || !levels) return fail(GB_NULL_POINTER, "gb_bfs_multi: NULL argument");
+    if (!A->built) return fail(GB_INVALID_VALUE, "gb_bfs_multi: matrix not built");
+    if (A->nrows != A->ncols) return fail(GB_DIMENSION_MISMATCH, "gb_bfs_multi: matrix must be square");
+    if (k == 0 || k > 64) return fail(GB_INVALID_VALUE, "gb_bfs_multi: k must be in 1..64");
+    for (uint32_t q = 0; q < k; ++q)
+        if (srcs[q] >= A->nrows) return fail(GB_INVALID_INDEX, "gb_bfs_multi: source %u out of range", srcs[q]);
+    GB_CUDA(cudaSetDevice(ctx->device));
+    Scratch ds(ctx), dl(ctx);
+    GB_CHECK(ds.alloc(64 * 4));
+    GB_CHECK(copy_in(ctx, ds.p, srcs, (size_t)k * 4, GB_HOST));
+    int32_t *out = levels;
+    size_t bytes = (size_t)k * A->nrows * 4;
+    if (mem == GB_HOST) { GB_CHECK(dl.alloc(bytes + 16)); out = dl.as<int32_t>(); }
+    BfsResult hs;
+    GB_CHECK(msbfs_launch(ctx, A, ds.as<uint32_t>(), k, out, desc, &hs));
+    if (mem == GB_HOST) GB_CUDA(cudaMemcpyAsync(levels, out, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    GB_CHECK(sync(ctx));
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->depth = hs.depth;
+        stats->push_levels = hs.push_levels;
+        stats->pull_levels = hs.pull_levels;
+        stats->status = (uint32_t)hs.err;
+        stats->vertices_reached = hs.reached;
+        stats->frontier_edges = hs.frontier_edges;
+    }
+    if (hs.err) return fail(GB_TIMEOUT, "gb_bfs_multi: a bounded grid barrier wait ran out");
+    return GB_SUCCESS;
+}

@@ -291,8 +291,10 @@ static gb_info relax_run(gb_context *ctx, const gb_matrix *A, bool weighted, uin
     if (occ < 1) return fail(GB_PANIC, "%s: kernel cannot be resident", who);
     void *args[] = {&a};
     int span = prof_begin(ctx, weighted ? "sssp" : "cc");
-    GB_CUDA(cudaLaunchCooperativeKernel((const void *)rlx::k_relax, dim3(occ * ctx->num_sms), dim3(rlx::BLOCK), args,
-                                        0, ctx->stream));
+    int grid = occ * ctx->num_sms;
+    if (ctx->grid_limit > 0 && ctx->grid_limit < grid) grid = ctx->grid_limit;
+    GB_CUDA(cudaLaunchCooperativeKernel((const void *)rlx::k_relax, dim3(grid), dim3(rlx::BLOCK), args, 0,
+                                        ctx->stream));
     prof_end(ctx, span);
     BfsResult hs;
     GB_CUDA(cudaMemcpyAsync(&hs, &st->res, sizeof(BfsResult), cudaMemcpyDeviceToHost, ctx->stream));

@@ -223,3 +223,35 @@ def test_tc_rmat_s20_full_size(ctx):
     assert gb.tc(ctx, L) == int(f["triangles"])
     for x in (A, B, L):
         x.free()
+
+
+# ------------------------------------------------------- multi-source BFS
+@pytest.mark.parametrize("case,k", [("rmat14", 64), ("rmat14", 1), ("rmat13", 37), ("grid", 64), ("small", 5)])
+def test_bfs_multi_matches_independent_bfs(ctx, case, k):
+    t = {"rmat14": lambda: gen.rmat(14, 16, seed=1),
+         "rmat13": lambda: gen.rmat(13, 8, seed=8),
+         "grid": lambda: gen.grid(60, 50, 0.1, seed=3),
+         "small": lambda: gen.from_edges(9, [(0, 1), (1, 2), (3, 4)])}[case]()
+    g = oracle.csr_from_tuples(t)
+    A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, flags=gb.SYMMETRIC)
+    rng = np.random.default_rng(k)
+    srcs = rng.integers(0, t.n, k).astype(np.uint32)      # any vertices, isolated and repeated ones included
+    want = oracle.multi_bfs(g, srcs)
+    for direction in (gb.AUTO, gb.PUSH, gb.PULL):
+        lv = np.empty((k, t.n), np.int32)
+        _, st = gb.bfs_multi(ctx, A, srcs, lv, gb.Descriptor(direction=direction))
+        assert np.array_equal(lv, want), direction
+        assert st["status"] == 0
+    A.free()
+
+
+def test_bfs_multi_errors(ctx):
+    t = gen.rmat(8, 4, seed=1)
+    A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, flags=gb.SYMMETRIC)
+    with pytest.raises(gb.GBError) as e:
+        gb.bfs_multi(ctx, A, np.zeros(65, np.uint32), np.empty((65, t.n), np.int32))
+    assert e.value.code == gb.INVALID_VALUE
+    with pytest.raises(gb.GBError) as e:
+        gb.bfs_multi(ctx, A, np.array([t.n], np.uint32), np.empty((1, t.n), np.int32))
+    assert e.value.code == gb.INVALID_INDEX
+    A.free()
