@@ -177,6 +177,12 @@ def run_gbx(args):
     desc = gb.Descriptor(beta=args.beta) if args.beta else None
     levels = torch.empty(n, dtype=torch.int32, device=dev)
     parents = torch.empty(n, dtype=torch.int32, device=dev)
+    # the push/pull threshold is picked by the autotuner on sources other
+    # than the benchmark's (seed 99), unless --beta fixes it
+    tuned_beta = None
+    if not args.beta:
+        import gen
+        tuned_beta, _ = gb.bfs_autotune(ctx, A, gen.sources(t, 8, seed=99))
 
     # untimed pass with statistics: algorithmic bytes and levels per source
     alg, depth, pushes, pulls = [], [], [], []
@@ -247,7 +253,7 @@ def run_gbx(args):
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "m_stored": m, "sources": NSRC, "l2": "inputs_larger_than_l2",
                    "parallelism": f"replicas{ws}" if ws > 1 else "single",
-                   "beta": args.beta or 10},
+                   "beta": args.beta or tuned_beta, "beta_from": "fixed" if args.beta else "autotuner"},
         "gpu_launches": int(args.steps * NSRC),
         "roofline": {"bound": "hbm", "kernel": "k_bfs", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
@@ -441,23 +447,44 @@ def serving_bench(args):
             "serial": serial, "speedup_qps": st["qps"] / serial["qps"]}
 
 
-def run_profile_bfs(args):
-    """A short fixed run for profilers: build the s22 graph, then a few
-    BFS launches from the first sources (no timing, no CPU baseline)."""
+def run_profile(args):
+    """A short fixed run for profilers: build the workload of one kernel and
+    launch it a few times (no timing, no CPU baseline). kinds: bfs (R-MAT
+    s22, the benchmark sources), pr (PageRank on s22, a few iterations),
+    sssp (s22, weights in [1, 255]), msbfs (s22, 64 sources), tc (s20)."""
     import torch
+    import gen
     import paper_1908_01407_gb300 as gb
-    t, srcs = make_inputs()
+    kind = args.profile
     ctx = gb.Context(0)
-    A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, flags=gb.SYMMETRIC)
-    desc = gb.Descriptor(beta=args.beta) if args.beta else None
-    lv = torch.empty(t.n, dtype=torch.int32, device="cuda")
-    pa = torch.empty(t.n, dtype=torch.int32, device="cuda")
-    for s in srcs[:args.profile_launches]:
-        gb.bfs(ctx, A, int(s), lv, pa, desc=desc, stats=True)
+    k = args.profile_launches
+    if kind == "tc":
+        t = gen.rmat(20, 16, seed=4)
+        A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, flags=gb.SYMMETRIC)
+        B, _ = A.degree_order()
+        L = B.tril()
+        for _ in range(k):
+            gb.tc(ctx, L)
+    else:
+        t = gen.rmat(SCALE, EF, seed=SEED, wmax=255 if kind == "sssp" else 0)
+        srcs = gen.sources(t, NSRC, seed=SRC_SEED)
+        A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, t.w if kind == "sssp" else None, type_=gb.UINT32,
+                                  flags=gb.SYMMETRIC)
+        out = torch.empty(t.n * (NSRC if kind == "msbfs" else 1), dtype=torch.int32, device="cuda")
+        out2 = torch.empty(t.n, dtype=torch.int32, device="cuda")
+        desc = gb.Descriptor(beta=args.beta) if args.beta else None
+        for i in range(k):
+            if kind == "bfs":
+                gb.bfs(ctx, A, int(srcs[i]), out, out2, desc=desc, stats=True)
+            elif kind == "sssp":
+                gb.sssp(ctx, A, int(srcs[i]), out)
+            elif kind == "msbfs":
+                gb.bfs_multi(ctx, A, srcs, out.view(NSRC, t.n), stats=False)
+            elif kind == "pr":
+                gb.pagerank(ctx, A, 0.85, 2, out.view(torch.float32), residuals=False)
     torch.cuda.synchronize()
-    A.free()
     ctx.close()
-    print("profile run done")
+    print(f"profile run done: {kind} x{k}")
 
 
 def main():
@@ -477,11 +504,12 @@ def main():
     ap.add_argument("--serve-load", type=float, default=2.0, help="offered load as a multiple of serial capacity")
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-window-us", type=int, default=300)
-    ap.add_argument("--profile-bfs", action="store_true", help="short fixed BFS run for ncu")
+    ap.add_argument("--profile", choices=["bfs", "pr", "sssp", "msbfs", "tc"], default=None,
+                    help="short fixed run of one kernel for ncu")
     ap.add_argument("--profile-launches", type=int, default=3)
     args = ap.parse_args()
-    if args.profile_bfs:
-        run_profile_bfs(args)
+    if args.profile:
+        run_profile(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -289,6 +289,15 @@ typedef struct {
  * entries in `mem`. stats may be NULL. desc: GB_DIRECTION, GB_SWITCH_BETA. */
 gb_info gb_bfs(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *levels, int32_t *parents,
                gb_mem mem, const gb_desc *desc, gb_bfs_stats *stats);
+/* Autotuner of the push/pull switch threshold (Table 8: pull iff
+ * |E_f| > |E| / beta; Section 5.4 suggests Table 8 as a starting point for
+ * finding the best threshold on given hardware). Runs gb_bfs from the k
+ * given sources (host array) for each beta in {4, 6, ..., 128}, timed with
+ * CUDA events, and stores the fastest beta on the matrix: later gb_bfs calls
+ * whose descriptor leaves GB_SWITCH_BETA at 0 use it (untuned matrices use
+ * the paper's beta = 10). *best_ms (may be NULL) = mean ms per BFS at it. */
+gb_info gb_bfs_autotune(gb_context *ctx, gb_matrix *A, const uint32_t *srcs, uint32_t k, uint32_t *best_beta,
+                        double *best_ms);
 /* BFS that allocates no device memory (the paper has no counterpart; it is
  * an extra for callers that cannot allocate on the call path: a process
  * whose device memory belongs to another allocator such as a framework's

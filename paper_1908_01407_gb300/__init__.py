@@ -124,7 +124,8 @@ _SIGS = {
     "gb_reduce_vector": [_P, _I, _I, _P], "gb_reduce_matrix": [_P, _I, _I, _P],
     "gb_reduce_rows": [_P, _P, _I, _I, _P, _P],
     "gb_bfs": [_P, _P, _U32, _P, _P, _I, _P, _P],
-    "gb_bfs_noalloc": [_P, _P, _P, _P, _U32, _U64, _U32, _P, _P, _P], "gb_bfs_multi": [_P, _P, _P, _U32, _P, _I, _P, _P],
+    "gb_bfs_noalloc": [_P, _P, _P, _P, _U32, _U64, _U32, _P, _P, _P],
+    "gb_bfs_autotune": [_P, _P, _P, _U32, _P, _P], "gb_bfs_multi": [_P, _P, _P, _U32, _P, _I, _P, _P],
     "gb_sssp": [_P, _P, _U32, _P, _I, _P, _P], "gb_pagerank": [_P, _P, ctypes.c_float, _U32, _P, _P, _I],
     "gb_cc": [_P, _P, _P, _I, _P], "gb_tc": [_P, _P, _P, _P],
     "gb_server_create": [_PP, _P, _P], "gb_server_add_graph": [_P, _P, _P], "gb_server_submit": [_P, _P, _P],
@@ -536,6 +537,17 @@ def bfs(ctx, A, src, levels=None, parents=None, desc=None, stats=True):
     st = BfsStats()
     check(lib().gb_bfs(ctx.h, A.h, src, pl, pp, ml, _h(desc), ctypes.byref(st) if stats else None))
     return levels, parents, (st.as_dict() if stats else None)
+
+
+def bfs_autotune(ctx, A, srcs):
+    """Pick the push/pull switch beta for A from timed BFS runs; returns
+    (beta, mean ms per BFS at that beta). The choice is kept on A."""
+    srcs = np.ascontiguousarray(srcs, dtype=np.uint32)
+    b = ctypes.c_uint32()
+    ms = ctypes.c_double()
+    check(lib().gb_bfs_autotune(ctx.h, A.h, srcs.ctypes.data, int(srcs.shape[0]), ctypes.byref(b),
+                                ctypes.byref(ms)))
+    return b.value, ms.value
 
 
 NOALLOC_MAX_VERTICES = 262144

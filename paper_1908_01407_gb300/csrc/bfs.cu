@@ -434,7 +434,7 @@ gb_info bfs_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *l
     a.ebits = 64 - bits_for((uint64_t)A->nrows + 1);
     a.emask = (a.ebits >= 64) ? ~0ull : ((1ull << a.ebits) - 1);
     a.mode = desc ? desc->direction : GB_AUTO;
-    a.beta = (desc && desc->beta > 0) ? (uint32_t)desc->beta : 10u;
+    a.beta = (desc && desc->beta > 0) ? (uint32_t)desc->beta : (A->tuned_beta ? A->tuned_beta : 10u);
     a.st = w->st;
     a.timeout_ns = 4000000000ull;
     a.total_limit_ns = 120000000000ull;
@@ -608,5 +608,54 @@ extern "C" gb_info gb_bfs_noalloc(const uint32_t *rowptr, const uint32_t *colidx
     GB_CUDA(cudaMemsetAsync(a.st, 0, sizeof(BfsState), s));
     void *args[] = {&a};
     GB_CUDA(cudaLaunchCooperativeKernel((const void *)bfsk::k_bfs, dim3(D->grid), dim3(bfsk::BLOCK), args, 0, s));
+    return GB_SUCCESS;
+}
+
+// Autotuner of the push/pull switch (Table 8's rule pull iff |E_f| > |E|/beta):
+// times BFS from the given sources for each candidate beta with CUDA
+// events on the context stream and keeps the fastest on the matrix.
+extern "C" gb_info gb_bfs_autotune(gb_context *ctx, gb_matrix *A, const uint32_t *srcs, uint32_t k,
+                                   uint32_t *best_beta, double *best_ms) {
+    if (!ctx || !A || !srcs || !best_beta) return fail(GB_NULL_POINTER, "gb_bfs_autotune: NULL argument");
+    if (!A->built || A->nrows != A->ncols) return fail(GB_INVALID_VALUE, "gb_bfs_autotune: needs a built square matrix");
+    if (k == 0) return fail(GB_INVALID_VALUE, "gb_bfs_autotune: no sources");
+    for (uint32_t q = 0; q < k; ++q)
+        if (srcs[q] >= A->nrows) return fail(GB_INVALID_INDEX, "gb_bfs_autotune: source out of range");
+    GB_CUDA(cudaSetDevice(ctx->device));
+    BfsWorkspace *w = nullptr;
+    GB_CHECK(bfs_workspace(ctx, A->nrows, &w));
+    Scratch lv(ctx), pa(ctx);
+    GB_CHECK(lv.alloc((size_t)A->nrows * 4 + 16));
+    GB_CHECK(pa.alloc((size_t)A->nrows * 4 + 16));
+    static const uint32_t cand[] = {4, 6, 8, 10, 12, 16, 20, 24, 32, 48, 64, 96, 128};
+    cudaEvent_t e0, e1;
+    GB_CUDA(cudaEventCreate(&e0));
+    GB_CUDA(cudaEventCreate(&e1));
+    gb_desc d;
+    double best = 1e30;
+    uint32_t bb = 10;
+    for (uint32_t c : cand) {
+        d.beta = (int)c;
+        // one warm launch, then the timed set
+        gb_info r = bfs_launch(ctx, A, srcs[0], lv.as<int32_t>(), pa.as<int32_t>(), &d, w, 0);
+        if (r == GB_SUCCESS) r = cudaEventRecord(e0, ctx->stream) == cudaSuccess ? GB_SUCCESS : GB_PANIC;
+        for (uint32_t q = 0; q < k && r == GB_SUCCESS; ++q)
+            r = bfs_launch(ctx, A, srcs[q], lv.as<int32_t>(), pa.as<int32_t>(), &d, w, 0);
+        if (r == GB_SUCCESS && cudaEventRecord(e1, ctx->stream) != cudaSuccess) r = GB_PANIC;
+        if (r == GB_SUCCESS && cudaEventSynchronize(e1) != cudaSuccess) r = GB_PANIC;
+        if (r != GB_SUCCESS) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return r == GB_PANIC ? fail(GB_PANIC, "gb_bfs_autotune: CUDA error") : r;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; bb = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    A->tuned_beta = bb;
+    *best_beta = bb;
+    if (best_ms) *best_ms = best / k;
     return GB_SUCCESS;
 }

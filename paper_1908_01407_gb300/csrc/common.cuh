@@ -76,6 +76,14 @@ struct gb_matrix_t {
     uint32_t *colptr = nullptr;   // [ncols + 1]
     uint32_t *rowidx = nullptr;   // [nvals]
     void *cvals = nullptr;        // [nvals]
+    // columns (CSC rows) longer than a threshold and their length prefixes,
+    // built on first use by the pull kernels (cached; freed with the matrix)
+    uint32_t *hub_list = nullptr, *hub_pre = nullptr;
+    uint32_t nhub = 0;
+    uint64_t hub_edges = 0;
+    bool hub_ready = false;
+    // push/pull switch threshold chosen by gb_bfs_autotune (0 = not tuned)
+    uint32_t tuned_beta = 0;
 };
 
 struct gb_vector_t {

@@ -56,6 +56,9 @@ void release(gb_matrix *A) {
     if (A->csc_alias) { A->colptr = nullptr; A->rowidx = nullptr; A->cvals = nullptr; }
     dfree(ctx, A->rowptr); dfree(ctx, A->colidx); dfree(ctx, A->vals);
     dfree(ctx, A->colptr); dfree(ctx, A->rowidx); dfree(ctx, A->cvals);
+    dfree(ctx, A->hub_list); dfree(ctx, A->hub_pre);
+    A->hub_list = A->hub_pre = nullptr;
+    A->nhub = 0; A->hub_edges = 0; A->hub_ready = false;
     A->rowptr = A->colidx = A->colptr = A->rowidx = nullptr;
     A->vals = A->cvals = nullptr;
     A->built = false; A->has_csc = false; A->csc_alias = false; A->nvals = 0;
@@ -99,6 +102,59 @@ gb_info matrix_build_device(gb_matrix *A, const uint32_t *rows, const uint32_t *
         A->cvals = cv;
         A->has_csc = true;
     }
+    return GB_SUCCESS;
+}
+
+namespace {
+__global__ void k_hub_flags(const uint32_t *ptr, uint32_t n, uint32_t min_len, uint32_t *flag, uint32_t *len) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        uint32_t l = ptr[i + 1] - ptr[i];
+        flag[i] = l > min_len ? 1u : 0u;
+        len[i] = l > min_len ? l : 0u;
+    }
+}
+__global__ void k_hub_emit(const uint32_t *flag, const uint32_t *pos, const uint32_t *lpre, uint32_t n, uint32_t *list,
+                           uint32_t *pre) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && flag[i]) {
+        list[pos[i]] = i;
+        pre[pos[i]] = lpre[i];
+    }
+}
+}  // namespace
+
+// Columns of A (rows of its CSC copy) with more than min_len entries, and
+// the exclusive prefix of their lengths; computed once and cached.
+gb_info matrix_hubs(const gb_matrix *Ac, uint32_t min_len) {
+    gb_matrix *A = const_cast<gb_matrix *>(Ac);
+    if (A->hub_ready) return GB_SUCCESS;
+    gb_context *ctx = A->ctx;
+    const uint32_t *ptr = A->has_csc ? A->colptr : A->rowptr;
+    uint32_t n = A->has_csc ? A->ncols : A->nrows;
+    Scratch flag(ctx), len(ctx), pos(ctx), lpre(ctx), cnt(ctx), tot(ctx);
+    GB_CHECK(flag.alloc(((size_t)n + 1) * 4));
+    GB_CHECK(len.alloc(((size_t)n + 1) * 4));
+    GB_CHECK(pos.alloc(((size_t)n + 1) * 4));
+    GB_CHECK(lpre.alloc(((size_t)n + 1) * 4));
+    GB_CHECK(cnt.alloc(4));
+    GB_CHECK(tot.alloc(4));
+    if (n) k_hub_flags<<<nblk(n), 256, 0, ctx->stream>>>(ptr, n, min_len, flag.as<uint32_t>(), len.as<uint32_t>());
+    GB_CHECK(scan_exclusive_u32(ctx, flag.as<uint32_t>(), pos.as<uint32_t>(), n, cnt.as<uint32_t>()));
+    GB_CHECK(scan_exclusive_u32(ctx, len.as<uint32_t>(), lpre.as<uint32_t>(), n, tot.as<uint32_t>()));
+    uint32_t h[2] = {0, 0};
+    GB_CUDA(cudaMemcpyAsync(&h[0], cnt.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    GB_CUDA(cudaMemcpyAsync(&h[1], tot.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    GB_CHECK(sync(ctx));
+    GB_CHECK(dalloc_t(ctx, &A->hub_list, (size_t)h[0] + 1));
+    GB_CHECK(dalloc_t(ctx, &A->hub_pre, (size_t)h[0] + 1));
+    if (n) k_hub_emit<<<nblk(n), 256, 0, ctx->stream>>>(flag.as<uint32_t>(), pos.as<uint32_t>(), lpre.as<uint32_t>(), n,
+                                                        A->hub_list, A->hub_pre);
+    GB_LAUNCH_CHECK();
+    GB_CHECK(sync(ctx));
+    A->nhub = h[0];
+    A->hub_edges = h[1];
+    A->hub_ready = true;
     return GB_SUCCESS;
 }
 

@@ -18,8 +18,11 @@ namespace gbx {
 namespace {
 
 constexpr int PR_BLOCK = 256;
-constexpr int PR_IPT = 7;
+constexpr int PR_IPT = 8;
+constexpr int PR_LOAD_BATCH = 8;
 constexpr int PR_TILE = PR_BLOCK * PR_IPT;
+constexpr int PR_RS_BYTES = ((PR_TILE + 2) * 4 + 15) / 16 * 16;
+constexpr int PR_SMEM_BYTES = PR_RS_BYTES + PR_IPT * PR_BLOCK * 4 + PR_TILE * 4;
 
 struct PrRec {
     uint32_t first_row;   // row finished by the block's first row end, if it began earlier
@@ -34,6 +37,7 @@ struct PrArgs {
     uint64_t nnz;
     const uint32_t *rp, *ci;      // rows = in-edges of each vertex
     const uint32_t *rp_out;       // out-degrees
+    bool rows_are_out;            // rp is also the out-edge structure (symmetric matrix)
     const float *x;               // p(j)/deg(j), 0 for deg(j) = 0
     const float *p_old;
     float *p_new, *x_new;
@@ -89,19 +93,29 @@ __device__ __forceinline__ Seg seg_op(Seg a, Seg b) {
     return r;
 }
 
-__device__ __forceinline__ void epilogue(const PrArgs &a, uint32_t i, float y, float base, double &res, double &dang) {
+// row i is complete with sum y: write p'(i), x'(i) = p'(i)/deg(i), and add
+// to the residual and dangling partials. rowlen is row i's length in the
+// pulled structure; it is the out-degree when that structure is the CSR
+// itself (symmetric matrix), otherwise the out-degree is read from rp_out.
+__device__ __forceinline__ void epilogue(const PrArgs &a, uint32_t i, float y, float base, float p_old, uint32_t rowlen,
+                                         double &res, double &dang) {
     float p = base + a.alpha * y;
-    uint32_t deg = __ldg(&a.rp_out[i + 1]) - __ldg(&a.rp_out[i]);
+    uint32_t deg = a.rows_are_out ? rowlen : __ldg(&a.rp_out[i + 1]) - __ldg(&a.rp_out[i]);
     a.p_new[i] = p;
     a.x_new[i] = deg ? p / (float)deg : 0.f;
-    res += fabs((double)p - (double)a.p_old[i]);
+    res += fabs((double)p - (double)p_old);
     if (!deg) dang += (double)p;
 }
 
 __global__ void __launch_bounds__(PR_BLOCK) k_pr_spmv(PrArgs a) {
-    __shared__ uint32_t s_re[PR_TILE + 2];
+    // dynamic shared memory: s_rs[0] = start of the chunk's first row,
+    // s_rs[r + 1] = end of its row r; gathered x values and previous ranks
+    extern __shared__ __align__(16) unsigned char pr_smem[];
+    uint32_t *s_rs = reinterpret_cast<uint32_t *>(pr_smem);
+    float (*s_xv)[PR_BLOCK] = reinterpret_cast<float (*)[PR_BLOCK]>(pr_smem + PR_RS_BYTES);
+    float *s_sum = reinterpret_cast<float *>(pr_smem + PR_RS_BYTES + PR_IPT * PR_BLOCK * 4);   // finished rows
     __shared__ Seg s_scan[PR_BLOCK / 32];
-    __shared__ uint32_t s_hdr[4];
+    __shared__ uint32_t s_x[PR_BLOCK + 1];
     __shared__ double s_red[2][PR_BLOCK / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t total = (uint64_t)a.n + a.nnz;
@@ -117,31 +131,55 @@ __global__ void __launch_bounds__(PR_BLOCK) k_pr_spmv(PrArgs a) {
     Seg carry = {0, 0.f};
     for (uint64_t c = D0; c < D1; c += PR_TILE) {
         const uint64_t ce = c + PR_TILE < D1 ? c + PR_TILE : D1;
-        const uint32_t ie = block_merge_search(a.rp, a.n, a.nnz, ce);
-        const uint32_t nrows = ie - ic;                 // row ends inside the chunk
-        const uint32_t nk = (uint32_t)((ce - ie) - kc); // nonzeros inside the chunk
-        for (uint32_t r = threadIdx.x; r < nrows; r += PR_BLOCK) s_re[r] = __ldg(&a.rp[ic + r + 1]);
-        __syncthreads();
-        // this thread's items [d0, d1) relative to the chunk
         const uint32_t clen = (uint32_t)(ce - c);
+        // stage the row bounds of every row the chunk can reach (one coalesced load)
+        const uint32_t avail = a.n - ic;
+        const uint32_t R = avail < clen + 1 ? avail : clen + 1;
+        for (uint32_t r = threadIdx.x; r <= R; r += PR_BLOCK) s_rs[r] = __ldg(&a.rp[ic + r]);
+        __syncthreads();
+        const uint32_t *s_re = s_rs + 1;
+        const uint64_t nk_left = a.nnz - kc;
+        const uint32_t bl = nk_left < clen ? (uint32_t)nk_left : clen;
+        // one merge-path search per thread for the start of its items; the
+        // last thread also finds the chunk end; neighbours exchange them
         uint32_t d0 = threadIdx.x * PR_IPT < clen ? threadIdx.x * PR_IPT : clen;
+        const uint32_t x0 = merge_search_smem(s_re, R, (uint32_t)kc, bl, d0);
+        s_x[threadIdx.x] = x0;
+        if (threadIdx.x == PR_BLOCK - 1) s_x[PR_BLOCK] = merge_search_smem(s_re, R, (uint32_t)kc, bl, clen);
+        __syncthreads();
+        const uint32_t nrows = s_x[PR_BLOCK];                  // row ends inside the chunk
+        const uint32_t nk = clen - nrows;
+        const uint32_t ie = ic + nrows;
         uint32_t d1 = d0 + PR_IPT < clen ? d0 + PR_IPT : clen;
-        uint32_t x0 = merge_search_smem(s_re, nrows, (uint32_t)kc, nk, d0);
-        uint32_t ti = x0;                          // relative row
-        uint32_t tk = (uint32_t)kc + (d0 - x0);    // absolute nonzero index
+        const uint32_t x1 = s_x[threadIdx.x + 1];
+        const uint32_t tk0 = (uint32_t)kc + (d0 - x0), tk1 = (uint32_t)kc + (d1 - x1);
+        // all loads of the thread at once: column indices, then the gathers,
+        // and the previous ranks of the rows it finishes
+#pragma unroll
+        for (int j0 = 0; j0 < PR_IPT; j0 += PR_LOAD_BATCH) {
+            float xv[PR_LOAD_BATCH];
+            uint32_t cidx[PR_LOAD_BATCH];
+#pragma unroll
+            for (int j = 0; j < PR_LOAD_BATCH; ++j) cidx[j] = tk0 + j0 + j < tk1 ? __ldg(&a.ci[tk0 + j0 + j]) : 0u;
+#pragma unroll
+            for (int j = 0; j < PR_LOAD_BATCH; ++j) xv[j] = tk0 + j0 + j < tk1 ? __ldg(&a.x[cidx[j]]) : 0.f;
+#pragma unroll
+            for (int j = 0; j < PR_LOAD_BATCH; ++j) s_xv[j0 + j][threadIdx.x] = xv[j];
+        }
+        // walk the items: a row end stores the row's sum (the first one
+        // also needs the partial sums of earlier threads, added after the scan)
+        uint32_t ti = x0, tk = tk0, jn = 0;
         float sum = 0.f;
         bool head = false;
-        uint32_t head_row = 0;
         float head_val = 0.f;
         for (uint32_t d = d0; d < d1; ++d) {
             if (ti < nrows && tk >= s_re[ti]) {
-                // row end of ic + ti
-                if (!head) { head = true; head_row = ic + ti; head_val = sum; }
-                else epilogue(a, ic + ti, sum, base, res, dang);
+                if (!head) { head = true; head_val = sum; }
+                else s_sum[ti] = sum;
                 sum = 0.f;
                 ++ti;
             } else {
-                sum += __ldg(&a.x[__ldg(&a.ci[tk])]);
+                sum += s_xv[jn++][threadIdx.x];
                 ++tk;
             }
         }
@@ -158,33 +196,38 @@ __global__ void __launch_bounds__(PR_BLOCK) k_pr_spmv(PrArgs a) {
         if (lane == 31) s_scan[warp] = incl;
         __syncthreads();
         Seg wpre = carry;                       // chunk carry-in, then earlier warps
-        for (int w = 0; w < warp; ++w) wpre = seg_op(wpre, s_scan[w]);
+        Seg tot_all = carry;
+        bool any_head = false;
+#pragma unroll
+        for (int w = 0; w < PR_BLOCK / 32; ++w) {
+            Seg sw = s_scan[w];
+            if (w < warp) wpre = seg_op(wpre, sw);
+            tot_all = seg_op(tot_all, sw);
+            any_head |= sw.reset != 0;
+        }
         Seg excl_lane;
         excl_lane.reset = __shfl_up_sync(0xffffffffu, incl.reset, 1);
         excl_lane.v = __shfl_up_sync(0xffffffffu, incl.v, 1);
         Seg into = lane == 0 ? wpre : seg_op(wpre, excl_lane);
-        if (head) {
-            float tot = into.v + head_val;
-            if (pending && head_row == i0) {
-                a.rec[blockIdx.x].first_row = head_row;
-                a.rec[blockIdx.x].first_val = tot;
+        if (head) s_sum[x0] = into.v + head_val;
+        __syncthreads();
+        // epilogue over the chunk's finished rows [ic, ie): coalesced, one row per thread
+        const bool first_pending = pending && nrows > 0;   // row ic began before this block
+        for (uint32_t r = threadIdx.x; r < nrows; r += PR_BLOCK) {
+            float y = s_sum[r];
+            if (r == 0 && first_pending) {
+                a.rec[blockIdx.x].first_row = ic;
+                a.rec[blockIdx.x].first_val = y;
             } else {
-                epilogue(a, head_row, tot, base, res, dang);
+                epilogue(a, ic + r, y, base, __ldg(&a.p_old[ic + r]), s_rs[r + 1] - s_rs[r], res, dang);
             }
         }
-        int any_head = __syncthreads_or(head ? 1 : 0);
-        if (threadIdx.x == PR_BLOCK - 1) {
-            Seg out = seg_op(into, me);
-            s_hdr[0] = (uint32_t)out.reset;
-            reinterpret_cast<float *>(s_hdr)[1] = out.v;
-        }
-        __syncthreads();
         carry.reset = 0;
-        carry.v = reinterpret_cast<float *>(s_hdr)[1];
+        carry.v = tot_all.v;
         if (any_head) { pending = false; has_end = true; }
         ic = ie;
-        kc = ce - ie;
-        __syncthreads();
+        kc = kc + nk;
+        __syncthreads();   // the staged arrays and s_scan are rewritten by the next chunk
     }
     // block records
     if (threadIdx.x == 0) {
@@ -233,7 +276,7 @@ __global__ void __launch_bounds__(PR_BLOCK) k_pr_fix(PrArgs a, double *residual_
                     tot += q.first_val;
                     break;
                 }
-                epilogue(a, row, tot, base, r, dn);
+                epilogue(a, row, tot, base, a.p_old[row], __ldg(&a.rp[row + 1]) - __ldg(&a.rp[row]), r, dn);
             }
             fix_res[b] = r;
             fix_dang[b] = dn;
@@ -325,7 +368,8 @@ extern "C" gb_info gb_pagerank(gb_context *ctx, const gb_matrix *A, float dampin
     if (n == 0) return GB_SUCCESS;
     GB_CUDA(cudaSetDevice(ctx->device));
     int occ = 0;
-    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pr_spmv, PR_BLOCK, 0));
+    GB_CUDA(cudaFuncSetAttribute(k_pr_spmv, cudaFuncAttributeMaxDynamicSharedMemorySize, PR_SMEM_BYTES));
+    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pr_spmv, PR_BLOCK, PR_SMEM_BYTES));
     uint64_t total = (uint64_t)n + A->nvals;
     uint32_t G = (uint32_t)(occ * ctx->num_sms);
     if (G < 1) G = 1;
@@ -356,6 +400,7 @@ extern "C" gb_info gb_pagerank(gb_context *ctx, const gb_matrix *A, float dampin
     a.rp = A->colptr;
     a.ci = A->rowidx;
     a.rp_out = A->rowptr;
+    a.rows_are_out = A->csc_alias;
     a.alpha = damping;
     a.rec = rec.as<PrRec>();
     a.part_res = pres.as<double>();
@@ -373,7 +418,7 @@ extern "C" gb_info gb_pagerank(gb_context *ctx, const gb_matrix *A, float dampin
     for (uint32_t it = 0; it < iters; ++it) {
         a.p_old = pc; a.x = xc; a.p_new = pn; a.x_new = xn;
         int span = prof_begin(ctx, "pagerank_spmv");
-        k_pr_spmv<<<G, PR_BLOCK, 0, ctx->stream>>>(a);
+        k_pr_spmv<<<G, PR_BLOCK, PR_SMEM_BYTES, ctx->stream>>>(a);
         prof_end(ctx, span);
         k_pr_fix<<<1, PR_BLOCK, 0, ctx->stream>>>(a, resid.as<double>() + it, dang, base, fres.as<double>(),
                                                  fdang.as<double>(), 0);

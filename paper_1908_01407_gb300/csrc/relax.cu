@@ -41,6 +41,9 @@ struct RelaxArgs {
     uint32_t beta;
     BfsState *st;
     uint64_t timeout_ns, total_limit_ns;
+    const uint32_t *hub_list, *hub_pre;   // pull rows longer than RPULL_HUB
+    uint32_t nhub;
+    uint64_t hub_edges;
 };
 
 constexpr int RPULL_WPW = 4;
@@ -49,52 +52,96 @@ __device__ __forceinline__ uint32_t relax_val(const RelaxArgs &a, uint32_t vu, u
     return a.weighted ? sat_add<uint32_t>(vu, __ldg(&w[p])) : vu;
 }
 
-// pull: lane per vertex (RPULL_WPW vertices per lane in flight), scanning
-// all in-edges; rows longer than 32 are scanned by the whole warp
+// pull: lane per vertex, RPULL_WPW vertices per lane in flight. Each round
+// reads an aligned 16-byte chunk (up to 4 in-edges) of every pending row
+// and tests its sources against the frontier bitmap, all loads of a round
+// independent; rows longer than RPULL_LONG are scanned by the whole warp.
+constexpr uint32_t RPULL_LONG = 64;
+constexpr uint32_t RPULL_HUB = 2048;     // rows longer than this are split over the whole grid
+
 __device__ void relax_pull(const RelaxArgs &a, int d, uint32_t *cnt_out, uint32_t *deg_out) {
     const uint32_t *F = a.front[d % 3];
     uint32_t *Fn = a.front[(d + 1) % 3];
     const uint32_t full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint4 *ci4 = reinterpret_cast<const uint4 *>(a.ci_in);
+    const uint4 *w4 = reinterpret_cast<const uint4 *>(a.w_in);
     const uint64_t ngroups = (a.nwords + RPULL_WPW - 1) / RPULL_WPW;
     const uint64_t nwarps = (uint64_t)gridDim.x * WARPS;
     uint32_t mycnt = 0, mydeg = 0;
     for (uint64_t g = (uint64_t)blockIdx.x * WARPS + warp; g < ngroups; g += nwarps) {
         const uint64_t w0 = g * RPULL_WPW;
-        uint32_t b[RPULL_WPW], e[RPULL_WPW], best[RPULL_WPW], cur[RPULL_WPW];
+        uint32_t b[RPULL_WPW], e[RPULL_WPW], p[RPULL_WPW], best[RPULL_WPW], cur[RPULL_WPW];
 #pragma unroll
         for (int j = 0; j < RPULL_WPW; ++j) {
             uint32_t v = (uint32_t)((w0 + j) * 32 + lane);
             b[j] = e[j] = 0;
-            cur[j] = best[j] = UINT32_MAX;
+            cur[j] = UINT32_MAX;
             if (v < a.n) {
                 b[j] = __ldg(&a.rp_in[v]);
                 e[j] = __ldg(&a.rp_in[v + 1]);
                 cur[j] = ldcg(&a.val[v]);
-                best[j] = cur[j];
+            }
+            best[j] = cur[j];
+            p[j] = b[j];
+        }
+        for (;;) {
+            bool pend[RPULL_WPW];
+            bool any = false;
+#pragma unroll
+            for (int j = 0; j < RPULL_WPW; ++j) {
+                pend[j] = p[j] < e[j] && e[j] - b[j] <= RPULL_LONG;
+                any |= pend[j];
+            }
+            if (!__any_sync(full, any)) break;
+            uint4 c[RPULL_WPW], wv[RPULL_WPW];
+#pragma unroll
+            for (int j = 0; j < RPULL_WPW; ++j) {
+                if (pend[j]) {
+                    c[j] = __ldg(&ci4[p[j] >> 2]);
+                    if (a.weighted) wv[j] = __ldg(&w4[p[j] >> 2]);
+                }
+            }
+            uint32_t fw[RPULL_WPW][4];
+#pragma unroll
+            for (int j = 0; j < RPULL_WPW; ++j) {
+                uint32_t q = p[j] & ~3u;
+                uint32_t cc[4] = {c[j].x, c[j].y, c[j].z, c[j].w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    bool in = pend[j] && q + k >= p[j] && q + k < e[j];
+                    fw[j][k] = in ? ((ldcg(&F[cc[k] >> 5]) >> (cc[k] & 31)) & 1u) : 0u;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < RPULL_WPW; ++j) {
+                if (!pend[j]) continue;
+                uint32_t cc[4] = {c[j].x, c[j].y, c[j].z, c[j].w};
+                uint32_t ww[4] = {0, 0, 0, 0};
+                if (a.weighted) { ww[0] = wv[j].x; ww[1] = wv[j].y; ww[2] = wv[j].z; ww[3] = wv[j].w; }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (fw[j][k]) {
+                        uint32_t vu = ldcg(&a.val[cc[k]]);
+                        uint32_t cand = a.weighted ? sat_add<uint32_t>(vu, ww[k]) : vu;
+                        if (cand < best[j]) best[j] = cand;
+                    }
+                }
+                p[j] = (p[j] & ~3u) + 4;
             }
         }
 #pragma unroll
         for (int j = 0; j < RPULL_WPW; ++j) {
-            if (e[j] - b[j] <= 32) {
-                for (uint32_t p = b[j]; p < e[j]; ++p) {
-                    uint32_t u = __ldg(&a.ci_in[p]);
-                    if ((ldcg(&F[u >> 5]) >> (u & 31)) & 1u) {
-                        uint32_t c = relax_val(a, ldcg(&a.val[u]), p, a.w_in);
-                        if (c < best[j]) best[j] = c;
-                    }
-                }
-            }
-            uint32_t coop = __ballot_sync(full, e[j] - b[j] > 32);
+            uint32_t coop = __ballot_sync(full, e[j] - b[j] > RPULL_LONG && e[j] - b[j] <= RPULL_HUB);
             while (coop) {
                 int l = __ffs(coop) - 1;
                 coop &= coop - 1;
                 uint32_t pb = __shfl_sync(full, b[j], l), pe = __shfl_sync(full, e[j], l);
                 uint32_t mn = UINT32_MAX;
-                for (uint32_t p = pb + lane; p < pe; p += 32) {
-                    uint32_t u = __ldg(&a.ci_in[p]);
+                for (uint32_t q = pb + lane; q < pe; q += 32) {
+                    uint32_t u = __ldg(&a.ci_in[q]);
                     if ((ldcg(&F[u >> 5]) >> (u & 31)) & 1u) {
-                        uint32_t c = relax_val(a, ldcg(&a.val[u]), p, a.w_in);
+                        uint32_t c = relax_val(a, ldcg(&a.val[u]), q, a.w_in);
                         if (c < mn) mn = c;
                     }
                 }
@@ -109,7 +156,7 @@ __device__ void relax_pull(const RelaxArgs &a, int d, uint32_t *cnt_out, uint32_
             uint32_t fm = __ballot_sync(full, improved);
             if (fm) {
                 const uint64_t word = w0 + j;
-                if (lane == 0) Fn[word] = fm;
+                if (lane == 0) atomicOr(&Fn[word], fm);    // hub bits of this word come from the hub phase
                 if (improved) {
                     uint32_t v = (uint32_t)(word * 32 + lane);
                     a.val[v] = best[j];
@@ -118,6 +165,37 @@ __device__ void relax_pull(const RelaxArgs &a, int d, uint32_t *cnt_out, uint32_
                 }
             }
         }
+    }
+    *cnt_out += mycnt;
+    *deg_out += mydeg;
+}
+
+// pull, hub rows: every in-edge of a row longer than RPULL_HUB is one work
+// item, spread evenly over the grid; improvements go through atomicMin (the
+// min is order independent, so the result does not depend on the split)
+__device__ void relax_pull_hubs(const RelaxArgs &a, int d, uint32_t *cnt_out, uint32_t *deg_out) {
+    if (!a.nhub) return;
+    const uint32_t *F = a.front[d % 3];
+    uint32_t *Fn = a.front[(d + 1) % 3];
+    const uint64_t nth = (uint64_t)gridDim.x * BLOCK;
+    uint32_t mycnt = 0, mydeg = 0;
+    for (uint64_t x = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; x < a.hub_edges; x += nth) {
+        uint32_t lo = 0, hi = a.nhub;   // last h with hub_pre[h] <= x
+        while (hi - lo > 1) {
+            uint32_t mid = (lo + hi) >> 1;
+            if ((uint64_t)__ldg(&a.hub_pre[mid]) <= x) lo = mid; else hi = mid;
+        }
+        const uint32_t v = __ldg(&a.hub_list[lo]);
+        const uint32_t p = __ldg(&a.rp_in[v]) + (uint32_t)(x - __ldg(&a.hub_pre[lo]));
+        const uint32_t u = __ldg(&a.ci_in[p]);
+        if (!((ldcg(&F[u >> 5]) >> (u & 31)) & 1u)) continue;
+        const uint32_t c = relax_val(a, ldcg(&a.val[u]), p, a.w_in);
+        if (c >= ldcg(&a.val[v])) continue;
+        if (c >= atomicMin(&a.val[v], c)) continue;
+        const uint32_t bit = 1u << (v & 31);
+        if (atomicOr(&Fn[v >> 5], bit) & bit) continue;
+        mycnt += 1;
+        mydeg += __ldg(&a.rp_out[v + 1]) - __ldg(&a.rp_out[v]);
     }
     *cnt_out += mycnt;
     *deg_out += mydeg;
@@ -189,6 +267,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_relax(RelaxArgs a) {
             __syncthreads();
             uint32_t c = 0, dg = 0;
             relax_pull(a, d, &c, &dg);
+            relax_pull_hubs(a, d, &c, &dg);
             c = dev::warp_sum<uint32_t>(c);
             dg = dev::warp_sum<uint32_t>(dg);
             if ((threadIdx.x & 31) == 0 && c) { atomicAdd(&s_cnt, c); atomicAdd(&s_deg, dg); }
@@ -240,6 +319,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_relax(RelaxArgs a) {
 }  // namespace rlx
 
 struct BfsWorkspace;
+gb_info matrix_hubs(const gb_matrix *A, uint32_t min_len);
 gb_info bfs_workspace_raw(gb_context *ctx, uint32_t n, uint32_t **visited, uint32_t **front, uint32_t **q,
                           uint32_t **qp, uint32_t **qr, BfsState **st);
 
@@ -286,6 +366,16 @@ static gb_info relax_run(gb_context *ctx, const gb_matrix *A, bool weighted, uin
     a.st = st;
     a.timeout_ns = 4000000000ull;
     a.total_limit_ns = 300000000000ull;
+    a.hub_list = a.hub_pre = nullptr;
+    a.nhub = 0;
+    a.hub_edges = 0;
+    if (A->has_csc) {
+        GB_CHECK(matrix_hubs(A, rlx::RPULL_HUB));
+        a.hub_list = A->hub_list;
+        a.hub_pre = A->hub_pre;
+        a.nhub = A->nhub;
+        a.hub_edges = A->hub_edges;
+    }
     int occ = 0;
     GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rlx::k_relax, rlx::BLOCK, 0));
     if (occ < 1) return fail(GB_PANIC, "%s: kernel cannot be resident", who);
