@@ -279,7 +279,8 @@ typedef struct {
     uint32_t trace_vertices[GB_TRACE_LEVELS];   /* frontier size */
     uint64_t trace_edges[GB_TRACE_LEVELS];      /* frontier out-edges */
     float trace_us[GB_TRACE_LEVELS];            /* level duration (device clock) */
-    float init_us;                              /* initialisation before level 0 */
+    float init_us;                              /* kernel entry to the start of level 0 */
+    float final_us;                             /* end of the last level to the kernel's exit */
 } gb_bfs_stats;
 
 /* Direction-optimised BFS (Algorithm 1, Section 6.1): levels[v] = hop count
@@ -311,7 +312,7 @@ gb_info gb_bfs_autotune(gb_context *ctx, gb_matrix *A, const uint32_t *srcs, uin
  * outputs levels[n] and parents[n] (parents may be NULL). colidx and rowidx
  * must start on a 16-byte boundary and stay readable for 16 bytes past
  * their last entry. All scratch lives in one array built into the library
- * (about 6.4 MB, enough for n <= GB_NOALLOC_MAX_VERTICES); each GPU that
+ * (about 8.5 MB, enough for n <= GB_NOALLOC_MAX_VERTICES); each GPU that
  * loads the library holds it until the process exits. n above that limit:
  * GB_INVALID_VALUE. The first call on a device looks up the array's device
  * address (with that device current); make that first call before any

@@ -55,7 +55,7 @@ class BfsStats(ctypes.Structure):
                 ("alg_bytes", ctypes.c_uint64), ("trace_len", ctypes.c_uint32),
                 ("trace_dir", ctypes.c_uint32 * 32), ("trace_vertices", ctypes.c_uint32 * 32),
                 ("trace_edges", ctypes.c_uint64 * 32), ("trace_us", ctypes.c_float * 32),
-                ("init_us", ctypes.c_float)]
+                ("init_us", ctypes.c_float), ("final_us", ctypes.c_float)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("trace")}

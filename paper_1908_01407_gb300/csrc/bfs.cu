@@ -50,48 +50,97 @@ __device__ void push_level(const BfsArgs &a, Smem &sm, int d, uint32_t cnt, uint
     });
 }
 
-// Pull: warps work independently over groups of PULL_WPW bitmap words
-// (PULL_WPW * 32 vertices), keeping each lane's PULL_WPW vertices in flight
-// together. A vertex checks its in-neighbours in aligned 16-byte chunks (up
-// to 4 per load) against the frontier bitmap, for PULL_ROUNDS chunks; the
-// rare longer scans continue warp-cooperatively, 32 neighbours per step,
-// with early exit. Pull writes the next frontier as a bitmap and only counts
-// it (vertices, out-edges); the list form is built when a push needs it.
-__device__ void pull_level(const BfsArgs &a, int d, unsigned long long *examined, uint32_t *cnt_out,
+// OR of `bits` over each run of adjacent lanes holding the same `key`;
+// true for the first lane of a run, which then holds the run's OR. A key
+// that recurs in a later run gets its own head (both heads then update the
+// same word, which an atomicOr tolerates).
+static __device__ __forceinline__ bool run_or_head(uint32_t key, uint32_t &bits) {
+    const uint32_t full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t ob = __shfl_down_sync(full, bits, o);
+        uint32_t ok = __shfl_down_sync(full, key, o);
+        if (lane + o < 32 && ok == key) bits |= ob;
+    }
+    uint32_t kp = __shfl_up_sync(full, key, 1);
+    return lane == 0 || kp != key;
+}
+
+// Appends a warp's staged candidates to the next list: one atomicAdd
+// reserves the space, the copy is coalesced.
+static __device__ __forceinline__ void flush_candidates(const uint32_t *sbuf, uint32_t &staged, uint32_t *Lout,
+                                                        unsigned int *lout_cnt) {
+    const int lane = threadIdx.x & 31;
+    if (!staged) return;
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(lout_cnt, staged);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (uint32_t i = lane; i < staged; i += 32) Lout[base + i] = sbuf[i];
+    staged = 0;
+    __syncwarp();
+}
+
+// Pull over a list of candidate vertices: the vertices with an in-edge for
+// the first pull of a traversal, afterwards the candidates the previous
+// pull left unvisited (vertices claimed by a push since then are skipped by
+// their visited bit). Vertices without in-edges can never be reached by a
+// pull, and a later pull only needs what an earlier one left, so the pull
+// touches |candidates| vertices rather than all n. Warps take groups of
+// PULL_WPW * 32 consecutive entries, each lane PULL_WPW vertices kept in
+// flight together. A vertex checks its in-neighbours in aligned 16-byte
+// chunks (up to 4 per load) against the frontier bitmap, for PULL_ROUNDS
+// chunks; the rare longer scans continue warp-cooperatively, 32 neighbours
+// per step, with early exit. Found vertices set their visited and next-
+// frontier bits (one atomicOr per run of lanes in the same bitmap word);
+// the others are collected per warp in shared memory and appended to the
+// next list STAGE_CAP at a time (ascending within each appended run).
+// Pull writes the next frontier as a bitmap and only counts it (vertices,
+// out-edges); the list form is built when a push needs it.
+__device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Lin, uint32_t nin, uint32_t *Lout,
+                           unsigned int *lout_cnt, unsigned long long *examined, uint32_t *cnt_out,
                            uint32_t *deg_out) {
     const uint32_t *F = a.front[d % 3];
     uint32_t *Fn = a.front[(d + 1) % 3];
     const uint32_t full = 0xffffffffu;
+    const uint32_t NONE = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint4 *ci4 = reinterpret_cast<const uint4 *>(a.ci_in);
-    const uint64_t ngroups = (a.nwords + PULL_WPW - 1) / PULL_WPW;
-    const uint64_t nwarps = (uint64_t)gridDim.x * WARPS;
+    constexpr uint32_t GROUP = PULL_WPW * 32;
+    const uint32_t ngroups = (uint32_t)(((uint64_t)nin + GROUP - 1) / GROUP);
+    const uint32_t nwarps = gridDim.x * WARPS;
     unsigned long long exam = 0;
     uint32_t mycnt = 0, mydeg = 0;
-    for (uint64_t g = (uint64_t)blockIdx.x * WARPS + warp; g < ngroups; g += nwarps) {
-        const uint64_t w0 = g * PULL_WPW;
-        uint32_t vis[PULL_WPW], b[PULL_WPW], e[PULL_WPW], p[PULL_WPW], par[PULL_WPW];
-        bool act[PULL_WPW], found[PULL_WPW];
+    uint32_t *sbuf = sm.stage.v[warp];   // this warp's candidates for the next list
+    uint32_t staged = 0;
+    static_assert(GROUP <= STAGE_CAP, "a group's candidates fit the staging row");
+    uint32_t g = blockIdx.x * WARPS + warp;
+    for (; g < ngroups; g += nwarps) {
+        uint32_t v[PULL_WPW], b[PULL_WPW], e[PULL_WPW], p[PULL_WPW], par[PULL_WPW], vw[PULL_WPW];
+        bool act[PULL_WPW], found[PULL_WPW], live[PULL_WPW];
 #pragma unroll
         for (int j = 0; j < PULL_WPW; ++j) {
-            vis[j] = (w0 + j < a.nwords) ? ldcg(&a.visited[w0 + j]) : full;
-            act[j] = !((vis[j] >> lane) & 1u);
-            found[j] = false;
-            par[j] = 0;
-            b[j] = e[j] = 0;
+            uint32_t idx = g * GROUP + j * 32 + lane;
+            v[j] = idx < nin ? (Lin ? ldcg(&Lin[idx]) : idx) : NONE;
         }
-        // row bounds are loaded for every vertex of the group, without
-        // waiting for the visited words, so the two loads overlap
+        // visited words and row bounds are loaded together, without waiting
+        // for one another
 #pragma unroll
         for (int j = 0; j < PULL_WPW; ++j) {
-            uint32_t v = (uint32_t)((w0 + j) * 32 + lane);
-            if (v < a.n) {
-                b[j] = __ldg(&a.rp_in[v]);
-                e[j] = __ldg(&a.rp_in[v + 1]);
+            vw[j] = full;
+            b[j] = e[j] = 0;
+            if (v[j] != NONE) {
+                vw[j] = ldcg(&a.visited[v[j] >> 5]);
+                b[j] = __ldg(&a.rp_in[v[j]]);
+                e[j] = __ldg(&a.rp_in[v[j] + 1]);
             }
         }
 #pragma unroll
         for (int j = 0; j < PULL_WPW; ++j) {
+            act[j] = v[j] != NONE && !((vw[j] >> (v[j] & 31)) & 1u);
+            live[j] = e[j] > b[j];
+            found[j] = false;
+            par[j] = 0;
             if (!act[j]) e[j] = b[j];
             p[j] = b[j];
         }
@@ -171,22 +220,39 @@ __device__ void pull_level(const BfsArgs &a, int d, unsigned long long *examined
         }
 #pragma unroll
         for (int j = 0; j < PULL_WPW; ++j) {
-            uint32_t fm = __ballot_sync(full, found[j]);
-            if (!fm) continue;
-            const uint64_t word = w0 + j;
-            if (lane == 0) {
-                a.visited[word] = vis[j] | fm;
-                Fn[word] = fm;
-            }
-            if (found[j]) {
-                uint32_t v = (uint32_t)(word * 32 + lane);
-                a.levels[v] = d + 1;
-                if (a.parents) a.parents[v] = (int32_t)par[j];
-                mydeg += a.csr_is_csc ? e[j] - b[j] : __ldg(&a.rp_out[v + 1]) - __ldg(&a.rp_out[v]);
-                mycnt += 1;
+            const bool f = found[j];
+            const uint32_t fm = __ballot_sync(full, f);
+            if (fm) {
+                uint32_t key = f ? (v[j] >> 5) : NONE;
+                uint32_t bits = f ? 1u << (v[j] & 31) : 0u;
+                if (run_or_head(key, bits) && f) {
+                    atomicOr(&a.visited[key], bits);
+                    atomicOr(&Fn[key], bits);
+                }
+                if (f) {
+                    a.levels[v[j]] = d + 1;
+                    if (a.parents) a.parents[v[j]] = (int32_t)par[j];
+                    mydeg += a.csr_is_csc ? e[j] - b[j] : __ldg(&a.rp_out[v[j] + 1]) - __ldg(&a.rp_out[v[j]]);
+                    mycnt += 1;
+                }
             }
         }
+        // candidates that stay unvisited (and can still be reached) go to the next list
+        uint32_t km[PULL_WPW], nkeep = 0;
+#pragma unroll
+        for (int j = 0; j < PULL_WPW; ++j) {
+            km[j] = __ballot_sync(full, act[j] && !found[j] && live[j]);
+            nkeep += __popc(km[j]);
+        }
+        if (staged + nkeep > (uint32_t)STAGE_CAP) flush_candidates(sbuf, staged, Lout, lout_cnt);
+#pragma unroll
+        for (int j = 0; j < PULL_WPW; ++j) {
+            if ((km[j] >> lane) & 1u) sbuf[staged + __popc(km[j] & dev::lanemask_lt())] = v[j];
+            staged += __popc(km[j]);
+        }
+        __syncwarp();
     }
+    flush_candidates(sbuf, staged, Lout, lout_cnt);
     *examined += exam;
     *cnt_out += mycnt;
     *deg_out += mydeg;
@@ -198,10 +264,11 @@ __device__ __forceinline__ bool choose_pull(const BfsArgs &a, uint64_t fe) {
     return fe * (uint64_t)a.beta > a.m;
 }
 
-__global__ void __launch_bounds__(BLOCK, 3) k_bfs(BfsArgs a) {
+__global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
     __shared__ Smem sm;
     __shared__ unsigned long long s_exam;
     __shared__ uint32_t s_cnt, s_deg;
+    const uint64_t t_entry = dev::globaltimer_ns();
     const uint32_t nthreads = gridDim.x * BLOCK;
     const uint32_t tid = blockIdx.x * BLOCK + threadIdx.x;
     BfsState *st = a.st;
@@ -228,6 +295,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_bfs(BfsArgs a) {
         a.qr[0][0] = r0;
         st->qstate[0] = (1ull << a.ebits) | deg;
         memset(res, 0, sizeof(BfsResult));
+        res->t_entry = t_entry;
     }
     bool ok = dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns);
     const uint64_t t_start = dev::globaltimer_ns();
@@ -237,6 +305,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_bfs(BfsArgs a) {
     uint64_t prev_fe = 0, prev_unvisited = 0;
     double alg = 8.0 * a.n;   // levels + parents writes
     bool list_valid = true;    // the list form of the current frontier exists
+    int npull = 0;             // pull steps so far (selects the candidate lists)
     int d = 0;
     for (; ok; ++d) {
         if (threadIdx.x == 0)
@@ -284,9 +353,21 @@ __global__ void __launch_bounds__(BLOCK, 3) k_bfs(BfsArgs a) {
         if (pull) {
             if (threadIdx.x == 0) { s_exam = 0; s_cnt = 0; s_deg = 0; }
             __syncthreads();
+            // candidates: the live vertices for the first pull, then what the previous pull left
+            const uint32_t *Lin;
+            uint32_t nin;
+            if (npull == 0) {
+                Lin = a.live;
+                nin = a.live ? ldcg(a.live_count) : a.n;
+            } else {
+                Lin = a.ul[(npull - 1) & 1];
+                nin = (uint32_t)dev::ld_relaxed_gpu_int((const int *)&st->ucnt[(npull - 1) % 3]);
+            }
+            if (tid == 0) st->ucnt[(npull + 1) % 3] = 0;
             unsigned long long ex = 0;
             uint32_t c = 0, dg = 0;
-            pull_level(a, d, &ex, &c, &dg);
+            pull_level(a, sm, d, Lin, nin, a.ul[npull & 1], &st->ucnt[npull % 3], &ex, &c, &dg);
+            ++npull;
             ex = dev::warp_sum<unsigned long long>(ex);
             c = dev::warp_sum<uint32_t>(c);
             dg = dev::warp_sum<uint32_t>(dg);
@@ -309,6 +390,10 @@ __global__ void __launch_bounds__(BLOCK, 3) k_bfs(BfsArgs a) {
             list_valid = true;
         }
         ok = dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns);
+    }
+    if (tid == 0) {
+        res->t_end = dev::globaltimer_ns();
+        if (d < GBX_MAX_LEVEL_LOG) res->lv_ns[d] = res->t_end;
     }
     // ---- vertices never reached get level and parent -1
     // (a warp per bitmap word: one broadcast load, 32 coalesced stores)
@@ -334,7 +419,6 @@ __global__ void __launch_bounds__(BLOCK, 3) k_bfs(BfsArgs a) {
         res->depth = d;
         res->reached = reached;
         res->alg_bytes = alg;
-        if (d < GBX_MAX_LEVEL_LOG) res->lv_ns[d] = dev::globaltimer_ns();
         res->t_begin = t_start;
     }
     // ---- leave: the last block out resets the working state for the next launch
@@ -345,9 +429,10 @@ __global__ void __launch_bounds__(BLOCK, 3) k_bfs(BfsArgs a) {
         if (old == gridDim.x - 1) {
             __threadfence();
             res->err = ld_relaxed_gpu_int_(&st->err);
+            res->t_exit = dev::globaltimer_ns();
             st->err = 0;
             st->bar.count = 0;
-            for (int k = 0; k < 3; ++k) { st->qstate[k] = 0; st->exam[k] = 0; st->cstate[k] = 0; }
+            for (int k = 0; k < 3; ++k) { st->qstate[k] = 0; st->exam[k] = 0; st->cstate[k] = 0; st->ucnt[k] = 0; }
             __threadfence();
             st->bar.exits = 0;
         }
@@ -358,7 +443,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_bfs(BfsArgs a) {
 
 struct BfsWorkspace {
     uint32_t n = 0;
-    uint32_t *visited = nullptr, *front = nullptr, *q = nullptr, *qp = nullptr, *qr = nullptr;
+    uint32_t *visited = nullptr, *front = nullptr, *q = nullptr, *qp = nullptr, *qr = nullptr, *ul = nullptr;
     BfsState *st = nullptr;
     int grid = 0;
 };
@@ -371,7 +456,7 @@ gb_info bfs_workspace(gb_context *ctx, uint32_t n, BfsWorkspace **out) {
     BfsWorkspace &w = g_ws[ctx];
     if (w.n < n || !w.st) {
         dfree(ctx, w.visited); dfree(ctx, w.front); dfree(ctx, w.q); dfree(ctx, w.qp); dfree(ctx, w.qr);
-        dfree(ctx, w.st);
+        dfree(ctx, w.ul); dfree(ctx, w.st);
         w = BfsWorkspace();
         uint32_t nw = (n + 31) / 32;
         GB_CHECK(dalloc_t(ctx, &w.visited, nw));
@@ -379,6 +464,7 @@ gb_info bfs_workspace(gb_context *ctx, uint32_t n, BfsWorkspace **out) {
         GB_CHECK(dalloc_t(ctx, &w.q, 2ull * n + 2));
         GB_CHECK(dalloc_t(ctx, &w.qp, 2ull * n + 2));
         GB_CHECK(dalloc_t(ctx, &w.qr, 2ull * n + 2));
+        GB_CHECK(dalloc_t(ctx, &w.ul, 2ull * n + 2));
         GB_CHECK(dalloc_t(ctx, &w.st, 1));
         // the only reset of the working state: launches leave it zeroed
         GB_CHECK(memset_async(ctx, w.st, 0, sizeof(BfsState)));
@@ -408,7 +494,7 @@ void bfs_workspace_release(gb_context *ctx) {
     if (it == g_ws.end()) return;
     BfsWorkspace &w = it->second;
     dfree(ctx, w.visited); dfree(ctx, w.front); dfree(ctx, w.q); dfree(ctx, w.qp); dfree(ctx, w.qr);
-    dfree(ctx, w.st);
+    dfree(ctx, w.ul); dfree(ctx, w.st);
     g_ws.erase(it);
 }
 
@@ -431,6 +517,9 @@ gb_info bfs_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *l
     a.q[0] = w->q; a.q[1] = w->q + A->nrows + 1;
     a.qp[0] = w->qp; a.qp[1] = w->qp + A->nrows + 1;
     a.qr[0] = w->qr; a.qr[1] = w->qr + A->nrows + 1;
+    a.live = A->has_csc ? A->live_list : nullptr;
+    a.live_count = A->has_csc ? A->live_count : nullptr;
+    a.ul[0] = w->ul; a.ul[1] = w->ul + A->nrows + 1;
     a.ebits = 64 - bits_for((uint64_t)A->nrows + 1);
     a.emask = (a.ebits >= 64) ? ~0ull : ((1ull << a.ebits) - 1);
     a.mode = desc ? desc->direction : GB_AUTO;
@@ -497,7 +586,8 @@ extern "C" gb_info gb_bfs(gb_context *ctx, const gb_matrix *A, uint32_t src, int
                 uint64_t t1 = (l + 1 < GBX_MAX_LEVEL_LOG) ? hs.lv_ns[l + 1] : hs.lv_ns[l];
                 stats->trace_us[l] = (float)((t1 - hs.lv_ns[l]) * 1e-3);
             }
-            stats->init_us = hs.depth ? (float)((hs.lv_ns[0] - hs.t_begin) * 1e-3) : 0.f;
+            stats->init_us = hs.depth ? (float)((hs.lv_ns[0] - hs.t_entry) * 1e-3) : 0.f;
+            stats->final_us = (float)((hs.t_exit - hs.t_end) * 1e-3);
         }
         if (hs.err) return fail(GB_TIMEOUT, "gb_bfs: a bounded grid barrier wait ran out");
     }
@@ -525,7 +615,8 @@ constexpr size_t OFF_FRONT = OFF_VISITED + NW * 4;
 constexpr size_t OFF_Q = ((OFF_FRONT + 3 * NW * 4) + 255) / 256 * 256;
 constexpr size_t OFF_QP = OFF_Q + (LIST + 255) / 256 * 256;
 constexpr size_t OFF_QR = OFF_QP + (LIST + 255) / 256 * 256;
-constexpr size_t OFF_ST = OFF_QR + (LIST + 255) / 256 * 256;
+constexpr size_t OFF_UL = OFF_QR + (LIST + 255) / 256 * 256;
+constexpr size_t OFF_ST = OFF_UL + (LIST + 255) / 256 * 256;
 constexpr size_t BYTES = OFF_ST + (sizeof(BfsState) + 255) / 256 * 256;
 
 struct Device {
@@ -597,6 +688,9 @@ extern "C" gb_info gb_bfs_noalloc(const uint32_t *rowptr, const uint32_t *colidx
     a.q[0] = (uint32_t *)(base + OFF_Q); a.q[1] = a.q[0] + n + 1;
     a.qp[0] = (uint32_t *)(base + OFF_QP); a.qp[1] = a.qp[0] + n + 1;
     a.qr[0] = (uint32_t *)(base + OFF_QR); a.qr[1] = a.qr[0] + n + 1;
+    a.live = nullptr;            // no cached list here: the first pull takes every vertex
+    a.live_count = nullptr;
+    a.ul[0] = (uint32_t *)(base + OFF_UL); a.ul[1] = a.ul[0] + n + 1;
     a.ebits = 64 - bits_for((uint64_t)n + 1);
     a.emask = (1ull << a.ebits) - 1;
     a.mode = GB_AUTO;

@@ -14,7 +14,10 @@ struct BfsResult {
     unsigned long long frontier_edges;
     unsigned long long reached;
     double alg_bytes;
-    unsigned long long t_begin;
+    unsigned long long t_begin;        // %globaltimer after the initial grid barrier
+    unsigned long long t_entry;        // block 0 entering the kernel
+    unsigned long long t_end;          // block 0 leaving the level loop
+    unsigned long long t_exit;         // the last block leaving the kernel
     unsigned int dir_log[GBX_MAX_LEVEL_LOG];        // 1 = push, 2 = pull
     unsigned int lv_cnt[GBX_MAX_LEVEL_LOG];         // frontier vertices per level
     unsigned long long lv_fe[GBX_MAX_LEVEL_LOG];    // frontier out-edges per level
@@ -30,6 +33,8 @@ struct BfsState {
     unsigned long long qstate[3];      // packed (list length << ebits | edge-prefix total), per level slot
     unsigned long long exam[3];        // adjacency entries read by pull, per level slot
     unsigned long long cstate[3];      // packed counter of the bitmap -> list compaction, per level slot
+    unsigned int ucnt[3];              // length of the candidate list a pull leaves, per pull slot
+    unsigned int pad1;
     BfsResult res;
 };
 
@@ -44,6 +49,9 @@ struct BfsArgs {
     uint32_t *visited;
     uint32_t *front[3];
     uint32_t *q[2], *qp[2], *qr[2];    // frontier list: vertex, out-edge prefix, row start
+    const uint32_t *live;              // vertices with an in-edge (ascending); null = all vertices
+    const uint32_t *live_count;        // device scalar: length of live
+    uint32_t *ul[2];                   // candidate lists of the pull steps (unvisited, with in-edges)
     int ebits;
     unsigned long long emask;
     int mode;

@@ -84,6 +84,12 @@ struct gb_matrix_t {
     bool hub_ready = false;
     // push/pull switch threshold chosen by gb_bfs_autotune (0 = not tuned)
     uint32_t tuned_beta = 0;
+    // vertices with at least one in-edge (nonempty CSC row), ascending,
+    // built with the CSC; live_count is a device scalar (live_list[nrows])
+    uint32_t *live_list = nullptr;
+    uint32_t *live_count = nullptr;
+    // guards the caches built on first use (hub list)
+    std::mutex cache_mu;
 };
 
 struct gb_vector_t {

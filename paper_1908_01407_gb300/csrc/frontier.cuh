@@ -14,7 +14,7 @@ constexpr int WARPS = BLOCK / 32;
 constexpr int PUSH_ITEMS = 4;
 constexpr int PUSH_TILE = BLOCK * PUSH_ITEMS;      // edges per block tile
 constexpr int PUSH_OWNERS = PUSH_TILE + 1;          // owner entries staged in smem
-constexpr int PULL_WPW = 4;                          // bitmap words per warp per tile
+constexpr int PULL_WPW = 2;                          // pull candidates per lane in flight
 constexpr int PULL_ROUNDS = 2;                       // 16-byte chunks a lane checks alone
 
 struct SmemPush {

@@ -57,6 +57,8 @@ void release(gb_matrix *A) {
     dfree(ctx, A->rowptr); dfree(ctx, A->colidx); dfree(ctx, A->vals);
     dfree(ctx, A->colptr); dfree(ctx, A->rowidx); dfree(ctx, A->cvals);
     dfree(ctx, A->hub_list); dfree(ctx, A->hub_pre);
+    dfree(ctx, A->live_list);
+    A->live_list = A->live_count = nullptr;
     A->hub_list = A->hub_pre = nullptr;
     A->nhub = 0; A->hub_edges = 0; A->hub_ready = false;
     A->rowptr = A->colidx = A->colptr = A->rowidx = nullptr;
@@ -68,6 +70,34 @@ void release(gb_matrix *A) {
 gb_info matrix_expand_rows(const gb_matrix *A, uint32_t *rows) {
     if (A->nrows)
         k_expand_rows<<<nblk(A->nrows), 256, 0, A->ctx->stream>>>(A->rowptr, A->nrows, rows);
+    GB_LAUNCH_CHECK();
+    return GB_SUCCESS;
+}
+
+namespace {
+__global__ void k_live_flags(const uint32_t *ptr, uint32_t n, uint32_t *flag) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = ptr[i + 1] > ptr[i] ? 1u : 0u;
+}
+__global__ void k_live_emit(const uint32_t *flag, const uint32_t *pos, uint32_t n, uint32_t *list) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && flag[i]) list[pos[i]] = i;
+}
+}  // namespace
+
+// The ascending list of vertices with a nonempty CSC row (an in-edge): the
+// only vertices a pull step can ever reach. Its length stays on the device.
+gb_info matrix_live(gb_matrix *A) {
+    gb_context *ctx = A->ctx;
+    const uint32_t n = A->ncols;
+    GB_CHECK(dalloc_t(ctx, &A->live_list, (size_t)n + 1));
+    A->live_count = A->live_list + n;
+    Scratch flag(ctx), pos(ctx);
+    GB_CHECK(flag.alloc(((size_t)n + 1) * 4));
+    GB_CHECK(pos.alloc(((size_t)n + 1) * 4));
+    if (n) k_live_flags<<<nblk(n), 256, 0, ctx->stream>>>(A->colptr, n, flag.as<uint32_t>());
+    GB_CHECK(scan_exclusive_u32(ctx, flag.as<uint32_t>(), pos.as<uint32_t>(), n, A->live_count));
+    if (n) k_live_emit<<<nblk(n), 256, 0, ctx->stream>>>(flag.as<uint32_t>(), pos.as<uint32_t>(), n, A->live_list);
     GB_LAUNCH_CHECK();
     return GB_SUCCESS;
 }
@@ -102,6 +132,7 @@ gb_info matrix_build_device(gb_matrix *A, const uint32_t *rows, const uint32_t *
         A->cvals = cv;
         A->has_csc = true;
     }
+    if (A->has_csc && A->nrows == A->ncols) GB_CHECK(matrix_live(A));
     return GB_SUCCESS;
 }
 
@@ -128,6 +159,7 @@ __global__ void k_hub_emit(const uint32_t *flag, const uint32_t *pos, const uint
 // the exclusive prefix of their lengths; computed once and cached.
 gb_info matrix_hubs(const gb_matrix *Ac, uint32_t min_len) {
     gb_matrix *A = const_cast<gb_matrix *>(Ac);
+    std::lock_guard<std::mutex> lock(A->cache_mu);
     if (A->hub_ready) return GB_SUCCESS;
     gb_context *ctx = A->ctx;
     const uint32_t *ptr = A->has_csc ? A->colptr : A->rowptr;

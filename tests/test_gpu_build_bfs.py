@@ -194,3 +194,44 @@ def test_bfs_autotune_picks_a_candidate_and_keeps_results(ctx):
     for s in gen.sources(t, 4, seed=1):
         check_bfs(ctx, g, A, int(s))          # default descriptor: the tuned beta
     A.free()
+
+
+def layered_graph(wide=300, nwide=4, clique=40, isolated=5000, seed=4):
+    """src - W1 - b1 - W2 - b2 - ...: every W is a clique joined completely
+    to the single vertices before and after it, so the frontier alternates
+    between many out-edges (a W) and few (a b); plus a separate clique
+    (reachable by a pull never) and vertices without edges. Vertex ids are
+    permuted. Returns (tuples, source)."""
+    edges = []
+    nxt, prev = 1, [0]
+    for _ in range(nwide):
+        W = list(range(nxt, nxt + wide))
+        nxt += wide
+        edges += [(u, v) for u in prev for v in W] + [(W[i], W[j]) for i in range(wide) for j in range(i)]
+        b = nxt
+        nxt += 1
+        edges += [(u, b) for u in W]
+        prev = [b]
+    c0 = nxt
+    edges += [(c0 + i, c0 + j) for i in range(clique) for j in range(i)]
+    nxt += clique + isolated
+    perm = np.random.default_rng(seed).permutation(nxt)
+    return gen.from_edges(nxt, [(int(perm[u]), int(perm[v])) for u, v in edges]), int(perm[0])
+
+
+def test_bfs_pull_push_pull_keeps_candidates(ctx):
+    """Directions alternate push, pull, push, pull, ...: each pull starts
+    from the candidates the previous pull left, some of which a push has
+    claimed in between; the clique component stays a candidate throughout."""
+    t, src = layered_graph()
+    g, A = make(ctx, t)
+    d = gb.Descriptor(beta=10)
+    st = check_bfs(ctx, g, A, src, d)
+    dirs = "".join("P" if x["dir"] == "pull" else "s" for x in st["trace"])
+    assert dirs == "sPsPsPsPs", dirs
+    d.free()
+    # the same graph with the pulls only
+    d = gb.Descriptor(direction=gb.PULL)
+    check_bfs(ctx, g, A, src, d)
+    d.free()
+    A.free()
