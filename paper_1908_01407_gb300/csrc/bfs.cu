@@ -81,22 +81,27 @@ static __device__ __forceinline__ void flush_candidates(const uint32_t *sbuf, ui
     __syncwarp();
 }
 
-// Pull over a list of candidate vertices: the vertices with an in-edge for
-// the first pull of a traversal, afterwards the candidates the previous
-// pull left unvisited (vertices claimed by a push since then are skipped by
-// their visited bit). Vertices without in-edges can never be reached by a
-// pull, and a later pull only needs what an earlier one left, so the pull
-// touches |candidates| vertices rather than all n. Warps take groups of
-// PULL_WPW * 32 consecutive entries, each lane PULL_WPW vertices kept in
-// flight together. A vertex checks its in-neighbours in aligned 16-byte
-// chunks (up to 4 per load) against the frontier bitmap, for PULL_ROUNDS
-// chunks; the rare longer scans continue warp-cooperatively, 32 neighbours
-// per step, with early exit. Found vertices set their visited and next-
-// frontier bits (one atomicOr per run of lanes in the same bitmap word);
-// the others are collected per warp in shared memory and appended to the
-// next list STAGE_CAP at a time (ascending within each appended run).
-// Pull writes the next frontier as a bitmap and only counts it (vertices,
-// out-edges); the list form is built when a push needs it.
+// Pull over a list of candidates: for the first pull of a traversal every
+// vertex with an in-edge, afterwards the candidates the previous pull left
+// unvisited (a push may have claimed some since; their visited bit skips
+// them). Vertices without in-edges can never be reached by a pull, and a
+// later pull needs only what an earlier one left, so a pull touches
+// |candidates| vertices rather than all n. With the matrix's live table a
+// candidate is an index into the live list, and its first four
+// in-neighbours, in-degree and out-degree come with coalesced loads in list
+// order; the visited word and the frontier words of those four neighbours
+// are then loaded together (two dependent memory steps in all). Without
+// the table a candidate is a vertex and its row is read through the row
+// pointers. Rows longer than four whose head has no frontier vertex
+// continue in aligned 16-byte chunks for PULL_ROUNDS chunks, then
+// warp-cooperatively (32 neighbours per step), all with early exit.
+// Warps take groups of PULL_WPW * 32 consecutive candidates, each lane
+// PULL_WPW in flight. Found vertices set their visited and next-frontier
+// bits (one atomicOr per run of lanes in the same bitmap word); the others
+// are collected per warp in shared memory and appended to the next list
+// STAGE_CAP at a time. Pull writes the next frontier as a bitmap and only
+// counts it (vertices, out-edges); the list form is built when a push needs
+// it.
 __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Lin, uint32_t nin, uint32_t *Lout,
                            unsigned int *lout_cnt, unsigned long long *examined, uint32_t *cnt_out,
                            uint32_t *deg_out) {
@@ -106,6 +111,7 @@ __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Li
     const uint32_t NONE = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint4 *ci4 = reinterpret_cast<const uint4 *>(a.ci_in);
+    const bool table = a.live_head != nullptr;
     constexpr uint32_t GROUP = PULL_WPW * 32;
     const uint32_t ngroups = (uint32_t)(((uint64_t)nin + GROUP - 1) / GROUP);
     const uint32_t nwarps = gridDim.x * WARPS;
@@ -114,115 +120,177 @@ __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Li
     uint32_t *sbuf = sm.stage.v[warp];   // this warp's candidates for the next list
     uint32_t staged = 0;
     static_assert(GROUP <= STAGE_CAP, "a group's candidates fit the staging row");
-    uint32_t g = blockIdx.x * WARPS + warp;
-    for (; g < ngroups; g += nwarps) {
-        uint32_t v[PULL_WPW], b[PULL_WPW], e[PULL_WPW], p[PULL_WPW], par[PULL_WPW], vw[PULL_WPW];
-        bool act[PULL_WPW], found[PULL_WPW], live[PULL_WPW];
+    for (uint32_t g = blockIdx.x * WARPS + warp; g < ngroups; g += nwarps) {
+        uint32_t c[PULL_WPW], v[PULL_WPW], h[PULL_WPW][4], len[PULL_WPW], dego[PULL_WPW], b[PULL_WPW];
+        uint32_t par[PULL_WPW], p[PULL_WPW], e[PULL_WPW];
+        bool act[PULL_WPW], found[PULL_WPW];
 #pragma unroll
         for (int j = 0; j < PULL_WPW; ++j) {
             uint32_t idx = g * GROUP + j * 32 + lane;
-            v[j] = idx < nin ? (Lin ? ldcg(&Lin[idx]) : idx) : NONE;
+            c[j] = idx < nin ? (Lin ? ldcg(&Lin[idx]) : idx) : NONE;
         }
-        // visited words and row bounds are loaded together, without waiting
-        // for one another
+        // the candidate's record: vertex, row head, degrees
 #pragma unroll
         for (int j = 0; j < PULL_WPW; ++j) {
-            vw[j] = full;
-            b[j] = e[j] = 0;
-            if (v[j] != NONE) {
-                vw[j] = ldcg(&a.visited[v[j] >> 5]);
-                b[j] = __ldg(&a.rp_in[v[j]]);
-                e[j] = __ldg(&a.rp_in[v[j] + 1]);
+            v[j] = NONE;
+            len[j] = dego[j] = b[j] = 0;
+            h[j][0] = h[j][1] = h[j][2] = h[j][3] = NONE;
+            if (c[j] != NONE) {
+                if (table) {
+                    v[j] = __ldg(&a.live[c[j]]);
+                    const uint4 hh = __ldg(&a.live_head[c[j]]);
+                    h[j][0] = hh.x; h[j][1] = hh.y; h[j][2] = hh.z; h[j][3] = hh.w;
+                    len[j] = __ldg(&a.live_len[c[j]]);
+                    dego[j] = __ldg(&a.live_deg[c[j]]);
+                } else {
+                    v[j] = c[j];
+                    b[j] = __ldg(&a.rp_in[v[j]]);
+                    len[j] = __ldg(&a.rp_in[v[j] + 1]) - b[j];
+                }
             }
         }
+        if (!table) {
+#pragma unroll
+            for (int j = 0; j < PULL_WPW; ++j)
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if ((uint32_t)k < len[j]) h[j][k] = __ldg(&a.ci_in[b[j] + k]);
+        }
+        // the visited word and the frontier words of the first two head
+        // entries, together; the other two only where those did not hit
+        uint32_t vw[PULL_WPW], fw[PULL_WPW][4];
+#pragma unroll
+        for (int j = 0; j < PULL_WPW; ++j) {
+            vw[j] = v[j] != NONE ? ldcg(&a.visited[v[j] >> 5]) : full;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) fw[j][k] = h[j][k] != NONE ? ldcg(&F[h[j][k] >> 5]) : 0u;
+        }
+        bool more = false;
 #pragma unroll
         for (int j = 0; j < PULL_WPW; ++j) {
             act[j] = v[j] != NONE && !((vw[j] >> (v[j] & 31)) & 1u);
-            live[j] = e[j] > b[j];
             found[j] = false;
             par[j] = 0;
-            if (!act[j]) e[j] = b[j];
-            p[j] = b[j];
-        }
-#pragma unroll 1
-        for (int r = 0; r < PULL_ROUNDS; ++r) {
-            uint4 c[PULL_WPW];
-            bool pend[PULL_WPW];
 #pragma unroll
-            for (int j = 0; j < PULL_WPW; ++j) {
-                pend[j] = act[j] && !found[j] && p[j] < e[j];
-                if (pend[j]) c[j] = __ldg(&ci4[p[j] >> 2]);
-            }
-            uint32_t fw[PULL_WPW][4];
-#pragma unroll
-            for (int j = 0; j < PULL_WPW; ++j) {
-                uint32_t q = p[j] & ~3u;
-                uint32_t cc[4] = {c[j].x, c[j].y, c[j].z, c[j].w};
-#pragma unroll
-                for (int k2 = 0; k2 < 4; ++k2) {
-                    bool in = pend[j] && q + k2 >= p[j] && q + k2 < e[j];
-                    fw[j][k2] = in ? ldcg(&F[cc[k2] >> 5]) : 0u;
+            for (int k = 1; k >= 0; --k)   // the first frontier neighbour in row order
+                if (h[j][k] != NONE && ((fw[j][k] >> (h[j][k] & 31)) & 1u)) {
+                    found[j] = true;
+                    par[j] = h[j][k];
                 }
-            }
-#pragma unroll
-            for (int j = 0; j < PULL_WPW; ++j) {
-                if (!pend[j]) continue;
-                uint32_t q = p[j] & ~3u;
-                uint32_t cc[4] = {c[j].x, c[j].y, c[j].z, c[j].w};
-                uint32_t stop = q + 4 < e[j] ? q + 4 : e[j];
-#pragma unroll
-                for (int k2 = 0; k2 < 4; ++k2) {
-                    uint32_t pos = q + k2;
-                    if (!found[j] && pos >= p[j] && pos < e[j] && ((fw[j][k2] >> (cc[k2] & 31)) & 1u)) {
-                        found[j] = true;
-                        par[j] = cc[k2];
-                        stop = pos + 1;
-                    }
-                }
-                exam += stop - p[j];
-                p[j] = found[j] ? stop : q + 4;
-            }
-            bool any = false;
-#pragma unroll
-            for (int j = 0; j < PULL_WPW; ++j) any |= act[j] && !found[j] && p[j] < e[j];
-            if (!__any_sync(full, any)) break;
+            found[j] = found[j] && act[j];
         }
+#pragma unroll
+        for (int j = 0; j < PULL_WPW; ++j)
+#pragma unroll
+            for (int k = 2; k < 4; ++k)
+                fw[j][k] = (act[j] && !found[j] && h[j][k] != NONE) ? ldcg(&F[h[j][k] >> 5]) : 0u;
 #pragma unroll
         for (int j = 0; j < PULL_WPW; ++j) {
-            uint32_t coop = __ballot_sync(full, act[j] && !found[j] && p[j] < e[j]);
-            while (coop) {
-                int l = __ffs(coop) - 1;
-                coop &= coop - 1;
-                uint32_t pb = __shfl_sync(full, p[j], l);
-                uint32_t pe = __shfl_sync(full, e[j], l);
-                bool got = false;
-                uint32_t gpar = 0;
-                for (uint32_t q0 = pb; q0 < pe; q0 += 32) {
-                    uint32_t q = q0 + lane;
-                    uint32_t u = 0;
-                    bool hit = false;
-                    if (q < pe) {
-                        u = __ldg(&a.ci_in[q]);
-                        hit = (ldcg(&F[u >> 5]) >> (u & 31)) & 1u;
+            uint32_t ex = len[j] < 4 ? len[j] : 4;
+            if (act[j] && !found[j]) {
+#pragma unroll
+                for (int k = 3; k >= 2; --k)
+                    if (h[j][k] != NONE && ((fw[j][k] >> (h[j][k] & 31)) & 1u)) {
+                        found[j] = true;
+                        par[j] = h[j][k];
+                        ex = k + 1;
                     }
-                    uint32_t hb = __ballot_sync(full, hit);
-                    if (hb) {
-                        int f = __ffs(hb) - 1;
-                        gpar = __shfl_sync(full, u, f);
-                        got = true;
-                        if (lane == 0) exam += (q0 - pb) + f + 1;
-                        break;
-                    }
-                    if (lane == 0) exam += (pe - q0 < 32 ? pe - q0 : 32);
+            } else if (found[j]) {
+                ex = par[j] == h[j][0] ? 1 : 2;
+            }
+            if (act[j]) exam += ex;
+            p[j] = e[j] = 0;
+            more |= act[j] && !found[j] && len[j] > 4;
+        }
+        // rows longer than four with no frontier vertex in their head
+        if (__any_sync(full, more)) {
+#pragma unroll
+            for (int j = 0; j < PULL_WPW; ++j) {
+                if (act[j] && !found[j] && len[j] > 4) {
+                    if (table) b[j] = __ldg(&a.rp_in[v[j]]);
+                    p[j] = b[j] + 4;
+                    e[j] = b[j] + len[j];
                 }
-                if (lane == l && got) { found[j] = true; par[j] = gpar; }
+            }
+#pragma unroll 1
+            for (int r = 0; r < PULL_ROUNDS; ++r) {
+                uint4 cw[PULL_WPW];
+                bool pend[PULL_WPW];
+#pragma unroll
+                for (int j = 0; j < PULL_WPW; ++j) {
+                    pend[j] = !found[j] && p[j] < e[j];
+                    if (pend[j]) cw[j] = __ldg(&ci4[p[j] >> 2]);
+                }
+                uint32_t f4[PULL_WPW][4];
+#pragma unroll
+                for (int j = 0; j < PULL_WPW; ++j) {
+                    uint32_t q = p[j] & ~3u;
+                    uint32_t cc[4] = {cw[j].x, cw[j].y, cw[j].z, cw[j].w};
+#pragma unroll
+                    for (int k2 = 0; k2 < 4; ++k2) {
+                        bool in = pend[j] && q + k2 >= p[j] && q + k2 < e[j];
+                        f4[j][k2] = in ? ldcg(&F[cc[k2] >> 5]) : 0u;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < PULL_WPW; ++j) {
+                    if (!pend[j]) continue;
+                    uint32_t q = p[j] & ~3u;
+                    uint32_t cc[4] = {cw[j].x, cw[j].y, cw[j].z, cw[j].w};
+                    uint32_t stop = q + 4 < e[j] ? q + 4 : e[j];
+#pragma unroll
+                    for (int k2 = 0; k2 < 4; ++k2) {
+                        uint32_t pos = q + k2;
+                        if (!found[j] && pos >= p[j] && pos < e[j] && ((f4[j][k2] >> (cc[k2] & 31)) & 1u)) {
+                            found[j] = true;
+                            par[j] = cc[k2];
+                            stop = pos + 1;
+                        }
+                    }
+                    exam += stop - p[j];
+                    p[j] = found[j] ? stop : q + 4;
+                }
+                bool any = false;
+#pragma unroll
+                for (int j = 0; j < PULL_WPW; ++j) any |= !found[j] && p[j] < e[j];
+                if (!__any_sync(full, any)) break;
+            }
+#pragma unroll
+            for (int j = 0; j < PULL_WPW; ++j) {
+                uint32_t coop = __ballot_sync(full, !found[j] && p[j] < e[j]);
+                while (coop) {
+                    int l = __ffs(coop) - 1;
+                    coop &= coop - 1;
+                    uint32_t pb = __shfl_sync(full, p[j], l);
+                    uint32_t pe = __shfl_sync(full, e[j], l);
+                    bool got = false;
+                    uint32_t gpar = 0;
+                    for (uint32_t q0 = pb; q0 < pe; q0 += 32) {
+                        uint32_t q = q0 + lane;
+                        uint32_t u = 0;
+                        bool hit = false;
+                        if (q < pe) {
+                            u = __ldg(&a.ci_in[q]);
+                            hit = (ldcg(&F[u >> 5]) >> (u & 31)) & 1u;
+                        }
+                        uint32_t hb = __ballot_sync(full, hit);
+                        if (hb) {
+                            int f = __ffs(hb) - 1;
+                            gpar = __shfl_sync(full, u, f);
+                            got = true;
+                            if (lane == 0) exam += (q0 - pb) + f + 1;
+                            break;
+                        }
+                        if (lane == 0) exam += (pe - q0 < 32 ? pe - q0 : 32);
+                    }
+                    if (lane == l && got) { found[j] = true; par[j] = gpar; }
+                }
             }
         }
 #pragma unroll
         for (int j = 0; j < PULL_WPW; ++j) {
             const bool f = found[j];
-            const uint32_t fm = __ballot_sync(full, f);
-            if (fm) {
+            if (__ballot_sync(full, f)) {
                 uint32_t key = f ? (v[j] >> 5) : NONE;
                 uint32_t bits = f ? 1u << (v[j] & 31) : 0u;
                 if (run_or_head(key, bits) && f) {
@@ -232,7 +300,9 @@ __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Li
                 if (f) {
                     a.levels[v[j]] = d + 1;
                     if (a.parents) a.parents[v[j]] = (int32_t)par[j];
-                    mydeg += a.csr_is_csc ? e[j] - b[j] : __ldg(&a.rp_out[v[j] + 1]) - __ldg(&a.rp_out[v[j]]);
+                    if (!table)
+                        dego[j] = a.csr_is_csc ? len[j] : __ldg(&a.rp_out[v[j] + 1]) - __ldg(&a.rp_out[v[j]]);
+                    mydeg += dego[j];
                     mycnt += 1;
                 }
             }
@@ -241,13 +311,13 @@ __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Li
         uint32_t km[PULL_WPW], nkeep = 0;
 #pragma unroll
         for (int j = 0; j < PULL_WPW; ++j) {
-            km[j] = __ballot_sync(full, act[j] && !found[j] && live[j]);
+            km[j] = __ballot_sync(full, act[j] && !found[j] && len[j] > 0);
             nkeep += __popc(km[j]);
         }
         if (staged + nkeep > (uint32_t)STAGE_CAP) flush_candidates(sbuf, staged, Lout, lout_cnt);
 #pragma unroll
         for (int j = 0; j < PULL_WPW; ++j) {
-            if ((km[j] >> lane) & 1u) sbuf[staged + __popc(km[j] & dev::lanemask_lt())] = v[j];
+            if ((km[j] >> lane) & 1u) sbuf[staged + __popc(km[j] & dev::lanemask_lt())] = c[j];
             staged += __popc(km[j]);
         }
         __syncwarp();
@@ -294,8 +364,13 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
         a.qp[0][0] = 0;
         a.qr[0][0] = r0;
         st->qstate[0] = (1ull << a.ebits) | deg;
-        memset(res, 0, sizeof(BfsResult));
-        res->t_entry = t_entry;
+    }
+    if (blockIdx.x == 0) {
+        // block 0 zeroes the result record, then its thread 0 owns it
+        unsigned long long *r8 = reinterpret_cast<unsigned long long *>(res);
+        for (uint32_t k = threadIdx.x; k < sizeof(BfsResult) / 8; k += BLOCK) r8[k] = 0ull;
+        __syncthreads();
+        if (threadIdx.x == 0) res->t_entry = t_entry;
     }
     bool ok = dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns);
     const uint64_t t_start = dev::globaltimer_ns();
@@ -353,11 +428,14 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
         if (pull) {
             if (threadIdx.x == 0) { s_exam = 0; s_cnt = 0; s_deg = 0; }
             __syncthreads();
-            // candidates: the live vertices for the first pull, then what the previous pull left
+            // candidates: all live ones for the first pull, then what the previous pull left;
+            // with the live table a candidate is a live-list index, otherwise a vertex
             const uint32_t *Lin;
             uint32_t nin;
             if (npull == 0) {
-                Lin = a.live;
+                // every candidate once: the live-list indices 0..count-1 (with
+                // the live table), otherwise the vertices 0..n-1
+                Lin = nullptr;
                 nin = a.live ? ldcg(a.live_count) : a.n;
             } else {
                 Lin = a.ul[(npull - 1) & 1];
@@ -395,20 +473,22 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
         res->t_end = dev::globaltimer_ns();
         if (d < GBX_MAX_LEVEL_LOG) res->lv_ns[d] = res->t_end;
     }
-    // ---- vertices never reached get level and parent -1
-    // (a warp per bitmap word: one broadcast load, 32 coalesced stores)
+    // ---- vertices never reached get level and parent -1: each lane loads
+    // one visited word, then the warp walks its 32 words with one broadcast
+    // and one coalesced store per word (a single dependent load per warp)
     if (ok) {
         const int lane = threadIdx.x & 31;
         const uint64_t nwarps = (uint64_t)gridDim.x * WARPS;
-        uint64_t w = (uint64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
-        for (; w < a.nwords; w += 4 * nwarps) {
-            uint32_t bits[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) bits[k] = w + k * nwarps < a.nwords ? ldcg(&a.visited[w + k * nwarps]) : ~0u;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (!((bits[k] >> lane) & 1u)) {
-                    uint64_t v = (w + k * nwarps) * 32 + lane;
+        for (uint64_t w0 = ((uint64_t)blockIdx.x * WARPS + (threadIdx.x >> 5)) * 32; w0 < a.nwords;
+             w0 += nwarps * 32) {
+            const uint32_t mine = w0 + lane < a.nwords ? ldcg(&a.visited[w0 + lane]) : ~0u;
+            uint32_t todo = __ballot_sync(0xffffffffu, mine != ~0u);
+            while (todo) {
+                const int k = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const uint32_t bits = __shfl_sync(0xffffffffu, mine, k);
+                if (!((bits >> lane) & 1u)) {
+                    const uint64_t v = (w0 + k) * 32 + lane;
                     a.levels[v] = -1;
                     if (a.parents) a.parents[v] = -1;
                 }
@@ -519,6 +599,9 @@ gb_info bfs_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *l
     a.qr[0] = w->qr; a.qr[1] = w->qr + A->nrows + 1;
     a.live = A->has_csc ? A->live_list : nullptr;
     a.live_count = A->has_csc ? A->live_count : nullptr;
+    a.live_head = a.live ? A->live_head : nullptr;
+    a.live_len = a.live ? A->live_len : nullptr;
+    a.live_deg = a.live ? A->live_deg : nullptr;
     a.ul[0] = w->ul; a.ul[1] = w->ul + A->nrows + 1;
     a.ebits = 64 - bits_for((uint64_t)A->nrows + 1);
     a.emask = (a.ebits >= 64) ? ~0ull : ((1ull << a.ebits) - 1);
@@ -690,6 +773,8 @@ extern "C" gb_info gb_bfs_noalloc(const uint32_t *rowptr, const uint32_t *colidx
     a.qr[0] = (uint32_t *)(base + OFF_QR); a.qr[1] = a.qr[0] + n + 1;
     a.live = nullptr;            // no cached list here: the first pull takes every vertex
     a.live_count = nullptr;
+    a.live_head = nullptr;
+    a.live_len = a.live_deg = nullptr;
     a.ul[0] = (uint32_t *)(base + OFF_UL); a.ul[1] = a.ul[0] + n + 1;
     a.ebits = 64 - bits_for((uint64_t)n + 1);
     a.emask = (1ull << a.ebits) - 1;

@@ -24,6 +24,8 @@ struct BfsResult {
     unsigned long long lv_ns[GBX_MAX_LEVEL_LOG];    // %globaltimer at each level start
 };
 
+static_assert(sizeof(BfsResult) % 8 == 0, "BfsResult is zeroed in 8-byte words");
+
 // Working state. It is all zero when a launch starts: the last block to
 // leave a launch zeroes it again (so no memset is needed between launches).
 struct BfsState {
@@ -51,6 +53,9 @@ struct BfsArgs {
     uint32_t *q[2], *qp[2], *qr[2];    // frontier list: vertex, out-edge prefix, row start
     const uint32_t *live;              // vertices with an in-edge (ascending); null = all vertices
     const uint32_t *live_count;        // device scalar: length of live
+    const uint4 *live_head;            // per live entry: first four in-neighbours (0xffffffff = none)
+    const uint32_t *live_len;          // per live entry: in-degree
+    const uint32_t *live_deg;          // per live entry: out-degree
     uint32_t *ul[2];                   // candidate lists of the pull steps (unvisited, with in-edges)
     int ebits;
     unsigned long long emask;

@@ -88,6 +88,11 @@ struct gb_matrix_t {
     // built with the CSC; live_count is a device scalar (live_list[nrows])
     uint32_t *live_list = nullptr;
     uint32_t *live_count = nullptr;
+    // per live vertex, in live-list order: its first four in-neighbours
+    // (0xffffffff past the end of the row), its in-degree, its out-degree
+    uint4 *live_head = nullptr;
+    uint32_t *live_len = nullptr;
+    uint32_t *live_deg = nullptr;    // == live_len for a symmetric matrix
     // guards the caches built on first use (hub list)
     std::mutex cache_mu;
 };

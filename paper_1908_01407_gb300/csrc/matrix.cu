@@ -58,7 +58,12 @@ void release(gb_matrix *A) {
     dfree(ctx, A->colptr); dfree(ctx, A->rowidx); dfree(ctx, A->cvals);
     dfree(ctx, A->hub_list); dfree(ctx, A->hub_pre);
     dfree(ctx, A->live_list);
+    dfree(ctx, A->live_head);
+    dfree(ctx, A->live_len);
+    if (A->live_deg != A->live_len) dfree(ctx, A->live_deg);
     A->live_list = A->live_count = nullptr;
+    A->live_head = nullptr;
+    A->live_len = A->live_deg = nullptr;
     A->hub_list = A->hub_pre = nullptr;
     A->nhub = 0; A->hub_edges = 0; A->hub_ready = false;
     A->rowptr = A->colidx = A->colptr = A->rowidx = nullptr;
@@ -83,10 +88,29 @@ __global__ void k_live_emit(const uint32_t *flag, const uint32_t *pos, uint32_t 
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n && flag[i]) list[pos[i]] = i;
 }
+__global__ void k_live_table(const uint32_t *list, const uint32_t *count, const uint32_t *colptr,
+                             const uint32_t *rowidx, const uint32_t *rowptr, uint4 *head, uint32_t *len,
+                             uint32_t *deg) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *count) return;
+    const uint32_t v = list[i];
+    const uint32_t b = colptr[v], l = colptr[v + 1] - b;
+    uint4 h;
+    h.x = rowidx[b];
+    h.y = l > 1 ? rowidx[b + 1] : 0xffffffffu;
+    h.z = l > 2 ? rowidx[b + 2] : 0xffffffffu;
+    h.w = l > 3 ? rowidx[b + 3] : 0xffffffffu;
+    head[i] = h;
+    len[i] = l;
+    if (deg != len) deg[i] = rowptr[v + 1] - rowptr[v];
+}
 }  // namespace
 
 // The ascending list of vertices with a nonempty CSC row (an in-edge): the
-// only vertices a pull step can ever reach. Its length stays on the device.
+// only vertices a pull step can ever reach, with, in list order, each one's
+// first four in-neighbours, in-degree and out-degree (so a pull over the
+// list reads its candidates with coalesced loads and needs the row pointers
+// only for rows longer than four). The list length stays on the device.
 gb_info matrix_live(gb_matrix *A) {
     gb_context *ctx = A->ctx;
     const uint32_t n = A->ncols;
@@ -98,6 +122,13 @@ gb_info matrix_live(gb_matrix *A) {
     if (n) k_live_flags<<<nblk(n), 256, 0, ctx->stream>>>(A->colptr, n, flag.as<uint32_t>());
     GB_CHECK(scan_exclusive_u32(ctx, flag.as<uint32_t>(), pos.as<uint32_t>(), n, A->live_count));
     if (n) k_live_emit<<<nblk(n), 256, 0, ctx->stream>>>(flag.as<uint32_t>(), pos.as<uint32_t>(), n, A->live_list);
+    GB_CHECK(dalloc_t(ctx, &A->live_head, (size_t)n + 1));
+    GB_CHECK(dalloc_t(ctx, &A->live_len, (size_t)n + 1));
+    if (A->csc_alias) A->live_deg = A->live_len;
+    else GB_CHECK(dalloc_t(ctx, &A->live_deg, (size_t)n + 1));
+    if (n)
+        k_live_table<<<nblk(n), 256, 0, ctx->stream>>>(A->live_list, A->live_count, A->colptr, A->rowidx, A->rowptr,
+                                                       A->live_head, A->live_len, A->live_deg);
     GB_LAUNCH_CHECK();
     return GB_SUCCESS;
 }
