@@ -4,7 +4,7 @@ seed 2) from 64 seeded random non-isolated sources, one GB300.
 
 A step = one BFS from each of the 64 sources (the Graph500-style batch);
 value = 64 * m_stored / step time in GTEPS (TEPS counts stored nonzeros as
-the paper's Table 9 does), which equals the harmonic mean of the per-BFS
+the paper's Table 12 does), which equals the harmonic mean of the per-BFS
 TEPS. The graph (0.5 GB of column indices) is larger than the 129 MB L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]

@@ -4,13 +4,13 @@ This module holds no arithmetic of the graph method itself: it emits edge
 tuples (R-MAT or a 2-D grid with random edge deletions) and chooses source
 vertices. Each side then builds its own matrix from the tuples.
 
-Input recipe (the workloads of the paper's Section 7, re-created
+Input recipe (the workloads of the paper's Section 8, re-created
 synthetically because the real datasets are not available):
 
-* R-MAT with a=0.57, b=0.19, c=0.19, d=0.05 (Section 7, dataset paragraph),
+* R-MAT with a=0.57, b=0.19, c=0.19, d=0.05 (Section 8, dataset paragraph),
   2^scale vertices, edgefactor * 2^scale generated edges, a seeded random
   vertex permutation, self-loops dropped, both directions emitted
-  (the paper's datasets are undirected without self-loops, Table 12
+  (the paper's datasets are undirected without self-loops, Table 11
   caption). Duplicates are left for the matrix build to remove.
 * Grid: rows x cols 4-neighbour lattice, each undirected edge deleted with
   probability p, weights uniform in [1, wmax]; a road-network stand-in.

@@ -10,7 +10,7 @@
  * be generated independently and in parallel with the same result.
  *
  * R-MAT (Chakrabarti, Zhan, Faloutsos 2004) with the paper's parameters
- * a=0.57 b=0.19 c=0.19 d=0.05 (Section 7, dataset paragraph). Quadrants are
+ * a=0.57 b=0.19 c=0.19 d=0.05 (Section 8, dataset paragraph). Quadrants are
  * chosen with integer thresholds floor(p * 2^32) so that no floating-point
  * rounding can make two machines disagree.
  */

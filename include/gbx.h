@@ -50,7 +50,7 @@ typedef enum {
 
 typedef enum { GB_HOST = 0, GB_DEVICE = 1 } gb_mem;
 
-/* Element types (the paper's Matrix<T>/Vector<T> template types, Section 3.4). */
+/* Element types (the paper's Matrix<T>/Vector<T> template types, Section 3.6). */
 typedef enum { GB_BOOL = 0, GB_INT32 = 1, GB_UINT32 = 2, GB_UINT64 = 3, GB_FP32 = 4, GB_FP64 = 5 } gb_type;
 
 /* Binary operators: accumulators, dup operators and eWise operators. */
@@ -60,15 +60,15 @@ typedef enum {
     GB_FIRST = 7, GB_SECOND = 8, GB_PAIR = 9, GB_MINUS = 10
 } gb_binop;
 
-/* Monoids of Table 4 (operator and identity). */
+/* Monoids of Table 5 (operator and identity). */
 typedef enum {
     GB_MONOID_PLUS = 0, GB_MONOID_TIMES = 1, GB_MONOID_MIN = 2, GB_MONOID_MAX = 3,
     GB_MONOID_LOR = 4, GB_MONOID_LAND = 5
 } gb_monoid;
 
-/* Semirings (add monoid, multiply operator): the five of Table 4, plus
+/* Semirings (add monoid, multiply operator): the five of Table 5, plus
  * min.second used by the connected-components listing (Appendix A.4) and
- * plus.pair used for triangle counting (Section 6.5). For integer types the
+ * plus.pair used for triangle counting (Section 7.5). For integer types the
  * "plus" of MIN_PLUS/MAX_PLUS saturates at the type's max/min, so the
  * identity behaves as infinity. Supported (semiring, type) pairs:
  *   PLUS_TIMES, MIN_PLUS, MIN_TIMES: INT32 UINT32 FP32 FP64
@@ -79,7 +79,7 @@ typedef enum {
     GB_MIN_TIMES = 4, GB_MIN_SECOND = 5, GB_PLUS_PAIR = 6
 } gb_semiring;
 
-/* Descriptor fields and values (Table 5; Descriptor::toggle, Section 3.4). */
+/* Descriptor fields and values (Table 6; Descriptor::toggle, Section 3.6). */
 typedef enum {
     GB_MASK = 0,        /* value: GB_DEFAULT, or a bitwise OR of GB_SCMP and GB_STRUCTURE */
     GB_OUTP = 1,        /* GB_DEFAULT or GB_REPLACE */
@@ -113,7 +113,7 @@ typedef struct gb_server_t gb_server;
 /* ---------------------------------------------------------------- context */
 
 /* Creates a context on CUDA device `device`, owning a device memory pool
- * (Section 5.1 keeps a pool of device memory for temporaries) and a stream
+ * (Section 6.1 keeps a pool of device memory for temporaries) and a stream
  * (default: a new non-blocking stream). */
 gb_info gb_init(int device, gb_context **ctx);
 /* Orders all later work on `stream` (a cudaStream_t, e.g. torch's current
@@ -140,11 +140,11 @@ const char *gb_version(void);
 
 /* ----------------------------------------------------------------- matrix */
 
-/* Table 2 "Matrix": an nrows x ncols matrix of `type`, initially empty. */
+/* Table 4 "Matrix": an nrows x ncols matrix of `type`, initially empty. */
 gb_info gb_matrix_new(gb_matrix **A, gb_context *ctx, gb_type type, uint64_t nrows, uint64_t ncols);
-/* Table 2 "build" (Section 4.3 storage): builds CSR and CSC from nvals
+/* Table 4 "build" (Section 4.3 storage): builds CSR and CSC from nvals
  * (row, col[, val]) tuples. vals == NULL builds a structural matrix whose
- * stored values are all 1 (Section 6.1 "structure-only"). Tuples with equal
+ * stored values are all 1 (Section 7.1 "structure-only"). Tuples with equal
  * (row, col) are combined with `dup` (PLUS/MIN/MAX/FIRST/SECOND/LOR/LAND;
  * FIRST/SECOND by tuple order). Columns within a row come out sorted.
  * rows/cols/vals live in `mem`. Index >= dimension: GB_INVALID_INDEX.
@@ -154,7 +154,7 @@ gb_info gb_matrix_build(gb_matrix *A, const uint32_t *rows, const uint32_t *cols
 gb_info gb_matrix_nrows(const gb_matrix *A, uint64_t *n);
 gb_info gb_matrix_ncols(const gb_matrix *A, uint64_t *n);
 gb_info gb_matrix_nvals(const gb_matrix *A, uint64_t *n);
-/* Table 2 "extractTuples": stored entries in CSR (row-major, sorted) order.
+/* Table 4 "extractTuples": stored entries in CSR (row-major, sorted) order.
  * *n_inout: capacity in, count out. vals may be NULL. */
 gb_info gb_matrix_extract_tuples(const gb_matrix *A, uint32_t *rows, uint32_t *cols, void *vals,
                                  uint64_t *n_inout, gb_mem mem);
@@ -162,27 +162,27 @@ gb_info gb_matrix_extract_tuples(const gb_matrix *A, uint32_t *rows, uint32_t *c
 gb_info gb_matrix_export_csr(const gb_matrix *A, uint32_t *rowptr, uint32_t *colidx, void *vals, gb_mem mem);
 /* Copies the CSC arrays: colptr[ncols+1], rowidx[nvals], vals[nvals] (may be NULL). */
 gb_info gb_matrix_export_csc(const gb_matrix *A, uint32_t *colptr, uint32_t *rowidx, void *vals, gb_mem mem);
-/* L = strictly lower triangle of A (entries with col < row), CSR + CSC (Section 6.5). */
+/* L = strictly lower triangle of A (entries with col < row), CSR + CSC (Section 7.5). */
 gb_info gb_matrix_tril(gb_matrix *L, const gb_matrix *A);
 /* B = A with vertex v renamed new_id[v], where the order is decreasing
- * degree, ties by lower old id (Section 6.5 sorts rows by nonzero count).
+ * degree, ties by lower old id (Section 7.5 sorts rows by nonzero count).
  * A must be square; new_id (nrows entries, may be NULL) receives the map. */
 gb_info gb_matrix_degree_order(gb_matrix *B, const gb_matrix *A, uint32_t *new_id, gb_mem mem);
 gb_info gb_matrix_free(gb_matrix **A);
 
 /* ----------------------------------------------------------------- vector */
 
-/* Table 2 "Vector": size n, no stored values. Storage holds a dense value
+/* Table 4 "Vector": size n, no stored values. Storage holds a dense value
  * array, a presence bitmap, and a sparse index list kept alongside
  * (Section 4.3: the backend switches dense/sparse; operand reuse). */
 gb_info gb_vector_new(gb_vector **v, gb_context *ctx, gb_type type, uint64_t n);
-/* Table 2 "build": stores vals[k] at idx[k] (vals == NULL stores 1);
+/* Table 4 "build": stores vals[k] at idx[k] (vals == NULL stores 1);
  * duplicates combined with dup. Previous contents are cleared. */
 gb_info gb_vector_build(gb_vector *v, const uint32_t *idx, const void *vals, uint64_t nvals,
                         gb_binop dup, gb_mem mem);
-/* Table 2 "buildDense": every position present with vals[i] (n entries). */
+/* Table 4 "buildDense": every position present with vals[i] (n entries). */
 gb_info gb_vector_build_dense(gb_vector *v, const void *vals, gb_mem mem);
-/* Table 2 "fill": every position present with *scalar (host pointer). */
+/* Table 4 "fill": every position present with *scalar (host pointer). */
 gb_info gb_vector_fill(gb_vector *v, const void *scalar);
 gb_info gb_vector_set_element(gb_vector *v, uint32_t idx, const void *scalar);
 /* GB_NO_VALUE if position idx holds no value. *out is a host pointer. */
@@ -196,9 +196,9 @@ gb_info gb_vector_extract_dense(const gb_vector *v, void *vals, uint8_t *present
                                 gb_mem mem);
 gb_info gb_vector_size(const gb_vector *v, uint64_t *n);
 gb_info gb_vector_nvals(const gb_vector *v, uint64_t *n);
-/* Table 2 "dup": *out becomes a new vector equal to v. */
+/* Table 4 "dup": *out becomes a new vector equal to v. */
 gb_info gb_vector_dup(gb_vector **out, const gb_vector *v);
-/* Table 2 "clear": no stored values. */
+/* Table 4 "clear": no stored values. */
 gb_info gb_vector_clear(gb_vector *v);
 gb_info gb_vector_free(gb_vector **v);
 
@@ -207,15 +207,15 @@ gb_info gb_vector_free(gb_vector **v);
 gb_info gb_desc_new(gb_desc **d);
 gb_info gb_desc_set(gb_desc *d, gb_field field, int value);
 gb_info gb_desc_get(const gb_desc *d, gb_field field, int *value);
-/* Descriptor::toggle (Section 3.4): GB_MASK flips GB_SCMP, GB_OUTP flips
+/* Descriptor::toggle (Section 3.6): GB_MASK flips GB_SCMP, GB_OUTP flips
  * GB_REPLACE, GB_INP0/GB_INP1 flip GB_TRAN. */
 gb_info gb_desc_toggle(gb_desc *d, gb_field field);
 gb_info gb_desc_free(gb_desc **d);
 
 /* ------------------------------------------------------------- operations */
 /*
- * Table 6 operations with the semantics of Section 3.2 (mask), Table 5
- * (descriptor) and the GraphBLAS C API for accum/replace (Section 3.4 notes
+ * Table 7 operations with the semantics of Section 3.2 (mask), Table 6
+ * (descriptor) and the GraphBLAS C API for accum/replace (Section 3.6 notes
  * the paper itself ignores accum and omits REPLACE; this library honours
  * both): with t the product,
  *   z = accum == GB_NOP ? t : accum(w, t)   (union of w and t)
@@ -227,18 +227,18 @@ gb_info gb_desc_free(gb_desc **d);
  * except that a structural matrix (built without values) acts as all-ones.
  */
 
-/* Table 6 mxv: w<mask> = accum(w, A (+).(x) u); GB_INP0 = GB_TRAN uses A^T.
+/* Table 7 mxv: w<mask> = accum(w, A (+).(x) u); GB_INP0 = GB_TRAN uses A^T.
  * Direction optimisation (Section 4): push = SpMSpV over the columns of A
  * (CSC) selected by u's stored entries; pull = SpMV over the rows of A
- * (CSR) the mask allows (Section 5.3 mask-first). GB_AUTO picks push when
- * the frontier's edge count |E_f| <= |E| / beta (Table 8). */
+ * (CSR) the mask allows (Section 5: mask first). GB_AUTO picks push when
+ * the frontier's edge count |E_f| <= |E| / beta (Table 9). */
 gb_info gb_mxv(gb_vector *w, const gb_vector *mask, gb_binop accum, gb_semiring s, const gb_matrix *A,
                const gb_vector *u, const gb_desc *desc);
-/* Table 6 vxm: w<mask> = accum(w, u (+).(x) A), i.e. w(j) = (+)_i u(i) (x) A(i,j);
+/* Table 7 vxm: w<mask> = accum(w, u (+).(x) A), i.e. w(j) = (+)_i u(i) (x) A(i,j);
  * identical to mxv with A transposed (Figure 4 caption). */
 gb_info gb_vxm(gb_vector *w, const gb_vector *mask, gb_binop accum, gb_semiring s, const gb_vector *u,
                const gb_matrix *A, const gb_desc *desc);
-/* Table 6 mxm with a mask (Section 5.4 masked SpGEMM, Section 6.5):
+/* Table 7 mxm with a mask (Section 6.3.4 masked SpGEMM, Section 7.5):
  * C<M> = accum(C, A (+).(x) B); GB_INP0/GB_INP1 = GB_TRAN transpose A/B.
  * Only the positions stored in M are computed (mask first): for each
  * M(i,j) the row A(i,:) is intersected with the column B(:,j). The mask must
@@ -246,17 +246,17 @@ gb_info gb_vxm(gb_vector *w, const gb_vector *mask, gb_binop accum, gb_semiring 
  * empty or have M's structure. */
 gb_info gb_mxm(gb_matrix *C, const gb_matrix *M, gb_binop accum, gb_semiring s, const gb_matrix *A,
                const gb_matrix *B, const gb_desc *desc);
-/* Table 6 eWiseAdd (union) and eWiseMult (intersection) of vectors with a
+/* Table 7 eWiseAdd (union) and eWiseMult (intersection) of vectors with a
  * binary operator. */
 gb_info gb_ewise_add(gb_vector *w, const gb_vector *mask, gb_binop accum, gb_binop op, const gb_vector *u,
                      const gb_vector *v, const gb_desc *desc);
 gb_info gb_ewise_mult(gb_vector *w, const gb_vector *mask, gb_binop accum, gb_binop op, const gb_vector *u,
                       const gb_vector *v, const gb_desc *desc);
-/* Table 6 reduce to scalar: monoid over the stored values (identity if none).
+/* Table 7 reduce to scalar: monoid over the stored values (identity if none).
  * *out (host) has the vector's type; accum combines with the prior *out. */
 gb_info gb_reduce_vector(void *out, gb_binop accum, gb_monoid m, const gb_vector *u);
 gb_info gb_reduce_matrix(void *out, gb_binop accum, gb_monoid m, const gb_matrix *A);
-/* Table 6 reduce to vector: w(i) = (+)_j A(i,j) (GB_INP0 = GB_TRAN: over columns). */
+/* Table 7 reduce to vector: w(i) = (+)_j A(i,j) (GB_INP0 = GB_TRAN: over columns). */
 gb_info gb_reduce_rows(gb_vector *w, const gb_vector *mask, gb_binop accum, gb_monoid m, const gb_matrix *A,
                        const gb_desc *desc);
 
@@ -283,15 +283,15 @@ typedef struct {
     float final_us;                             /* end of the last level to the kernel's exit */
 } gb_bfs_stats;
 
-/* Direction-optimised BFS (Algorithm 1, Section 6.1): levels[v] = hop count
+/* Direction-optimised BFS (Algorithm 1, Section 7.1): levels[v] = hop count
  * from src (src 0, unreachable -1; the paper's depth minus one), and, if
  * parents != NULL, a BFS-tree parent (parents[src] = src, unreachable -1).
  * A must be square and symmetric-or-CSC-built. levels/parents have nrows
  * entries in `mem`. stats may be NULL. desc: GB_DIRECTION, GB_SWITCH_BETA. */
 gb_info gb_bfs(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *levels, int32_t *parents,
                gb_mem mem, const gb_desc *desc, gb_bfs_stats *stats);
-/* Autotuner of the push/pull switch threshold (Table 8: pull iff
- * |E_f| > |E| / beta; Section 5.4 suggests Table 8 as a starting point for
+/* Autotuner of the push/pull switch threshold (Table 9: pull iff
+ * |E_f| > |E| / beta; Section 5.3 suggests Table 9 as a starting point for
  * finding the best threshold on given hardware). Runs gb_bfs from the k
  * given sources (host array) for each beta in {4, 6, ..., 128}, timed with
  * CUDA events, and stores the fastest beta on the matrix: later gb_bfs calls
@@ -325,27 +325,27 @@ gb_info gb_bfs_autotune(gb_context *ctx, gb_matrix *A, const uint32_t *srcs, uin
 gb_info gb_bfs_noalloc(const uint32_t *rowptr, const uint32_t *colidx, const uint32_t *colptr, const uint32_t *rowidx,
                        uint32_t n, uint64_t nnz, uint32_t src, int32_t *levels, int32_t *parents, void *stream);
 /* Multi-source BFS as Boolean SpMM over 64-bit bit-packed frontiers
- * (Section 3.3 multi-nodeset traversal; Section 8 matrix direction
+ * (Section 3.3 multi-nodeset traversal; Section 9 matrix direction
  * optimisation): k <= 64 sources, levels is k x nrows (row q = source q). */
 gb_info gb_bfs_multi(gb_context *ctx, const gb_matrix *A, const uint32_t *srcs, uint32_t k, int32_t *levels,
                      gb_mem mem, const gb_desc *desc, gb_bfs_stats *stats);
-/* SSSP (Section 6.2): adaptive Bellman-Ford by min.plus mxv restricted to
+/* SSSP (Section 7.2): adaptive Bellman-Ford by min.plus mxv restricted to
  * the vertices whose distance changed. A holds uint32 weights. dist[v] =
  * shortest distance (UINT32_MAX unreachable). iterations may be NULL. */
 gb_info gb_sssp(gb_context *ctx, const gb_matrix *A, uint32_t src, uint32_t *dist, gb_mem mem,
                 const gb_desc *desc, uint32_t *iterations);
-/* PageRank (Section 6.3), pull SpMV in FP32 with FP32 accumulation:
+/* PageRank (Section 7.3), pull SpMV in FP32 with FP32 accumulation:
  * p0 = 1/n; p' = (1-damping)/n + damping * (sum_{j in N(i)} p(j)/deg(j)
  * + dangling/n), exactly `iters` iterations; the per-iteration L1 residual
  * sum|p'-p| and the final normalisation are reduced in FP64.
  * rank[n] in `mem`; residuals[iters] (host, may be NULL). */
 gb_info gb_pagerank(gb_context *ctx, const gb_matrix *A, float damping, uint32_t iters, float *rank,
                     double *residuals, gb_mem mem);
-/* Connected components (Section 6.4) by min-label propagation
+/* Connected components (Section 7.4) by min-label propagation
  * (min.second mxv to a fixed point): labels[v] = smallest vertex id in v's
  * component. iterations may be NULL. */
 gb_info gb_cc(gb_context *ctx, const gb_matrix *A, uint32_t *labels, gb_mem mem, uint32_t *iterations);
-/* Triangle counting (Section 6.5) as the masked SpGEMM C<L> = L (+).(x) L
+/* Triangle counting (Section 7.5) as the masked SpGEMM C<L> = L (+).(x) L
  * over plus.pair, reduced on the fly: L is a strictly lower-triangular
  * matrix with CSR and CSC (gb_matrix_tril). *count (host) = number of
  * triangles. If C != NULL it also receives C's values in L's structure. */

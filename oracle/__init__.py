@@ -98,7 +98,7 @@ class CSR:
 
 
 def csr_build(nrows, rows, cols, vals=None, dup=DUP_FIRST, ncols=None) -> CSR:
-    """Sorted, de-duplicated CSR from tuples (Table 2 'build')."""
+    """Sorted, de-duplicated CSR from tuples (Table 4 'build')."""
     lib = _load()
     ncols = nrows if ncols is None else ncols
     rows = np.ascontiguousarray(rows, dtype=np.uint32)

@@ -2,14 +2,14 @@
 
 Semantics of the generic GraphBLAS operations as plain Python loops over
 dictionaries, for small inputs. Written from Section 3 of the GraphBLAST
-paper: semirings and monoids (Section 3.1.3-3.1.4, Table 4), masking and its
-structural complement (Section 3.2.1), the descriptor (Table 5), and the
-operations of Table 6 (mxv, vxm, mxm, eWiseAdd, eWiseMult, reduce).
+paper: semirings and monoids (Section 3.1.3-3.1.4, Table 5), masking and its
+structural complement (Section 3.2.1), the descriptor (Table 6), and the
+operations of Table 7 (mxv, vxm, mxm, eWiseAdd, eWiseMult, reduce).
 
 Readings where the paper is silent (also listed in the design notes):
-* accum: the paper ignores it (Section 3.4); here w = accum(w, t) on the
+* accum: the paper ignores it (Section 3.6); here w = accum(w, t) on the
   positions the mask lets through, as the GraphBLAS C API defines it.
-* REPLACE: the paper leaves it out (Section 3.4); here positions outside the
+* REPLACE: the paper leaves it out (Section 3.6); here positions outside the
   mask are cleared when it is set.
 * No mask allows every position; the complement of no mask allows none.
 * A matrix built without values is structural: every stored entry is 1.
@@ -81,7 +81,7 @@ MONOIDS = {
     "LAND": ("LAND", lambda t: cast(t, 1)),
 }
 
-# semiring: (add monoid, multiply op); Table 4 plus the two used by the
+# semiring: (add monoid, multiply op); Table 5 plus the two used by the
 # connected-components and triangle-counting listings (min.second, plus.pair)
 SEMIRINGS = {
     "PLUS_TIMES": ("PLUS", "TIMES"),
@@ -173,7 +173,7 @@ def _finish(w_e, t_e, allowed, accum, t, replace, keys):
 
 def mxv(w: Vec, mask: Vec | None, accum, sr, A: Mat, u: Vec, *, tran=False,
         structural=False, scmp=False, replace=False) -> Vec:
-    """w<mask> = accum(w, A (+).(x) u) (Table 6 mxv; TRAN uses A^T)."""
+    """w<mask> = accum(w, A (+).(x) u) (Table 7 mxv; TRAN uses A^T)."""
     if tran:
         A = A.T()
     t = w.t
@@ -206,7 +206,7 @@ def vxm(w: Vec, mask: Vec | None, accum, sr, u: Vec, A: Mat, *, tran=False,
 
 def mxm(C: Mat, M: Mat | None, accum, sr, A: Mat, B: Mat, *, tran0=False, tran1=False,
         structural=False, scmp=False, replace=False) -> Mat:
-    """C<M> = accum(C, A (+).(x) B) (Table 6 mxm; Section 5.4 masked SpGEMM)."""
+    """C<M> = accum(C, A (+).(x) B) (Table 7 mxm; Section 6.3.4 masked SpGEMM)."""
     if tran0:
         A = A.T()
     if tran1:
@@ -228,7 +228,7 @@ def mxm(C: Mat, M: Mat | None, accum, sr, A: Mat, B: Mat, *, tran0=False, tran1=
 
 def ewise_add(w: Vec, mask, accum, op, u: Vec, v: Vec, *, structural=False, scmp=False,
               replace=False) -> Vec:
-    """Union: op where both present, the present value otherwise (Table 6)."""
+    """Union: op where both present, the present value otherwise (Table 7)."""
     t = w.t
     prod = {}
     for i in set(u.e) | set(v.e):
@@ -243,7 +243,7 @@ def ewise_add(w: Vec, mask, accum, op, u: Vec, v: Vec, *, structural=False, scmp
 
 def ewise_mult(w: Vec, mask, accum, op, u: Vec, v: Vec, *, structural=False, scmp=False,
                replace=False) -> Vec:
-    """Intersection: op where both present (Table 6)."""
+    """Intersection: op where both present (Table 7)."""
     t = w.t
     prod = {i: BINOPS[op](t, cast(t, u.e[i]), cast(t, v.e[i])) for i in set(u.e) & set(v.e)}
     me = mask.e if mask is not None else None
@@ -252,7 +252,7 @@ def ewise_mult(w: Vec, mask, accum, op, u: Vec, v: Vec, *, structural=False, scm
 
 
 def reduce_vector(t, monoid, u: Vec):
-    """Monoid reduction of the stored values to a scalar (Table 6 reduce)."""
+    """Monoid reduction of the stored values to a scalar (Table 7 reduce)."""
     op, ident = MONOIDS[monoid]
     acc = ident(t)
     for i in sorted(u.e):
@@ -271,7 +271,7 @@ def reduce_matrix(t, monoid, A: Mat):
 def reduce_rows(w: Vec, mask, accum, monoid, A: Mat, *, tran=False, structural=False,
                 scmp=False, replace=False) -> Vec:
     """w(i) = (+)_j A(i, j) over stored entries, starting from the monoid's
-    identity; rows without entries give no value (Table 6 reduce to vector)."""
+    identity; rows without entries give no value (Table 7 reduce to vector)."""
     if tran:
         A = A.T()
     t = w.t

@@ -17,7 +17,7 @@
 #include <math.h>
 
 /* ------------------------------------------------------------------ */
-/* Matrix build (Section 4.3: CSR storage; Table 2 "build" with a dup  */
+/* Matrix build (Section 4.3: CSR storage; Table 4 "build" with a dup  */
 /* operator combining repeated (i, j) tuples).                          */
 /* ------------------------------------------------------------------ */
 enum { ORC_DUP_FIRST = 0, ORC_DUP_SECOND = 1, ORC_DUP_PLUS = 2, ORC_DUP_MIN = 3, ORC_DUP_MAX = 4 };
@@ -86,7 +86,7 @@ int64_t orc_csr_build(uint32_t nrows, uint32_t ncols, uint64_t ntup,
 }
 
 /* ------------------------------------------------------------------ */
-/* BFS (Algorithm 1; Section 6.1): depth of every vertex from s.        */
+/* BFS (Algorithm 1; Section 7.1): depth of every vertex from s.        */
 /* Plain FIFO-queue breadth-first search. level[s] = 0, unreachable -1  */
 /* (the paper counts the source as depth 1 and unvisited as 0; this is  */
 /* that value minus one).                                               */
@@ -123,7 +123,7 @@ static int has_edge(const uint64_t *rowptr, const uint32_t *colidx, uint32_t u, 
 }
 
 /*
- * Checks a BFS parent array against exact levels (Section 6.1: BFS yields
+ * Checks a BFS parent array against exact levels (Section 7.1: BFS yields
  * a spanning tree of shortest paths). Valid iff parent[s] = s, every reached
  * v != s has an edge (parent[v], v) with level[parent[v]] = level[v] - 1,
  * and unreached vertices have parent -1. Needs sorted CSR rows.
@@ -144,7 +144,7 @@ uint64_t orc_bfs_parent_violations(uint32_t n, const uint64_t *rowptr, const uin
 }
 
 /* ------------------------------------------------------------------ */
-/* SSSP (Section 6.2): exact shortest distances. The paper's adaptive   */
+/* SSSP (Section 7.2): exact shortest distances. The paper's adaptive   */
 /* Bellman-Ford converges to the shortest-path distances; the plain     */
 /* definition is Dijkstra's algorithm with a binary heap. Distances are */
 /* summed in 64 bits; unreachable = UINT32_MAX.                         */
@@ -215,7 +215,7 @@ int orc_sssp(uint32_t n, const uint64_t *rowptr, const uint32_t *colidx,
 }
 
 /* ------------------------------------------------------------------ */
-/* PageRank (Section 6.3): pull formulation, p' = (1-a)/n + a * (A^T   */
+/* PageRank (Section 7.3): pull formulation, p' = (1-a)/n + a * (A^T   */
 /* scaled p). Each vertex j shares p(j) equally among its deg(j)        */
 /* neighbours; the mass of vertices with no edges is spread uniformly   */
 /* (the paper leaves dangling vertices unaddressed; this reading keeps  */
@@ -246,7 +246,7 @@ void orc_pagerank(uint32_t n, const uint64_t *rowptr, const uint32_t *colidx,
 }
 
 /* ------------------------------------------------------------------ */
-/* Connected components (Section 6.4): label(v) = smallest vertex id in */
+/* Connected components (Section 7.4): label(v) = smallest vertex id in */
 /* v's component. Union-find with path halving, union by smaller root.  */
 /* ------------------------------------------------------------------ */
 static uint32_t uf_find(uint32_t *par, uint32_t x) {
@@ -265,7 +265,7 @@ void orc_cc(uint32_t n, const uint64_t *rowptr, const uint32_t *colidx, uint32_t
 }
 
 /* ------------------------------------------------------------------ */
-/* Triangle counting (Section 6.5): the number of vertex triples        */
+/* Triangle counting (Section 7.5): the number of vertex triples        */
 /* u < v < w with all three edges present. Node iterator over sorted    */
 /* adjacency: for every edge u < v, count common neighbours w > v.      */
 /* ------------------------------------------------------------------ */
@@ -288,7 +288,7 @@ uint64_t orc_tc(uint32_t n, const uint64_t *rowptr, const uint32_t *colidx) {
 }
 
 /*
- * Degree ordering for triangle counting (Section 6.5 sorts rows of L by
+ * Degree ordering for triangle counting (Section 7.5 sorts rows of L by
  * their number of nonzeros). Reading used here: new ids in order of
  * decreasing degree, ties broken by lower old id first. new_id[old] out.
  */
@@ -311,8 +311,8 @@ void orc_degree_order(uint32_t n, const uint64_t *rowptr, uint32_t *new_id) {
 
 /*
  * Entries of the masked product C<L> = L * L over (plus, pair) for a
- * symmetric graph given by its full sorted adjacency (Section 5.4 masked
- * SpGEMM; Section 6.5). L is the strictly lower triangle. For the k-th
+ * symmetric graph given by its full sorted adjacency (Section 6.3.4 masked
+ * SpGEMM; Section 7.5). L is the strictly lower triangle. For the k-th
  * stored entry (i, j), j < i, of L in row-major order:
  *   C(i,j) = |{k : L(i,k) != 0 and L(k,j) != 0}| = |{k : j < k < i, (i,k), (k,j) in E}|.
  * Writes nnz(L) counts; returns their sum.

@@ -1,19 +1,19 @@
-// Direction-optimised BFS (Algorithm 1, Section 6.1) as one persistent
+// Direction-optimised BFS (Algorithm 1, Section 7.1) as one persistent
 // cooperative kernel: every level runs either
 //   push  = SpMSpV over the out-edges (CSR rows) of the sparse frontier list,
 //           claiming unvisited vertices with atomicOr on the visited bitmap
-//           (the mask is applied before the write, not after: Section 5.3), or
+//           (the mask is tested before the write; Section 6.3.1's SpMSpV applies it after the product), or
 //   pull  = masked SpMV over the in-edges (CSC columns) of unvisited vertices
 //           only (mask first), stopping at the first frontier parent (the
-//           Boolean semiring's early exit, Table 3) and reading no values
+//           Boolean semiring's early exit, Section 7.1) and reading no values
 //           (structure only),
 // with the assign of the level, the frontier count and the next frontier's
-// edge count fused in. The direction rule is Table 8's: pull iff the
+// edge count fused in. The direction rule is Table 9's: pull iff the
 // frontier's edge count |E_f| > |E| / beta, with |E_f| exact (each appended
 // vertex carries an exclusive prefix of out-degrees, see below).
 //
 // Frontier representation: both a bitmap (for pull) and a list with edge
-// prefixes (for push) are produced every level (operand reuse, Section 6.1).
+// prefixes (for push) are produced every level (operand reuse, Section 7.1).
 // Appends use a single 64-bit atomicAdd on a packed (count, edge-sum) word,
 // so list positions and edge prefixes come out consistent and monotone: the
 // push of the next level balances its edges over the grid by a merge-path
@@ -790,7 +790,7 @@ extern "C" gb_info gb_bfs_noalloc(const uint32_t *rowptr, const uint32_t *colidx
     return GB_SUCCESS;
 }
 
-// Autotuner of the push/pull switch (Table 8's rule pull iff |E_f| > |E|/beta):
+// Autotuner of the push/pull switch (Table 9's rule pull iff |E_f| > |E|/beta):
 // times BFS from the given sources for each candidate beta with CUDA
 // events on the context stream and keeps the fastest on the matrix.
 extern "C" gb_info gb_bfs_autotune(gb_context *ctx, gb_matrix *A, const uint32_t *srcs, uint32_t k,

@@ -125,7 +125,7 @@ namespace gbx {
 size_t type_size(gb_type t);
 bool valid_type(int t);
 
-// Stream-ordered pool allocations on the context stream (Section 5.1 keeps
+// Stream-ordered pool allocations on the context stream (Section 6.1 keeps
 // a pool of device memory; here the CUDA stream-ordered pool backs it).
 gb_info dalloc(gb_context *ctx, void **p, size_t bytes);
 void dfree(gb_context *ctx, void *p);

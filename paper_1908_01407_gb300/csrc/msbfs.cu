@@ -1,6 +1,6 @@
 // Multi-source BFS as a Boolean SpMM over 64-bit bit-packed frontiers
 // (Section 3.3: mxm is a traversal from several independent sets of active
-// vertices at once; Section 8 proposes direction optimisation for it). Up to
+// vertices at once; Section 9 proposes direction optimisation for it). Up to
 // 64 BFS share one launch: bit q of F[v] says that v is on source q's
 // frontier. Per level, either
 //   push: every vertex u on some frontier ORs F[u] into the next-frontier
@@ -9,7 +9,7 @@
 //   pull: every vertex v that some live source has not reached ORs the
 //         frontier words of its in-neighbours, stopping as soon as all live
 //         sources are covered (the Boolean early exit, per 64 searches),
-// chosen by the rule of Table 8 on the union frontier's edge count. The
+// chosen by the rule of Table 9 on the union frontier's edge count. The
 // visited words are merged one level late (V | F is the visited set), so a
 // level needs a single grid barrier.
 #include "common.cuh"

@@ -1,7 +1,7 @@
-// Table 6 operations at the C ABI: mxv, vxm, mxm, eWiseAdd, eWiseMult and
+// Table 7 operations at the C ABI: mxv, vxm, mxm, eWiseAdd, eWiseMult and
 // reduce, with the mask / accumulator / REPLACE semantics of Section 3.2
 // and the GraphBLAS C API (see gbx.h), and the direction choice of
-// Section 4 (Table 8) for mxv/vxm.
+// Section 4 (Table 9) for mxv/vxm.
 #include "ops_impl.cuh"
 #include "vector_impl.cuh"
 
@@ -318,7 +318,7 @@ gb_info mxv_common(gb_vector *w, const gb_vector *mask, gb_binop accum, gb_semir
     p.uvals = u->vals;
     p.ubits = u->bitmap;
     bool can_pull = p.p_ptr != nullptr, can_push = p.s_ptr != nullptr;
-    // direction (Table 8): push iff |E_f| ~ d * nnz(u) <= |E| / beta
+    // direction (Table 9): push iff |E_f| ~ d * nnz(u) <= |E| / beta
     uint64_t ulen = 0;
     GB_CHECK(vector_list(const_cast<gb_vector *>(u), &ulen));
     bool push;
@@ -462,7 +462,7 @@ gb_info gb_reduce_rows(gb_vector *w, const gb_vector *mask, gb_binop accum, gb_m
 gb_info gb_mxm(gb_matrix *C, const gb_matrix *M, gb_binop accum, gb_semiring s, const gb_matrix *A,
                const gb_matrix *B, const gb_desc *desc) {
     if (!C || !A || !B) return fail(GB_NULL_POINTER, "gb_mxm: NULL argument");
-    if (!M) return fail(GB_NOT_IMPLEMENTED, "gb_mxm: only the masked product (Section 5.4) is provided");
+    if (!M) return fail(GB_NOT_IMPLEMENTED, "gb_mxm: only the masked product (Section 6.3.4) is provided");
     if (!A->built || !B->built || !M->built) return fail(GB_INVALID_VALUE, "gb_mxm: an input is not built");
     if (!valid_accum(accum)) return fail(GB_INVALID_VALUE, "gb_mxm: bad accumulator");
     if (s < GB_PLUS_TIMES || s > GB_PLUS_PAIR) return fail(GB_INVALID_VALUE, "gb_mxm: bad semiring");

@@ -1,7 +1,7 @@
 // Generic masked semiring matrix-vector and matrix-matrix kernels
 // (Sections 4-5): mxv/vxm as pull (masked SpMV, mask first, Boolean early
 // exit) or push (SpMSpV over the stored entries of u, the mask tested
-// before the atomic write), and the masked SpGEMM of Section 5.4.
+// before the atomic write), and the masked SpGEMM of Section 6.3.4.
 #pragma once
 
 #include "common.cuh"
@@ -155,7 +155,7 @@ gb_info mxv_run(const MxvPlan &p) {
 
 // masked SpGEMM: a warp per row i of M; for each M(i,j) the lanes take the
 // entries of the shorter of A(i,:), B(:,j) and binary-search them in the
-// longer (Section 6.5: repeated binary search from the shorter list)
+// longer (Section 7.5: repeated binary search from the shorter list)
 __device__ __forceinline__ bool bsearch_u32(const uint32_t *a, uint32_t lo, uint32_t hi, uint32_t x, uint32_t *pos) {
     while (lo < hi) {
         uint32_t mid = (lo + hi) >> 1;

@@ -1,8 +1,8 @@
-// PageRank (Section 6.3), pull formulation, in FP32 with FP32 accumulation:
+// PageRank (Section 7.3), pull formulation, in FP32 with FP32 accumulation:
 //   p'(i) = (1 - a)/n + a * ( sum_{j in N(i)} p(j)/deg(j) + D/n ),
 // D = sum of p over vertices without edges (spread uniformly), p0 = 1/n,
 // a fixed number of iterations. The SpMV is merge-path load balanced
-// (Section 5.3.2; Merrill and Garland's 2-D diagonal split of row ends
+// (Section 6.3.2; Merrill and Garland's 2-D diagonal split of row ends
 // against nonzeros): every block gets an equal share of the merged
 // sequence, so rows of any length cost the same per item. The update is
 // fused into the SpMV's row epilogue, which also writes x' = p'/deg for the

@@ -1,16 +1,16 @@
 // Min-relaxation over a frontier of changed vertices, as one persistent
-// cooperative kernel (the loop of Section 6.2 run on the device):
-//  * SSSP, adaptive Bellman-Ford with sparsification (Section 6.2):
+// cooperative kernel (the loop of Section 7.2 run on the device):
+//  * SSSP, adaptive Bellman-Ford with sparsification (Section 7.2):
 //      dist(v) <- min(dist(v), min_{u in F, (u,v) in E} dist(u) + w(u,v))
 //    over the min.plus semiring (saturating add, UINT32_MAX = infinity);
 //  * connected components by min-label propagation (min.second):
 //      label(v) <- min(label(v), min_{u in F, (u,v) in E} label(u)),
 //    labels starting at the vertex ids, every vertex active at first.
 // The next frontier is exactly the set of vertices whose value decreased
-// (the sparsification step: Section 6.2 keeps only vertices that improved).
+// (the sparsification step: Section 7.2 keeps only vertices that improved).
 // Each iteration is a push (merge-path over the frontier's out-edges,
 // atomicMin into the target) or a pull (every vertex scans its in-edges,
-// taking only frontier sources into account) by the rule of Table 8. The
+// taking only frontier sources into account) by the rule of Table 9. The
 // loop ends when no value changes, which is the exact fixed point.
 #include "common.cuh"
 #include "bfs_common.cuh"

@@ -1,11 +1,11 @@
-// Triangle counting (Section 6.5) as the masked SpGEMM C<L> = L (+).(x) L
-// over (plus, pair) (Section 5.4), reduced on the fly: for every stored
+// Triangle counting (Section 7.5) as the masked SpGEMM C<L> = L (+).(x) L
+// over (plus, pair) (Section 6.3.4), reduced on the fly: for every stored
 // L(i,j), C(i,j) = |row_i(L) intersect col_j(L)|, computed by binary
 // search of the shorter list's entries in the longer one. With L strictly
 // lower triangular each triangle {k < j < i} is counted once, at (i, j)
 // through its middle vertex k... in the L*L form, at (i,j) with j < k < i.
 // The per-entry counts are optionally written (the C of the paper); the
-// total is reduced in uint64 without writing C at all (the fusion Section 7
+// total is reduced in uint64 without writing C at all (the fusion Section 8.3
 // names as the gap to hardwired code).
 #include "common.cuh"
 #include "ops_impl.cuh"

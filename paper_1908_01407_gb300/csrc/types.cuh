@@ -1,5 +1,5 @@
 // Element types, binary operators, monoids and semirings as __device__
-// functors (Section 5.2: semirings and monoids are __host__ __device__
+// functors (Section 6.2: semirings and monoids are __host__ __device__
 // functors carrying an identity; here they are compile-time template
 // parameters of the kernels and selected at the C ABI by enum).
 #pragma once

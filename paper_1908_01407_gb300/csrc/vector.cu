@@ -1,4 +1,4 @@
-// Vector objects (Table 2): a dense value array plus a presence bitmap,
+// Vector objects (Table 4): a dense value array plus a presence bitmap,
 // with a sorted index list built on demand (Section 4.3: the backend keeps
 // both dense and sparse forms and switches between them).
 #include "common.cuh"

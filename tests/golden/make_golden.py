@@ -23,7 +23,7 @@ def main():
     with open(os.path.join(HERE, "tc_rmat_s20.txt"), "w") as f:
         f.write("# Triangle count of R-MAT scale 20, edge factor 16, seed 4 (a=.57 b=.19 c=.19 d=.05,\n"
                 "# symmetrised, self-loops and duplicates removed), by the oracle's node iterator\n"
-                "# (Section 6.5 counts triangles as the reduction of the masked product).\n"
+                "# (Section 7.5 counts triangles as the reduction of the masked product).\n"
                 "# Written by tests/golden/make_golden.py.\n")
         f.write(f"n: {g.n}\nm_stored: {g.m}\ntriangles: {count}\n")
     print(f"tc_rmat_s20: {count} ({time.time() - t0:.0f} s)")

@@ -70,7 +70,7 @@ def test_null_arguments_return_codes_not_crashes(L):
 
 def test_teps_metric_matches_paper_table9():
     from tests.conftest import read_golden
-    f = read_golden("table9_bfs_teps.txt")
+    f = read_golden("table12_bfs_teps.txt")
     got = gb.teps(float(f["edges"]), float(f["runtime_ms"]) / 1e3) / 1e6
     want = float(f["mteps"])
     assert abs(got - want) / want < float(f["rel_tol"])

@@ -1,5 +1,5 @@
 """The seeded input generators: determinism and the structural properties
-the paper's datasets have (undirected, no self-loops; Table 12 caption)."""
+the paper's datasets have (undirected, no self-loops; Table 11 caption)."""
 import numpy as np
 
 import gen

@@ -184,7 +184,7 @@ def test_csr_only_matrix_falls_back_to_the_available_direction(ctx):
 
 
 def test_running_example_on_gpu():
-    """The paper's running example (Section 3.3) through vxm with the
+    """The paper's running example (Section 3.4) through vxm with the
     complemented visited mask."""
     from tests.conftest import read_golden
     import torch

@@ -526,7 +526,7 @@ def test_running_example_masked_vxm():
     assert sorted(nb.e) == [int(x) for x in f["neighbours_of_frontier"].split()]
     nxt = gbo.vxm(gbo.Vec(n, "bool"), v, None, "LOR_LAND", u, A, scmp=True)
     assert sorted(nxt.e) == [int(x) for x in f["next_frontier"].split()]
-    # Table 6 costs: SpMSpV reads the columns of the frontier, the mask-first
+    # Table 8 costs: SpMSpV reads the columns of the frontier, the mask-first
     # SpMV reads the rows (of A^T) of the unvisited vertices, GEMV reads n^2
     assert sum(1 for (i, j) in edges if i in fr) == int(f["spmspv_loads"])
     unvisited = set(range(n)) - set(vis)
