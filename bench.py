@@ -95,6 +95,44 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.samples)}
 
 
+# Sources of the BFS kernel whose code (comments and blank lines aside) the
+# DRAM traffic record in the kernel's profile summary was measured on.
+BFS_KERNEL_SOURCES = ["paper_1908_01407_gb300/csrc/bfs.cu", "paper_1908_01407_gb300/csrc/bfs_common.cuh",
+                      "paper_1908_01407_gb300/csrc/frontier.cuh", "paper_1908_01407_gb300/csrc/common.cuh"]
+BFS_PROFILE = "profiles/k_bfs_rmat_s22.md"
+
+
+def code_digest(paths, root=ROOT):
+    """sha256 of the code of `paths` with comments and blank lines removed."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for p in paths:
+        src = open(os.path.join(root, p)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for line in src.splitlines():
+            line = line.strip()
+            if line:
+                h.update(line.encode() + b"\n")
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(profile, sources):
+    """DRAM bytes per launch from a profile summary's `traffic-record` line,
+    or None when the kernel's code changed since that capture."""
+    try:
+        text = open(os.path.join(ROOT, profile)).read()
+    except OSError:
+        return None
+    for line in text.splitlines():
+        if line.startswith("traffic-record:"):
+            kv = dict(x.split("=", 1) for x in line.split(":", 1)[1].split())
+            if kv.get("digest") == code_digest(sources):
+                return float(kv["bytes_per_launch"])
+    return None
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -256,7 +294,8 @@ def run_gbx(args):
                    "beta": args.beta or tuned_beta, "beta_from": "fixed" if args.beta else "autotuner"},
         "gpu_launches": int(args.steps * NSRC),
         "roofline": {"bound": "hbm", "kernel": "k_bfs", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
+                     "frac": achieved / hbm, "peak_kind": peak_kind,
+                     "traffic": recorded_traffic(BFS_PROFILE, BFS_KERNEL_SOURCES),
                      "alg_bytes_per_launch": alg_per_bfs, "avg_launch_ms": avg_kernel_ms},
         "e2e": {"value": e2e_val, "unit": "GTEPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": int(NSRC * 2 * 4 * n)},

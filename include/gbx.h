@@ -125,6 +125,15 @@ gb_info gb_context_pool_stats(gb_context *ctx, uint64_t *held_bytes, uint64_t *p
 /* Fault injection for tests: the next `count` pool allocations fail with
  * GB_OUT_OF_MEMORY (host-side; no GPU fault). */
 gb_info gb_context_inject_alloc_failures(gb_context *ctx, uint32_t count);
+/* Self-test of the bounded device waits that every persistent kernel uses
+ * (their grid barriers): launches one block that waits at a barrier sized
+ * for two blocks, so the wait can only run out. After limit_us (clamped to
+ * 1..1,000,000) the block records GB_TIMEOUT in its status word and leaves;
+ * *status receives that word (GB_TIMEOUT on a correct wait). Returns
+ * GB_SUCCESS when the kernel finished and the context is still usable. The
+ * paper has no counterpart: it is how failure handling is tested without a
+ * GPU fault. */
+gb_info gb_context_selftest_wait(gb_context *ctx, uint32_t limit_us, int32_t *status);
 /* Kernel timing: while enabled, each operation records a pair of CUDA
  * events on the context stream around its main kernel launch. Enabling or
  * disabling clears earlier records. profile_get sums the recorded spans of

@@ -102,6 +102,7 @@ _PP = ctypes.POINTER(ctypes.c_void_p)
 _SIGS = {
     "gb_init": [_I, _PP], "gb_context_set_stream": [_P, _P], "gb_context_synchronize": [_P],
     "gb_context_pool_stats": [_P, _P, _P], "gb_context_inject_alloc_failures": [_P, _U32],
+    "gb_context_selftest_wait": [_P, _U32, _P],
     "gb_finalize": [_P], "gb_context_profile": [_P, _I],
     "gb_context_profile_get": [_P, ctypes.c_char_p, _P, _P], "gb_last_error": [ctypes.c_char_p, ctypes.c_size_t],
     "gb_matrix_new": [_PP, _P, _I, _U64, _U64],
@@ -243,6 +244,13 @@ class Context:
 
     def inject_alloc_failures(self, count: int):
         check(lib().gb_context_inject_alloc_failures(self.h, count))
+
+    def selftest_wait(self, limit_us: int) -> int:
+        """Run the bounded-wait self-test; returns the status word the
+        waiting block recorded (TIMEOUT when the wait ran out as it must)."""
+        st = ctypes.c_int32(-1)
+        check(lib().gb_context_selftest_wait(self.h, limit_us, ctypes.byref(st)))
+        return st.value
 
     def close(self):
         if self.h:

@@ -221,6 +221,34 @@ gb_info gb_context_inject_alloc_failures(gb_context *ctx, uint32_t count) {
     return GB_SUCCESS;
 }
 
+namespace {
+struct WaitProbe {
+    gbx::dev::GridBarrier bar;
+    int err;
+};
+// One block waiting at a barrier of two: the bounded wait must run out.
+__global__ void k_selftest_wait(WaitProbe *p, uint64_t limit_ns) {
+    gbx::dev::grid_sync(&p->bar, 2u, &p->err, limit_ns);
+}
+}  // namespace
+
+gb_info gb_context_selftest_wait(gb_context *ctx, uint32_t limit_us, int32_t *status) {
+    if (!ctx || !status) return fail(GB_NULL_POINTER, "gb_context_selftest_wait: NULL argument");
+    if (limit_us < 1) limit_us = 1;
+    if (limit_us > 1000000u) limit_us = 1000000u;
+    GB_CUDA(cudaSetDevice(ctx->device));
+    Scratch probe(ctx);
+    GB_CHECK(probe.alloc(sizeof(WaitProbe)));
+    GB_CHECK(memset_async(ctx, probe.p, 0, sizeof(WaitProbe)));
+    k_selftest_wait<<<1, 32, 0, ctx->stream>>>(probe.as<WaitProbe>(), (uint64_t)limit_us * 1000ull);
+    GB_LAUNCH_CHECK();
+    int32_t err = 0;
+    GB_CUDA(cudaMemcpyAsync(&err, &probe.as<WaitProbe>()->err, sizeof(err), cudaMemcpyDeviceToHost, ctx->stream));
+    GB_CHECK(sync(ctx));
+    *status = err;
+    return GB_SUCCESS;
+}
+
 gb_info gb_context_profile(gb_context *ctx, int enable) {
     if (!ctx) return fail(GB_NULL_POINTER, "gb_context_profile: ctx is NULL");
     GB_CUDA(cudaSetDevice(ctx->device));
