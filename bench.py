@@ -404,6 +404,10 @@ def extra_rows(args, hbm):
     its = []
     ms = cuda_time_ms(lambda: its.append(gb.cc(ctx, A, d)[1]), stream)
     g_out.update({"cc_ms": ms, "cc_iterations": its[0]})
+    its = []
+    gb.cc_fastsv(ctx, A, d)
+    ms = cuda_time_ms(lambda: its.append(gb.cc_fastsv(ctx, A, d)[1]), stream)
+    g_out.update({"cc_fastsv_ms": ms, "cc_fastsv_iterations": its[0]})
     out["grid_4096"] = g_out
     A.free()
     ctx.close()

@@ -354,6 +354,17 @@ gb_info gb_pagerank(gb_context *ctx, const gb_matrix *A, float damping, uint32_t
  * (min.second mxv to a fixed point): labels[v] = smallest vertex id in v's
  * component. iterations may be NULL. */
 gb_info gb_cc(gb_context *ctx, const gb_matrix *A, uint32_t *labels, gb_mem mem, uint32_t *iterations);
+/* Connected components by FastSV (Section 7.4: the paper's CC algorithm):
+ * per iteration mngf = A min.second gf, stochastic hooking
+ * f(f(u)) = min(f(f(u)), mngf(u)), aggressive hooking and shortcut
+ * f(u) = min(f(u), mngf(u), gf(u)), grandparents gf = f(f), until gf stops
+ * changing. labels[v] = smallest vertex id in v's component (the same
+ * result as gb_cc). A must be square and built symmetric or with its CSC;
+ * for a non-symmetric A the components are the weak ones (both edge
+ * directions). labels[nrows] in `mem`; *iterations (may be NULL) = FastSV
+ * iterations. GB_TIMEOUT if a bounded device wait or the iteration budget
+ * ran out; GB_INVALID_VALUE for a CSR-only matrix. */
+gb_info gb_cc_fastsv(gb_context *ctx, const gb_matrix *A, uint32_t *labels, gb_mem mem, uint32_t *iterations);
 /* Triangle counting (Section 7.5) as the masked SpGEMM C<L> = L (+).(x) L
  * over plus.pair, reduced on the fly: L is a strictly lower-triangular
  * matrix with CSR and CSC (gb_matrix_tril). *count (host) = number of

@@ -129,6 +129,7 @@ _SIGS = {
     "gb_bfs_autotune": [_P, _P, _P, _U32, _P, _P], "gb_bfs_multi": [_P, _P, _P, _U32, _P, _I, _P, _P],
     "gb_sssp": [_P, _P, _U32, _P, _I, _P, _P], "gb_pagerank": [_P, _P, ctypes.c_float, _U32, _P, _P, _I],
     "gb_cc": [_P, _P, _P, _I, _P], "gb_tc": [_P, _P, _P, _P],
+    "gb_cc_fastsv": [_P, _P, _P, _I, _P],
     "gb_server_create": [_PP, _P, _P], "gb_server_add_graph": [_P, _P, _P], "gb_server_submit": [_P, _P, _P],
     "gb_server_wait": [_P, _U64, _U32, _P], "gb_server_fetch": [_P, _U64, _P, _I],
     "gb_server_stats_get": [_P, _P], "gb_server_destroy": [_PP],
@@ -608,6 +609,18 @@ def pagerank(ctx, A, damping=0.85, iters=50, rank=None, residuals=True):
     res = np.empty(max(iters, 1), np.float64) if residuals else None
     check(lib().gb_pagerank(ctx.h, A.h, damping, iters, pr, res.ctypes.data if res is not None else None, mr))
     return rank, (res[:iters] if res is not None else None)
+
+
+def cc_fastsv(ctx, A, labels=None):
+    """Connected components by FastSV; returns (labels, iterations)."""
+    n = A.nrows
+    if labels is None:
+        torch = _torch()
+        labels = torch.empty(n, dtype=torch.int32, device=f"cuda:{ctx.device}")
+    pl, ml = _out_mem(labels)
+    it = ctypes.c_uint32()
+    check(lib().gb_cc_fastsv(ctx.h, A.h, pl, ml, ctypes.byref(it)))
+    return labels, it.value
 
 
 def cc(ctx, A, labels=None):

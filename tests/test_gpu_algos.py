@@ -96,6 +96,46 @@ def test_cc(ctx, case):
     A.free()
 
 
+@pytest.mark.parametrize("case", ["rmat14", "rmat_sparse", "grid", "small", "single", "path"])
+def test_cc_fastsv(ctx, case):
+    t = {"rmat14": lambda: gen.rmat(14, 16, seed=1),
+         "rmat_sparse": lambda: gen.rmat(13, 1, seed=9),
+         "grid": lambda: gen.grid(96, 80, 0.45, seed=3),
+         "small": lambda: gen.random_small(12, 0.15, 205),
+         "single": lambda: gen.from_edges(1, []),
+         "path": lambda: gen.from_edges(300, [(i + 1, i) for i in range(299)])}[case]()
+    g, A = build(ctx, t, weights=False)
+    want = oracle.cc(g)
+    lab = np.empty(t.n, np.uint32)
+    _, it = gb.cc_fastsv(ctx, A, lab)
+    assert np.array_equal(lab, want)
+    assert it >= 1
+    # device output buffer gives the same labels
+    dl = torch.empty(t.n, dtype=torch.int32, device="cuda")
+    gb.cc_fastsv(ctx, A, dl)
+    assert np.array_equal(dl.cpu().numpy().view(np.uint32), want)
+    A.free()
+
+
+def test_cc_fastsv_weak_components_and_errors(ctx):
+    """A directed matrix: components of the underlying undirected graph."""
+    rng = np.random.default_rng(8)
+    n = 2000
+    r = rng.integers(0, n, 1500).astype(np.uint32)
+    c = rng.integers(0, n, 1500).astype(np.uint32)
+    A = gb.Matrix.from_tuples(ctx, n, r, c)
+    g = oracle.csr_build(n, np.concatenate([r, c]), np.concatenate([c, r]))
+    lab = np.empty(n, np.uint32)
+    gb.cc_fastsv(ctx, A, lab)
+    assert np.array_equal(lab, oracle.cc(g))
+    A.free()
+    B = gb.Matrix.from_tuples(ctx, n, r, c, flags=gb.CSR_ONLY)
+    with pytest.raises(gb.GBError) as e:
+        gb.cc_fastsv(ctx, B, lab)
+    assert e.value.code == gb.INVALID_VALUE
+    B.free()
+
+
 # ---------------------------------------------------------------- PageRank
 @pytest.mark.parametrize("case", ["rmat14", "rmat12_e4", "grid", "star", "cycle"])
 def test_pagerank_l1_vs_fp64_oracle(ctx, case):
@@ -208,7 +248,10 @@ def test_grid_4096_bfs_sssp_cc_full_size(ctx):
     assert np.array_equal(got, oracle.sssp(g, src))
     lab = np.empty(t.n, np.uint32)
     gb.cc(ctx, A, lab)
-    assert np.array_equal(lab, oracle.cc(g))
+    want = oracle.cc(g)
+    assert np.array_equal(lab, want)
+    gb.cc_fastsv(ctx, A, lab)
+    assert np.array_equal(lab, want)
     A.free()
 
 
