@@ -137,11 +137,11 @@ __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Li
             h[j][0] = h[j][1] = h[j][2] = h[j][3] = NONE;
             if (c[j] != NONE) {
                 if (table) {
-                    v[j] = __ldg(&a.live[c[j]]);
-                    const uint4 hh = __ldg(&a.live_head[c[j]]);
+                    v[j] = ld_stream(&a.live[c[j]]);
+                    const uint4 hh = ld_stream(&a.live_head[c[j]]);
                     h[j][0] = hh.x; h[j][1] = hh.y; h[j][2] = hh.z; h[j][3] = hh.w;
-                    len[j] = __ldg(&a.live_len[c[j]]);
-                    dego[j] = __ldg(&a.live_deg[c[j]]);
+                    len[j] = ld_stream(&a.live_len[c[j]]);
+                    dego[j] = ld_stream(&a.live_deg[c[j]]);
                 } else {
                     v[j] = c[j];
                     b[j] = __ldg(&a.rp_in[v[j]]);
@@ -154,7 +154,7 @@ __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Li
             for (int j = 0; j < PULL_WPW; ++j)
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
-                    if ((uint32_t)k < len[j]) h[j][k] = __ldg(&a.ci_in[b[j] + k]);
+                    if ((uint32_t)k < len[j]) h[j][k] = ld_stream(&a.ci_in[b[j] + k]);
         }
         // the visited word and the frontier words of the first two head
         // entries, together; the other two only where those did not hit
@@ -219,7 +219,7 @@ __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Li
 #pragma unroll
                 for (int j = 0; j < PULL_WPW; ++j) {
                     pend[j] = !found[j] && p[j] < e[j];
-                    if (pend[j]) cw[j] = __ldg(&ci4[p[j] >> 2]);
+                    if (pend[j]) cw[j] = ld_stream(&ci4[p[j] >> 2]);
                 }
                 uint32_t f4[PULL_WPW][4];
 #pragma unroll
@@ -270,7 +270,7 @@ __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Li
                         uint32_t u = 0;
                         bool hit = false;
                         if (q < pe) {
-                            u = __ldg(&a.ci_in[q]);
+                            u = ld_stream(&a.ci_in[q]);
                             hit = (ldcg(&F[u >> 5]) >> (u & 31)) & 1u;
                         }
                         uint32_t hb = __ballot_sync(full, hit);

@@ -42,6 +42,12 @@ struct Smem {
 };
 
 static __device__ __forceinline__ uint32_t ldcg(const uint32_t *p) { return __ldcg(p); }
+// Loads of data a traversal streams through once (adjacency, the live
+// table): evict-first in L1 and L2, so the 0.5 GB of column indices does not
+// push the small working set out of L2 (bitmaps, frontier lists, and the
+// levels/parents lines whose sectors fill up over a traversal).
+template <class T>
+static __device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
 static __device__ __forceinline__ int ld_relaxed_gpu_int_(const int *p) { return dev::ld_relaxed_gpu_int(p); }
 
 // largest k in [0, cnt) with P[k] <= e (P[0] == 0 <= e)
@@ -192,7 +198,7 @@ __device__ void push_edges(const Args &a, Smem &sm, int d, uint32_t cnt, uint64_
                 }
                 uint32_t u = sm.push.Q[lo];
                 uint32_t p = sm.push.R[lo] + (uint32_t)(e - sm.push.P[lo]);
-                v = __ldg(&a.ci_out[p]);
+                v = ld_stream(&a.ci_out[p]);
                 win = visit(u, v, p, Fn, &deg);
             }
             stage_add(sm.stage, staged, wdeg, win, v, deg);
