@@ -282,7 +282,7 @@ typedef struct {
     uint64_t edges_examined;     /* adjacency entries read (push and pull) */
     uint64_t frontier_edges;     /* sum of degrees of all frontiers */
     uint64_t alg_bytes;          /* algorithmic bytes moved (see the design notes) */
-    /* per-level trace of the first GB_TRACE_LEVELS levels (single-source BFS) */
+    /* per-level trace of the first GB_TRACE_LEVELS levels (gb_bfs, gb_bfs_multi) */
     uint32_t trace_len;
     uint32_t trace_dir[GB_TRACE_LEVELS];        /* 1 = push, 2 = pull */
     uint32_t trace_vertices[GB_TRACE_LEVELS];   /* frontier size */

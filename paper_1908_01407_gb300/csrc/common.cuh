@@ -61,6 +61,11 @@ struct gb_context_t {
     int grid_limit = 0;
 };
 
+// In-rows longer than this are "hubs": the pull kernels (SSSP/CC relaxation,
+// multi-source BFS) split their edges over the whole grid instead of giving
+// each one to a single warp. The matrix caches the hub list for this length.
+constexpr uint32_t GBX_HUB_MIN_LEN = 2048;
+
 struct gb_matrix_t {
     gb_context *ctx = nullptr;
     gb_type type = GB_UINT32;
@@ -154,6 +159,9 @@ gb_info sync(gb_context *ctx);
 // Exclusive prefix sum of n uint32 values (in may equal out); if total is
 // non-null the device total is written there (a device pointer).
 gb_info scan_exclusive_u32(gb_context *ctx, const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *total);
+// Columns of A with more than min_len entries and their length prefix,
+// computed on first use and cached on the matrix (matrix.cu).
+gb_info matrix_hubs(const gb_matrix *A, uint32_t min_len);
 // Stable LSD radix sort of (key, value) pairs by the low `key_bits` bits.
 // Results end in keys/vals (the buffers are ping-ponged with the scratch).
 gb_info radix_sort_pairs(gb_context *ctx, uint64_t *keys, uint32_t *vals, uint64_t n, int key_bits);

@@ -42,6 +42,9 @@ struct MsArgs {
     uint32_t beta;
     BfsState *st;
     uint64_t timeout_ns, total_limit_ns;
+    const uint32_t *hub_list, *hub_pre;   // in-rows longer than GBX_HUB_MIN_LEN and their edge prefix
+    uint32_t nhub;
+    uint64_t hub_edges;
 };
 
 __device__ __forceinline__ unsigned long long ldcg64(const unsigned long long *p) { return __ldcg(p); }
@@ -101,8 +104,13 @@ __device__ void ms_compact(const MsArgs &a, Smem &sm, int d) {
     }
 }
 
-// pull: lane per vertex, 2 vertices per lane in flight; long rows continue
-// warp-cooperatively; every vertex also merges its frontier bits here
+// pull: lane per vertex, 2 vertices per lane in flight. A lane scans a
+// row of up to 32 in-neighbours alone, four independent loads at a time;
+// longer rows continue warp-cooperatively (128 neighbours per step), and
+// hub rows (longer than GBX_HUB_MIN_LEN) are left to ms_pull_hubs. Every
+// vertex also merges its frontier bits into its visited word here, and
+// sources whose bits are all covered stop the scan (the Boolean early exit
+// per 64 searches).
 __device__ void ms_pull(const MsArgs &a, int d, uint32_t *cnt_out, uint32_t *deg_out) {
     const unsigned long long *F = a.F[d % 3];
     unsigned long long *Fn = a.F[(d + 1) % 3];
@@ -127,26 +135,38 @@ __device__ void ms_pull(const MsArgs &a, int d, uint32_t *cnt_out, uint32_t *deg
                 e = __ldg(&a.rp_in[v + 1]);
             }
             write_levels(a, v, valid, f, d);
+            const bool hub = e - b > GBX_HUB_MIN_LEN;
             unsigned long long acc = 0;
-            bool need = valid && vis != a.live;
+            const bool need = valid && vis != a.live && !hub;
             uint32_t p = b;
             if (need) {
-                uint32_t lim = e - b > 32 ? b + 32 : e;
-                for (; p < lim; ++p) {
-                    acc |= ldcg64(&F[__ldg(&a.ci_in[p])]);
+                const uint32_t lim = e - b > 32 ? b + 32 : e;
+                for (; p < lim; p += 4) {
+                    unsigned long long x[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t u = p + k < lim ? fr::ld_stream(&a.ci_in[p + k]) : 0u;
+                        x[k] = p + k < lim ? ldcg64(&F[u]) : 0ull;
+                    }
+                    acc |= (x[0] | x[1]) | (x[2] | x[3]);
                     if ((acc | vis) == a.live) { p = e; break; }
                 }
+                if (p > lim) p = lim;
             }
             uint32_t coop = __ballot_sync(full, need && p < e);
             while (coop) {
-                int l = __ffs(coop) - 1;
+                const int l = __ffs(coop) - 1;
                 coop &= coop - 1;
-                uint32_t pb = __shfl_sync(full, p, l), pe = __shfl_sync(full, e, l);
-                unsigned long long lv = __shfl_sync(full, vis, l);
+                const uint32_t pb = __shfl_sync(full, p, l), pe = __shfl_sync(full, e, l);
+                const unsigned long long lv = __shfl_sync(full, vis, l);
                 unsigned long long la = __shfl_sync(full, acc, l);
-                for (uint32_t q0 = pb; q0 < pe; q0 += 32) {
+                for (uint32_t q0 = pb; q0 < pe; q0 += 128) {
                     unsigned long long x = 0;
-                    if (q0 + lane < pe) x = ldcg64(&F[__ldg(&a.ci_in[q0 + lane])]);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t q = q0 + k * 32 + lane;
+                        if (q < pe) x |= ldcg64(&F[fr::ld_stream(&a.ci_in[q])]);
+                    }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) x |= __shfl_xor_sync(full, x, o);
                     la |= x;
@@ -154,12 +174,74 @@ __device__ void ms_pull(const MsArgs &a, int d, uint32_t *cnt_out, uint32_t *deg
                 }
                 if (lane == l) acc = la;
             }
-            unsigned long long nb = acc & ~vis;
+            const unsigned long long nb = acc & ~vis;
             if (nb) {
                 Fn[v] = nb;
                 mycnt += 1;
                 mydeg += a.csr_is_csc ? e - b : __ldg(&a.rp_out[v + 1]) - __ldg(&a.rp_out[v]);
             }
+        }
+    }
+    *cnt_out += mycnt;
+    *deg_out += mydeg;
+}
+
+// pull, hub rows: the hubs' in-edges are cut into one contiguous range per
+// warp (equal lengths over the whole grid). A warp finds the hub of its
+// range start once, then walks the range 32 edges per step (a step spans at
+// most two hubs, as every hub has more than GBX_HUB_MIN_LEN edges), ORs the
+// frontier words of the step's edges per hub and sets the new bits of the
+// hub's next-frontier word with one atomicOr; it jumps past the rest of a
+// hub once every live source has reached or found it. A hub is counted by
+// the contribution that turns its word from zero to nonzero. The OR over a
+// hub's in-edges is the same whichever warps its edges fall to.
+__device__ void ms_pull_hubs(const MsArgs &a, int d, uint32_t *cnt_out, uint32_t *deg_out) {
+    if (!a.nhub) return;
+    const unsigned long long *F = a.F[d % 3];
+    unsigned long long *Fn = a.F[(d + 1) % 3];
+    const uint32_t full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint64_t nwarps = (uint64_t)gridDim.x * WARPS;
+    const uint64_t wid = (uint64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    const uint64_t X0 = a.hub_edges * wid / nwarps, X1 = a.hub_edges * (wid + 1) / nwarps;
+    uint32_t mycnt = 0, mydeg = 0;
+    if (X0 < X1) {
+        uint32_t h = 0, hi = a.nhub;   // last h with hub_pre[h] <= X0
+        while (hi - h > 1) {
+            const uint32_t mid = (h + hi) >> 1;
+            if ((uint64_t)__ldg(&a.hub_pre[mid]) <= X0) h = mid; else hi = mid;
+        }
+        uint64_t x0 = X0;
+        while (x0 < X1) {
+            const uint64_t hb = __ldg(&a.hub_pre[h]);
+            const uint64_t he = h + 1 < a.nhub ? (uint64_t)__ldg(&a.hub_pre[h + 1]) : a.hub_edges;
+            if (x0 >= he) { ++h; continue; }
+            const uint32_t v = __ldg(&a.hub_list[h]);
+            const unsigned long long vis = ldcg64(&a.V[v]) | ldcg64(&F[v]);
+            if (((ldcg64(&Fn[v]) | vis) & a.live) == a.live) {   // nothing left to find here
+                x0 = he;
+                ++h;
+                continue;
+            }
+            // one step: the edges [x0, x0+32) of this hub (the part past he is the next hub's)
+            const uint64_t x = x0 + lane;
+            const bool mine = x < X1 && x < he;
+            unsigned long long bits = 0;
+            if (mine) {
+                const uint32_t p = __ldg(&a.rp_in[v]) + (uint32_t)(x - hb);
+                bits = ldcg64(&F[fr::ld_stream(&a.ci_in[p])]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) bits |= __shfl_xor_sync(full, bits, o);
+            bits &= ~vis & a.live;
+            if (lane == 0 && bits && (ldcg64(&Fn[v]) | bits) != ldcg64(&Fn[v])) {
+                const unsigned long long old = atomicOr(&Fn[v], bits);
+                if (!old) {
+                    mycnt += 1;
+                    mydeg += a.csr_is_csc ? (uint32_t)(he - hb) : __ldg(&a.rp_out[v + 1]) - __ldg(&a.rp_out[v]);
+                }
+            }
+            x0 = x0 + 32 < he ? x0 + 32 : he;
         }
     }
     *cnt_out += mycnt;
@@ -235,6 +317,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_msbfs(MsArgs a) {
             __syncthreads();
             uint32_t c = 0, dg = 0;
             ms_pull(a, d, &c, &dg);
+            ms_pull_hubs(a, d, &c, &dg);
             c = dev::warp_sum<uint32_t>(c);
             dg = dev::warp_sum<uint32_t>(dg);
             if ((threadIdx.x & 31) == 0 && c) { atomicAdd(&s_cnt, c); atomicAdd(&s_deg, dg); }
@@ -380,6 +463,16 @@ gb_info msbfs_launch(gb_context *ctx, const gb_matrix *A, const uint32_t *d_srcs
     a.st = w->st;
     a.timeout_ns = 4000000000ull;
     a.total_limit_ns = 120000000000ull;
+    a.hub_list = a.hub_pre = nullptr;
+    a.nhub = 0;
+    a.hub_edges = 0;
+    if (A->has_csc) {
+        GB_CHECK(matrix_hubs(A, GBX_HUB_MIN_LEN));
+        a.hub_list = A->hub_list;
+        a.hub_pre = A->hub_pre;
+        a.nhub = A->nhub;
+        a.hub_edges = A->hub_edges;
+    }
     int occ = 0;
     GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, msk::k_msbfs, msk::BLOCK, 0));
     if (occ < 1) return fail(GB_PANIC, "multi-source BFS kernel cannot be resident");
@@ -423,6 +516,15 @@ extern "C" gb_info gb_bfs_multi(gb_context *ctx, const gb_matrix *A, const uint3
         stats->status = (uint32_t)hs.err;
         stats->vertices_reached = hs.reached;
         stats->frontier_edges = hs.frontier_edges;
+        uint32_t nl = hs.depth < GB_TRACE_LEVELS ? hs.depth : GB_TRACE_LEVELS;
+        stats->trace_len = nl;
+        for (uint32_t l = 0; l < nl; ++l) {
+            stats->trace_dir[l] = hs.dir_log[l];
+            stats->trace_vertices[l] = hs.lv_cnt[l];
+            stats->trace_edges[l] = hs.lv_fe[l];
+            uint64_t t1 = (l + 1 < GBX_MAX_LEVEL_LOG) ? hs.lv_ns[l + 1] : hs.lv_ns[l];
+            stats->trace_us[l] = (float)((t1 - hs.lv_ns[l]) * 1e-3);
+        }
     }
     if (hs.err) return fail(GB_TIMEOUT, "gb_bfs_multi: a bounded grid barrier wait ran out");
     return GB_SUCCESS;

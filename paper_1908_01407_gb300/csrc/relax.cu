@@ -57,7 +57,7 @@ __device__ __forceinline__ uint32_t relax_val(const RelaxArgs &a, uint32_t vu, u
 // and tests its sources against the frontier bitmap, all loads of a round
 // independent; rows longer than RPULL_LONG are scanned by the whole warp.
 constexpr uint32_t RPULL_LONG = 64;
-constexpr uint32_t RPULL_HUB = 2048;     // rows longer than this are split over the whole grid
+constexpr uint32_t RPULL_HUB = GBX_HUB_MIN_LEN;   // rows longer than this are split over the whole grid
 
 __device__ void relax_pull(const RelaxArgs &a, int d, uint32_t *cnt_out, uint32_t *deg_out) {
     const uint32_t *F = a.front[d % 3];
@@ -319,7 +319,6 @@ __global__ void __launch_bounds__(BLOCK, 3) k_relax(RelaxArgs a) {
 }  // namespace rlx
 
 struct BfsWorkspace;
-gb_info matrix_hubs(const gb_matrix *A, uint32_t min_len);
 gb_info bfs_workspace_raw(gb_context *ctx, uint32_t n, uint32_t **visited, uint32_t **front, uint32_t **q,
                           uint32_t **qp, uint32_t **qr, BfsState **st);
 
