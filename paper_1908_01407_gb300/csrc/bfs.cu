@@ -87,14 +87,15 @@ static __device__ __forceinline__ void flush_candidates(const uint32_t *sbuf, ui
 // them). Vertices without in-edges can never be reached by a pull, and a
 // later pull needs only what an earlier one left, so a pull touches
 // |candidates| vertices rather than all n. With the matrix's live table a
-// candidate is an index into the live list, and its first four
-// in-neighbours, in-degree and out-degree come with coalesced loads in list
-// order; the visited word and the frontier words of those four neighbours
-// are then loaded together (two dependent memory steps in all). Without
-// the table a candidate is a vertex and its row is read through the row
-// pointers. Rows longer than four whose head has no frontier vertex
-// continue in aligned 16-byte chunks for PULL_ROUNDS chunks, then
-// warp-cooperatively (32 neighbours per step), all with early exit.
+// candidate is an index into the live list, and its four in-neighbours of
+// largest degree, in-degree and out-degree come with coalesced loads in
+// list order; the visited word and the frontier words of the first two head
+// entries are then loaded together, the other two only where those missed
+// (two dependent memory steps for almost every vertex). Without the table a
+// candidate is a vertex and its head is the first four entries of its row,
+// read through the row pointers. Rows longer than four whose head has no
+// frontier vertex are scanned in aligned 16-byte chunks for PULL_ROUNDS
+// chunks, then warp-cooperatively (32 neighbours per step), with early exit.
 // Warps take groups of PULL_WPW * 32 consecutive candidates, each lane
 // PULL_WPW in flight. Found vertices set their visited and next-frontier
 // bits (one atomicOr per run of lanes in the same bitmap word); the others
@@ -207,8 +208,11 @@ __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Li
 #pragma unroll
             for (int j = 0; j < PULL_WPW; ++j) {
                 if (act[j] && !found[j] && len[j] > 4) {
+                    // the table's head is not a row prefix: scan the whole row
+                    // (its four head entries again, harmlessly); without the
+                    // table the head is the first four entries
                     if (table) b[j] = __ldg(&a.rp_in[v[j]]);
-                    p[j] = b[j] + 4;
+                    p[j] = table ? b[j] : b[j] + 4;
                     e[j] = b[j] + len[j];
                 }
             }

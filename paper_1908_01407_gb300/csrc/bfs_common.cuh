@@ -53,7 +53,7 @@ struct BfsArgs {
     uint32_t *q[2], *qp[2], *qr[2];    // frontier list: vertex, out-edge prefix, row start
     const uint32_t *live;              // vertices with an in-edge (ascending); null = all vertices
     const uint32_t *live_count;        // device scalar: length of live
-    const uint4 *live_head;            // per live entry: first four in-neighbours (0xffffffff = none)
+    const uint4 *live_head;            // per live entry: four in-neighbours of largest degree (0xffffffff = none)
     const uint32_t *live_len;          // per live entry: in-degree
     const uint32_t *live_deg;          // per live entry: out-degree
     uint32_t *ul[2];                   // candidate lists of the pull steps (unvisited, with in-edges)

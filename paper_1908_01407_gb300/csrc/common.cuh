@@ -93,8 +93,9 @@ struct gb_matrix_t {
     // built with the CSC; live_count is a device scalar (live_list[nrows])
     uint32_t *live_list = nullptr;
     uint32_t *live_count = nullptr;
-    // per live vertex, in live-list order: its first four in-neighbours
-    // (0xffffffff past the end of the row), its in-degree, its out-degree
+    // per live vertex, in live-list order: its four in-neighbours of largest
+    // out-degree (0xffffffff for rows shorter than four), its in-degree, its
+    // out-degree
     uint4 *live_head = nullptr;
     uint32_t *live_len = nullptr;
     uint32_t *live_deg = nullptr;    // == live_len for a symmetric matrix

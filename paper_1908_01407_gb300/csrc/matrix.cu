@@ -88,6 +88,12 @@ __global__ void k_live_emit(const uint32_t *flag, const uint32_t *pos, uint32_t 
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n && flag[i]) list[pos[i]] = i;
 }
+// The head of a live vertex: its four in-neighbours of largest out-degree
+// (ties: earlier in the row), taken from the first LIVE_HEAD_SCAN entries of
+// its row; a pull finds a frontier vertex among them far more often than
+// among the first four in row order, since large-degree vertices join the
+// frontier early.
+constexpr uint32_t LIVE_HEAD_SCAN = 256;
 __global__ void k_live_table(const uint32_t *list, const uint32_t *count, const uint32_t *colptr,
                              const uint32_t *rowidx, const uint32_t *rowptr, uint4 *head, uint32_t *len,
                              uint32_t *deg) {
@@ -95,12 +101,23 @@ __global__ void k_live_table(const uint32_t *list, const uint32_t *count, const 
     if (i >= *count) return;
     const uint32_t v = list[i];
     const uint32_t b = colptr[v], l = colptr[v + 1] - b;
-    uint4 h;
-    h.x = rowidx[b];
-    h.y = l > 1 ? rowidx[b + 1] : 0xffffffffu;
-    h.z = l > 2 ? rowidx[b + 2] : 0xffffffffu;
-    h.w = l > 3 ? rowidx[b + 3] : 0xffffffffu;
-    head[i] = h;
+    uint32_t best[4] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu};
+    uint32_t bd[4] = {0, 0, 0, 0};
+    const uint32_t lim = l < LIVE_HEAD_SCAN ? l : LIVE_HEAD_SCAN;
+    for (uint32_t k = 0; k < lim; ++k) {
+        const uint32_t u = rowidx[b + k];
+        const uint32_t du = rowptr[u + 1] - rowptr[u] + 1;   // +1: a neighbour always beats an empty slot
+        if (du <= bd[3]) continue;
+        int p = 3;
+        while (p > 0 && du > bd[p - 1]) {
+            best[p] = best[p - 1];
+            bd[p] = bd[p - 1];
+            --p;
+        }
+        best[p] = u;
+        bd[p] = du;
+    }
+    head[i] = make_uint4(best[0], best[1], best[2], best[3]);
     len[i] = l;
     if (deg != len) deg[i] = rowptr[v + 1] - rowptr[v];
 }
@@ -108,9 +125,10 @@ __global__ void k_live_table(const uint32_t *list, const uint32_t *count, const 
 
 // The ascending list of vertices with a nonempty CSC row (an in-edge): the
 // only vertices a pull step can ever reach, with, in list order, each one's
-// first four in-neighbours, in-degree and out-degree (so a pull over the
-// list reads its candidates with coalesced loads and needs the row pointers
-// only for rows longer than four). The list length stays on the device.
+// four in-neighbours of largest out-degree, in-degree and out-degree (so a
+// pull over the list reads its candidates with coalesced loads and needs the
+// row pointers only for rows longer than four whose head has no frontier
+// vertex). The list length stays on the device.
 gb_info matrix_live(gb_matrix *A) {
     gb_context *ctx = A->ctx;
     const uint32_t n = A->ncols;
