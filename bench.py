@@ -215,12 +215,12 @@ def run_gbx(args):
     desc = gb.Descriptor(beta=args.beta) if args.beta else None
     levels = torch.empty(n, dtype=torch.int32, device=dev)
     parents = torch.empty(n, dtype=torch.int32, device=dev)
-    # the push/pull threshold is picked by the autotuner on sources other
+    # the push/pull threshold is picked by the autotuner on 16 sources other
     # than the benchmark's (seed 99), unless --beta fixes it
     tuned_beta = None
     if not args.beta:
         import gen
-        tuned_beta, _ = gb.bfs_autotune(ctx, A, gen.sources(t, 8, seed=99))
+        tuned_beta, _ = gb.bfs_autotune(ctx, A, gen.sources(t, 16, seed=99))
 
     # untimed pass with statistics: algorithmic bytes and levels per source
     alg, depth, pushes, pulls = [], [], [], []

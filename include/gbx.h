@@ -302,8 +302,10 @@ gb_info gb_bfs(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *level
 /* Autotuner of the push/pull switch threshold (Table 9: pull iff
  * |E_f| > |E| / beta; Section 5.3 suggests Table 9 as a starting point for
  * finding the best threshold on given hardware). Runs gb_bfs from the k
- * given sources (host array) for each beta in {4, 6, ..., 128}, timed with
- * CUDA events, and stores the fastest beta on the matrix: later gb_bfs calls
+ * given sources (host array) for each beta in {4, 6, 8, 10, 12, 16, 20, 24,
+ * 32, 48, 64, 96, 128, 192, 256}, timed with CUDA events in two passes over
+ * the candidates (forward, then backward; each keeps its faster pass), and
+ * stores the fastest beta on the matrix: later gb_bfs calls
  * whose descriptor leaves GB_SWITCH_BETA at 0 use it (untuned matrices use
  * the paper's beta = 10). *best_ms (may be NULL) = mean ms per BFS at it. */
 gb_info gb_bfs_autotune(gb_context *ctx, gb_matrix *A, const uint32_t *srcs, uint32_t k, uint32_t *best_beta,

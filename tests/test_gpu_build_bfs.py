@@ -190,7 +190,7 @@ def test_bfs_autotune_picks_a_candidate_and_keeps_results(ctx):
     t = gen.rmat(13, 16, seed=12)
     g, A = make(ctx, t)
     beta, ms = gb.bfs_autotune(ctx, A, gen.sources(t, 4, seed=99))
-    assert beta in (4, 6, 8, 10, 12, 16, 20, 24, 32, 48, 64, 96, 128) and ms > 0
+    assert beta in (4, 6, 8, 10, 12, 16, 20, 24, 32, 48, 64, 96, 128, 192, 256) and ms > 0
     for s in gen.sources(t, 4, seed=1):
         check_bfs(ctx, g, A, int(s))          # default descriptor: the tuned beta
     A.free()
