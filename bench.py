@@ -394,9 +394,13 @@ def extra_rows(args, hbm):
     src = gen.first_nonisolated(t)
     lvg = torch.empty(t.n, dtype=torch.int32, device="cuda")
     pag = torch.empty(t.n, dtype=torch.int32, device="cuda")
+    # the autotuner picks the push/pull threshold and the schedule (persistent
+    # grid or single cluster) for this graph, on its own source
+    beta_g, _ = gb.bfs_autotune(ctx, A, np.array([src], np.uint32))
     _, _, st = gb.bfs(ctx, A, src, lvg, pag)
     ms = cuda_time_ms(lambda: gb.bfs(ctx, A, src, lvg, pag, stats=False), stream)
-    g_out = {"bfs_ms": ms, "bfs_levels": st["depth"], "bfs_us_per_level": 1e3 * ms / max(st["depth"], 1)}
+    g_out = {"bfs_ms": ms, "bfs_levels": st["depth"], "bfs_us_per_level": 1e3 * ms / max(st["depth"], 1),
+             "bfs_schedule": "cluster" if st["schedule"] == gb.SCHED_CLUSTER else "grid", "bfs_beta": beta_g}
     d = torch.empty(t.n, dtype=torch.int32, device="cuda")
     its = []
     ms = cuda_time_ms(lambda: its.append(gb.sssp(ctx, A, src, d)[1]), stream)
@@ -458,28 +462,41 @@ def serving_bench(args):
     serial_s = time.perf_counter() - t0
     serial = {"qps": N / serial_s, "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99))}
     # served: Poisson arrivals at lam = load * serial capacity
-    lam = args.serve_load * serial["qps"]
-    S = gb.Server(ctx, max_inflight=args.serve_slots, batch_window_us=args.serve_window_us)
-    ids = [S.add_graph(A) for A, _, _ in graphs]
-    arrivals = np.cumsum(rng.exponential(1.0 / lam, N))
-    tickets = [None] * N
     import threading
-    def fetcher():
-        for i in range(N):
-            while tickets[i] is None:
-                time.sleep(0.0002)
-            r = S.wait(tickets[i], 600000)
-            S.fetch_into(tickets[i], outb[:r.n])
-    th = threading.Thread(target=fetcher)
-    th.start()
-    t0 = time.perf_counter()
-    for i in range(N):
-        while time.perf_counter() - t0 < arrivals[i]:
-            pass
-        tickets[i] = S.submit(int(kinds[i]), ids[gids[i]], srcs[i])
-    th.join()
-    st = S.stats()
-    S.destroy()
+
+    def run_served(load, nreq, seed):
+        lam = load * serial["qps"]
+        S = gb.Server(ctx, max_inflight=args.serve_slots, batch_window_us=args.serve_window_us)
+        ids = [S.add_graph(A) for A, _, _ in graphs]
+        arrivals = np.cumsum(np.random.default_rng(seed).exponential(1.0 / lam, nreq))
+        tickets = [None] * nreq
+
+        def fetcher():
+            for i in range(nreq):
+                while tickets[i] is None:
+                    time.sleep(0.0002)
+                r = S.wait(tickets[i], 600000)
+                S.fetch_into(tickets[i], outb[:r.n])
+        th = threading.Thread(target=fetcher)
+        th.start()
+        t0 = time.perf_counter()
+        for i in range(nreq):
+            while time.perf_counter() - t0 < arrivals[i]:
+                pass
+            tickets[i] = S.submit(int(kinds[i]), ids[gids[i]], srcs[i])
+        th.join()
+        st = S.stats()
+        S.destroy()
+        return lam, st
+
+    lam, st = run_served(args.serve_load, N, 6)
+    # latency against offered load (the first requests of the same stream)
+    sweep = []
+    for load in (0.25, 0.5, 1.0, 2.0, 4.0):
+        nreq = min(N, args.serve_sweep_requests)
+        lam_s, st_s = run_served(load, nreq, 7)
+        sweep.append({"load": load, "offered_qps": lam_s, "qps": st_s["qps"], "p50_us": st_s["p50_us"],
+                      "p99_us": st_s["p99_us"], "requests": nreq})
     for A, _, _ in graphs:
         A.free()
     ctx.close()
@@ -487,7 +504,7 @@ def serving_bench(args):
             "offered_qps": lam, "served": {"qps": st["qps"], "p50_us": st["p50_us"], "p99_us": st["p99_us"],
                                            "batches": st["batches"], "bfs_batched": st["batched_bfs"],
                                            "slots": args.serve_slots},
-            "serial": serial, "speedup_qps": st["qps"] / serial["qps"]}
+            "serial": serial, "speedup_qps": st["qps"] / serial["qps"], "load_sweep": sweep}
 
 
 def run_profile(args):
@@ -547,6 +564,8 @@ def main():
     ap.add_argument("--serve-load", type=float, default=2.0, help="offered load as a multiple of serial capacity")
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-window-us", type=int, default=300)
+    ap.add_argument("--serve-sweep-requests", type=int, default=800,
+                    help="requests per point of the latency-vs-load sweep")
     ap.add_argument("--profile", choices=["bfs", "pr", "sssp", "msbfs", "tc"], default=None,
                     help="short fixed run of one kernel for ncu")
     ap.add_argument("--profile-launches", type=int, default=3)

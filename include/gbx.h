@@ -86,7 +86,8 @@ typedef enum {
     GB_INP0 = 2,        /* GB_DEFAULT or GB_TRAN */
     GB_INP1 = 3,        /* GB_DEFAULT or GB_TRAN */
     GB_DIRECTION = 4,   /* GB_AUTO (default), GB_PUSH or GB_PULL */
-    GB_SWITCH_BETA = 5  /* integer beta of the push/pull rule |E_f| > |E| / beta; 0 = tuned default */
+    GB_SWITCH_BETA = 5, /* integer beta of the push/pull rule |E_f| > |E| / beta; 0 = tuned default */
+    GB_SCHEDULE = 6     /* BFS: GB_SCHED_AUTO (default), GB_SCHED_GRID or GB_SCHED_CLUSTER */
 } gb_field;
 
 enum {
@@ -94,7 +95,13 @@ enum {
     GB_SCMP = 1, GB_STRUCTURE = 2,   /* GB_MASK bits */
     GB_REPLACE = 1,                  /* GB_OUTP */
     GB_TRAN = 1,                     /* GB_INP0 / GB_INP1 */
-    GB_AUTO = 0, GB_PUSH = 1, GB_PULL = 2
+    GB_AUTO = 0, GB_PUSH = 1, GB_PULL = 2,
+    /* GB_SCHEDULE values. GRID: one persistent cooperative kernel over the
+     * whole GPU, push or pull per level. CLUSTER: the whole traversal in one
+     * thread-block cluster (push only, levels separated by the cluster
+     * barrier; for graphs of high diameter). AUTO: what gb_bfs_autotune
+     * chose for the matrix, GRID if it was not tuned. */
+    GB_SCHED_AUTO = 0, GB_SCHED_GRID = 1, GB_SCHED_CLUSTER = 2
 };
 
 /* Matrix build flags. */
@@ -290,13 +297,15 @@ typedef struct {
     float trace_us[GB_TRACE_LEVELS];            /* level duration (device clock) */
     float init_us;                              /* kernel entry to the start of level 0 */
     float final_us;                             /* end of the last level to the kernel's exit */
+    uint32_t schedule;                          /* GB_SCHED_GRID or GB_SCHED_CLUSTER: the kernel that ran */
 } gb_bfs_stats;
 
 /* Direction-optimised BFS (Algorithm 1, Section 7.1): levels[v] = hop count
  * from src (src 0, unreachable -1; the paper's depth minus one), and, if
  * parents != NULL, a BFS-tree parent (parents[src] = src, unreachable -1).
  * A must be square and symmetric-or-CSC-built. levels/parents have nrows
- * entries in `mem`. stats may be NULL. desc: GB_DIRECTION, GB_SWITCH_BETA. */
+ * entries in `mem`. stats may be NULL. desc: GB_DIRECTION, GB_SWITCH_BETA,
+ * GB_SCHEDULE (a device that cannot co-schedule a cluster runs GB_SCHED_GRID). */
 gb_info gb_bfs(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *levels, int32_t *parents,
                gb_mem mem, const gb_desc *desc, gb_bfs_stats *stats);
 /* Autotuner of the push/pull switch threshold (Table 9: pull iff
@@ -305,7 +314,9 @@ gb_info gb_bfs(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *level
  * given sources (host array) for each beta in {4, 6, 8, 10, 12, 16, 20, 24,
  * 32, 48, 64, 96, 128, 192, 256}, timed with CUDA events in two passes over
  * the candidates (forward, then backward; each keeps its faster pass), and
- * stores the fastest beta on the matrix: later gb_bfs calls
+ * stores the fastest beta on the matrix; the single-cluster schedule is
+ * timed the same way and kept for the matrix when it is faster still
+ * (graphs of high diameter). Later gb_bfs calls
  * whose descriptor leaves GB_SWITCH_BETA at 0 use it (untuned matrices use
  * the paper's beta = 10). *best_ms (may be NULL) = mean ms per BFS at it. */
 gb_info gb_bfs_autotune(gb_context *ctx, gb_matrix *A, const uint32_t *srcs, uint32_t k, uint32_t *best_beta,

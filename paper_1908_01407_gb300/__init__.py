@@ -29,11 +29,12 @@ BOOL, INT32, UINT32, UINT64, FP32, FP64 = range(6)
 NOP, PLUS, TIMES, MIN, MAX, LOR, LAND, FIRST, SECOND, PAIR, MINUS = range(11)
 MONOID_PLUS, MONOID_TIMES, MONOID_MIN, MONOID_MAX, MONOID_LOR, MONOID_LAND = range(6)
 PLUS_TIMES, LOR_LAND, MIN_PLUS, MAX_PLUS, MIN_TIMES, MIN_SECOND, PLUS_PAIR = range(7)
-F_MASK, F_OUTP, F_INP0, F_INP1, F_DIRECTION, F_SWITCH_BETA = range(6)
+F_MASK, F_OUTP, F_INP0, F_INP1, F_DIRECTION, F_SWITCH_BETA, F_SCHEDULE = range(7)
 DEFAULT, SCMP, STRUCTURE = 0, 1, 2
 REPLACE = 1
 TRAN = 1
 AUTO, PUSH, PULL = 0, 1, 2
+SCHED_AUTO, SCHED_GRID, SCHED_CLUSTER = 0, 1, 2
 BUILD_DEFAULT, SYMMETRIC, CSR_ONLY = 0, 1, 2
 REQ_BFS, REQ_SSSP, REQ_PAGERANK = 0, 1, 2
 
@@ -55,7 +56,7 @@ class BfsStats(ctypes.Structure):
                 ("alg_bytes", ctypes.c_uint64), ("trace_len", ctypes.c_uint32),
                 ("trace_dir", ctypes.c_uint32 * 32), ("trace_vertices", ctypes.c_uint32 * 32),
                 ("trace_edges", ctypes.c_uint64 * 32), ("trace_us", ctypes.c_float * 32),
-                ("init_us", ctypes.c_float), ("final_us", ctypes.c_float)]
+                ("init_us", ctypes.c_float), ("final_us", ctypes.c_float), ("schedule", ctypes.c_uint32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("trace")}
@@ -452,7 +453,7 @@ class Descriptor:
         check(lib().gb_desc_new(ctypes.byref(h)))
         self.h = h
         names = {"mask": F_MASK, "outp": F_OUTP, "inp0": F_INP0, "inp1": F_INP1,
-                 "direction": F_DIRECTION, "beta": F_SWITCH_BETA}
+                 "direction": F_DIRECTION, "beta": F_SWITCH_BETA, "schedule": F_SCHEDULE}
         for k, v in fields.items():
             self.set(names[k], v)
 

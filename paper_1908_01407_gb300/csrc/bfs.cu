@@ -525,10 +525,18 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
 
 }  // namespace bfsk
 
+// the single-cluster schedule (bfs_cluster.cu)
+bool bfs_cluster_available(gb_context *ctx);
+gb_info bfs_cluster_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *levels, int32_t *parents,
+                           uint32_t *visited, uint32_t *ov0, uint32_t *ov1, void *state);
+size_t bfs_cluster_state_bytes();
+gb_info bfs_cluster_result(gb_context *ctx, const void *state, gb_bfs_stats *stats);
+
 struct BfsWorkspace {
     uint32_t n = 0;
     uint32_t *visited = nullptr, *front = nullptr, *q = nullptr, *qp = nullptr, *qr = nullptr, *ul = nullptr;
     BfsState *st = nullptr;
+    void *cl_state = nullptr;   // state block of the single-cluster schedule
     int grid = 0;
 };
 
@@ -540,7 +548,7 @@ gb_info bfs_workspace(gb_context *ctx, uint32_t n, BfsWorkspace **out) {
     BfsWorkspace &w = g_ws[ctx];
     if (w.n < n || !w.st) {
         dfree(ctx, w.visited); dfree(ctx, w.front); dfree(ctx, w.q); dfree(ctx, w.qp); dfree(ctx, w.qr);
-        dfree(ctx, w.ul); dfree(ctx, w.st);
+        dfree(ctx, w.ul); dfree(ctx, w.st); dfree(ctx, w.cl_state);
         w = BfsWorkspace();
         uint32_t nw = (n + 31) / 32;
         GB_CHECK(dalloc_t(ctx, &w.visited, nw));
@@ -550,6 +558,7 @@ gb_info bfs_workspace(gb_context *ctx, uint32_t n, BfsWorkspace **out) {
         GB_CHECK(dalloc_t(ctx, &w.qr, 2ull * n + 2));
         GB_CHECK(dalloc_t(ctx, &w.ul, 2ull * n + 2));
         GB_CHECK(dalloc_t(ctx, &w.st, 1));
+        GB_CHECK(dalloc(ctx, &w.cl_state, bfs_cluster_state_bytes()));
         // the only reset of the working state: launches leave it zeroed
         GB_CHECK(memset_async(ctx, w.st, 0, sizeof(BfsState)));
         w.n = n;
@@ -578,8 +587,22 @@ void bfs_workspace_release(gb_context *ctx) {
     if (it == g_ws.end()) return;
     BfsWorkspace &w = it->second;
     dfree(ctx, w.visited); dfree(ctx, w.front); dfree(ctx, w.q); dfree(ctx, w.qp); dfree(ctx, w.qr);
-    dfree(ctx, w.ul); dfree(ctx, w.st);
+    dfree(ctx, w.ul); dfree(ctx, w.st); dfree(ctx, w.cl_state);
     g_ws.erase(it);
+}
+
+// The schedule a gb_bfs call runs: the descriptor's, else the matrix's tuned
+// one, else the persistent grid; the cluster needs a device that can
+// co-schedule it.
+static int bfs_schedule(gb_context *ctx, const gb_matrix *A, const gb_desc *desc) {
+    int sch = (desc && desc->schedule != GB_SCHED_AUTO) ? desc->schedule : A->tuned_schedule;
+    if (sch == GB_SCHED_CLUSTER && !bfs_cluster_available(ctx)) sch = GB_SCHED_GRID;
+    return sch == GB_SCHED_CLUSTER ? GB_SCHED_CLUSTER : GB_SCHED_GRID;
+}
+
+static gb_info bfs_cluster_run(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *levels,
+                               int32_t *parents, BfsWorkspace *w) {
+    return bfs_cluster_launch(ctx, A, src, levels, parents, w->visited, w->q, w->q + A->nrows + 1, w->cl_state);
 }
 
 gb_info bfs_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *levels, int32_t *parents,
@@ -646,10 +669,19 @@ extern "C" gb_info gb_bfs(gb_context *ctx, const gb_matrix *A, uint32_t src, int
             dp = tp.as<int32_t>();
         }
     }
-    GB_CHECK(bfs_launch(ctx, A, src, dl, dp, desc, w, 0));
+    const int sch = bfs_schedule(ctx, A, desc);
+    if (sch == GB_SCHED_CLUSTER) GB_CHECK(bfs_cluster_run(ctx, A, src, dl, dp, w));
+    else GB_CHECK(bfs_launch(ctx, A, src, dl, dp, desc, w, 0));
     if (mem == GB_HOST) {
         GB_CUDA(cudaMemcpyAsync(levels, dl, (size_t)A->nrows * 4, cudaMemcpyDeviceToHost, ctx->stream));
         if (parents) GB_CUDA(cudaMemcpyAsync(parents, dp, (size_t)A->nrows * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    if (sch == GB_SCHED_CLUSTER) {
+        if (stats || mem == GB_HOST) {
+            GB_CHECK(bfs_cluster_result(ctx, w->cl_state, stats));
+            if (stats) stats->schedule = GB_SCHED_CLUSTER;
+        }
+        return GB_SUCCESS;
     }
     if (stats || mem == GB_HOST) {
         BfsResult hs;
@@ -675,6 +707,7 @@ extern "C" gb_info gb_bfs(gb_context *ctx, const gb_matrix *A, uint32_t src, int
             }
             stats->init_us = hs.depth ? (float)((hs.lv_ns[0] - hs.t_entry) * 1e-3) : 0.f;
             stats->final_us = (float)((hs.t_exit - hs.t_end) * 1e-3);
+            stats->schedule = GB_SCHED_GRID;
         }
         if (hs.err) return fail(GB_TIMEOUT, "gb_bfs: a bounded grid barrier wait ran out");
     }
@@ -845,6 +878,47 @@ extern "C" gb_info gb_bfs_autotune(gb_context *ctx, gb_matrix *A, const uint32_t
     uint32_t bb = 10;
     for (int c = 0; c < NC; ++c)
         if (tmin[c] < best) { best = tmin[c]; bb = cand[c]; }
+    // the single-cluster schedule, timed the same way (two passes)
+    int sched = GB_SCHED_GRID;
+    if (bfs_cluster_available(ctx)) {
+        double tcl = 1e30;
+        // one untimed and one timed launch first: a schedule four times slower
+        // per BFS than the best grid one is not timed any further
+        bool hopeless = false;
+        {
+            gb_info r = bfs_cluster_run(ctx, A, srcs[0], lv.as<int32_t>(), pa.as<int32_t>(), w);
+            if (r == GB_SUCCESS) r = cudaEventRecord(e0, ctx->stream) == cudaSuccess ? GB_SUCCESS : GB_PANIC;
+            if (r == GB_SUCCESS) r = bfs_cluster_run(ctx, A, srcs[0], lv.as<int32_t>(), pa.as<int32_t>(), w);
+            if (r == GB_SUCCESS && cudaEventRecord(e1, ctx->stream) != cudaSuccess) r = GB_PANIC;
+            if (r == GB_SUCCESS && cudaEventSynchronize(e1) != cudaSuccess) r = GB_PANIC;
+            if (r != GB_SUCCESS) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return r == GB_PANIC ? fail(GB_PANIC, "gb_bfs_autotune: CUDA error") : r;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            hopeless = (double)ms > 4.0 * best / k;
+        }
+        for (int pass = 0; pass < 2 && !hopeless; ++pass) {
+            gb_info r = bfs_cluster_run(ctx, A, srcs[0], lv.as<int32_t>(), pa.as<int32_t>(), w);
+            if (r == GB_SUCCESS) r = cudaEventRecord(e0, ctx->stream) == cudaSuccess ? GB_SUCCESS : GB_PANIC;
+            for (uint32_t q = 0; q < k && r == GB_SUCCESS; ++q)
+                r = bfs_cluster_run(ctx, A, srcs[q], lv.as<int32_t>(), pa.as<int32_t>(), w);
+            if (r == GB_SUCCESS && cudaEventRecord(e1, ctx->stream) != cudaSuccess) r = GB_PANIC;
+            if (r == GB_SUCCESS && cudaEventSynchronize(e1) != cudaSuccess) r = GB_PANIC;
+            if (r != GB_SUCCESS) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return r == GB_PANIC ? fail(GB_PANIC, "gb_bfs_autotune: CUDA error") : r;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < tcl) tcl = ms;
+        }
+        if (tcl < best) { best = tcl; sched = GB_SCHED_CLUSTER; }
+    }
+    A->tuned_schedule = sched;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     A->tuned_beta = bb;

@@ -89,6 +89,8 @@ struct gb_matrix_t {
     bool hub_ready = false;
     // push/pull switch threshold chosen by gb_bfs_autotune (0 = not tuned)
     uint32_t tuned_beta = 0;
+    // BFS schedule chosen by gb_bfs_autotune (GB_SCHED_AUTO = not tuned)
+    int tuned_schedule = GB_SCHED_AUTO;
     // vertices with at least one in-edge (nonempty CSC row), ascending,
     // built with the CSC; live_count is a device scalar (live_list[nrows])
     uint32_t *live_list = nullptr;
@@ -123,6 +125,7 @@ struct gb_desc_t {
     int inp1 = GB_DEFAULT;
     int direction = GB_AUTO;
     int beta = 0;
+    int schedule = GB_SCHED_AUTO;
 };
 
 // ------------------------------------------------------------------ memory

@@ -316,6 +316,10 @@ gb_info gb_desc_set(gb_desc *d, gb_field field, int value) {
     case GB_SWITCH_BETA:
         if (value < 0) return fail(GB_INVALID_VALUE, "bad GB_SWITCH_BETA value %d", value);
         d->beta = value; break;
+    case GB_SCHEDULE:
+        if (value < GB_SCHED_AUTO || value > GB_SCHED_CLUSTER)
+            return fail(GB_INVALID_VALUE, "bad GB_SCHEDULE value %d", value);
+        d->schedule = value; break;
     default:
         return fail(GB_INVALID_VALUE, "unknown descriptor field %d", (int)field);
     }
@@ -330,6 +334,7 @@ gb_info gb_desc_get(const gb_desc *d, gb_field field, int *value) {
     case GB_INP0: *value = d->inp0; break;
     case GB_INP1: *value = d->inp1; break;
     case GB_DIRECTION: *value = d->direction; break;
+    case GB_SCHEDULE: *value = d->schedule; break;
     case GB_SWITCH_BETA: *value = d->beta; break;
     default: return fail(GB_INVALID_VALUE, "unknown descriptor field %d", (int)field);
     }

@@ -235,3 +235,44 @@ def test_bfs_pull_push_pull_keeps_candidates(ctx):
     check_bfs(ctx, g, A, src, d)
     d.free()
     A.free()
+
+
+@pytest.mark.parametrize("case", ["rmat14", "rmat18", "grid", "path", "star", "two", "single", "isolated_src"])
+def test_bfs_single_cluster_schedule(ctx, case):
+    """The single-cluster schedule gives the same levels (and valid parents)
+    as the oracle; rmat18's middle frontiers overflow the CTAs' shared lists
+    into the global list, the star's hub row is expanded warp-cooperatively,
+    the path has 300 levels."""
+    t = {"rmat14": lambda: gen.rmat(14, 16, seed=1),
+         "rmat18": lambda: gen.rmat(18, 16, seed=5),
+         "grid": lambda: gen.grid(200, 150, 0.1, seed=3),
+         "path": lambda: gen.from_edges(300, [(i, i + 1) for i in range(299)]),
+         "star": lambda: gen.from_edges(5000, [(0, i) for i in range(1, 5000)]),
+         "two": lambda: gen.from_edges(6, [(0, 1), (1, 2), (3, 4), (4, 5)]),
+         "single": lambda: gen.from_edges(1, []),
+         "isolated_src": lambda: gen.from_edges(70, [(1, 2), (2, 3)])}[case]()
+    g, A = make(ctx, t)
+    d = gb.Descriptor(schedule=gb.SCHED_CLUSTER)
+    srcs = [0, t.n - 1] if t.n > 1 else [0]
+    if case.startswith("rmat"):
+        srcs = [int(s) for s in gen.sources(t, 3, seed=4)]
+    for src in srcs:
+        st = check_bfs(ctx, g, A, src, d)
+        assert st["schedule"] == gb.SCHED_CLUSTER
+    d.free()
+    A.free()
+
+
+def test_bfs_autotune_chooses_cluster_for_a_long_path(ctx):
+    """A 3000-vertex path has 3000 levels of one vertex each: the cluster
+    schedule wins and becomes the matrix's default."""
+    t = gen.from_edges(3000, [(i, i + 1) for i in range(2999)])
+    g, A = make(ctx, t)
+    gb.bfs_autotune(ctx, A, np.array([0, 1500], np.uint32))
+    st = check_bfs(ctx, g, A, 0)
+    assert st["schedule"] == gb.SCHED_CLUSTER
+    d = gb.Descriptor(schedule=gb.SCHED_GRID)      # the descriptor overrides the tuned choice
+    st = check_bfs(ctx, g, A, 0, d)
+    assert st["schedule"] == gb.SCHED_GRID
+    d.free()
+    A.free()
