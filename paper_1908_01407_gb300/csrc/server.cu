@@ -79,6 +79,13 @@ namespace {
 
 size_t work_bytes(uint32_t n) { return (size_t)n * 64 + (1u << 20); }
 
+// Below SINGLE_BFS_MAX_K sources on a graph of at least SINGLE_BFS_MIN_N
+// vertices, k single-source traversals (direction-optimised, with early exit
+// per vertex) beat one 64-bit bit-frontier launch, whose pulls scan until
+// every source is covered.
+constexpr uint32_t SINGLE_BFS_MIN_N = 1u << 21;
+constexpr uint32_t SINGLE_BFS_MAX_K = 24;
+
 void worker_loop(gb_server *S, int w) {
     gb_context *ctx = S->wctx[w];
     cudaSetDevice(ctx->device);
@@ -103,8 +110,10 @@ void worker_loop(gb_server *S, int w) {
         if (req.kind == GB_REQ_BFS) {
             gather();
             double age = now_us() - H.t_submit;
-            if (job.size() < 64 && S->cfg.batch_window_us > 0 && age < S->cfg.batch_window_us) {
-                // give concurrent requests on the same graph a short window to join
+            if (job.size() < 64 && S->cfg.batch_window_us > 0 && age < S->cfg.batch_window_us &&
+                S->running + 1 >= (int)S->cfg.max_inflight) {
+                // every other slot is busy: give concurrent requests on the same
+                // graph a short window to join (an idle GPU starts at once)
                 S->cv_work.wait_for(lk, std::chrono::microseconds((int64_t)(S->cfg.batch_window_us - age)));
                 if (S->stop) break;
                 if (S->pending.empty() || S->pending.front() != head) continue;   // another slot took it
@@ -151,7 +160,14 @@ void worker_loop(gb_server *S, int w) {
         res->refs = (int)k;
         gb_info st = dalloc(ctx, &res->dev, rbytes);
         if (st == GB_SUCCESS) {
-            if (req.kind == GB_REQ_BFS) {
+            if (req.kind == GB_REQ_BFS && (k == 1 || (n >= SINGLE_BFS_MIN_N && k < SINGLE_BFS_MAX_K))) {
+                // one request, or a few on a large graph: the single-source
+                // kernel, one launch per source, each into its own row
+                for (uint32_t q = 0; q < k && st == GB_SUCCESS; ++q)
+                    st = gb_bfs(ctx, A, srcs[q], (int32_t *)res->dev + (size_t)q * n, nullptr, GB_DEVICE, nullptr,
+                                nullptr);
+                if (st == GB_SUCCESS) st = sync(ctx);
+            } else if (req.kind == GB_REQ_BFS) {
                 Scratch ds(ctx);
                 st = ds.alloc(64 * 4);
                 if (st == GB_SUCCESS) st = copy_in(ctx, ds.p, srcs.data(), (size_t)k * 4, GB_HOST);
