@@ -353,7 +353,11 @@ gb_info gb_bfs_multi(gb_context *ctx, const gb_matrix *A, const uint32_t *srcs, 
                      gb_mem mem, const gb_desc *desc, gb_bfs_stats *stats);
 /* SSSP (Section 7.2): adaptive Bellman-Ford by min.plus mxv restricted to
  * the vertices whose distance changed. A holds uint32 weights. dist[v] =
- * shortest distance (UINT32_MAX unreachable). iterations may be NULL. */
+ * shortest distance (UINT32_MAX unreachable). iterations may be NULL.
+ * desc: GB_DIRECTION, GB_SWITCH_BETA, GB_SCHEDULE (GB_SCHED_CLUSTER relaxes
+ * by push inside one thread-block cluster; GB_SCHED_AUTO and GB_SCHED_GRID
+ * use the persistent grid kernel, which is faster wherever the frontiers of
+ * improved vertices are large, as on the weighted 4096^2 grid). */
 gb_info gb_sssp(gb_context *ctx, const gb_matrix *A, uint32_t src, uint32_t *dist, gb_mem mem,
                 const gb_desc *desc, uint32_t *iterations);
 /* PageRank (Section 7.3), pull SpMV in FP32 with FP32 accumulation:

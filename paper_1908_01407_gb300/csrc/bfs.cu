@@ -574,10 +574,11 @@ gb_info bfs_workspace(gb_context *ctx, uint32_t n, BfsWorkspace **out) {
 }
 
 gb_info bfs_workspace_raw(gb_context *ctx, uint32_t n, uint32_t **visited, uint32_t **front, uint32_t **q,
-                          uint32_t **qp, uint32_t **qr, BfsState **st) {
+                          uint32_t **qp, uint32_t **qr, BfsState **st, void **cl_state) {
     BfsWorkspace *w = nullptr;
     GB_CHECK(bfs_workspace(ctx, n, &w));
     *visited = w->visited; *front = w->front; *q = w->q; *qp = w->qp; *qr = w->qr; *st = w->st;
+    if (cl_state) *cl_state = w->cl_state;
     return GB_SUCCESS;
 }
 

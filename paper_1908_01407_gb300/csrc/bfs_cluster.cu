@@ -17,6 +17,11 @@
 //    distributed-shared-memory atomics, read by every CTA after the barrier.
 // Levels and parents are those of Algorithm 1 (levels 0-based, -1 for
 // unreached vertices), exactly as the persistent-grid kernel writes them.
+// The same frontier machinery runs SSSP (Section 7.2) as min.plus
+// relaxation: an edge (u, v, w) lowers dist(v) to dist(u) + w (saturating)
+// by atomicMin, and v joins the next frontier the first time it improves in
+// an iteration (an iteration stamp per vertex); the loop ends when no
+// distance changes, the exact fixed point.
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -48,7 +53,10 @@ struct ClArgs {
     uint32_t src;
     const uint32_t *rp, *ci;       // CSR (out-edges)
     int32_t *levels, *parents;
-    uint32_t *visited;
+    uint32_t *visited;             // BFS
+    uint32_t *dist;                // SSSP: distances (UINT32_MAX = unreached)
+    const uint32_t *wt;            // SSSP: edge weights, CSR order
+    uint32_t *stamp;               // SSSP: last iteration + 1 in which a vertex joined a frontier
     uint32_t *ov[2];               // overflow frontier lists, n entries each
     ClState *st;
     uint64_t total_limit_ns;
@@ -74,7 +82,13 @@ __device__ __forceinline__ bool claim(const ClArgs &a, uint32_t u, uint32_t v, i
     return true;
 }
 
-__global__ void __launch_bounds__(CT, 1) k_bfs_cluster(ClArgs a) {
+__device__ __forceinline__ uint32_t sat_add(uint32_t x, uint32_t w) {
+    const uint32_t r = x + w;
+    return r < x ? 0xffffffffu : r;
+}
+
+template <bool SSSP>
+__global__ void __launch_bounds__(CT, 1) k_cluster(ClArgs a) {
     extern __shared__ __align__(16) unsigned char cl_smem_raw[];
     ClSmem &s = *reinterpret_cast<ClSmem *>(cl_smem_raw);
     cg::cluster_group cl = cg::this_cluster();
@@ -84,11 +98,18 @@ __global__ void __launch_bounds__(CT, 1) k_bfs_cluster(ClArgs a) {
     ClState *st = a.st;
     ClSmem *s0 = cl.map_shared_rank(&s, 0);   // CTA 0's copy: cluster-wide counters
     // ---- init: visited bits (vertices past n are marked visited), the source
-    const uint32_t tail = (a.n & 31) ? ~((1u << (a.n & 31)) - 1u) : 0u;
-    for (uint32_t w = gtid; w < a.nwords; w += gthreads) {
-        uint32_t vis = (w == a.nwords - 1) ? tail : 0u;
-        if (w == (a.src >> 5)) vis |= 1u << (a.src & 31);
-        a.visited[w] = vis;
+    if (SSSP) {
+        for (uint32_t i = gtid; i < a.n; i += gthreads) {
+            a.dist[i] = i == a.src ? 0u : 0xffffffffu;
+            a.stamp[i] = 0u;
+        }
+    } else {
+        const uint32_t tail = (a.n & 31) ? ~((1u << (a.n & 31)) - 1u) : 0u;
+        for (uint32_t w = gtid; w < a.nwords; w += gthreads) {
+            uint32_t vis = (w == a.nwords - 1) ? tail : 0u;
+            if (w == (a.src >> 5)) vis |= 1u << (a.src & 31);
+            a.visited[w] = vis;
+        }
     }
     if (threadIdx.x == 0) {
         s.cnt[0] = (rank == 0) ? 1u : 0u;
@@ -99,8 +120,10 @@ __global__ void __launch_bounds__(CT, 1) k_bfs_cluster(ClArgs a) {
         s.stop = 0;
         if (rank == 0) {
             s.list[0][0] = a.src;
-            a.levels[a.src] = 0;
-            if (a.parents) a.parents[a.src] = (int32_t)a.src;
+            if (!SSSP) {
+                a.levels[a.src] = 0;
+                if (a.parents) a.parents[a.src] = (int32_t)a.src;
+            }
         }
     }
     cl.sync();
@@ -155,6 +178,30 @@ __global__ void __launch_bounds__(CT, 1) k_bfs_cluster(ClArgs a) {
                 const unsigned int h = atomicAdd(&s.nheavy, 1u);
                 if (h < HCAP) { s.heavy[h] = u; continue; }
             }
+            if (SSSP) {
+                const uint32_t du = __ldcg(&a.dist[u]);
+                for (uint32_t k0 = b; k0 < e; k0 += 4) {
+                    uint32_t v[4], nd[4], cur_d[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const bool in = k0 + k < e;
+                        v[k] = in ? __ldg(&a.ci[k0 + k]) : 0u;
+                        nd[k] = in ? sat_add(du, __ldg(&a.wt[k0 + k])) : 0xffffffffu;
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) cur_d[k] = nd[k] != 0xffffffffu ? __ldcg(&a.dist[v[k]]) : 0u;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (nd[k] >= cur_d[k]) continue;
+                        if (nd[k] >= atomicMin(&a.dist[v[k]], nd[k])) continue;
+                        if (atomicExch(&a.stamp[v[k]], (uint32_t)d + 1) == (uint32_t)d + 1) continue;
+                        const unsigned int idx = atomicAdd(&s.cnt[nxt], 1u);
+                        if (idx < CAP) s.list[nxt][idx] = v[k];
+                        else ov_nxt[atomicAdd(&st->ov_cnt[(d + 1) % 3], 1u)] = v[k];
+                    }
+                }
+                continue;
+            }
             // four neighbours at a time: their loads, then their claims, in flight together
             for (uint32_t k0 = b; k0 < e; k0 += 4) {
                 uint32_t v[4], bit[4], old[4];
@@ -182,9 +229,18 @@ __global__ void __launch_bounds__(CT, 1) k_bfs_cluster(ClArgs a) {
         for (unsigned int h = warp; h < nh; h += CT / 32) {
             const uint32_t u = s.heavy[h];
             const uint32_t b = __ldg(&a.rp[u]), e = __ldg(&a.rp[u + 1]);
+            const uint32_t du = SSSP ? __ldcg(&a.dist[u]) : 0u;
             for (uint32_t k = b + lane; k < e; k += 32) {
                 const uint32_t v = __ldg(&a.ci[k]);
-                if (claim(a, u, v, d)) {
+                bool joins;
+                if (SSSP) {
+                    const uint32_t nd = sat_add(du, __ldg(&a.wt[k]));
+                    joins = nd < __ldcg(&a.dist[v]) && nd < atomicMin(&a.dist[v], nd) &&
+                            atomicExch(&a.stamp[v], (uint32_t)d + 1) != (uint32_t)d + 1;
+                } else {
+                    joins = claim(a, u, v, d);
+                }
+                if (joins) {
                     const unsigned int idx = atomicAdd(&s.cnt[nxt], 1u);
                     if (idx < CAP) s.list[nxt][idx] = v;
                     else ov_nxt[atomicAdd(&st->ov_cnt[(d + 1) % 3], 1u)] = v;
@@ -210,7 +266,7 @@ __global__ void __launch_bounds__(CT, 1) k_bfs_cluster(ClArgs a) {
         }
     }
     // ---- vertices never reached get level and parent -1
-    if (!s0->stop) {
+    if (!SSSP && !s0->stop) {
         for (uint32_t w0 = (rank * (CT / 32) + warp) * 32; w0 < a.nwords; w0 += (gthreads / 32) * 32) {
             const uint32_t me = w0 + lane < a.nwords ? __ldcg(&a.visited[w0 + lane]) : ~0u;
             uint32_t todo = __ballot_sync(0xffffffffu, me != ~0u);
@@ -248,9 +304,12 @@ static int cluster_size(gb_context *ctx) {
     if (it != cache.end()) return it->second;
     int best = 0;
     const size_t smem = sizeof(clk::ClSmem);
-    if (cudaFuncSetAttribute(clk::k_bfs_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
-            cudaSuccess &&
-        cudaFuncSetAttribute(clk::k_bfs_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+    bool attrs = true;
+    for (const void *fn : {(const void *)clk::k_cluster<false>, (const void *)clk::k_cluster<true>}) {
+        attrs = attrs && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
+                cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+    }
+    if (attrs) {
         for (int c : {16, 8}) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(c);
@@ -264,7 +323,8 @@ static int cluster_size(gb_context *ctx) {
             cfg.attrs = at;
             cfg.numAttrs = 1;
             int nclusters = 0;
-            if (cudaOccupancyMaxActiveClusters(&nclusters, clk::k_bfs_cluster, &cfg) == cudaSuccess && nclusters > 0) {
+            if (cudaOccupancyMaxActiveClusters(&nclusters, clk::k_cluster<true>, &cfg) == cudaSuccess && nclusters > 0 &&
+                cudaOccupancyMaxActiveClusters(&nclusters, clk::k_cluster<false>, &cfg) == cudaSuccess && nclusters > 0) {
                 best = c;
                 break;
             }
@@ -292,6 +352,9 @@ gb_info bfs_cluster_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, in
     a.levels = levels;
     a.parents = parents;
     a.visited = visited;
+    a.dist = nullptr;
+    a.wt = nullptr;
+    a.stamp = nullptr;
     a.ov[0] = ov0;
     a.ov[1] = ov1;
     a.st = (clk::ClState *)state;
@@ -310,8 +373,58 @@ gb_info bfs_cluster_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, in
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int span = prof_begin(ctx, "bfs");
-    GB_CUDA(cudaLaunchKernelEx(&cfg, clk::k_bfs_cluster, a));
+    GB_CUDA(cudaLaunchKernelEx(&cfg, clk::k_cluster<false>, a));
     prof_end(ctx, span);
+    return GB_SUCCESS;
+}
+
+// SSSP from src in a single cluster: dist[n] out (device), stamp[n] scratch.
+gb_info sssp_cluster_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, uint32_t *dist, uint32_t *stamp,
+                            uint32_t *ov0, uint32_t *ov1, void *state) {
+    const int c = cluster_size(ctx);
+    if (!c) return fail(GB_NOT_IMPLEMENTED, "gb_sssp: this device cannot co-schedule a thread-block cluster");
+    clk::ClArgs a;
+    a.n = A->nrows;
+    a.nwords = (A->nrows + 31) / 32;
+    a.src = src;
+    a.rp = A->rowptr;
+    a.ci = A->colidx;
+    a.levels = nullptr;
+    a.parents = nullptr;
+    a.visited = nullptr;
+    a.dist = dist;
+    a.wt = (const uint32_t *)A->vals;
+    a.stamp = stamp;
+    a.ov[0] = ov0;
+    a.ov[1] = ov1;
+    a.st = (clk::ClState *)state;
+    a.total_limit_ns = 300000000000ull;
+    GB_CHECK(memset_async(ctx, state, 0, sizeof(clk::ClState)));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c);
+    cfg.blockDim = dim3(clk::CT);
+    cfg.dynamicSmemBytes = sizeof(clk::ClSmem);
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = c;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int span = prof_begin(ctx, "sssp");
+    GB_CUDA(cudaLaunchKernelEx(&cfg, clk::k_cluster<true>, a));
+    prof_end(ctx, span);
+    return GB_SUCCESS;
+}
+
+// Iterations and status of a finished cluster traversal (after a sync).
+gb_info cluster_iterations(gb_context *ctx, const void *state, uint32_t *iterations) {
+    clk::ClState hs;
+    GB_CUDA(cudaMemcpyAsync(&hs, state, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+    GB_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (iterations) *iterations = hs.depth;
+    if (hs.err) return fail(GB_TIMEOUT, "the cluster traversal ran out of its time budget");
     return GB_SUCCESS;
 }
 

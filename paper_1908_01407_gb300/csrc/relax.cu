@@ -320,7 +320,11 @@ __global__ void __launch_bounds__(BLOCK, 3) k_relax(RelaxArgs a) {
 
 struct BfsWorkspace;
 gb_info bfs_workspace_raw(gb_context *ctx, uint32_t n, uint32_t **visited, uint32_t **front, uint32_t **q,
-                          uint32_t **qp, uint32_t **qr, BfsState **st);
+                          uint32_t **qp, uint32_t **qr, BfsState **st, void **cl_state);
+bool bfs_cluster_available(gb_context *ctx);
+gb_info sssp_cluster_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, uint32_t *dist, uint32_t *stamp,
+                            uint32_t *ov0, uint32_t *ov1, void *state);
+gb_info cluster_iterations(gb_context *ctx, const void *state, uint32_t *iterations);
 
 static gb_info relax_run(gb_context *ctx, const gb_matrix *A, bool weighted, uint32_t src, uint32_t *out, gb_mem mem,
                          const gb_desc *desc, uint32_t *iterations, const char *who) {
@@ -335,7 +339,8 @@ static gb_info relax_run(gb_context *ctx, const gb_matrix *A, bool weighted, uin
     GB_CUDA(cudaSetDevice(ctx->device));
     uint32_t *visited, *front, *q, *qp, *qr;
     BfsState *st;
-    GB_CHECK(bfs_workspace_raw(ctx, A->nrows, &visited, &front, &q, &qp, &qr, &st));
+    void *cl_state = nullptr;
+    GB_CHECK(bfs_workspace_raw(ctx, A->nrows, &visited, &front, &q, &qp, &qr, &st, &cl_state));
     rlx::RelaxArgs a;
     a.n = A->nrows;
     a.nwords = (A->nrows + 31) / 32;
@@ -353,6 +358,18 @@ static gb_info relax_run(gb_context *ctx, const gb_matrix *A, bool weighted, uin
     if (mem == GB_HOST) {
         GB_CHECK(ob.alloc((size_t)A->nrows * 4 + 16));
         a.val = ob.as<uint32_t>();
+    }
+    // SSSP in a single cluster only when the descriptor asks for it: on
+    // weighted graphs the frontiers of improved vertices stay large even
+    // where BFS frontiers are small, and the whole GPU relaxes them faster
+    const int sch = desc ? desc->schedule : GB_SCHED_AUTO;
+    if (weighted && sch == GB_SCHED_CLUSTER && bfs_cluster_available(ctx)) {
+        Scratch stamp(ctx);
+        GB_CHECK(stamp.alloc((size_t)A->nrows * 4 + 16));
+        GB_CHECK(sssp_cluster_launch(ctx, A, src, a.val, stamp.as<uint32_t>(), q, q + A->nrows + 1, cl_state));
+        if (mem == GB_HOST)
+            GB_CUDA(cudaMemcpyAsync(out, a.val, (size_t)A->nrows * 4, cudaMemcpyDeviceToHost, ctx->stream));
+        return cluster_iterations(ctx, cl_state, iterations);
     }
     for (int k = 0; k < 3; ++k) a.front[k] = front + (size_t)k * a.nwords;
     a.q[0] = q; a.q[1] = q + A->nrows + 1;

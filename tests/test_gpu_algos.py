@@ -298,3 +298,23 @@ def test_bfs_multi_errors(ctx):
         gb.bfs_multi(ctx, A, np.array([t.n], np.uint32), np.empty((1, t.n), np.int32))
     assert e.value.code == gb.INVALID_INDEX
     A.free()
+
+
+@pytest.mark.parametrize("case", ["grid", "rmat14", "path", "two"])
+def test_sssp_single_cluster_schedule(ctx, case):
+    """SSSP relaxed inside one thread-block cluster: distances equal Dijkstra's."""
+    t = {"grid": lambda: gen.grid(120, 90, 0.15, seed=5, wmax=1000),
+         "rmat14": lambda: gen.rmat(14, 16, seed=3, wmax=255),
+         "path": lambda: gen.from_edges(400, [(i, i + 1) for i in range(399)],
+                                        weights=[(7 * i) % 13 + 1 for i in range(399)]),
+         "two": lambda: gen.from_edges(6, [(0, 1), (1, 2), (3, 4), (4, 5)], weights=[3, 5, 2, 9])}[case]()
+    g, A = build(ctx, t)
+    d = gb.Descriptor(schedule=gb.SCHED_CLUSTER)
+    srcs = [int(s) for s in gen.sources(t, 3, seed=2)] if t.n > 10 else [0, 5]
+    for src in srcs:
+        dist = np.empty(t.n, np.uint32)
+        _, it = gb.sssp(ctx, A, src, dist, desc=d)
+        assert np.array_equal(dist, oracle.sssp(g, src))
+        assert it >= 1
+    d.free()
+    A.free()
