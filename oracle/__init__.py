@@ -60,6 +60,8 @@ def _load():
             lib.orc_sssp.argtypes = [u32, vp, vp, vp, u32, vp]
             lib.orc_pagerank.restype = None
             lib.orc_pagerank.argtypes = [u32, vp, vp, ctypes.c_double, u32, vp, vp]
+            lib.orc_pagerank_delta.restype = u32
+            lib.orc_pagerank_delta.argtypes = [u32, vp, vp, ctypes.c_double, ctypes.c_float, u32, vp, vp]
             lib.orc_cc.restype = None
             lib.orc_cc.argtypes = [u32, vp, vp, vp]
             lib.orc_tc.restype = u64
@@ -154,6 +156,15 @@ def pagerank(g: CSR, alpha: float = 0.85, iters: int = 50):
     r = np.empty(max(iters, 1), dtype=np.float64)
     _load().orc_pagerank(g.n, _p(g.rowptr), _p(g.colidx), alpha, iters, _p(p), _p(r))
     return p, r[:iters]
+
+
+def pagerank_delta(g: CSR, alpha: float = 0.85, eps: float = 1e-6, max_iters: int = 100):
+    """FP64 adaptive PageRank (PageRankDelta): (p, iterations, active per
+    iteration). Converged vertices are masked out of later iterations."""
+    p = np.empty(g.n, dtype=np.float64)
+    act = np.zeros(max(max_iters, 1), dtype=np.uint32)
+    it = _load().orc_pagerank_delta(g.n, _p(g.rowptr), _p(g.colidx), alpha, eps, max_iters, _p(p), _p(act))
+    return p, int(it), act[:it]
 
 
 def cc(g: CSR) -> np.ndarray:

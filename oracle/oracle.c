@@ -246,6 +246,55 @@ void orc_pagerank(uint32_t n, const uint64_t *rowptr, const uint32_t *colidx,
 }
 
 /* ------------------------------------------------------------------ */
+/* Adaptive PageRank, also called PageRankDelta (Section 5.1 lists it   */
+/* among the uses of the output mask; Section 7.3 names it and leaves it */
+/* out). The recurrence of orc_pagerank, except that a vertex whose value */
+/* moved by at most eps times its new value in an iteration has          */
+/* converged: it is masked out of every later iteration (its value stays */
+/* as it is, and other vertices keep reading it). The decision           */
+/* |p'(i) - p(i)| <= eps * p'(i) is taken on the values rounded to FP32, */
+/* in FP32 arithmetic, the precision of the GPU path; everything else is */
+/* FP64. The dangling mass D = sum of p over vertices without edges is   */
+/* taken over all of them, frozen or not. Stops when no vertex is active */
+/* or after max_iters iterations; returns the iterations run.            */
+/* active[k] = vertices updated in iteration k (may be NULL).            */
+/* ------------------------------------------------------------------ */
+uint32_t orc_pagerank_delta(uint32_t n, const uint64_t *rowptr, const uint32_t *colidx, double alpha, float eps,
+                            uint32_t max_iters, double *p, uint32_t *active) {
+    double *q = (double *)malloc(sizeof(double) * (n ? n : 1));
+    unsigned char *on = (unsigned char *)malloc(n ? n : 1);
+    uint32_t nact = n, it = 0;
+    for (uint32_t i = 0; i < n; ++i) { p[i] = 1.0 / n; on[i] = 1; }
+    while (it < max_iters && nact > 0) {
+        if (active) active[it] = nact;
+        double dangling = 0.0;
+        for (uint32_t j = 0; j < n; ++j)
+            if (rowptr[j + 1] == rowptr[j]) dangling += p[j];
+        for (uint32_t i = 0; i < n; ++i) {
+            if (!on[i]) { q[i] = p[i]; continue; }
+            double s = 0.0;
+            for (uint64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+                uint32_t j = colidx[e];
+                s += p[j] / (double)(rowptr[j + 1] - rowptr[j]);
+            }
+            q[i] = (1.0 - alpha) / n + alpha * (s + dangling / n);
+        }
+        uint32_t next = 0;
+        for (uint32_t i = 0; i < n; ++i) {
+            if (on[i]) {
+                float a = (float)q[i], b = (float)p[i];
+                if (fabsf(a - b) <= eps * a) on[i] = 0; else ++next;
+            }
+            p[i] = q[i];
+        }
+        nact = next;
+        ++it;
+    }
+    free(q);
+    free(on);
+    return it;
+}
+
 /* Connected components (Section 7.4): label(v) = smallest vertex id in */
 /* v's component. Union-find with path halving, union by smaller root.  */
 /* ------------------------------------------------------------------ */

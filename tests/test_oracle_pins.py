@@ -296,6 +296,61 @@ def test_pagerank_uniform_on_regular_graphs(kind):
         assert np.all(r < 1e-14)
 
 
+# ---------------------------------------------------- adaptive PageRank ---
+@pytest.mark.parametrize("name", ["gnp", "dangling", "star"])
+def test_pagerank_delta_without_freezing_is_the_power_iteration(name):
+    """eps = -1 never freezes a vertex: k iterations of the adaptive form
+    are k steps of the dense Google-matrix power iteration."""
+    alpha = 0.85
+    if name == "gnp":
+        edges, _ = small_edges(11, 0.3, 43)
+        g = g_from_edges(11, edges)
+    elif name == "dangling":
+        g = g_from_edges(10, [(0, 1), (1, 2), (2, 0), (3, 4), (2, 5)])
+    else:
+        g = g_from_edges(8, [(0, i) for i in range(1, 8)])
+    G = google_matrix(g, alpha)
+    for k in (1, 3, 20):
+        p, it, act = oracle.pagerank_delta(g, alpha, -1.0, k)
+        y = np.full(g.n, 1.0 / g.n)
+        for _ in range(k):
+            y = G @ y
+        assert it == k and np.all(act == g.n)
+        assert np.abs(p - y).sum() < 1e-12
+
+
+def test_pagerank_delta_regular_graph_converges_at_once():
+    n = 13
+    g = g_from_edges(n, [(i, (i + 1) % n) for i in range(n)])
+    p, it, act = oracle.pagerank_delta(g, 0.85, 1e-6, 50)
+    assert it == 1 and list(act) == [n]
+    assert np.max(np.abs(p - 1.0 / n)) < 1e-15
+
+
+def test_pagerank_delta_frozen_vertices_stay_frozen():
+    """A vertex that stops changing never changes again, active counts never
+    grow, and a tiny eps ends next to the exact fixed point."""
+    edges, _ = small_edges(12, 0.25, 7)
+    g = g_from_edges(12, edges + [(0, 11)])
+    alpha, eps = 0.85, 1e-4
+    runs = [oracle.pagerank_delta(g, alpha, eps, k)[0] for k in range(1, 40)]
+    _, it, act = oracle.pagerank_delta(g, alpha, eps, 200)
+    assert np.all(np.diff(act.astype(np.int64)) <= 0)
+    same_prev = set()
+    for k in range(len(runs) - 1):
+        same = {i for i in range(g.n) if runs[k][i] == runs[k + 1][i]}
+        assert same_prev <= same
+        same_prev = same
+    G = google_matrix(g, alpha)
+    M = np.eye(g.n) - G
+    M[-1, :] = 1.0
+    rhs = np.zeros(g.n)
+    rhs[-1] = 1.0
+    pstar = np.linalg.solve(M, rhs)
+    p, it, _ = oracle.pagerank_delta(g, alpha, 1e-9, 500)
+    assert it < 500 and np.abs(p - pstar).sum() < 1e-6
+
+
 # ------------------------------------------------------------------- CC ---
 def test_cc_known_components_and_full_grid():
     edges = [(0, 3), (3, 7), (1, 2), (5, 6), (6, 8), (8, 5)]
