@@ -59,9 +59,9 @@ def _load():
             lib.orc_sssp.restype = ctypes.c_int
             lib.orc_sssp.argtypes = [u32, vp, vp, vp, u32, vp]
             lib.orc_pagerank.restype = None
-            lib.orc_pagerank.argtypes = [u32, vp, vp, ctypes.c_double, u32, vp, vp]
+            lib.orc_pagerank.argtypes = [u32, vp, vp, vp, ctypes.c_double, u32, vp, vp]
             lib.orc_pagerank_delta.restype = u32
-            lib.orc_pagerank_delta.argtypes = [u32, vp, vp, ctypes.c_double, ctypes.c_float, u32, vp, vp]
+            lib.orc_pagerank_delta.argtypes = [u32, vp, vp, vp, ctypes.c_double, ctypes.c_float, u32, vp, vp]
             lib.orc_cc.restype = None
             lib.orc_cc.argtypes = [u32, vp, vp, vp]
             lib.orc_tc.restype = u64
@@ -150,20 +150,34 @@ def sssp(g: CSR, src: int) -> np.ndarray:
     return d
 
 
-def pagerank(g: CSR, alpha: float = 0.85, iters: int = 50):
-    """FP64 PageRank vector and per-iteration L1 residuals."""
+def _in_edges(g: CSR, directed: bool):
+    """(in-neighbour CSR, out-degree row pointer or None) of graph g, whose
+    rows are out-edges; a symmetric graph is its own transpose."""
+    if not directed:
+        return g, None
+    rows = np.repeat(np.arange(g.n, dtype=np.uint32), np.diff(g.rowptr).astype(np.int64))
+    return csr_build(g.n, g.colidx, rows), g.rowptr
+
+
+def pagerank(g: CSR, alpha: float = 0.85, iters: int = 50, directed: bool = False):
+    """FP64 PageRank vector and per-iteration L1 residuals. g's rows are
+    out-edges; directed=False reads g as symmetric (rows are in-edges too)."""
+    gi, od = _in_edges(g, directed)
     p = np.empty(g.n, dtype=np.float64)
     r = np.empty(max(iters, 1), dtype=np.float64)
-    _load().orc_pagerank(g.n, _p(g.rowptr), _p(g.colidx), alpha, iters, _p(p), _p(r))
+    _load().orc_pagerank(g.n, _p(gi.rowptr), _p(gi.colidx), _p(od) if od is not None else None, alpha, iters,
+                         _p(p), _p(r))
     return p, r[:iters]
 
 
-def pagerank_delta(g: CSR, alpha: float = 0.85, eps: float = 1e-6, max_iters: int = 100):
+def pagerank_delta(g: CSR, alpha: float = 0.85, eps: float = 1e-6, max_iters: int = 100, directed: bool = False):
     """FP64 adaptive PageRank (PageRankDelta): (p, iterations, active per
     iteration). Converged vertices are masked out of later iterations."""
+    gi, od = _in_edges(g, directed)
     p = np.empty(g.n, dtype=np.float64)
     act = np.zeros(max(max_iters, 1), dtype=np.uint32)
-    it = _load().orc_pagerank_delta(g.n, _p(g.rowptr), _p(g.colidx), alpha, eps, max_iters, _p(p), _p(act))
+    it = _load().orc_pagerank_delta(g.n, _p(gi.rowptr), _p(gi.colidx), _p(od) if od is not None else None, alpha,
+                                    eps, max_iters, _p(p), _p(act))
     return p, int(it), act[:it]
 
 

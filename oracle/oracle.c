@@ -222,19 +222,22 @@ int orc_sssp(uint32_t n, const uint64_t *rowptr, const uint32_t *colidx,
 /* sum(p) = 1). p0 = 1/n, exactly `iters` iterations, FP64 throughout.  */
 /* residual[k] = sum_i |p_k+1(i) - p_k(i)|.                             */
 /* ------------------------------------------------------------------ */
-void orc_pagerank(uint32_t n, const uint64_t *rowptr, const uint32_t *colidx,
+/* rowptr/colidx list each vertex's in-neighbours; out_rowptr gives the  */
+/* out-degrees (NULL: the same structure, a symmetric graph).           */
+void orc_pagerank(uint32_t n, const uint64_t *rowptr, const uint32_t *colidx, const uint64_t *out_rowptr,
                   double alpha, uint32_t iters, double *p, double *residual) {
+    const uint64_t *od = out_rowptr ? out_rowptr : rowptr;
     double *q = (double *)malloc(sizeof(double) * (n ? n : 1));
     for (uint32_t i = 0; i < n; ++i) p[i] = 1.0 / n;
     for (uint32_t it = 0; it < iters; ++it) {
         double dangling = 0.0;
         for (uint32_t j = 0; j < n; ++j)
-            if (rowptr[j + 1] == rowptr[j]) dangling += p[j];
+            if (od[j + 1] == od[j]) dangling += p[j];
         for (uint32_t i = 0; i < n; ++i) {
             double s = 0.0;
             for (uint64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
                 uint32_t j = colidx[e];
-                s += p[j] / (double)(rowptr[j + 1] - rowptr[j]);
+                s += p[j] / (double)(od[j + 1] - od[j]);
             }
             q[i] = (1.0 - alpha) / n + alpha * (s + dangling / n);
         }
@@ -259,8 +262,9 @@ void orc_pagerank(uint32_t n, const uint64_t *rowptr, const uint32_t *colidx,
 /* or after max_iters iterations; returns the iterations run.            */
 /* active[k] = vertices updated in iteration k (may be NULL).            */
 /* ------------------------------------------------------------------ */
-uint32_t orc_pagerank_delta(uint32_t n, const uint64_t *rowptr, const uint32_t *colidx, double alpha, float eps,
-                            uint32_t max_iters, double *p, uint32_t *active) {
+uint32_t orc_pagerank_delta(uint32_t n, const uint64_t *rowptr, const uint32_t *colidx, const uint64_t *out_rowptr,
+                            double alpha, float eps, uint32_t max_iters, double *p, uint32_t *active) {
+    const uint64_t *od = out_rowptr ? out_rowptr : rowptr;
     double *q = (double *)malloc(sizeof(double) * (n ? n : 1));
     unsigned char *on = (unsigned char *)malloc(n ? n : 1);
     uint32_t nact = n, it = 0;
@@ -269,13 +273,13 @@ uint32_t orc_pagerank_delta(uint32_t n, const uint64_t *rowptr, const uint32_t *
         if (active) active[it] = nact;
         double dangling = 0.0;
         for (uint32_t j = 0; j < n; ++j)
-            if (rowptr[j + 1] == rowptr[j]) dangling += p[j];
+            if (od[j + 1] == od[j]) dangling += p[j];
         for (uint32_t i = 0; i < n; ++i) {
             if (!on[i]) { q[i] = p[i]; continue; }
             double s = 0.0;
             for (uint64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
                 uint32_t j = colidx[e];
-                s += p[j] / (double)(rowptr[j + 1] - rowptr[j]);
+                s += p[j] / (double)(od[j + 1] - od[j]);
             }
             q[i] = (1.0 - alpha) / n + alpha * (s + dangling / n);
         }

@@ -351,6 +351,27 @@ def test_pagerank_delta_frozen_vertices_stay_frozen():
     assert it < 500 and np.abs(p - pstar).sum() < 1e-6
 
 
+def test_pagerank_directed_matches_dense_power_iteration():
+    """A directed graph (rows = out-edges, some vertices without out-edges):
+    the pull over in-neighbours divided by out-degrees is the dense
+    random-surfer model, for plain and (never freezing) adaptive PageRank."""
+    rng = np.random.default_rng(17)
+    n = 12
+    r = rng.integers(0, n, 30).astype(np.uint32)
+    c = rng.integers(0, n, 30).astype(np.uint32)
+    keep = (r != c) & (r < 9)              # vertices 9..11 have no out-edges
+    g = oracle.csr_build(n, r[keep], c[keep])
+    G = google_matrix(g, 0.85)
+    for k in (1, 4, 30):
+        y = np.full(n, 1.0 / n)
+        for _ in range(k):
+            y = G @ y
+        p, _ = oracle.pagerank(g, 0.85, k, directed=True)
+        assert np.abs(p - y).sum() < 1e-12
+        q, it, _ = oracle.pagerank_delta(g, 0.85, -1.0, k, directed=True)
+        assert it == k and np.abs(q - y).sum() < 1e-12
+
+
 # ------------------------------------------------------------------- CC ---
 def test_cc_known_components_and_full_grid():
     edges = [(0, 3), (3, 7), (1, 2), (5, 6), (6, 8), (8, 5)]
