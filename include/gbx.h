@@ -367,6 +367,17 @@ gb_info gb_sssp(gb_context *ctx, const gb_matrix *A, uint32_t src, uint32_t *dis
  * rank[n] in `mem`; residuals[iters] (host, may be NULL). */
 gb_info gb_pagerank(gb_context *ctx, const gb_matrix *A, float damping, uint32_t iters, float *rank,
                     double *residuals, gb_mem mem);
+/* Adaptive PageRank, also called PageRankDelta (Section 5.1: converged
+ * vertices as the output mask; Section 7.3 names the variant): the
+ * gb_pagerank recurrence, where a vertex whose value moved by at most eps
+ * times its new value (tested in FP32) is masked out of every later
+ * iteration, its value kept and still read by the others. Stops when no
+ * vertex is active or after max_iters iterations. rank[nrows] in `mem`;
+ * iterations, residuals[max_iters] (L1 change per iteration, FP64) and
+ * active[max_iters] (vertices updated per iteration) are host pointers and
+ * may be NULL. Results are bit-reproducible. */
+gb_info gb_pagerank_delta(gb_context *ctx, const gb_matrix *A, float damping, float eps, uint32_t max_iters,
+                          float *rank, gb_mem mem, uint32_t *iterations, double *residuals, uint32_t *active);
 /* Connected components (Section 7.4) by min-label propagation
  * (min.second mxv to a fixed point): labels[v] = smallest vertex id in v's
  * component. iterations may be NULL. */

@@ -131,6 +131,7 @@ _SIGS = {
     "gb_sssp": [_P, _P, _U32, _P, _I, _P, _P], "gb_pagerank": [_P, _P, ctypes.c_float, _U32, _P, _P, _I],
     "gb_cc": [_P, _P, _P, _I, _P], "gb_tc": [_P, _P, _P, _P],
     "gb_cc_fastsv": [_P, _P, _P, _I, _P],
+    "gb_pagerank_delta": [_P, _P, ctypes.c_float, ctypes.c_float, _U32, _P, _I, _P, _P, _P],
     "gb_server_create": [_PP, _P, _P], "gb_server_add_graph": [_P, _P, _P], "gb_server_submit": [_P, _P, _P],
     "gb_server_wait": [_P, _U64, _U32, _P], "gb_server_fetch": [_P, _U64, _P, _I],
     "gb_server_stats_get": [_P, _P], "gb_server_destroy": [_PP],
@@ -610,6 +611,23 @@ def pagerank(ctx, A, damping=0.85, iters=50, rank=None, residuals=True):
     res = np.empty(max(iters, 1), np.float64) if residuals else None
     check(lib().gb_pagerank(ctx.h, A.h, damping, iters, pr, res.ctypes.data if res is not None else None, mr))
     return rank, (res[:iters] if res is not None else None)
+
+
+def pagerank_delta(ctx, A, damping=0.85, eps=1e-6, max_iters=100, rank=None):
+    """Adaptive PageRank (PageRankDelta). Returns (rank, iterations,
+    residuals[iterations], active[iterations])."""
+    n = A.nrows
+    if rank is None:
+        torch = _torch()
+        rank = torch.empty(n, dtype=torch.float32, device=f"cuda:{ctx.device}")
+    pr, mr = _out_mem(rank)
+    it = ctypes.c_uint32()
+    res = np.zeros(max(max_iters, 1), np.float64)
+    act = np.zeros(max(max_iters, 1), np.uint32)
+    check(lib().gb_pagerank_delta(ctx.h, A.h, damping, eps, max_iters, pr, mr, ctypes.byref(it),
+                                  res.ctypes.data, act.ctypes.data))
+    k = it.value
+    return rank, k, res[:k], act[:k]
 
 
 def cc_fastsv(ctx, A, labels=None):

@@ -318,3 +318,66 @@ def test_sssp_single_cluster_schedule(ctx, case):
         assert it >= 1
     d.free()
     A.free()
+
+
+# ------------------------------------------------------- adaptive PageRank
+@pytest.mark.parametrize("case", ["rmat14", "grid", "star", "cycle", "dangling"])
+def test_pagerank_delta_vs_fp64_oracle(ctx, case):
+    """Adaptive PageRank against the FP64 oracle with the same eps. Both take
+    the freeze decision in FP32; they can differ only for vertices within
+    FP32 rounding of the threshold, and such a vertex moves values by about
+    eps * p, so L1 <= 1e-5 (the FP32 PageRank bound) + 10 * eps. Runs are
+    bit-identical; iteration counts agree within 2."""
+    t = {"rmat14": lambda: gen.rmat(14, 16, seed=21),
+         "grid": lambda: gen.grid(100, 90, 0.1, seed=2),
+         "star": lambda: gen.from_edges(6000, [(0, i) for i in range(1, 6000)]),   # a row past 4096: block row
+         "cycle": lambda: gen.from_edges(97, [(i, (i + 1) % 97) for i in range(97)]),
+         "dangling": lambda: gen.from_edges(50, [(0, 1), (1, 2), (2, 0), (3, 4), (2, 5)])}[case]()
+    g, A = build(ctx, t, weights=False)
+    for eps in (1e-4, 1e-6):
+        want, it_o, act_o = oracle.pagerank_delta(g, 0.85, eps, 200)
+        got = np.empty(t.n, np.float32)
+        _, it, res, act = gb.pagerank_delta(ctx, A, 0.85, eps, 200, got)
+        assert abs(it - it_o) <= 2
+        assert np.abs(got.astype(np.float64) - want).sum() <= 1e-5 + 10 * eps
+        again = np.empty(t.n, np.float32)
+        gb.pagerank_delta(ctx, A, 0.85, eps, 200, again)
+        assert np.array_equal(got.view(np.uint32), again.view(np.uint32))
+        assert act[0] == t.n and np.all(np.diff(act.astype(np.int64)) <= 0)
+        if case == "cycle":
+            assert it == 1
+    A.free()
+
+
+def test_pagerank_delta_without_freezing_is_pagerank(ctx):
+    """eps = -1 never freezes: 50 iterations equal plain PageRank's."""
+    t = gen.rmat(13, 16, seed=22)
+    g, A = build(ctx, t, weights=False)
+    got = np.empty(t.n, np.float32)
+    _, it, res, act = gb.pagerank_delta(ctx, A, 0.85, -1.0, 50, got)
+    assert it == 50 and np.all(act == t.n)
+    want, r = oracle.pagerank(g, 0.85, 50)
+    assert np.abs(got.astype(np.float64) - want).sum() <= 1e-5
+    assert np.allclose(res, r, rtol=1e-3, atol=1e-7)
+    A.free()
+
+
+def test_pagerank_and_delta_directed_matrix(ctx):
+    """A non-symmetric matrix: rows are the in-edges (CSC), degrees the
+    out-degrees; plain and adaptive PageRank against the directed oracle."""
+    rng = np.random.default_rng(3)
+    n = 3000
+    r = rng.integers(0, n, 30000).astype(np.uint32)
+    c = rng.integers(0, n, 30000).astype(np.uint32)
+    A = gb.Matrix.from_tuples(ctx, n, r, c)
+    g = oracle.csr_build(n, r, c)
+    got = np.empty(n, np.float32)
+    gb.pagerank(ctx, A, 0.85, 30, got, residuals=False)
+    want, _ = oracle.pagerank(g, 0.85, 30, directed=True)
+    assert np.abs(got.astype(np.float64) - want).sum() <= 1e-5
+    eps = 1e-5
+    want, it_o, _ = oracle.pagerank_delta(g, 0.85, eps, 200, directed=True)
+    _, it, _, _ = gb.pagerank_delta(ctx, A, 0.85, eps, 200, got)
+    assert abs(it - it_o) <= 2
+    assert np.abs(got.astype(np.float64) - want).sum() <= 1e-5 + 10 * eps
+    A.free()
