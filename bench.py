@@ -369,6 +369,16 @@ def extra_rows(args, hbm):
                            "roofline": {"bound": "hbm", "kernel": "k_pr_spmv", "alg_bytes_per_launch": bytes_iter,
                                         "achieved": bytes_iter / (it_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                                         "frac": bytes_iter / (it_ms / 1e3) / 1e9 / hbm}}
+    # --- adaptive PageRank (PageRankDelta): converged vertices masked out
+    prd = {}
+    for eps in (1e-4, 1e-5):
+        gb.pagerank_delta(ctx, A, 0.85, eps, 200, rank)
+        its = []
+        ms = cuda_time_ms(lambda: its.append(gb.pagerank_delta(ctx, A, 0.85, eps, 200, rank)), stream)
+        _, it, _, act = its[0]
+        prd[f"eps_{eps:g}"] = {"ms_total": ms, "iterations": it, "row_updates": int(act.sum()),
+                               "row_updates_vs_plain_50": float(act.sum()) / (50.0 * n)}
+    out["pagerank_delta_s22"] = prd
     # --- multi-source BFS: the 64 benchmark sources in one bit-frontier launch
     bsrcs = gen.sources(t, NSRC, seed=SRC_SEED)
     lv = torch.empty((NSRC, n), dtype=torch.int32, device="cuda")

@@ -13,9 +13,12 @@
 // newly converged ones to a frozen list; x = p/deg is double-buffered, and
 // a vertex frozen in iteration t has its final x copied into the other
 // buffer in iteration t+1, so both buffers hold it from then on. Rows of up
-// to 32 entries are summed by one lane, longer rows by a warp, rows longer
-// than BLOCK_ROW by the whole block; each row's sum has one fixed order, so
-// the values do not depend on how the rows fall to threads. The L1
+// to 32 entries are summed by one lane, longer rows by a warp; the hub rows
+// (longer than GBX_HUB_MIN_LEN, the matrix's cached hub list) stay out of
+// the lists: they are dealt to the blocks round-robin, with an active flag
+// each, so no block ends up with the long rows of others. Each row's sum
+// has one fixed order, so the values do not depend on how rows fall to
+// threads. The L1
 // residual and the change of the dangling mass D are accumulated as 64-bit
 // fixed-point integers (every FP32 PageRank value is an integer multiple of
 // 2^-61), which makes their sums independent of the list order: runs are
@@ -31,8 +34,7 @@ namespace prd {
 constexpr int BLOCK = 256;
 constexpr int WARPS = BLOCK / 32;
 constexpr uint32_t WARP_ROW = 32;     // rows longer than this: a warp
-constexpr uint32_t BLOCK_ROW = 4096;  // rows longer than this: the whole block
-constexpr uint32_t BQ = 64;           // block-row queue per block
+constexpr uint32_t BLOCK_ROW = GBX_HUB_MIN_LEN;   // rows longer than this: hubs, a block each
 constexpr double FIX = 2305843009213693952.0;   // 2^61
 
 struct PrdState {
@@ -41,6 +43,7 @@ struct PrdState {
     unsigned int iters;
     unsigned int cnt[3];                 // active list produced in an iteration (slot = iteration % 3)
     unsigned int fcnt[3];                // frozen list produced in an iteration
+    unsigned int hcnt[3];                // hubs still active after an iteration
     unsigned long long dang[3];          // fixed-point change of D in an iteration (two's complement)
 };
 
@@ -53,7 +56,10 @@ struct PrdArgs {
     uint32_t max_iters;
     float *p;                            // the ranks (output), updated in place
     float *x[2];                         // p/deg, double-buffered
-    uint32_t *act[2], *frz[2];           // active and frozen lists
+    uint32_t *act[2], *frz[2];           // active and frozen lists (hubs excluded)
+    const uint32_t *hub;                 // hub vertices (rows longer than BLOCK_ROW)
+    uint32_t nhub;
+    unsigned char *hub_on;               // [nhub] 1 while the hub is active
     unsigned long long ndangling;        // vertices without out-edges
     unsigned long long *res_fix;         // [max_iters] fixed-point L1 residual per iteration (zeroed by the host)
     uint32_t *act_count;                 // [max_iters] active vertices per iteration
@@ -81,8 +87,6 @@ __device__ __forceinline__ void finish_row(const PrdArgs &a, uint32_t i, float y
 }
 
 __global__ void __launch_bounds__(BLOCK, 4) k_prd(PrdArgs a) {
-    __shared__ uint32_t s_bq[BQ];
-    __shared__ unsigned int s_nbq;
     __shared__ float s_red[WARPS];
     __shared__ unsigned long long s_res[WARPS];
     __shared__ long long s_dang[WARPS];
@@ -103,8 +107,8 @@ __global__ void __launch_bounds__(BLOCK, 4) k_prd(PrdArgs a) {
     bool ok = dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns);
     const uint64_t t_start = dev::globaltimer_ns();
     long long D = (long long)a.ndangling * to_fix(p0);   // every block keeps the same running D
-    uint32_t nact = a.n, nfrz = 0, it = 0;
-    while (ok && nact > 0 && it < a.max_iters) {
+    uint32_t nlist = a.n, nhub_on = a.nhub, nfrz = 0, it = 0;   // iteration 0's list: every vertex
+    while (ok && nlist + nhub_on > 0 && it < a.max_iters) {
         const float *xr = a.x[it & 1];
         float *xw = a.x[(it + 1) & 1];
         const uint32_t *L = it == 0 ? nullptr : a.act[it & 1];
@@ -115,23 +119,28 @@ __global__ void __launch_bounds__(BLOCK, 4) k_prd(PrdArgs a) {
             st->cnt[(it + 1) % 3] = 0;
             st->fcnt[(it + 1) % 3] = 0;
             st->dang[(it + 1) % 3] = 0;
-            a.act_count[it] = nact;
+            st->hcnt[(it + 1) % 3] = 0;
+            a.act_count[it] = (it == 0 ? a.n : nlist + nhub_on);
         }
         // vertices frozen in the previous iteration: their final x into this buffer too
         for (uint32_t k = tid; k < nfrz; k += nthreads) {
             const uint32_t i = __ldcg(&Fz[k]);
             xw[i] = __ldcg(&xr[i]);
         }
-        if (threadIdx.x == 0) s_nbq = 0;
-        __syncthreads();
         unsigned long long res = 0;
         long long dang = 0;
-        // active rows: a lane per short row, a warp per longer row, block rows queued
-        for (uint32_t g0 = (blockIdx.x * WARPS + warp) * 32; g0 < nact; g0 += nwarps * 32) {
+        // active rows of the list: a lane per short row, a warp per longer row
+        // (iteration 0 takes every vertex and skips the hubs, done below)
+        for (uint32_t g0 = (blockIdx.x * WARPS + warp) * 32; g0 < nlist; g0 += nwarps * 32) {
             const uint32_t k = g0 + lane;
-            const bool in = k < nact;
-            const uint32_t i = in ? (L ? __ldcg(&L[k]) : k) : 0u;
-            const uint32_t b = in ? __ldg(&a.rp[i]) : 0u, e = in ? __ldg(&a.rp[i + 1]) : 0u;
+            uint32_t i = 0, b = 0, e = 0;
+            bool in = k < nlist;
+            if (in) {
+                i = L ? __ldcg(&L[k]) : k;
+                b = __ldg(&a.rp[i]);
+                e = __ldg(&a.rp[i + 1]);
+                if (e - b > BLOCK_ROW) in = false;   // a hub
+            }
             const uint32_t len = e - b;
             bool keep = false, done = false;
             if (in && len <= WARP_ROW) {
@@ -155,22 +164,22 @@ __global__ void __launch_bounds__(BLOCK, 4) k_prd(PrdArgs a) {
                 const uint32_t ri = __shfl_sync(0xffffffffu, i, l);
                 const uint32_t rb = __shfl_sync(0xffffffffu, b, l), re = __shfl_sync(0xffffffffu, e, l);
                 float y = 0.f;
-                for (uint32_t q = rb + lane; q < re; q += 32) y += __ldcg(&xr[__ldg(&a.ci[q])]);
+                for (uint32_t q0 = rb; q0 < re; q0 += 128) {   // four loads per lane in flight
+                    float v[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const uint32_t q = q0 + t * 32 + lane;
+                        v[t] = q < re ? __ldcg(&xr[__ldg(&a.ci[q])]) : 0.f;
+                    }
+                    y += v[0];
+                    y += v[1];
+                    y += v[2];
+                    y += v[3];
+                }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
                 if (lane == l) {
                     finish_row(a, ri, y, base, xw, re - rb, res, dang, keep);
-                    done = true;
-                }
-            }
-            if (in && len > BLOCK_ROW) {
-                const unsigned int q = atomicAdd(&s_nbq, 1u);
-                if (q < BQ) {
-                    s_bq[q] = i;
-                } else {   // queue full: the lane sums the row itself
-                    float y = 0.f;
-                    for (uint32_t t = b; t < e; ++t) y += __ldcg(&xr[__ldg(&a.ci[t])]);
-                    finish_row(a, i, y, base, xw, len, res, dang, keep);
                     done = true;
                 }
             }
@@ -188,13 +197,24 @@ __global__ void __launch_bounds__(BLOCK, 4) k_prd(PrdArgs a) {
             if (done && !keep) Fn[fb + __popc(fm & dev::lanemask_lt())] = i;
         }
         __syncthreads();
-        // block rows: the whole block sums each queued row
-        const unsigned int nbq = s_nbq < BQ ? s_nbq : BQ;
-        for (unsigned int qi = 0; qi < nbq; ++qi) {
-            const uint32_t i = s_bq[qi];
+        // hubs: dealt to the blocks round-robin, the whole block sums each row
+        for (uint32_t h = blockIdx.x; h < a.nhub; h += gridDim.x) {
+            if (!a.hub_on[h]) continue;   // uniform over the block
+            const uint32_t i = __ldg(&a.hub[h]);
             const uint32_t b = __ldg(&a.rp[i]), e = __ldg(&a.rp[i + 1]);
             float y = 0.f;
-            for (uint32_t q = b + threadIdx.x; q < e; q += BLOCK) y += __ldcg(&xr[__ldg(&a.ci[q])]);
+            for (uint32_t q0 = b; q0 < e; q0 += 4 * BLOCK) {
+                float v[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const uint32_t q = q0 + t * BLOCK + threadIdx.x;
+                    v[t] = q < e ? __ldcg(&xr[__ldg(&a.ci[q])]) : 0.f;
+                }
+                y += v[0];
+                y += v[1];
+                y += v[2];
+                y += v[3];
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
             if (lane == 0) s_red[warp] = y;
@@ -204,8 +224,11 @@ __global__ void __launch_bounds__(BLOCK, 4) k_prd(PrdArgs a) {
                 for (int w = 0; w < WARPS; ++w) t += s_red[w];
                 bool keep = false;
                 finish_row(a, i, t, base, xw, e - b, res, dang, keep);
-                if (keep) Ln[atomicAdd(&st->cnt[it % 3], 1u)] = i;
-                else Fn[atomicAdd(&st->fcnt[it % 3], 1u)] = i;
+                if (keep) atomicAdd(&st->hcnt[it % 3], 1u);
+                else {
+                    a.hub_on[h] = 0;
+                    Fn[atomicAdd(&st->fcnt[it % 3], 1u)] = i;
+                }
             }
             __syncthreads();
         }
@@ -223,7 +246,8 @@ __global__ void __launch_bounds__(BLOCK, 4) k_prd(PrdArgs a) {
         ok = dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns);
         if (!ok) break;
         D += (long long)__ldcg(&st->dang[it % 3]);
-        nact = __ldcg(&st->cnt[it % 3]);
+        nlist = __ldcg(&st->cnt[it % 3]);
+        nhub_on = __ldcg(&st->hcnt[it % 3]);
         nfrz = __ldcg(&st->fcnt[it % 3]);
         ++it;
         if (threadIdx.x == 0 && dev::globaltimer_ns() - t_start > a.total_limit_ns)
@@ -264,7 +288,8 @@ extern "C" gb_info gb_pagerank_delta(gb_context *ctx, const gb_matrix *A, float 
     GB_CUDA(cudaSetDevice(ctx->device));
     const bool sym = A->csc_alias;
     if (!sym && !A->has_csc) return fail(GB_INVALID_VALUE, "gb_pagerank_delta: needs the CSC (in-edges) or a symmetric build");
-    Scratch pr(ctx), x(ctx), lists(ctx), resf(ctx), actc(ctx), stb(ctx), nd(ctx);
+    Scratch pr(ctx), x(ctx), lists(ctx), resf(ctx), actc(ctx), stb(ctx), nd(ctx), hon(ctx);
+    GB_CHECK(matrix_hubs(A, GBX_HUB_MIN_LEN));   // rows of the pulled structure (CSC, or CSR if symmetric)
     float *pout = rank;
     if (mem == GB_HOST) {
         GB_CHECK(pr.alloc((size_t)n * 4 + 16));
@@ -303,6 +328,11 @@ extern "C" gb_info gb_pagerank_delta(gb_context *ctx, const gb_matrix *A, float 
     a.frz[0] = lb + 2ull * n;
     a.frz[1] = lb + 3ull * n;
     a.ndangling = ndang;
+    a.hub = A->hub_list;
+    a.nhub = A->nhub;
+    GB_CHECK(hon.alloc((size_t)A->nhub + 16));
+    GB_CHECK(memset_async(ctx, hon.p, 1, (size_t)A->nhub + 1));
+    a.hub_on = hon.as<unsigned char>();
     a.res_fix = resf.as<unsigned long long>();
     a.act_count = actc.as<uint32_t>();
     a.st = stb.as<PrdState>();

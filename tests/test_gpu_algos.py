@@ -326,15 +326,18 @@ def test_pagerank_delta_vs_fp64_oracle(ctx, case):
     """Adaptive PageRank against the FP64 oracle with the same eps. Both take
     the freeze decision in FP32; they can differ only for vertices within
     FP32 rounding of the threshold, and such a vertex moves values by about
-    eps * p, so L1 <= 1e-5 (the FP32 PageRank bound) + 10 * eps. Runs are
-    bit-identical; iteration counts agree within 2."""
+    eps * p, so L1 <= 1e-5 (the FP32 PageRank bound) + 10 * eps. eps stays
+    at 80 FP32 ulps (1e-5) or more: closer to FP32 resolution the rounding of
+    the GPU's FP32 values decides the threshold crossing, and a graph whose
+    vertices all freeze together (the star's leaves) can shift by several
+    iterations. Runs are bit-identical; iteration counts agree within 2."""
     t = {"rmat14": lambda: gen.rmat(14, 16, seed=21),
          "grid": lambda: gen.grid(100, 90, 0.1, seed=2),
          "star": lambda: gen.from_edges(6000, [(0, i) for i in range(1, 6000)]),   # a row past 4096: block row
          "cycle": lambda: gen.from_edges(97, [(i, (i + 1) % 97) for i in range(97)]),
          "dangling": lambda: gen.from_edges(50, [(0, 1), (1, 2), (2, 0), (3, 4), (2, 5)])}[case]()
     g, A = build(ctx, t, weights=False)
-    for eps in (1e-4, 1e-6):
+    for eps in (1e-4, 1e-5):
         want, it_o, act_o = oracle.pagerank_delta(g, 0.85, eps, 200)
         got = np.empty(t.n, np.float32)
         _, it, res, act = gb.pagerank_delta(ctx, A, 0.85, eps, 200, got)
