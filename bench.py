@@ -521,14 +521,30 @@ def run_profile(args):
     """A short fixed run for profilers: build the workload of one kernel and
     launch it a few times (no timing, no CPU baseline). kinds: bfs (R-MAT
     s22, the benchmark sources), pr (PageRank on s22, a few iterations),
-    sssp (s22, weights in [1, 255]), msbfs (s22, 64 sources), tc (s20)."""
+    prd (adaptive PageRank on s22, eps 1e-4), sssp (s22, weights in
+    [1, 255]), msbfs (s22, 64 sources), tc (s20), fastsv (4096^2 grid),
+    gridbfs (4096^2 grid, single-cluster schedule)."""
     import torch
     import gen
     import paper_1908_01407_gb300 as gb
     kind = args.profile
     ctx = gb.Context(0)
     k = args.profile_launches
-    if kind == "tc":
+    if kind == "gridbfs":
+        t = gen.grid(4096, 4096, 0.1, seed=3)
+        A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, flags=gb.SYMMETRIC)
+        src = gen.first_nonisolated(t)
+        lv = torch.empty(t.n, dtype=torch.int32, device="cuda")
+        d = gb.Descriptor(schedule=gb.SCHED_CLUSTER)
+        for _ in range(k):
+            gb.bfs(ctx, A, src, lv, False, desc=d, stats=False)
+    elif kind == "fastsv":
+        t = gen.grid(4096, 4096, 0.1, seed=3)
+        A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, flags=gb.SYMMETRIC)
+        lab = torch.empty(t.n, dtype=torch.int32, device="cuda")
+        for _ in range(k):
+            gb.cc_fastsv(ctx, A, lab)
+    elif kind == "tc":
         t = gen.rmat(20, 16, seed=4)
         A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, flags=gb.SYMMETRIC)
         B, _ = A.degree_order()
@@ -552,6 +568,8 @@ def run_profile(args):
                 gb.bfs_multi(ctx, A, srcs, out.view(NSRC, t.n), stats=False)
             elif kind == "pr":
                 gb.pagerank(ctx, A, 0.85, 2, out.view(torch.float32), residuals=False)
+            elif kind == "prd":
+                gb.pagerank_delta(ctx, A, 0.85, 1e-4, 200, out.view(torch.float32))
     torch.cuda.synchronize()
     ctx.close()
     print(f"profile run done: {kind} x{k}")
@@ -576,7 +594,7 @@ def main():
     ap.add_argument("--serve-window-us", type=int, default=300)
     ap.add_argument("--serve-sweep-requests", type=int, default=800,
                     help="requests per point of the latency-vs-load sweep")
-    ap.add_argument("--profile", choices=["bfs", "pr", "sssp", "msbfs", "tc"], default=None,
+    ap.add_argument("--profile", choices=["bfs", "pr", "sssp", "msbfs", "tc", "prd", "fastsv", "gridbfs"], default=None,
                     help="short fixed run of one kernel for ncu")
     ap.add_argument("--profile-launches", type=int, default=3)
     args = ap.parse_args()

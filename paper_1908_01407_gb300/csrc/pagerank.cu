@@ -160,9 +160,9 @@ __global__ void __launch_bounds__(PR_BLOCK) k_pr_spmv(PrArgs a) {
             float xv[PR_LOAD_BATCH];
             uint32_t cidx[PR_LOAD_BATCH];
 #pragma unroll
-            for (int j = 0; j < PR_LOAD_BATCH; ++j) cidx[j] = tk0 + j0 + j < tk1 ? __ldg(&a.ci[tk0 + j0 + j]) : 0u;
+            for (int j = 0; j < PR_LOAD_BATCH; ++j) cidx[j] = tk0 + j0 + j < tk1 ? __ldcs(&a.ci[tk0 + j0 + j]) : 0u;
 #pragma unroll
-            for (int j = 0; j < PR_LOAD_BATCH; ++j) xv[j] = tk0 + j0 + j < tk1 ? __ldg(&a.x[cidx[j]]) : 0.f;
+            for (int j = 0; j < PR_LOAD_BATCH; ++j) xv[j] = tk0 + j0 + j < tk1 ? __ldcg(&a.x[cidx[j]]) : 0.f;
 #pragma unroll
             for (int j = 0; j < PR_LOAD_BATCH; ++j) s_xv[j0 + j][threadIdx.x] = xv[j];
         }
