@@ -31,22 +31,31 @@ namespace gbx {
 namespace bfsk {
 using namespace fr;
 
+// claim v for the next frontier: the first atomicOr on its visited bit wins.
+// On large pushes the bit is read first, which saves the atomic for the
+// many targets already visited; on small ones that read would only add a
+// dependent memory step.
 __device__ __forceinline__ bool claim(const BfsArgs &a, uint32_t v, uint32_t parent, int d, uint32_t *Fn,
-                                      uint32_t *deg_out) {
+                                      uint32_t *deg_out, uint32_t *r0_out, bool precheck) {
     uint32_t w = v >> 5, bit = 1u << (v & 31);
-    if (ldcg(&a.visited[w]) & bit) return false;
+    if (precheck && (ldcg(&a.visited[w]) & bit)) return false;
     uint32_t old = atomicOr(&a.visited[w], bit);
     if (old & bit) return false;
     a.levels[v] = d + 1;
     if (a.parents) a.parents[v] = (int32_t)parent;
     atomicOr(&Fn[w], bit);
-    *deg_out = __ldg(&a.rp_out[v + 1]) - __ldg(&a.rp_out[v]);
+    const uint32_t r0 = __ldg(&a.rp_out[v]);
+    *deg_out = __ldg(&a.rp_out[v + 1]) - r0;
+    *r0_out = r0;
     return true;
 }
 
+constexpr uint64_t PRECHECK_MIN_EDGES = 32768;
+
 __device__ void push_level(const BfsArgs &a, Smem &sm, int d, uint32_t cnt, uint64_t fe) {
-    push_edges(a, sm, d, cnt, fe, [&](uint32_t u, uint32_t v, uint32_t, uint32_t *Fn, uint32_t *deg) {
-        return claim(a, v, u, d, Fn, deg);
+    const bool precheck = fe >= PRECHECK_MIN_EDGES;
+    push_edges(a, sm, d, cnt, fe, [&](uint32_t u, uint32_t v, uint32_t, uint32_t *Fn, uint32_t *deg, uint32_t *r0) {
+        return claim(a, v, u, d, Fn, deg, r0, precheck);
     });
 }
 

@@ -31,6 +31,7 @@ static_assert(PUSH_ITEMS * 32 <= STAGE_CAP && PULL_WPW * 32 <= STAGE_CAP, "stagi
 struct Stage {
     uint32_t v[WARPS][STAGE_CAP];
     uint32_t deg[WARPS][STAGE_CAP];
+    uint32_t r0[WARPS][STAGE_CAP];   // row start (rp_out[v]), loaded with the degree
     uint32_t wcnt[WARPS];
     uint32_t wdeg[WARPS];
     unsigned long long base;
@@ -62,7 +63,7 @@ static __device__ __forceinline__ uint32_t owner_search_global(const uint32_t *P
 
 // warp-level: add this lane's discovery (if win) to the warp's staging row
 static __device__ __forceinline__ void stage_add(Stage &sg, uint32_t &staged, uint32_t &wdeg, bool win, uint32_t v,
-                                          uint32_t deg) {
+                                          uint32_t deg, uint32_t r0) {
     const uint32_t full = 0xffffffffu;
     const int warp = threadIdx.x >> 5;
     uint32_t wm = __ballot_sync(full, win);
@@ -71,6 +72,7 @@ static __device__ __forceinline__ void stage_add(Stage &sg, uint32_t &staged, ui
         uint32_t idx = staged + __popc(wm & dev::lanemask_lt());
         sg.v[warp][idx] = v;
         sg.deg[warp][idx] = deg;
+        sg.r0[warp][idx] = r0;
     }
     staged += __popc(wm);
     wdeg += dev::warp_sum<uint32_t>(win ? deg : 0u);
@@ -114,7 +116,7 @@ __device__ void stage_flush(const Args &a, Stage &sg, int slot_next, uint32_t *Q
                 uint32_t v = sg.v[warp][idx];
                 Qn[pos + idx] = v;
                 Pn[pos + idx] = pre + ex;
-                Rn[pos + idx] = __ldg(&a.rp_out[v]);
+                Rn[pos + idx] = sg.r0[warp][idx];
             }
             pre += tot;
         }
@@ -147,7 +149,8 @@ static __device__ uint32_t block_owner_search(const uint32_t *P, uint32_t cnt, u
 // vertices of a tile (prefix, id, row start) in shared memory and maps each
 // edge to its owner by binary search there. visit(u, v, p, Fn, &deg) handles
 // the edge u -> v stored at position p and returns whether v joins the next
-// frontier for the first time (then with its out-degree in deg).
+// frontier for the first time (then with its out-degree in deg and its row
+// start in r0).
 template <class Args, class Visit>
 __device__ void push_edges(const Args &a, Smem &sm, int d, uint32_t cnt, uint64_t fe, Visit visit) {
     const int cur = d & 1, nxt = (d + 1) & 1;
@@ -189,7 +192,7 @@ __device__ void push_edges(const Args &a, Smem &sm, int d, uint32_t cnt, uint64_
         for (int it = 0; it < PUSH_ITEMS; ++it) {
             uint64_t e = E + (uint64_t)it * BLOCK + threadIdx.x;
             bool win = false;
-            uint32_t v = 0, deg = 0;
+            uint32_t v = 0, deg = 0, r0 = 0;
             if (e < Eend) {
                 uint32_t lo = 0, hi = W;
                 while (hi - lo > 1) {
@@ -199,9 +202,9 @@ __device__ void push_edges(const Args &a, Smem &sm, int d, uint32_t cnt, uint64_
                 uint32_t u = sm.push.Q[lo];
                 uint32_t p = sm.push.R[lo] + (uint32_t)(e - sm.push.P[lo]);
                 v = ld_stream(&a.ci_out[p]);
-                win = visit(u, v, p, Fn, &deg);
+                win = visit(u, v, p, Fn, &deg, &r0);
             }
-            stage_add(sm.stage, staged, wdeg, win, v, deg);
+            stage_add(sm.stage, staged, wdeg, win, v, deg, r0);
         }
         // the owner of the next tile's first edge
         uint32_t knext = k + W;

@@ -349,13 +349,14 @@ __global__ void __launch_bounds__(BLOCK, 3) k_msbfs(MsArgs a) {
             }
             const unsigned long long *F = a.F[d % 3];
             unsigned long long *Fn = a.F[(d + 1) % 3];
-            push_edges(a, sm, d, cnt, fe, [&](uint32_t u, uint32_t v, uint32_t, uint32_t *, uint32_t *deg) {
+            push_edges(a, sm, d, cnt, fe, [&](uint32_t u, uint32_t v, uint32_t, uint32_t *, uint32_t *deg, uint32_t *r0) {
                 unsigned long long nb = ldcg64(&F[u]) & ~(ldcg64(&a.V[v]) | ldcg64(&F[v]));
                 if (!nb) return false;
                 if ((ldcg64(&Fn[v]) | nb) == ldcg64(&Fn[v])) return false;
                 unsigned long long old = atomicOr(&Fn[v], nb);
                 if (old) return false;
-                *deg = __ldg(&a.rp_out[v + 1]) - __ldg(&a.rp_out[v]);
+                *r0 = __ldg(&a.rp_out[v]);
+                *deg = __ldg(&a.rp_out[v + 1]) - *r0;
                 return true;
             });
             list_valid = true;

@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_relax(RelaxArgs a) {
                 compact_level(a, sm, d);
                 if (!dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns)) { ok = false; break; }
             }
-            push_edges(a, sm, d, cnt, fe, [&](uint32_t u, uint32_t v, uint32_t p, uint32_t *Fn, uint32_t *deg) {
+            push_edges(a, sm, d, cnt, fe, [&](uint32_t u, uint32_t v, uint32_t p, uint32_t *Fn, uint32_t *deg, uint32_t *r0) {
                 uint32_t c = relax_val(a, ldcg(&a.val[u]), p, a.w_out);
                 if (c >= ldcg(&a.val[v])) return false;
                 uint32_t old = atomicMin(&a.val[v], c);
@@ -288,7 +288,8 @@ __global__ void __launch_bounds__(BLOCK, 3) k_relax(RelaxArgs a) {
                 uint32_t bit = 1u << (v & 31);
                 uint32_t o = atomicOr(&Fn[v >> 5], bit);
                 if (o & bit) return false;
-                *deg = __ldg(&a.rp_out[v + 1]) - __ldg(&a.rp_out[v]);
+                *r0 = __ldg(&a.rp_out[v]);
+                *deg = __ldg(&a.rp_out[v + 1]) - *r0;
                 return true;
             });
             list_valid = true;
