@@ -73,7 +73,7 @@ static __device__ __forceinline__ void rows_min_long(const uint32_t *ci, const u
     }
 }
 
-__global__ void __launch_bounds__(BLOCK, 4) k_fastsv(SvArgs a) {
+__global__ void __launch_bounds__(BLOCK, 8) k_fastsv(SvArgs a) {
     __shared__ unsigned int s_changed;
     SvState *st = a.st;
     const uint32_t nthreads = gridDim.x * BLOCK;

@@ -248,7 +248,7 @@ __device__ void ms_pull_hubs(const MsArgs &a, int d, uint32_t *cnt_out, uint32_t
     *deg_out += mydeg;
 }
 
-__global__ void __launch_bounds__(BLOCK, 3) k_msbfs(MsArgs a) {
+__global__ void __launch_bounds__(BLOCK, 5) k_msbfs(MsArgs a) {
     __shared__ Smem sm;
     __shared__ uint32_t s_cnt, s_deg;
     const uint32_t nthreads = gridDim.x * BLOCK;

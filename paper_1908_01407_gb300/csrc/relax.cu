@@ -46,7 +46,7 @@ struct RelaxArgs {
     uint64_t hub_edges;
 };
 
-constexpr int RPULL_WPW = 4;
+constexpr int RPULL_WPW = 1;
 
 __device__ __forceinline__ uint32_t relax_val(const RelaxArgs &a, uint32_t vu, uint32_t p, const uint32_t *w) {
     return a.weighted ? sat_add<uint32_t>(vu, __ldg(&w[p])) : vu;
@@ -201,7 +201,7 @@ __device__ void relax_pull_hubs(const RelaxArgs &a, int d, uint32_t *cnt_out, ui
     *deg_out += mydeg;
 }
 
-__global__ void __launch_bounds__(BLOCK, 3) k_relax(RelaxArgs a) {
+__global__ void __launch_bounds__(BLOCK, 6) k_relax(RelaxArgs a) {
     __shared__ Smem sm;
     __shared__ uint32_t s_cnt, s_deg;
     const uint32_t nthreads = gridDim.x * BLOCK;
