@@ -203,6 +203,21 @@ def test_tc_count_and_entries(ctx, case):
         x.free()
 
 
+def test_tc_total_with_rows_longer_than_the_shared_buffer(ctx):
+    """K_600: equal degrees, so after the relabel row i of L holds i entries;
+    rows past 512 are searched in global memory. C(600, 3) triangles, the
+    same total with and without the per-entry C."""
+    n = 600
+    t = gen.from_edges(n, list(itertools.combinations(range(n), 2)))
+    A, B, L, _ = tc_pipeline(ctx, t)
+    want = n * (n - 1) * (n - 2) // 6
+    assert gb.tc(ctx, L) == want
+    C = gb.Matrix(ctx, gb.UINT32, n, n)
+    assert gb.tc(ctx, L, C) == want
+    for x in (A, B, L, C):
+        x.free()
+
+
 def test_tc_agrees_with_generic_masked_mxm(ctx):
     t = gen.rmat(11, 16, seed=6)
     A, B, L, _ = tc_pipeline(ctx, t)
