@@ -348,7 +348,10 @@ gb_info gb_bfs_noalloc(const uint32_t *rowptr, const uint32_t *colidx, const uin
                        uint32_t n, uint64_t nnz, uint32_t src, int32_t *levels, int32_t *parents, void *stream);
 /* Multi-source BFS as Boolean SpMM over 64-bit bit-packed frontiers
  * (Section 3.3 multi-nodeset traversal; Section 9 matrix direction
- * optimisation): k <= 64 sources, levels is k x nrows (row q = source q). */
+ * optimisation): k >= 1 sources, levels is k x nrows (row q = source q).
+ * One launch serves up to 64 sources; more are served by consecutive
+ * launches of 64 (the statistics then sum or maximise over them, the trace
+ * is the first launch's). */
 gb_info gb_bfs_multi(gb_context *ctx, const gb_matrix *A, const uint32_t *srcs, uint32_t k, int32_t *levels,
                      gb_mem mem, const gb_desc *desc, gb_bfs_stats *stats);
 /* SSSP (Section 7.2): adaptive Bellman-Ford by min.plus mxv restricted to

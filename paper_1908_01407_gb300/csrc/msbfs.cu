@@ -492,23 +492,40 @@ gb_info msbfs_launch(gb_context *ctx, const gb_matrix *A, const uint32_t *d_srcs
 
 extern "C" gb_info gb_bfs_multi(gb_context *ctx, const gb_matrix *A, const uint32_t *srcs, uint32_t k, int32_t *levels,
                                 gb_mem mem, const gb_desc *desc, gb_bfs_stats *stats) {
+    if (k == 0) return fail(GB_INVALID_VALUE, "gb_bfs_multi: no sources");
     if (!ctx || !A || !srcs || !levels) return fail(GB_NULL_POINTER, "gb_bfs_multi: NULL argument");
     if (!A->built) return fail(GB_INVALID_VALUE, "gb_bfs_multi: matrix not built");
     if (A->nrows != A->ncols) return fail(GB_DIMENSION_MISMATCH, "gb_bfs_multi: matrix must be square");
-    if (k == 0 || k > 64) return fail(GB_INVALID_VALUE, "gb_bfs_multi: k must be in 1..64");
     for (uint32_t q = 0; q < k; ++q)
         if (srcs[q] >= A->nrows) return fail(GB_INVALID_INDEX, "gb_bfs_multi: source %u out of range", srcs[q]);
     GB_CUDA(cudaSetDevice(ctx->device));
     Scratch ds(ctx), dl(ctx);
-    GB_CHECK(ds.alloc(64 * 4));
+    GB_CHECK(ds.alloc((size_t)k * 4 + 16));
     GB_CHECK(copy_in(ctx, ds.p, srcs, (size_t)k * 4, GB_HOST));
     int32_t *out = levels;
     size_t bytes = (size_t)k * A->nrows * 4;
     if (mem == GB_HOST) { GB_CHECK(dl.alloc(bytes + 16)); out = dl.as<int32_t>(); }
-    BfsResult hs;
-    GB_CHECK(msbfs_launch(ctx, A, ds.as<uint32_t>(), k, out, desc, &hs));
+    // more than 64 sources: consecutive launches of up to 64, each with its
+    // own push/pull decisions; the statistics are those of the first launch
+    // (depth and counts are summed and maximised over all of them)
+    std::vector<BfsResult> parts((k + 63) / 64);
+    for (uint32_t q0 = 0; q0 < k; q0 += 64) {
+        const uint32_t kc = k - q0 < 64 ? k - q0 : 64;
+        GB_CHECK(msbfs_launch(ctx, A, ds.as<uint32_t>() + q0, kc, out + (size_t)q0 * A->nrows, desc,
+                              &parts[q0 / 64]));
+    }
     if (mem == GB_HOST) GB_CUDA(cudaMemcpyAsync(levels, out, bytes, cudaMemcpyDeviceToHost, ctx->stream));
     GB_CHECK(sync(ctx));
+    BfsResult hs = parts[0];
+    for (size_t c = 1; c < parts.size(); ++c) {
+        const BfsResult &hk = parts[c];
+        if (hk.depth > hs.depth) hs.depth = hk.depth;
+        hs.push_levels += hk.push_levels;
+        hs.pull_levels += hk.pull_levels;
+        hs.reached += hk.reached;
+        hs.frontier_edges += hk.frontier_edges;
+        if (!hs.err) hs.err = hk.err;
+    }
     if (stats) {
         memset(stats, 0, sizeof(*stats));
         stats->depth = hs.depth;

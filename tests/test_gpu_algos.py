@@ -284,7 +284,8 @@ def test_tc_rmat_s20_full_size(ctx):
 
 
 # ------------------------------------------------------- multi-source BFS
-@pytest.mark.parametrize("case,k", [("rmat14", 64), ("rmat14", 1), ("rmat13", 37), ("grid", 64), ("small", 5)])
+@pytest.mark.parametrize("case,k", [("rmat14", 64), ("rmat14", 1), ("rmat13", 37), ("grid", 64), ("small", 5),
+                                    ("rmat13", 150)])
 def test_bfs_multi_matches_independent_bfs(ctx, case, k):
     t = {"rmat14": lambda: gen.rmat(14, 16, seed=1),
          "rmat13": lambda: gen.rmat(13, 8, seed=8),
@@ -307,7 +308,7 @@ def test_bfs_multi_errors(ctx):
     t = gen.rmat(8, 4, seed=1)
     A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, flags=gb.SYMMETRIC)
     with pytest.raises(gb.GBError) as e:
-        gb.bfs_multi(ctx, A, np.zeros(65, np.uint32), np.empty((65, t.n), np.int32))
+        gb.bfs_multi(ctx, A, np.zeros(0, np.uint32), np.empty((1, t.n), np.int32))
     assert e.value.code == gb.INVALID_VALUE
     with pytest.raises(gb.GBError) as e:
         gb.bfs_multi(ctx, A, np.array([t.n], np.uint32), np.empty((1, t.n), np.int32))
