@@ -98,8 +98,8 @@ __device__ void relax_pull(const RelaxArgs &a, int d, uint32_t *cnt_out, uint32_
 #pragma unroll
             for (int j = 0; j < RPULL_WPW; ++j) {
                 if (pend[j]) {
-                    c[j] = __ldg(&ci4[p[j] >> 2]);
-                    if (a.weighted) wv[j] = __ldg(&w4[p[j] >> 2]);
+                    c[j] = ld_stream(&ci4[p[j] >> 2]);
+                    if (a.weighted) wv[j] = ld_stream(&w4[p[j] >> 2]);
                 }
             }
             uint32_t fw[RPULL_WPW][4];
@@ -139,7 +139,7 @@ __device__ void relax_pull(const RelaxArgs &a, int d, uint32_t *cnt_out, uint32_
                 uint32_t pb = __shfl_sync(full, b[j], l), pe = __shfl_sync(full, e[j], l);
                 uint32_t mn = UINT32_MAX;
                 for (uint32_t q = pb + lane; q < pe; q += 32) {
-                    uint32_t u = __ldg(&a.ci_in[q]);
+                    uint32_t u = ld_stream(&a.ci_in[q]);
                     if ((ldcg(&F[u >> 5]) >> (u & 31)) & 1u) {
                         uint32_t c = relax_val(a, ldcg(&a.val[u]), q, a.w_in);
                         if (c < mn) mn = c;
@@ -187,7 +187,7 @@ __device__ void relax_pull_hubs(const RelaxArgs &a, int d, uint32_t *cnt_out, ui
         }
         const uint32_t v = __ldg(&a.hub_list[lo]);
         const uint32_t p = __ldg(&a.rp_in[v]) + (uint32_t)(x - __ldg(&a.hub_pre[lo]));
-        const uint32_t u = __ldg(&a.ci_in[p]);
+        const uint32_t u = ld_stream(&a.ci_in[p]);
         if (!((ldcg(&F[u >> 5]) >> (u & 31)) & 1u)) continue;
         const uint32_t c = relax_val(a, ldcg(&a.val[u]), p, a.w_in);
         if (c >= ldcg(&a.val[v])) continue;
