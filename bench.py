@@ -268,19 +268,20 @@ def run_gbx(args):
     ms_per_step = total_ms / args.steps
     value = ws * NSRC * m / (ms_per_step / 1e3) / 1e9
 
-    # end to end through the C ABI with host buffers: outputs copied to pinned host memory
-    lv_h = torch.empty(n, dtype=torch.int32).pin_memory()
-    pa_h = torch.empty(n, dtype=torch.int32).pin_memory()
-    srcs_h = torch.from_numpy(srcs.astype(np.int64)).pin_memory()
+    # end to end through the C ABI with host buffers: one gb_bfs_batch call per step writes every
+    # source's levels and parents to pinned host memory (each run's copy overlaps the next run)
+    lv_h = torch.empty((NSRC, n), dtype=torch.int32, pin_memory=True)
+    pa_h = torch.empty((NSRC, n), dtype=torch.int32, pin_memory=True)
+    srcs_u = srcs.astype(np.uint32)
+    gb.bfs_batch(ctx, A, srcs_u[:2], lv_h[:2], pa_h[:2], desc=desc)
     torch.cuda.synchronize()
+    e_steps = max(1, min(args.steps, 3))
     e0 = time.perf_counter()
-    for _ in range(max(1, min(args.steps, 2))):
-        sl = srcs_h.tolist()
-        for s in sl:
-            gb.bfs(ctx, A, int(s), lv_h, pa_h, desc=desc, stats=False)
-    e_steps = max(1, min(args.steps, 2))
+    for _ in range(e_steps):
+        gb.bfs_batch(ctx, A, srcs_u, lv_h, pa_h, desc=desc)
     e2e_s = (time.perf_counter() - e0) / e_steps
     e2e_val = NSRC * m / e2e_s / 1e9
+    del lv_h, pa_h
 
     hbm, peak_kind = peaks()
     avg_kernel_ms = k_ms / max(k_n, 1)

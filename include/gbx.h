@@ -308,6 +308,19 @@ typedef struct {
  * GB_SCHEDULE (a device that cannot co-schedule a cluster runs GB_SCHED_GRID). */
 gb_info gb_bfs(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *levels, int32_t *parents,
                gb_mem mem, const gb_desc *desc, gb_bfs_stats *stats);
+/* k independent direction-optimised BFS runs (Algorithm 1, Section 7.1),
+ * one per source srcs[q] (host array, k >= 1, every entry < nrows or
+ * GB_INVALID_INDEX before anything runs): row q of levels and of parents
+ * (each k x nrows, row-major, in `mem`; parents may be NULL) holds what
+ * gb_bfs from srcs[q] would give. With GB_HOST outputs the runs write to two
+ * alternating device buffers and the device-to-host copy of run q, on a
+ * stream of the call's own, overlaps run q+1 (the paper has no counterpart:
+ * it keeps the copy engines busy while the traversal kernels run; host
+ * buffers should be pinned, pageable ones work but serialise the copies).
+ * desc as for gb_bfs. The call synchronises and returns GB_TIMEOUT if a
+ * bounded device wait ran out in any run. */
+gb_info gb_bfs_batch(gb_context *ctx, const gb_matrix *A, const uint32_t *srcs, uint32_t k, int32_t *levels,
+                     int32_t *parents, gb_mem mem, const gb_desc *desc);
 /* Autotuner of the push/pull switch threshold (Table 9: pull iff
  * |E_f| > |E| / beta; Section 5.3 suggests Table 9 as a starting point for
  * finding the best threshold on given hardware). Runs gb_bfs from the k

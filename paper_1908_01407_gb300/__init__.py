@@ -128,6 +128,7 @@ _SIGS = {
     "gb_bfs": [_P, _P, _U32, _P, _P, _I, _P, _P],
     "gb_bfs_noalloc": [_P, _P, _P, _P, _U32, _U64, _U32, _P, _P, _P],
     "gb_bfs_autotune": [_P, _P, _P, _U32, _P, _P], "gb_bfs_multi": [_P, _P, _P, _U32, _P, _I, _P, _P],
+    "gb_bfs_batch": [_P, _P, _P, _U32, _P, _P, _I, _P],
     "gb_sssp": [_P, _P, _U32, _P, _I, _P, _P], "gb_pagerank": [_P, _P, ctypes.c_float, _U32, _P, _P, _I],
     "gb_cc": [_P, _P, _P, _I, _P], "gb_tc": [_P, _P, _P, _P],
     "gb_cc_fastsv": [_P, _P, _P, _I, _P],
@@ -575,6 +576,28 @@ def bfs_noalloc(rowptr, colidx, colptr, rowidx, n, nnz, src, levels, parents=Non
     ptrs = [x.data_ptr() if x is not None else None for x in (rowptr, colidx, colptr, rowidx, levels, parents)]
     check(lib().gb_bfs_noalloc(ptrs[0], ptrs[1], ptrs[2], ptrs[3], n, nnz, src, ptrs[4], ptrs[5],
                                ctypes.c_void_p(stream.cuda_stream)))
+    return levels, parents
+
+
+def bfs_batch(ctx, A, srcs, levels=None, parents=None, desc=None):
+    """gb_bfs_batch: one direction-optimised BFS per source; row q of the
+    k x nrows int32 levels/parents (torch CUDA tensors or host arrays, e.g.
+    pinned CPU tensors) is source q's result. Host outputs are copied while
+    the next run traverses. parents=False skips parents."""
+    srcs = np.ascontiguousarray(srcs, dtype=np.uint32)
+    k, n = int(srcs.shape[0]), A.nrows
+    if levels is None:
+        torch = _torch()
+        levels = torch.empty((k, n), dtype=torch.int32, device=f"cuda:{ctx.device}")
+        if parents is None:
+            parents = torch.empty((k, n), dtype=torch.int32, device=f"cuda:{ctx.device}")
+    if parents is False:
+        parents = None
+    pl, ml = _out_mem(levels)
+    pp, mp = _out_mem(parents) if parents is not None else (None, ml)
+    if parents is not None and mp != ml:
+        raise ValueError("levels and parents must both be host or both device")
+    check(lib().gb_bfs_batch(ctx.h, A.h, srcs.ctypes.data, k, pl, pp, ml, _h(desc)))
     return levels, parents
 
 

@@ -521,7 +521,9 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
         unsigned int old = atomicAdd(&st->bar.exits, 1u);
         if (old == gridDim.x - 1) {
             __threadfence();
-            res->err = ld_relaxed_gpu_int_(&st->err);
+            const int e = ld_relaxed_gpu_int_(&st->err);
+            res->err = e;
+            if (e && a.err_sticky) atomicMax(a.err_sticky, e);
             res->t_exit = dev::globaltimer_ns();
             st->err = 0;
             st->bar.count = 0;
@@ -537,7 +539,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
 // the single-cluster schedule (bfs_cluster.cu)
 bool bfs_cluster_available(gb_context *ctx);
 gb_info bfs_cluster_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *levels, int32_t *parents,
-                           uint32_t *visited, uint32_t *ov0, uint32_t *ov1, void *state);
+                           uint32_t *visited, uint32_t *ov0, uint32_t *ov1, void *state, int *err_sticky);
 size_t bfs_cluster_state_bytes();
 gb_info bfs_cluster_result(gb_context *ctx, const void *state, gb_bfs_stats *stats);
 
@@ -611,12 +613,13 @@ static int bfs_schedule(gb_context *ctx, const gb_matrix *A, const gb_desc *desc
 }
 
 static gb_info bfs_cluster_run(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *levels,
-                               int32_t *parents, BfsWorkspace *w) {
-    return bfs_cluster_launch(ctx, A, src, levels, parents, w->visited, w->q, w->q + A->nrows + 1, w->cl_state);
+                               int32_t *parents, BfsWorkspace *w, int *err_sticky = nullptr) {
+    return bfs_cluster_launch(ctx, A, src, levels, parents, w->visited, w->q, w->q + A->nrows + 1, w->cl_state,
+                              err_sticky);
 }
 
 gb_info bfs_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *levels, int32_t *parents,
-                   const gb_desc *desc, BfsWorkspace *w, int grid_override) {
+                   const gb_desc *desc, BfsWorkspace *w, int grid_override, int *err_sticky = nullptr) {
     BfsArgs a;
     a.n = A->nrows;
     a.nwords = (A->nrows + 31) / 32;
@@ -647,6 +650,7 @@ gb_info bfs_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *l
     a.st = w->st;
     a.timeout_ns = 4000000000ull;
     a.total_limit_ns = 120000000000ull;
+    a.err_sticky = err_sticky;
     int grid = w->grid;
     if (ctx->grid_limit > 0 && ctx->grid_limit < grid) grid = ctx->grid_limit;
     if (grid_override > 0 && grid_override < grid) grid = grid_override;
@@ -721,6 +725,87 @@ extern "C" gb_info gb_bfs(gb_context *ctx, const gb_matrix *A, uint32_t src, int
         }
         if (hs.err) return fail(GB_TIMEOUT, "gb_bfs: a bounded grid barrier wait ran out");
     }
+    return GB_SUCCESS;
+}
+
+// k independent BFS runs. With host outputs, run q writes one of two device
+// result buffers and a second stream copies it to row q of the host arrays
+// while run q+1 traverses; run q+2 waits for that copy before it reuses the
+// buffer. Each kernel max-es a nonzero exit status into one device word.
+namespace {
+struct CopyPipe {
+    cudaStream_t cs = nullptr;
+    cudaEvent_t done[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+    ~CopyPipe() {
+        // the device buffers are freed after this (declared before): no copy may still read them
+        if (cs) {
+            cudaStreamSynchronize(cs);
+            cudaStreamDestroy(cs);
+        }
+        for (int b = 0; b < 2; ++b) {
+            if (done[b]) cudaEventDestroy(done[b]);
+            if (copied[b]) cudaEventDestroy(copied[b]);
+        }
+    }
+    gb_info init() {
+        GB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; ++b) {
+            GB_CUDA(cudaEventCreateWithFlags(&done[b], cudaEventDisableTiming));
+            GB_CUDA(cudaEventCreateWithFlags(&copied[b], cudaEventDisableTiming));
+        }
+        return GB_SUCCESS;
+    }
+};
+}  // namespace
+
+extern "C" gb_info gb_bfs_batch(gb_context *ctx, const gb_matrix *A, const uint32_t *srcs, uint32_t k,
+                                int32_t *levels, int32_t *parents, gb_mem mem, const gb_desc *desc) {
+    if (!ctx || !A || !srcs || !levels) return fail(GB_NULL_POINTER, "gb_bfs_batch: NULL argument");
+    if (!A->built) return fail(GB_INVALID_VALUE, "gb_bfs_batch: matrix not built");
+    if (A->nrows != A->ncols) return fail(GB_DIMENSION_MISMATCH, "gb_bfs_batch: matrix must be square");
+    if (k == 0) return fail(GB_INVALID_VALUE, "gb_bfs_batch: no sources");
+    const uint32_t n = A->nrows;
+    for (uint32_t q = 0; q < k; ++q)
+        if (srcs[q] >= n) return fail(GB_INVALID_INDEX, "gb_bfs_batch: source %u (entry %u) out of range", srcs[q], q);
+    GB_CUDA(cudaSetDevice(ctx->device));
+    BfsWorkspace *w = nullptr;
+    GB_CHECK(bfs_workspace(ctx, n, &w));
+    const int sch = bfs_schedule(ctx, A, desc);
+    const size_t row = (size_t)n;
+    Scratch eb(ctx), lb(ctx), pb(ctx);
+    GB_CHECK(eb.alloc(sizeof(int)));
+    GB_CHECK(memset_async(ctx, eb.p, 0, sizeof(int)));
+    int *err = eb.as<int>();
+    auto run = [&](uint32_t q, int32_t *dl, int32_t *dp) -> gb_info {
+        if (sch == GB_SCHED_CLUSTER) return bfs_cluster_run(ctx, A, srcs[q], dl, dp, w, err);
+        return bfs_launch(ctx, A, srcs[q], dl, dp, desc, w, 0, err);
+    };
+    if (mem == GB_DEVICE) {
+        for (uint32_t q = 0; q < k; ++q)
+            GB_CHECK(run(q, levels + q * row, parents ? parents + q * row : nullptr));
+    } else {
+        GB_CHECK(lb.alloc(2 * row * 4));
+        if (parents) GB_CHECK(pb.alloc(2 * row * 4));
+        CopyPipe cp;
+        GB_CHECK(cp.init());
+        for (uint32_t q = 0; q < k; ++q) {
+            const int b = q & 1;
+            int32_t *dl = lb.as<int32_t>() + b * row;
+            int32_t *dp = parents ? pb.as<int32_t>() + b * row : nullptr;
+            if (q >= 2) GB_CUDA(cudaStreamWaitEvent(ctx->stream, cp.copied[b], 0));
+            GB_CHECK(run(q, dl, dp));
+            GB_CUDA(cudaEventRecord(cp.done[b], ctx->stream));
+            GB_CUDA(cudaStreamWaitEvent(cp.cs, cp.done[b], 0));
+            GB_CUDA(cudaMemcpyAsync(levels + q * row, dl, row * 4, cudaMemcpyDeviceToHost, cp.cs));
+            if (dp) GB_CUDA(cudaMemcpyAsync(parents + q * row, dp, row * 4, cudaMemcpyDeviceToHost, cp.cs));
+            GB_CUDA(cudaEventRecord(cp.copied[b], cp.cs));
+        }
+        GB_CUDA(cudaStreamSynchronize(cp.cs));
+    }
+    int herr = 0;
+    GB_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    GB_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (herr) return fail(GB_TIMEOUT, "gb_bfs_batch: a run's bounded device wait ran out");
     return GB_SUCCESS;
 }
 
@@ -830,6 +915,7 @@ extern "C" gb_info gb_bfs_noalloc(const uint32_t *rowptr, const uint32_t *colidx
     a.st = (BfsState *)(base + OFF_ST);
     a.timeout_ns = 4000000000ull;
     a.total_limit_ns = 120000000000ull;
+    a.err_sticky = nullptr;
     // the kernel needs a zeroed working state; the last call's contents may remain
     GB_CUDA(cudaMemsetAsync(a.st, 0, sizeof(BfsState), s));
     void *args[] = {&a};

@@ -60,6 +60,7 @@ struct ClArgs {
     uint32_t *ov[2];               // overflow frontier lists, n entries each
     ClState *st;
     uint64_t total_limit_ns;
+    int *err_sticky;               // optional: a timeout is also max-ed in here (batched runs)
 };
 
 struct ClSmem {
@@ -261,7 +262,10 @@ __global__ void __launch_bounds__(CT, 1) k_cluster(ClArgs a) {
         reached += frontier_total;
         ++d;
         if (stop) {
-            if (rank == 0 && threadIdx.x == 0) atomicCAS(&st->err, 0, (int)GB_TIMEOUT);
+            if (rank == 0 && threadIdx.x == 0) {
+                atomicCAS(&st->err, 0, (int)GB_TIMEOUT);
+                if (a.err_sticky) atomicMax(a.err_sticky, (int)GB_TIMEOUT);
+            }
             break;
         }
     }
@@ -340,7 +344,7 @@ bool bfs_cluster_available(gb_context *ctx) { return cluster_size(ctx) > 0; }
 // Runs one BFS in a single cluster; the overflow lists use the BFS
 // workspace's frontier lists.
 gb_info bfs_cluster_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *levels, int32_t *parents,
-                           uint32_t *visited, uint32_t *ov0, uint32_t *ov1, void *state) {
+                           uint32_t *visited, uint32_t *ov0, uint32_t *ov1, void *state, int *err_sticky) {
     const int c = cluster_size(ctx);
     if (!c) return fail(GB_NOT_IMPLEMENTED, "gb_bfs: this device cannot co-schedule a thread-block cluster");
     clk::ClArgs a;
@@ -359,6 +363,7 @@ gb_info bfs_cluster_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, in
     a.ov[1] = ov1;
     a.st = (clk::ClState *)state;
     a.total_limit_ns = 120000000000ull;
+    a.err_sticky = err_sticky;
     GB_CHECK(memset_async(ctx, state, 0, sizeof(clk::ClState)));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(c);
@@ -399,6 +404,7 @@ gb_info sssp_cluster_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, u
     a.ov[1] = ov1;
     a.st = (clk::ClState *)state;
     a.total_limit_ns = 300000000000ull;
+    a.err_sticky = nullptr;
     GB_CHECK(memset_async(ctx, state, 0, sizeof(clk::ClState)));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(c);

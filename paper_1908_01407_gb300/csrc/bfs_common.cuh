@@ -64,6 +64,7 @@ struct BfsArgs {
     BfsState *st;
     uint64_t timeout_ns;       // bound on one grid-barrier wait
     uint64_t total_limit_ns;   // bound on the whole traversal
+    int *err_sticky;           // optional: a nonzero exit status is also max-ed in here (batched runs)
 };
 
 }  // namespace gbx

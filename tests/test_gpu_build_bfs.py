@@ -276,3 +276,51 @@ def test_bfs_autotune_chooses_cluster_for_a_long_path(ctx):
     assert st["schedule"] == gb.SCHED_GRID
     d.free()
     A.free()
+
+
+@pytest.mark.parametrize("schedule", [gb.SCHED_GRID, gb.SCHED_CLUSTER])
+@pytest.mark.parametrize("out", ["pinned", "numpy", "device", "levels_only"])
+def test_bfs_batch_rows_match_the_oracle(ctx, schedule, out):
+    """gb_bfs_batch: row q is the BFS from source q (levels exactly, parents a
+    valid BFS tree), with host outputs through the two alternating device
+    buffers (odd k, so both buffers and the last half-filled pair are used)."""
+    t = gen.rmat(15, 16, seed=2)
+    g, A = make(ctx, t)
+    srcs = [int(s) for s in gen.sources(t, 7, seed=11)]
+    srcs[3] = srcs[1]                                  # a repeated source
+    k, n = len(srcs), t.n
+    d = gb.Descriptor(schedule=schedule)
+    if out == "pinned":
+        lv = torch.empty((k, n), dtype=torch.int32).pin_memory()
+        par = torch.empty((k, n), dtype=torch.int32).pin_memory()
+    elif out == "numpy":
+        lv, par = np.empty((k, n), np.int32), np.empty((k, n), np.int32)
+    elif out == "levels_only":
+        lv, par = np.empty((k, n), np.int32), False
+    else:
+        lv, par = None, None
+    lv, par = gb.bfs_batch(ctx, A, np.array(srcs, np.uint32), lv, par, desc=d)
+    torch.cuda.synchronize()
+    lv = lv.cpu().numpy() if isinstance(lv, torch.Tensor) else lv
+    if par is not None:
+        par = par.cpu().numpy() if isinstance(par, torch.Tensor) else par
+    for q, s in enumerate(srcs):
+        want = oracle.bfs(g, s)
+        assert np.array_equal(lv[q], want), q
+        if par is not None:
+            assert oracle.bfs_parent_violations(g, s, lv[q], par[q]) == 0, q
+    d.free()
+    A.free()
+
+
+def test_bfs_batch_errors(ctx):
+    t = gen.rmat(10, 8, seed=3)
+    g, A = make(ctx, t)
+    lv = np.empty((2, t.n), np.int32)
+    with pytest.raises(gb.GBError) as e:
+        gb.bfs_batch(ctx, A, np.array([0, t.n], np.uint32), lv, False)
+    assert e.value.code == gb.INVALID_INDEX
+    with pytest.raises(gb.GBError) as e:
+        gb.bfs_batch(ctx, A, np.array([], np.uint32), lv, False)
+    assert e.value.code == gb.INVALID_VALUE
+    A.free()
