@@ -111,10 +111,11 @@ static __device__ __forceinline__ void flush_candidates(const uint32_t *sbuf, ui
 // are collected per warp in shared memory and appended to the next list
 // STAGE_CAP at a time. Pull writes the next frontier as a bitmap and only
 // counts it (vertices, out-edges); the list form is built when a push needs
-// it.
+// it. It also counts the unvisited candidates it walked and sums the
+// in-degrees of those it leaves (what a later pull over them reads at most).
 __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Lin, uint32_t nin, uint32_t *Lout,
                            unsigned int *lout_cnt, unsigned long long *examined, uint32_t *cnt_out,
-                           uint32_t *deg_out) {
+                           uint32_t *deg_out, uint32_t *act_out, unsigned long long *left_edges) {
     const uint32_t *F = a.front[d % 3];
     uint32_t *Fn = a.front[(d + 1) % 3];
     const uint32_t full = 0xffffffffu;
@@ -125,8 +126,8 @@ __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Li
     constexpr uint32_t GROUP = PULL_WPW * 32;
     const uint32_t ngroups = (uint32_t)(((uint64_t)nin + GROUP - 1) / GROUP);
     const uint32_t nwarps = gridDim.x * WARPS;
-    unsigned long long exam = 0;
-    uint32_t mycnt = 0, mydeg = 0;
+    unsigned long long exam = 0, lefte = 0;
+    uint32_t mycnt = 0, mydeg = 0, myact = 0;
     uint32_t *sbuf = sm.stage.v[warp];   // this warp's candidates for the next list
     uint32_t staged = 0;
     static_assert(GROUP <= STAGE_CAP, "a group's candidates fit the staging row");
@@ -208,7 +209,7 @@ __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Li
             } else if (found[j]) {
                 ex = par[j] == h[j][0] ? 1 : 2;
             }
-            if (act[j]) exam += ex;
+            if (act[j]) { exam += ex; ++myact; }
             p[j] = e[j] = 0;
             more |= act[j] && !found[j] && len[j] > 4;
         }
@@ -330,7 +331,10 @@ __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Li
         if (staged + nkeep > (uint32_t)STAGE_CAP) flush_candidates(sbuf, staged, Lout, lout_cnt);
 #pragma unroll
         for (int j = 0; j < PULL_WPW; ++j) {
-            if ((km[j] >> lane) & 1u) sbuf[staged + __popc(km[j] & dev::lanemask_lt())] = c[j];
+            if ((km[j] >> lane) & 1u) {
+                sbuf[staged + __popc(km[j] & dev::lanemask_lt())] = c[j];
+                lefte += len[j];
+            }
             staged += __popc(km[j]);
         }
         __syncwarp();
@@ -339,18 +343,32 @@ __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Li
     *examined += exam;
     *cnt_out += mycnt;
     *deg_out += mydeg;
+    *act_out += myact;
+    *left_edges += lefte;
 }
 
-__device__ __forceinline__ bool choose_pull(const BfsArgs &a, uint64_t fe) {
+// Table 9's rule: pull iff |E_f| * beta > |E|. Once a pull has run, the
+// next pull would walk only the candidates it left (uc of them, ue in-edges
+// in all), so a level also pulls when that walk reads no more than the push
+// would: the frontier's out-edges, its list, and, after a pull (the list form
+// does not exist yet), one pass over the frontier bitmap to build it. In the
+// last levels of a traversal of a low-diameter graph this keeps a frontier of
+// many leaves with few unvisited vertices left in pull.
+__device__ __forceinline__ bool choose_pull(const BfsArgs &a, uint64_t fe, uint32_t cnt, int npull, bool list_valid,
+                                            uint32_t uc, unsigned long long ue) {
     if (a.mode == GB_PUSH || !a.rp_in) return false;
     if (a.mode == GB_PULL) return true;
-    return fe * (uint64_t)a.beta > a.m;
+    if (fe * (uint64_t)a.beta > a.m) return true;
+    if (npull == 0) return false;
+    const unsigned long long pull_reads = 8ull * uc + ue;
+    const unsigned long long push_reads = fe + 4ull * cnt + (list_valid ? 0ull : (unsigned long long)a.nwords);
+    return pull_reads <= push_reads;
 }
 
 __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
     __shared__ Smem sm;
-    __shared__ unsigned long long s_exam;
-    __shared__ uint32_t s_cnt, s_deg;
+    __shared__ unsigned long long s_exam, s_left;
+    __shared__ uint32_t s_cnt, s_deg, s_act;
     const uint64_t t_entry = dev::globaltimer_ns();
     const uint32_t nthreads = gridDim.x * BLOCK;
     const uint32_t tid = blockIdx.x * BLOCK + threadIdx.x;
@@ -389,27 +407,39 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
     const uint64_t t_start = dev::globaltimer_ns();
     uint64_t reached = 0;
     // previous level's numbers for the algorithmic byte count
-    uint32_t prev_dir = 0, prev_cnt = 0;
-    uint64_t prev_fe = 0, prev_unvisited = 0;
+    uint32_t prev_dir = 0, prev_cnt = 0, prev_nin = 0;
+    uint64_t prev_fe = 0;
     double alg = 8.0 * a.n;   // levels + parents writes
     bool list_valid = true;    // the list form of the current frontier exists
     int npull = 0;             // pull steps so far (selects the candidate lists)
     int d = 0;
     for (; ok; ++d) {
-        if (threadIdx.x == 0)
+        if (threadIdx.x == 0) {
             sm.qs = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>(st->qstate[d % 3])
                         .load(cuda::memory_order_relaxed);
+            if (npull > 0) {
+                sm.uc = (uint32_t)dev::ld_relaxed_gpu_int((const int *)&st->ucnt[(npull - 1) % 3]);
+                sm.ue = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>(st->uedg[(npull - 1) % 3])
+                            .load(cuda::memory_order_relaxed);
+            }
+        }
         __syncthreads();
         const unsigned long long qs = sm.qs;
+        const uint32_t uc = npull > 0 ? sm.uc : 0u;
+        const unsigned long long ue = npull > 0 ? sm.ue : 0ull;
         __syncthreads();
         uint32_t cnt = (uint32_t)(qs >> a.ebits);
         uint64_t fe = qs & a.emask;
         if (tid == 0 && d > 0) {
             unsigned long long ex = st->exam[(d - 1) % 3];
-            if (prev_dir == 0)
+            if (prev_dir == 0) {
                 alg += 8.0 * prev_cnt + 4.0 * prev_fe + 12.0 * cnt;
-            else
-                alg += a.n / 8.0 + 8.0 * prev_unvisited + 4.0 * ex + 12.0 * cnt;
+            } else {
+                // the mask words the pull reads, the row pointers of the unvisited candidates it
+                // walked, the adjacency entries it examined and the discoveries it wrote
+                const double mask = a.n / 8.0 < 4.0 * prev_nin ? a.n / 8.0 : 4.0 * prev_nin;
+                alg += mask + 8.0 * (double)st->uact[(d - 1) % 3] + 4.0 * ex + 12.0 * cnt;
+            }
             res->edges_examined += prev_dir == 0 ? prev_fe : ex;
         }
         if (cnt == 0) break;
@@ -417,7 +447,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
         if (d > (int)a.n || (threadIdx.x == 0 && dev::globaltimer_ns() - t_start > a.total_limit_ns)) {
             atomicCAS(&st->err, 0, (int)GB_TIMEOUT);
         }
-        const bool pull = choose_pull(a, fe);
+        const bool pull = choose_pull(a, fe, cnt, npull, list_valid, uc, ue);
         if (tid == 0) {
             if (d < GBX_MAX_LEVEL_LOG) {
                 res->dir_log[d] = pull ? 2 : 1;
@@ -428,9 +458,9 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
             if (pull) res->pull_levels++; else res->push_levels++;
             st->qstate[(d + 2) % 3] = 0;
             st->exam[(d + 2) % 3] = 0;
+            st->uact[(d + 2) % 3] = 0;
             st->cstate[(d + 2) % 3] = 0;
             res->frontier_edges += fe;
-            prev_unvisited = a.n - reached - cnt;
             prev_dir = pull ? 1u : 0u;
             prev_cnt = cnt;
             prev_fe = fe;
@@ -439,7 +469,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
         uint32_t *Fclr = a.front[(d + 2) % 3];
         for (uint64_t w = tid; w < a.nwords; w += nthreads) Fclr[w] = 0u;
         if (pull) {
-            if (threadIdx.x == 0) { s_exam = 0; s_cnt = 0; s_deg = 0; }
+            if (threadIdx.x == 0) { s_exam = 0; s_left = 0; s_cnt = 0; s_deg = 0; s_act = 0; }
             __syncthreads();
             // candidates: all live ones for the first pull, then what the previous pull left;
             // with the live table a candidate is a live-list index, otherwise a vertex
@@ -454,21 +484,32 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
                 Lin = a.ul[(npull - 1) & 1];
                 nin = (uint32_t)dev::ld_relaxed_gpu_int((const int *)&st->ucnt[(npull - 1) % 3]);
             }
-            if (tid == 0) st->ucnt[(npull + 1) % 3] = 0;
-            unsigned long long ex = 0;
-            uint32_t c = 0, dg = 0;
-            pull_level(a, sm, d, Lin, nin, a.ul[npull & 1], &st->ucnt[npull % 3], &ex, &c, &dg);
+            if (tid == 0) {
+                st->ucnt[(npull + 1) % 3] = 0;
+                st->uedg[(npull + 1) % 3] = 0;
+                prev_nin = nin;
+            }
+            const int us = npull % 3;
+            unsigned long long ex = 0, le = 0;
+            uint32_t c = 0, dg = 0, na = 0;
+            pull_level(a, sm, d, Lin, nin, a.ul[npull & 1], &st->ucnt[us], &ex, &c, &dg, &na, &le);
             ++npull;
             ex = dev::warp_sum<unsigned long long>(ex);
+            le = dev::warp_sum<unsigned long long>(le);
             c = dev::warp_sum<uint32_t>(c);
             dg = dev::warp_sum<uint32_t>(dg);
+            na = dev::warp_sum<uint32_t>(na);
             if ((threadIdx.x & 31) == 0) {
                 if (ex) atomicAdd(&s_exam, ex);
+                if (le) atomicAdd(&s_left, le);
+                if (na) atomicAdd(&s_act, na);
                 if (c) { atomicAdd(&s_cnt, c); atomicAdd(&s_deg, dg); }
             }
             __syncthreads();
             if (threadIdx.x == 0) {
                 if (s_exam) atomicAdd(&st->exam[d % 3], s_exam);
+                if (s_left) atomicAdd(&st->uedg[us], s_left);
+                if (s_act) atomicAdd(&st->uact[d % 3], (unsigned long long)s_act);
                 if (s_cnt) atomicAdd(&st->qstate[(d + 1) % 3], ((unsigned long long)s_cnt << a.ebits) | s_deg);
             }
             list_valid = false;
@@ -527,7 +568,10 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
             res->t_exit = dev::globaltimer_ns();
             st->err = 0;
             st->bar.count = 0;
-            for (int k = 0; k < 3; ++k) { st->qstate[k] = 0; st->exam[k] = 0; st->cstate[k] = 0; st->ucnt[k] = 0; }
+            for (int k = 0; k < 3; ++k) {
+                st->qstate[k] = 0; st->exam[k] = 0; st->cstate[k] = 0; st->ucnt[k] = 0;
+                st->uedg[k] = 0; st->uact[k] = 0;
+            }
             __threadfence();
             st->bar.exits = 0;
         }

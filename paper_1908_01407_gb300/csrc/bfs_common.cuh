@@ -37,6 +37,8 @@ struct BfsState {
     unsigned long long cstate[3];      // packed counter of the bitmap -> list compaction, per level slot
     unsigned int ucnt[3];              // length of the candidate list a pull leaves, per pull slot
     unsigned int pad1;
+    unsigned long long uedg[3];        // in-edges of the candidates a pull leaves, per pull slot
+    unsigned long long uact[3];        // unvisited candidates a pull walked, per level slot
     BfsResult res;
 };
 

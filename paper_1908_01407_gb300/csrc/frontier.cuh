@@ -40,6 +40,8 @@ struct Smem {
     SmemPush push;
     Stage stage;
     unsigned long long qs;
+    unsigned long long ue;   // in-edges of the last pull's leftover candidates
+    unsigned int uc;         // their number
 };
 
 static __device__ __forceinline__ uint32_t ldcg(const uint32_t *p) { return __ldcg(p); }

@@ -324,3 +324,36 @@ def test_bfs_batch_errors(ctx):
         gb.bfs_batch(ctx, A, np.array([], np.uint32), lv, False)
     assert e.value.code == gb.INVALID_VALUE
     A.free()
+
+
+def test_bfs_stays_in_pull_when_few_candidates_are_left(ctx):
+    """src - 200 hubs (a clique) - 50 leaves each, 5 leaves with one child,
+    and a separate 150-clique. With beta = 4, Table 9's rule pushes the
+    level of the 10,000 leaves (|E_f| * 4 < |E|), but the first pull left
+    only the 5 children and the clique (155 candidates, 22,355 in-edges),
+    fewer reads than the push plus building its list: that level pulls. The
+    last level (the 5 children, the clique still left) pushes."""
+    edges, nxt = [], 1
+    hubs = list(range(nxt, nxt + 200))
+    nxt += 200
+    edges += [(0, h) for h in hubs] + [(hubs[i], hubs[j]) for i in range(200) for j in range(i)]
+    leaves = []
+    for h in hubs:
+        edges += [(h, nxt + k) for k in range(50)]
+        leaves += list(range(nxt, nxt + 50))
+        nxt += 50
+    for k in range(5):
+        edges.append((leaves[k * 997], nxt))
+        nxt += 1
+    c0 = nxt
+    edges += [(c0 + i, c0 + j) for i in range(150) for j in range(i)]
+    nxt += 150 + 64
+    perm = np.random.default_rng(7).permutation(nxt)
+    t = gen.from_edges(nxt, [(int(perm[u]), int(perm[v])) for u, v in edges])
+    g, A = make(ctx, t)
+    d = gb.Descriptor(beta=4)
+    st = check_bfs(ctx, g, A, int(perm[0]), d)
+    dirs = "".join("P" if x["dir"] == "pull" else "s" for x in st["trace"])
+    assert dirs == "sPPs", dirs
+    d.free()
+    A.free()
