@@ -164,7 +164,12 @@ gb_info gb_matrix_new(gb_matrix **A, gb_context *ctx, gb_type type, uint64_t nro
  * (row, col) are combined with `dup` (PLUS/MIN/MAX/FIRST/SECOND/LOR/LAND;
  * FIRST/SECOND by tuple order). Columns within a row come out sorted.
  * rows/cols/vals live in `mem`. Index >= dimension: GB_INVALID_INDEX.
- * Rebuilding a built matrix replaces its contents. */
+ * Rebuilding a built matrix replaces its contents. A square matrix with a
+ * CSC also gets, on the device, the traversal tables of its pulls (the
+ * vertices with in-edges and their heads) and the size of every vertex's
+ * weakly connected component (FastSV; 4 bytes per vertex), with which a BFS
+ * that has reached its source's whole component stops without expanding
+ * its last frontier (the paper has neither). */
 gb_info gb_matrix_build(gb_matrix *A, const uint32_t *rows, const uint32_t *cols, const void *vals,
                         uint64_t nvals, gb_binop dup, gb_mem mem, uint32_t flags);
 gb_info gb_matrix_nrows(const gb_matrix *A, uint64_t *n);

@@ -412,6 +412,10 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
     double alg = 8.0 * a.n;   // levels + parents writes
     bool list_valid = true;    // the list form of the current frontier exists
     int npull = 0;             // pull steps so far (selects the candidate lists)
+    // the source's component size: once that many vertices are reached the
+    // last frontier has nothing left to discover and is not expanded
+    const uint32_t csize = a.comp_size ? __ldg(&a.comp_size[a.src]) : 0u;
+    bool exhausted = false;
     int d = 0;
     for (; ok; ++d) {
         if (threadIdx.x == 0) {
@@ -443,6 +447,11 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
             res->edges_examined += prev_dir == 0 ? prev_fe : ex;
         }
         if (cnt == 0) break;
+        if (csize && reached + cnt >= csize) {
+            reached += cnt;
+            exhausted = true;
+            break;
+        }
         // guard: no BFS has more than n levels; the traversal has a wall-clock budget
         if (d > (int)a.n || (threadIdx.x == 0 && dev::globaltimer_ns() - t_start > a.total_limit_ns)) {
             atomicCAS(&st->err, 0, (int)GB_TIMEOUT);
@@ -550,7 +559,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
         }
     }
     if (tid == 0) {
-        res->depth = d;
+        res->depth = d + (exhausted ? 1 : 0);
         res->reached = reached;
         res->alg_bytes = alg;
         res->t_begin = t_start;
@@ -687,6 +696,7 @@ gb_info bfs_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *l
     a.live_len = a.live ? A->live_len : nullptr;
     a.live_deg = a.live ? A->live_deg : nullptr;
     a.ul[0] = w->ul; a.ul[1] = w->ul + A->nrows + 1;
+    a.comp_size = A->comp_size;
     a.ebits = 64 - bits_for((uint64_t)A->nrows + 1);
     a.emask = (a.ebits >= 64) ? ~0ull : ((1ull << a.ebits) - 1);
     a.mode = desc ? desc->direction : GB_AUTO;
@@ -754,7 +764,10 @@ extern "C" gb_info gb_bfs(gb_context *ctx, const gb_matrix *A, uint32_t src, int
             stats->edges_examined = hs.edges_examined;
             stats->frontier_edges = hs.frontier_edges;
             stats->alg_bytes = (uint64_t)hs.alg_bytes;
-            uint32_t nl = hs.depth < GB_TRACE_LEVELS ? hs.depth : GB_TRACE_LEVELS;
+            // the expanded levels (a traversal that exhausted the source's
+            // component does not expand its last frontier)
+            const uint32_t nexp = hs.push_levels + hs.pull_levels;
+            uint32_t nl = nexp < GB_TRACE_LEVELS ? nexp : GB_TRACE_LEVELS;
             stats->trace_len = nl;
             for (uint32_t l = 0; l < nl; ++l) {
                 stats->trace_dir[l] = hs.dir_log[l];
@@ -952,6 +965,7 @@ extern "C" gb_info gb_bfs_noalloc(const uint32_t *rowptr, const uint32_t *colidx
     a.live_head = nullptr;
     a.live_len = a.live_deg = nullptr;
     a.ul[0] = (uint32_t *)(base + OFF_UL); a.ul[1] = a.ul[0] + n + 1;
+    a.comp_size = nullptr;
     a.ebits = 64 - bits_for((uint64_t)n + 1);
     a.emask = (1ull << a.ebits) - 1;
     a.mode = GB_AUTO;

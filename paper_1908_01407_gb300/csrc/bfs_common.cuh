@@ -59,6 +59,7 @@ struct BfsArgs {
     const uint32_t *live_len;          // per live entry: in-degree
     const uint32_t *live_deg;          // per live entry: out-degree
     uint32_t *ul[2];                   // candidate lists of the pull steps (unvisited, with in-edges)
+    const uint32_t *comp_size;         // per vertex, its component's size; null = unknown
     int ebits;
     unsigned long long emask;
     int mode;

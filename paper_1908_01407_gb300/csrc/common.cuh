@@ -101,6 +101,10 @@ struct gb_matrix_t {
     uint4 *live_head = nullptr;
     uint32_t *live_len = nullptr;
     uint32_t *live_deg = nullptr;    // == live_len for a symmetric matrix
+    // per vertex, the size of its weakly connected component (built with
+    // the CSC of a square matrix): a traversal that has reached that many
+    // vertices can stop without expanding its last frontier
+    uint32_t *comp_size = nullptr;
     // guards the caches built on first use (hub list)
     std::mutex cache_mu;
 };
@@ -166,6 +170,9 @@ gb_info scan_exclusive_u32(gb_context *ctx, const uint32_t *in, uint32_t *out, u
 // Columns of A with more than min_len entries and their length prefix,
 // computed on first use and cached on the matrix (matrix.cu).
 gb_info matrix_hubs(const gb_matrix *A, uint32_t min_len);
+// Per-vertex component sizes (weak components, by FastSV), cached on the
+// matrix (fastsv.cu).
+gb_info matrix_components(gb_context *ctx, gb_matrix *A);
 // Stable LSD radix sort of (key, value) pairs by the low `key_bits` bits.
 // Results end in keys/vals (the buffers are ping-ponged with the scratch).
 gb_info radix_sort_pairs(gb_context *ctx, uint64_t *keys, uint32_t *vals, uint64_t n, int key_bits);

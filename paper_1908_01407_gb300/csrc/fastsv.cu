@@ -163,7 +163,46 @@ __global__ void __launch_bounds__(BLOCK, 8) k_fastsv(SvArgs a) {
     if (tid == 0) st->iters = it;
 }
 
+// size of each vertex's component from its label: a warp adds the lanes
+// with equal labels in one atomic (the giant component of an R-MAT graph
+// would otherwise take millions of atomics on one word)
+__global__ void k_comp_count(uint32_t n, const uint32_t *labels, uint32_t *count) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lab = i < n ? labels[i] : INF;
+    const uint32_t same = __match_any_sync(0xffffffffu, lab);
+    if (lab != INF && lane == __ffs(same) - 1) atomicAdd(&count[lab], (uint32_t)__popc(same));
+}
+
+__global__ void k_comp_gather(uint32_t n, const uint32_t *labels, const uint32_t *count, uint32_t *csize) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) csize[i] = count[labels[i]];
+}
+
 }  // namespace svk
+
+gb_info matrix_components(gb_context *ctx, gb_matrix *A) {
+    std::lock_guard<std::mutex> g(A->cache_mu);
+    if (A->comp_size || !A->has_csc || A->nrows == 0 || A->nrows != A->ncols) return GB_SUCCESS;
+    const uint32_t n = A->nrows;
+    Scratch lab(ctx), cnt(ctx);
+    GB_CHECK(lab.alloc((size_t)n * 4 + 16));
+    GB_CHECK(cnt.alloc((size_t)n * 4 + 16));
+    GB_CHECK(gb_cc_fastsv(ctx, A, lab.as<uint32_t>(), GB_DEVICE, nullptr));
+    GB_CHECK(memset_async(ctx, cnt.p, 0, (size_t)n * 4));
+    uint32_t *cs = nullptr;
+    GB_CHECK(dalloc(ctx, (void **)&cs, (size_t)n * 4 + 16));
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    svk::k_comp_count<<<nb, 256, 0, ctx->stream>>>(n, lab.as<uint32_t>(), cnt.as<uint32_t>());
+    svk::k_comp_gather<<<nb, 256, 0, ctx->stream>>>(n, lab.as<uint32_t>(), cnt.as<uint32_t>(), cs);
+    if (cudaGetLastError() != cudaSuccess) {
+        dfree(ctx, cs);
+        return fail(GB_PANIC, "matrix_components: launch failed");
+    }
+    A->comp_size = cs;
+    return GB_SUCCESS;
+}
+
 }  // namespace gbx
 
 extern "C" gb_info gb_cc_fastsv(gb_context *ctx, const gb_matrix *A, uint32_t *labels, gb_mem mem,

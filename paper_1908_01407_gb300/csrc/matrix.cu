@@ -61,6 +61,8 @@ void release(gb_matrix *A) {
     dfree(ctx, A->live_head);
     dfree(ctx, A->live_len);
     if (A->live_deg != A->live_len) dfree(ctx, A->live_deg);
+    dfree(ctx, A->comp_size);
+    A->comp_size = nullptr;
     A->live_list = A->live_count = nullptr;
     A->live_head = nullptr;
     A->live_len = A->live_deg = nullptr;
@@ -181,7 +183,10 @@ gb_info matrix_build_device(gb_matrix *A, const uint32_t *rows, const uint32_t *
         A->cvals = cv;
         A->has_csc = true;
     }
-    if (A->has_csc && A->nrows == A->ncols) GB_CHECK(matrix_live(A));
+    if (A->has_csc && A->nrows == A->ncols) {
+        GB_CHECK(matrix_live(A));
+        GB_CHECK(matrix_components(ctx, A));
+    }
     return GB_SUCCESS;
 }
 

@@ -228,7 +228,7 @@ def test_bfs_pull_push_pull_keeps_candidates(ctx):
     d = gb.Descriptor(beta=10)
     st = check_bfs(ctx, g, A, src, d)
     dirs = "".join("P" if x["dir"] == "pull" else "s" for x in st["trace"])
-    assert dirs == "sPsPsPsPs", dirs
+    assert dirs == "sPsPsPsP", dirs     # b4 ends the component: its level is not expanded
     d.free()
     # the same graph with the pulls only
     d = gb.Descriptor(direction=gb.PULL)
@@ -332,7 +332,9 @@ def test_bfs_stays_in_pull_when_few_candidates_are_left(ctx):
     level of the 10,000 leaves (|E_f| * 4 < |E|), but the first pull left
     only the 5 children and the clique (155 candidates, 22,355 in-edges),
     fewer reads than the push plus building its list: that level pulls. The
-    last level (the 5 children, the clique still left) pushes."""
+    next level (the 5 children, one of which has a child; the clique still
+    left) pushes, and the level of that grandchild, which completes the
+    component, is not expanded."""
     edges, nxt = [], 1
     hubs = list(range(nxt, nxt + 200))
     nxt += 200
@@ -345,6 +347,8 @@ def test_bfs_stays_in_pull_when_few_candidates_are_left(ctx):
     for k in range(5):
         edges.append((leaves[k * 997], nxt))
         nxt += 1
+    edges.append((nxt - 1, nxt))
+    nxt += 1
     c0 = nxt
     edges += [(c0 + i, c0 + j) for i in range(150) for j in range(i)]
     nxt += 150 + 64
@@ -355,5 +359,27 @@ def test_bfs_stays_in_pull_when_few_candidates_are_left(ctx):
     st = check_bfs(ctx, g, A, int(perm[0]), d)
     dirs = "".join("P" if x["dir"] == "pull" else "s" for x in st["trace"])
     assert dirs == "sPPs", dirs
+    d.free()
+    A.free()
+
+
+def test_bfs_stops_once_the_component_is_reached(ctx):
+    """The build keeps each vertex's component size on the matrix; a BFS that
+    has reached its source's whole component leaves its last frontier
+    unexpanded (one traced level fewer than the depth) while levels,
+    parents, depth and reached count still match the oracle: sources in the
+    giant component, in a small one, and an isolated source."""
+    t = gen.rmat(14, 16, seed=1)
+    g, A = make(ctx, t)
+    lab = oracle.cc(g)
+    size = np.bincount(lab, minlength=t.n)[lab]
+    deg = g.degrees()
+    giant = [int(s) for s in gen.sources(t, 3, seed=5)]
+    small = [int(np.flatnonzero((size > 1) & (size < 10))[0])]
+    isolated = [int(np.flatnonzero(deg == 0)[0])]
+    d = gb.Descriptor(schedule=gb.SCHED_GRID)
+    for s in giant + small + isolated:
+        st = check_bfs(ctx, g, A, s, d)
+        assert len(st["trace"]) == st["depth"] - 1, (s, st["depth"], len(st["trace"]))
     d.free()
     A.free()
