@@ -7,7 +7,7 @@
 // The per-entry counts are optionally written (the C of the paper); the
 // total is reduced in uint64 without writing C at all (the fusion Section 8.3
 // names as the gap to hardwired code). When only the total is asked for, a
-// cheaper equivalent count runs instead (k_tc_forward).
+// cheaper equivalent count runs instead (k_tc_hash).
 #include "common.cuh"
 #include "ops_impl.cuh"
 
@@ -75,59 +75,101 @@ __global__ void __launch_bounds__(TC_BLOCK) k_tc(uint32_t n, const uint32_t *rp,
     if (threadIdx.x == 0 && s_tot) atomicAdd(total, s_tot);
 }
 
-// Total only: a warp per row i stages row_i (the neighbours of i below i,
-// ascending) in shared memory; lane t takes the t-th entry k of the row and
-// counts the entries j of row_k (all below k) that row_i also holds: those
-// sit in row_i before k's own position, found by a binary search that only
-// moves forward. Each triangle j < k < i is counted once, at (i, k). This is
-// the L.Lt .* L form of the count; the total equals C<L> = L.L's, and with
-// the degree-descending relabel every row is short. Rows longer than
-// TC_CAP are searched in global memory instead.
-constexpr int TC_CAP = 512;
-__global__ void __launch_bounds__(TC_BLOCK) k_tc_forward(uint32_t n, const uint32_t *rp, const uint32_t *ci,
-                                                         unsigned long long *total) {
-    __shared__ uint32_t s_row[TC_BLOCK / 32][TC_CAP];
+// Total only, by columns of L: a warp per vertex k puts row_k (the
+// neighbours of k below k) in a set in shared memory; its lanes take the
+// rows i of column k (the neighbours of k above k, from the CSC) and count
+// the entries of row_i below k that the set holds (a prefix of row_i, since
+// rows are sorted). Each triangle j < k < i is counted once, at (k, i): this
+// is the L.Lt .* L form of the count, Σ over L(i,k) of |row_i ∩ row_k|,
+// whose total equals C<L> = L.L's. The set is a bitmap of the ids below k
+// while k <= 32 * TC_WORDS (after the degree relabel the rows of small k
+// carry most of the work), otherwise a hash table of row_k with linear
+// probing at load factor at most one half; rows longer than TC_HROW beyond
+// the bitmap's range are probed by binary search in global memory. The
+// prefixes are read 16 bytes at a time (the index arrays are 16-byte
+// aligned and padded).
+constexpr uint32_t TC_WORDS = 1024;   // per warp: a bitmap of 32768 ids or 1024 hash slots
+constexpr uint32_t TC_HROW = TC_WORDS / 2;
+constexpr uint32_t TC_EMPTY = 0xffffffffu;
+
+// multiplicative hash (Knuth's golden-ratio constant), top `bits` bits
+__device__ __forceinline__ uint32_t tc_slot(uint32_t v, int bits) { return (v * 2654435761u) >> (32 - bits); }
+
+__global__ void __launch_bounds__(TC_BLOCK) k_tc_hash(uint32_t n, const uint32_t *rp, const uint32_t *ci,
+                                                      const uint32_t *cp, const uint32_t *ri,
+                                                      unsigned long long *total) {
+    __shared__ uint32_t s_tab[TC_BLOCK / 32][TC_WORDS];
     __shared__ unsigned long long s_tot;
     if (threadIdx.x == 0) s_tot = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t nwarps = (uint64_t)gridDim.x * (TC_BLOCK / 32);
-    uint32_t *row = s_row[warp];
+    const uint4 *ci4 = reinterpret_cast<const uint4 *>(ci);
+    uint32_t *tab = s_tab[warp];
     unsigned long long mine = 0;
-    for (uint64_t i = (uint64_t)blockIdx.x * (TC_BLOCK / 32) + warp; i < n; i += nwarps) {
-        const uint32_t rb = __ldg(&rp[i]), re = __ldg(&rp[i + 1]);
-        const uint32_t li = re - rb;
-        if (li < 2) continue;   // warp-uniform
-        const bool staged = li <= (uint32_t)TC_CAP;
-        if (staged) {
-            for (uint32_t t = lane; t < li; t += 32) row[t] = __ldg(&ci[rb + t]);
+    for (uint64_t kk = (uint64_t)blockIdx.x * (TC_BLOCK / 32) + warp; kk < n; kk += nwarps) {
+        const uint32_t k = (uint32_t)kk;
+        const uint32_t kb = __ldg(&rp[k]), ke = __ldg(&rp[k + 1]);
+        const uint32_t cb = __ldg(&cp[k]), ce = __ldg(&cp[k + 1]);
+        const uint32_t lk = ke - kb;
+        if (lk == 0 || ce == cb) continue;   // warp-uniform
+        // 0: bitmap of the ids below k, 1: hash table, 2: binary search of row_k
+        const int mode = k <= 32u * TC_WORDS ? 0 : (lk <= TC_HROW ? 1 : 2);
+        int bits = 5;
+        if (mode == 0) {
+            const uint32_t nw = (k + 31) >> 5;
+            for (uint32_t s = lane; s < nw; s += 32) tab[s] = 0u;
+            __syncwarp();
+            for (uint32_t t = lane; t < lk; t += 32) {
+                const uint32_t v = __ldg(&ci[kb + t]);
+                atomicOr(&tab[v >> 5], 1u << (v & 31));
+            }
+            __syncwarp();
+        } else if (mode == 1) {
+            while ((1u << bits) < 2 * lk) ++bits;
+            const uint32_t S = 1u << bits;
+            for (uint32_t s = lane; s < S; s += 32) tab[s] = TC_EMPTY;
+            __syncwarp();
+            for (uint32_t t = lane; t < lk; t += 32) {   // the entries are distinct
+                const uint32_t v = __ldg(&ci[kb + t]);
+                uint32_t h = tc_slot(v, bits);
+                while (atomicCAS(&tab[h], TC_EMPTY, v) != TC_EMPTY) h = (h + 1) & (S - 1);
+            }
             __syncwarp();
         }
-        for (uint32_t t = 1 + lane; t < li; t += 32) {   // k = row_i[t]; entries before t are below k
-            const uint32_t k = staged ? row[t] : __ldg(&ci[rb + t]);
-            const uint32_t kb = __ldg(&rp[k]), ke = __ldg(&rp[k + 1]);
-            uint32_t lo = 0, cnt = 0;
-            for (uint32_t x0 = kb; x0 < ke && lo < t; x0 += 4) {
-                uint32_t jj[4];   // four entries of row_k in flight, then their searches
-#pragma unroll
-                for (int u = 0; u < 4; ++u) jj[u] = x0 + u < ke ? __ldg(&ci[x0 + u]) : 0xffffffffu;
+        const uint32_t mask = (1u << bits) - 1;
+        for (uint32_t q = cb + lane; q < ce; q += 32) {
+            const uint32_t i = __ldg(&ri[q]);
+            const uint32_t ib = __ldg(&rp[i]), ie = __ldg(&rp[i + 1]);
+            uint32_t cnt = 0;
+            bool more = true;
+            for (uint32_t x0 = ib & ~3u; x0 < ie && more; x0 += 4) {
+                const uint4 w4 = __ldg(&ci4[x0 >> 2]);
+                const uint32_t jj[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const uint32_t j = jj[u];
-                    if (j == 0xffffffffu || lo >= t) continue;
-                    uint32_t a = lo, b = t;   // lower_bound of j in row_i[lo, t)
-                    while (a < b) {
-                        const uint32_t mid = (a + b) >> 1;
-                        const uint32_t r = staged ? row[mid] : __ldg(&ci[rb + mid]);
-                        if (r < j) a = mid + 1; else b = mid;
+                    const uint32_t x = x0 + u, j = jj[u];
+                    if (x < ib) continue;
+                    if (!more || x >= ie || j >= k) { more = false; continue; }   // the prefix ends at k
+                    if (mode == 0) {
+                        cnt += (tab[j >> 5] >> (j & 31)) & 1u;
+                    } else if (mode == 1) {
+                        uint32_t h = tc_slot(j, bits), sv;
+                        while ((sv = tab[h]) != TC_EMPTY && sv != j) h = (h + 1) & mask;
+                        cnt += sv == j;
+                    } else {
+                        uint32_t a = kb, b = ke;   // lower_bound of j in row_k
+                        while (a < b) {
+                            const uint32_t mid = (a + b) >> 1;
+                            if (__ldg(&ci[mid]) < j) a = mid + 1; else b = mid;
+                        }
+                        cnt += a < ke && __ldg(&ci[a]) == j;
                     }
-                    lo = a;
-                    if (a < t && (staged ? row[a] : __ldg(&ci[rb + a])) == j) { ++cnt; ++lo; }
                 }
             }
             mine += cnt;
         }
-        __syncwarp();   // the row buffer is rewritten for the next row
+        __syncwarp();   // the set is rebuilt for the next k
     }
     mine = dev::warp_sum<unsigned long long>(mine);
     if (lane == 0 && mine) atomicAdd(&s_tot, mine);
@@ -158,7 +200,7 @@ extern "C" gb_info gb_tc(gb_context *ctx, const gb_matrix *L, uint64_t *count, g
     uint32_t n = L->nrows;
     if (n) {
         int occ = 0;
-        GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, C ? (const void *)k_tc : (const void *)k_tc_forward,
+        GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, C ? (const void *)k_tc : (const void *)k_tc_hash,
                                                               TC_BLOCK, 0));
         unsigned blocks = (unsigned)(occ * ctx->num_sms * 4);
         uint64_t need = ((uint64_t)n + 7) / 8;
@@ -169,7 +211,8 @@ extern "C" gb_info gb_tc(gb_context *ctx, const gb_matrix *L, uint64_t *count, g
             k_tc<<<blocks, TC_BLOCK, 0, ctx->stream>>>(n, L->rowptr, L->colidx, L->colptr, L->rowidx,
                                                        cv.as<uint32_t>(), tot.as<unsigned long long>());
         else     // the total alone
-            k_tc_forward<<<blocks, TC_BLOCK, 0, ctx->stream>>>(n, L->rowptr, L->colidx, tot.as<unsigned long long>());
+            k_tc_hash<<<blocks, TC_BLOCK, 0, ctx->stream>>>(n, L->rowptr, L->colidx, L->colptr, L->rowidx,
+                                                            tot.as<unsigned long long>());
         prof_end(ctx, span);
         GB_LAUNCH_CHECK();
     }
