@@ -169,7 +169,9 @@ gb_info gb_matrix_new(gb_matrix **A, gb_context *ctx, gb_type type, uint64_t nro
  * vertices with in-edges and their heads) and the size of every vertex's
  * weakly connected component (FastSV; 4 bytes per vertex), with which a BFS
  * that has reached its source's whole component stops without expanding
- * its last frontier (the paper has neither). */
+ * its last frontier (the paper has neither; matrices that calls such as
+ * gb_mxm or gb_matrix_tril build as results get the tables but not the
+ * component sizes). */
 gb_info gb_matrix_build(gb_matrix *A, const uint32_t *rows, const uint32_t *cols, const void *vals,
                         uint64_t nvals, gb_binop dup, gb_mem mem, uint32_t flags);
 gb_info gb_matrix_nrows(const gb_matrix *A, uint64_t *n);
@@ -417,7 +419,8 @@ gb_info gb_cc_fastsv(gb_context *ctx, const gb_matrix *A, uint32_t *labels, gb_m
 /* Triangle counting (Section 7.5) as the masked SpGEMM C<L> = L (+).(x) L
  * over plus.pair, reduced on the fly: L is a strictly lower-triangular
  * matrix with CSR and CSC (gb_matrix_tril). *count (host) = number of
- * triangles. If C != NULL it also receives C's values in L's structure. */
+ * triangles. If C != NULL it also receives C's values in L's structure
+ * (C(i,j) = the k with L(i,k) and L(k,j); GB_UINT32). */
 gb_info gb_tc(gb_context *ctx, const gb_matrix *L, uint64_t *count, gb_matrix *C);
 
 /* ---------------------------------------------------------------- serving */

@@ -101,9 +101,9 @@ struct gb_matrix_t {
     uint4 *live_head = nullptr;
     uint32_t *live_len = nullptr;
     uint32_t *live_deg = nullptr;    // == live_len for a symmetric matrix
-    // per vertex, the size of its weakly connected component (built with
-    // the CSC of a square matrix): a traversal that has reached that many
-    // vertices can stop without expanding its last frontier
+    // per vertex, the size of its weakly connected component (built by
+    // gb_matrix_build for a square matrix with a CSC): a traversal that has
+    // reached that many vertices can stop without expanding its last frontier
     uint32_t *comp_size = nullptr;
     // guards the caches built on first use (hub list)
     std::mutex cache_mu;

@@ -183,10 +183,7 @@ gb_info matrix_build_device(gb_matrix *A, const uint32_t *rows, const uint32_t *
         A->cvals = cv;
         A->has_csc = true;
     }
-    if (A->has_csc && A->nrows == A->ncols) {
-        GB_CHECK(matrix_live(A));
-        GB_CHECK(matrix_components(ctx, A));
-    }
+    if (A->has_csc && A->nrows == A->ncols) GB_CHECK(matrix_live(A));
     return GB_SUCCESS;
 }
 
@@ -285,6 +282,9 @@ gb_info gb_matrix_build(gb_matrix *A, const uint32_t *rows, const uint32_t *cols
         }
     }
     GB_CHECK(matrix_build_device(A, dr, dc, dv, nvals, dup, flags));
+    // a user's square matrix with a CSC also gets its component sizes, for
+    // the early stop of BFS (matrices the library builds as results do not)
+    if (A->has_csc && A->nrows == A->ncols) GB_CHECK(matrix_components(ctx, A));
     GB_CHECK(sync(ctx));
     return GB_SUCCESS;
 }

@@ -1,13 +1,10 @@
-// Triangle counting (Section 7.5) as the masked SpGEMM C<L> = L (+).(x) L
-// over (plus, pair) (Section 6.3.4), reduced on the fly: for every stored
-// L(i,j), C(i,j) = |row_i(L) intersect col_j(L)|, computed by binary
-// search of the shorter list's entries in the longer one. With L strictly
-// lower triangular each triangle {k < j < i} is counted once, at (i, j)
-// through its middle vertex k... in the L*L form, at (i,j) with j < k < i.
-// The per-entry counts are optionally written (the C of the paper); the
-// total is reduced in uint64 without writing C at all (the fusion Section 8.3
-// names as the gap to hardwired code). When only the total is asked for, a
-// cheaper equivalent count runs instead (k_tc_hash).
+// Triangle counting (Section 7.5) as the masked SpGEMM C<L> = L (+).(pair) L
+// (Section 6.3.4): with L strictly lower triangular, C(i,j) counts the k
+// with j < k < i and L(i,k), L(k,j), so every triangle {j < k < i} adds one
+// to exactly one entry, C(i,j), and the total is the triangle count. The
+// per-entry counts are optionally written (the C of the paper); the total is
+// reduced in uint64 without writing C at all (the fusion Section 8.3 names as
+// the gap to hardwired code).
 #include "common.cuh"
 #include "ops_impl.cuh"
 
@@ -18,64 +15,7 @@ namespace {
 
 constexpr int TC_BLOCK = 256;
 
-// lower_bound of x in a[lo, hi)
-__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t *a, uint32_t lo, uint32_t hi, uint32_t x) {
-    while (lo < hi) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (__ldg(&a[mid]) < x) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-// A warp per row i of L. Lanes take the row's mask entries j in turn; for
-// each (i, j) the lane intersects row_i (entries k < i) with col_j
-// (entries k > j) by binary searching each entry of the shorter list in the
-// longer. Only k in (j, i) can be common, which bounds both searches.
-__global__ void __launch_bounds__(TC_BLOCK) k_tc(uint32_t n, const uint32_t *rp, const uint32_t *ci,
-                                                 const uint32_t *cp, const uint32_t *ri, uint32_t *cvals,
-                                                 unsigned long long *total) {
-    __shared__ unsigned long long s_tot;
-    if (threadIdx.x == 0) s_tot = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const uint64_t nwarps = (uint64_t)gridDim.x * (TC_BLOCK / 32);
-    unsigned long long mine = 0;
-    for (uint64_t i = (uint64_t)blockIdx.x * (TC_BLOCK / 32) + (threadIdx.x >> 5); i < n; i += nwarps) {
-        const uint32_t rb = __ldg(&rp[i]), re = __ldg(&rp[i + 1]);
-        for (uint32_t q = rb + lane; q < re; q += 32) {
-            const uint32_t j = __ldg(&ci[q]);
-            // row_i restricted to (j, i): entries after q (rows are sorted)
-            const uint32_t ab = q + 1, ae = re;
-            // col_j restricted to (j, i): entries below i
-            const uint32_t bb = __ldg(&cp[j]);
-            const uint32_t be = lower_bound_u32(ri, bb, __ldg(&cp[j + 1]), (uint32_t)i);
-            uint32_t cnt = 0;
-            if (ae - ab <= be - bb) {
-                uint32_t lo = bb;
-                for (uint32_t x = ab; x < ae && lo < be; ++x) {
-                    uint32_t k = __ldg(&ci[x]);
-                    lo = lower_bound_u32(ri, lo, be, k);
-                    if (lo < be && __ldg(&ri[lo]) == k) ++cnt;
-                }
-            } else {
-                uint32_t lo = ab;
-                for (uint32_t x = bb; x < be && lo < ae; ++x) {
-                    uint32_t k = __ldg(&ri[x]);
-                    lo = lower_bound_u32(ci, lo, ae, k);
-                    if (lo < ae && __ldg(&ci[lo]) == k) ++cnt;
-                }
-            }
-            if (cvals) cvals[q] = cnt;
-            mine += cnt;
-        }
-    }
-    mine = dev::warp_sum<unsigned long long>(mine);
-    if (lane == 0 && mine) atomicAdd(&s_tot, mine);
-    __syncthreads();
-    if (threadIdx.x == 0 && s_tot) atomicAdd(total, s_tot);
-}
-
-// Total only, by columns of L: a warp per vertex k puts row_k (the
+// By columns of L: a warp per vertex k puts row_k (the
 // neighbours of k below k) in a set in shared memory; its lanes take the
 // rows i of column k (the neighbours of k above k, from the CSC) and count
 // the entries of row_i below k that the set holds (a prefix of row_i, since
@@ -87,7 +27,9 @@ __global__ void __launch_bounds__(TC_BLOCK) k_tc(uint32_t n, const uint32_t *rp,
 // probing at load factor at most one half; rows longer than TC_HROW beyond
 // the bitmap's range are probed by binary search in global memory. The
 // prefixes are read 16 bytes at a time (the index arrays are 16-byte
-// aligned and padded).
+// aligned and padded). A hit (i, k, j) is the term L(i,k) L(k,j) of C(i,j),
+// and L(i,j) is the probed entry of row i, so when C is asked for the hit
+// adds one to that entry's count in place.
 constexpr uint32_t TC_WORDS = 1024;   // per warp: a bitmap of 32768 ids or 1024 hash slots
 constexpr uint32_t TC_HROW = TC_WORDS / 2;
 constexpr uint32_t TC_EMPTY = 0xffffffffu;
@@ -95,8 +37,9 @@ constexpr uint32_t TC_EMPTY = 0xffffffffu;
 // multiplicative hash (Knuth's golden-ratio constant), top `bits` bits
 __device__ __forceinline__ uint32_t tc_slot(uint32_t v, int bits) { return (v * 2654435761u) >> (32 - bits); }
 
+template <bool WITH_C>
 __global__ void __launch_bounds__(TC_BLOCK) k_tc_hash(uint32_t n, const uint32_t *rp, const uint32_t *ci,
-                                                      const uint32_t *cp, const uint32_t *ri,
+                                                      const uint32_t *cp, const uint32_t *ri, uint32_t *cvals,
                                                       unsigned long long *total) {
     __shared__ uint32_t s_tab[TC_BLOCK / 32][TC_WORDS];
     __shared__ unsigned long long s_tot;
@@ -151,19 +94,25 @@ __global__ void __launch_bounds__(TC_BLOCK) k_tc_hash(uint32_t n, const uint32_t
                     const uint32_t x = x0 + u, j = jj[u];
                     if (x < ib) continue;
                     if (!more || x >= ie || j >= k) { more = false; continue; }   // the prefix ends at k
+                    bool hit;
                     if (mode == 0) {
-                        cnt += (tab[j >> 5] >> (j & 31)) & 1u;
+                        hit = (tab[j >> 5] >> (j & 31)) & 1u;
                     } else if (mode == 1) {
                         uint32_t h = tc_slot(j, bits), sv;
                         while ((sv = tab[h]) != TC_EMPTY && sv != j) h = (h + 1) & mask;
-                        cnt += sv == j;
+                        hit = sv == j;
                     } else {
                         uint32_t a = kb, b = ke;   // lower_bound of j in row_k
                         while (a < b) {
                             const uint32_t mid = (a + b) >> 1;
                             if (__ldg(&ci[mid]) < j) a = mid + 1; else b = mid;
                         }
-                        cnt += a < ke && __ldg(&ci[a]) == j;
+                        hit = a < ke && __ldg(&ci[a]) == j;
+                    }
+                    // L(i,k) L(k,j) with L(i,j) at position x: one term of C(i,j)
+                    if (hit) {
+                        ++cnt;
+                        if (WITH_C) atomicAdd(&cvals[x], 1u);
                     }
                 }
             }
@@ -196,23 +145,26 @@ extern "C" gb_info gb_tc(gb_context *ctx, const gb_matrix *L, uint64_t *count, g
     Scratch tot(ctx), cv(ctx), rows(ctx);
     GB_CHECK(tot.alloc(8));
     GB_CHECK(memset_async(ctx, tot.p, 0, 8));
-    if (C) GB_CHECK(cv.alloc((L->nvals + 1) * 4));
+    if (C) {
+        GB_CHECK(cv.alloc((L->nvals + 1) * 4));
+        GB_CHECK(memset_async(ctx, cv.p, 0, (L->nvals + 1) * 4));
+    }
     uint32_t n = L->nrows;
     if (n) {
         int occ = 0;
-        GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, C ? (const void *)k_tc : (const void *)k_tc_hash,
-                                                              TC_BLOCK, 0));
+        GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ, C ? (const void *)k_tc_hash<true> : (const void *)k_tc_hash<false>, TC_BLOCK, 0));
         unsigned blocks = (unsigned)(occ * ctx->num_sms * 4);
         uint64_t need = ((uint64_t)n + 7) / 8;
         if (need < blocks) blocks = (unsigned)need;
         if (blocks < 1) blocks = 1;
         int span = prof_begin(ctx, "tc");
-        if (C)   // per-entry C<L> = L.L: the intersection kernel
-            k_tc<<<blocks, TC_BLOCK, 0, ctx->stream>>>(n, L->rowptr, L->colidx, L->colptr, L->rowidx,
-                                                       cv.as<uint32_t>(), tot.as<unsigned long long>());
-        else     // the total alone
-            k_tc_hash<<<blocks, TC_BLOCK, 0, ctx->stream>>>(n, L->rowptr, L->colidx, L->colptr, L->rowidx,
-                                                            tot.as<unsigned long long>());
+        if (C)
+            k_tc_hash<true><<<blocks, TC_BLOCK, 0, ctx->stream>>>(n, L->rowptr, L->colidx, L->colptr, L->rowidx,
+                                                                  cv.as<uint32_t>(), tot.as<unsigned long long>());
+        else
+            k_tc_hash<false><<<blocks, TC_BLOCK, 0, ctx->stream>>>(n, L->rowptr, L->colidx, L->colptr, L->rowidx,
+                                                                   nullptr, tot.as<unsigned long long>());
         prof_end(ctx, span);
         GB_LAUNCH_CHECK();
     }
