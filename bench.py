@@ -118,9 +118,10 @@ def code_digest(paths, root=ROOT):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(profile, sources):
-    """DRAM bytes per launch from a profile summary's `traffic-record` line,
-    or None when the kernel's code changed since that capture."""
+def recorded_traffic(profile, sources, beta=None):
+    """DRAM bytes per launch from a profile summary's `traffic-record` line
+    for this push/pull threshold, or None when the kernel's code changed
+    since that capture or no capture used this threshold."""
     try:
         text = open(os.path.join(ROOT, profile)).read()
     except OSError:
@@ -128,7 +129,7 @@ def recorded_traffic(profile, sources):
     for line in text.splitlines():
         if line.startswith("traffic-record:"):
             kv = dict(x.split("=", 1) for x in line.split(":", 1)[1].split())
-            if kv.get("digest") == code_digest(sources):
+            if kv.get("digest") == code_digest(sources) and (beta is None or kv.get("beta") == str(beta)):
                 return float(kv["bytes_per_launch"])
     return None
 
@@ -215,12 +216,12 @@ def run_gbx(args):
     desc = gb.Descriptor(beta=args.beta) if args.beta else None
     levels = torch.empty(n, dtype=torch.int32, device=dev)
     parents = torch.empty(n, dtype=torch.int32, device=dev)
-    # the push/pull threshold is picked by the autotuner on 16 sources other
+    # the push/pull threshold is picked by the autotuner on 64 sources other
     # than the benchmark's (seed 99), unless --beta fixes it
     tuned_beta = None
     if not args.beta:
         import gen
-        tuned_beta, _ = gb.bfs_autotune(ctx, A, gen.sources(t, 16, seed=99))
+        tuned_beta, _ = gb.bfs_autotune(ctx, A, gen.sources(t, 64, seed=99))
 
     # untimed pass with statistics: algorithmic bytes and levels per source
     alg, depth, pushes, pulls = [], [], [], []
@@ -296,7 +297,7 @@ def run_gbx(args):
         "gpu_launches": int(args.steps * NSRC),
         "roofline": {"bound": "hbm", "kernel": "k_bfs", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": peak_kind,
-                     "traffic": recorded_traffic(BFS_PROFILE, BFS_KERNEL_SOURCES),
+                     "traffic": recorded_traffic(BFS_PROFILE, BFS_KERNEL_SOURCES, args.beta or tuned_beta),
                      "alg_bytes_per_launch": alg_per_bfs, "avg_launch_ms": avg_kernel_ms},
         "e2e": {"value": e2e_val, "unit": "GTEPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": int(NSRC * 2 * 4 * n)},

@@ -11,7 +11,11 @@
 //         sources are covered (the Boolean early exit, per 64 searches),
 // chosen by the rule of Table 9 on the union frontier's edge count. The
 // visited words are merged one level late (V | F is the visited set), so a
-// level needs a single grid barrier.
+// level needs a single grid barrier. Levels are first recorded per vertex:
+// byte q of a vertex's 64-byte record is 1 + its level for source q (0 =
+// not reached, 255 = level 254 or more, written to the output directly), so
+// the stores of a level stay inside one record per vertex; the last pass
+// turns the records into the k x n output with coalesced row stores.
 #include "common.cuh"
 #include "bfs_common.cuh"
 #include "frontier.cuh"
@@ -32,6 +36,7 @@ struct MsArgs {
     unsigned long long live;          // bits of the k sources
     const uint32_t *srcs;
     int32_t *levels;                   // k x n
+    unsigned long long *rec;           // n x 8 words: per vertex, one level byte per source
     unsigned long long *V;             // visited, merged one level late
     unsigned long long *F[3];          // frontier words, rotating
     uint32_t *front[3];                // unused by this kernel (frontier helpers' interface)
@@ -49,17 +54,29 @@ struct MsArgs {
 
 __device__ __forceinline__ unsigned long long ldcg64(const unsigned long long *p) { return __ldcg(p); }
 
-// levels[q][v] = d for the bits q of f (lane per vertex; the warp loops over
-// the union of its lanes' bits so each store instruction is coalesced)
-__device__ __forceinline__ void write_levels(const MsArgs &a, uint64_t v, bool valid, unsigned long long f, int d) {
-    unsigned long long u = valid ? f : 0ull;
+// bit i of m -> 0xff in byte i
+__device__ __forceinline__ unsigned long long spread8(unsigned long long m) {
+    m &= 0xffull;
+    m = (m | (m << 28)) & 0x0000000F0000000Full;
+    m = (m | (m << 14)) & 0x0003000300030003ull;
+    m = (m | (m << 7)) & 0x0101010101010101ull;
+    return m * 0xffull;
+}
+
+// records level d for the sources q in f at vertex v: one 64-bit atomicOr per
+// group of eight sources (the bytes it sets are still zero, each (q, v) is
+// reached once); from level 254 on the output is written directly
+__device__ __forceinline__ void record_levels(const MsArgs &a, uint64_t v, unsigned long long f, int d) {
+    if (!f) return;
+    const unsigned long long b = d < 254 ? (unsigned long long)(d + 1) * 0x0101010101010101ull : ~0ull;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) u |= __shfl_xor_sync(0xffffffffu, u, o);
-    while (u) {
-        int q = __ffsll((long long)u) - 1;
-        u &= u - 1;
-        if (valid && ((f >> q) & 1ull)) a.levels[(uint64_t)q * a.n + v] = d;
+    for (int c = 0; c < 8; ++c) {
+        const unsigned long long m = (f >> (8 * c)) & 0xffull;
+        if (m) atomicOr(&a.rec[v * 8 + c], spread8(m) & b);
     }
+    if (d >= 254)
+        for (unsigned long long u = f; u; u &= u - 1)
+            a.levels[(uint64_t)(__ffsll((long long)u) - 1) * a.n + v] = d;
 }
 
 // Builds the list form (vertex, out-degree prefix, row start) of the
@@ -134,7 +151,7 @@ __device__ void ms_pull(const MsArgs &a, int d, uint32_t *cnt_out, uint32_t *deg
                 b = __ldg(&a.rp_in[v]);
                 e = __ldg(&a.rp_in[v + 1]);
             }
-            write_levels(a, v, valid, f, d);
+            if (valid) record_levels(a, v, f, d);
             const bool hub = e - b > GBX_HUB_MIN_LEN;
             unsigned long long acc = 0;
             const bool need = valid && vis != a.live && !hub;
@@ -261,6 +278,10 @@ __global__ void __launch_bounds__(BLOCK, 5) k_msbfs(MsArgs a) {
         a.F[1][v] = 0ull;
         a.F[2][v] = 0ull;
     }
+    {
+        ulonglong2 *r2 = reinterpret_cast<ulonglong2 *>(a.rec);
+        for (uint64_t x = tid; x < (uint64_t)a.n * 4; x += nthreads) r2[x] = make_ulonglong2(0ull, 0ull);
+    }
     bool ok = dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns);
     if (ok && tid == 0) {
         memset(res, 0, sizeof(BfsResult));
@@ -340,11 +361,10 @@ __global__ void __launch_bounds__(BLOCK, 5) k_msbfs(MsArgs a) {
                     bool valid = x < cnt;
                     uint32_t v = valid ? ldcg(&Q[x]) : 0u;
                     unsigned long long f = valid ? ldcg64(&a.F[d % 3][v]) : 0ull;
-                    if (valid) atomicOr(&a.V[v], f);
-                    // levels[q][v]: per-vertex stores (list order is not vertex order)
-                    if (valid)
-                        for (unsigned long long u = f; u; u &= u - 1)
-                            a.levels[(uint64_t)(__ffsll((long long)u) - 1) * a.n + v] = d;
+                    if (valid) {
+                        atomicOr(&a.V[v], f);
+                        record_levels(a, v, f, d);
+                    }
                 }
             }
             const unsigned long long *F = a.F[d % 3];
@@ -363,15 +383,29 @@ __global__ void __launch_bounds__(BLOCK, 5) k_msbfs(MsArgs a) {
         }
         ok = dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns);
     }
-    // ---- (source, vertex) pairs never reached get -1
+    // ---- the records become the output: lane per vertex, each row q stored
+    // for 32 consecutive vertices at once; (source, vertex) pairs never
+    // reached get -1, pairs at level 254 or more are already written
     if (ok) {
         const int lane = threadIdx.x & 31;
         const uint64_t nwarps = (uint64_t)gridDim.x * WARPS;
+        const ulonglong2 *r2 = reinterpret_cast<const ulonglong2 *>(a.rec);
         for (uint64_t g = (uint64_t)blockIdx.x * WARPS + (threadIdx.x >> 5); g * 32 < a.n; g += nwarps) {
-            uint64_t v = g * 32 + lane;
-            bool valid = v < a.n;
-            unsigned long long unv = valid ? (a.live & ~ldcg64(&a.V[v])) : 0ull;
-            write_levels(a, v, valid, unv, -1);
+            const uint64_t v = g * 32 + lane;
+            const bool valid = v < a.n;
+            unsigned long long w[8];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const ulonglong2 x = valid ? __ldcg(&r2[v * 4 + c]) : make_ulonglong2(0ull, 0ull);
+                w[2 * c] = x.x;
+                w[2 * c + 1] = x.y;
+            }
+#pragma unroll
+            for (int q = 0; q < 64; ++q) {
+                if ((uint32_t)q >= a.k) break;
+                const uint32_t byte = (uint32_t)(w[q >> 3] >> (8 * (q & 7))) & 0xffu;
+                if (valid && byte != 0xffu) a.levels[(uint64_t)q * a.n + v] = byte ? (int32_t)byte - 1 : -1;
+            }
         }
     }
     if (tid == 0) {
@@ -399,7 +433,7 @@ __global__ void __launch_bounds__(BLOCK, 5) k_msbfs(MsArgs a) {
 
 struct MsWorkspace {
     uint32_t n = 0;
-    unsigned long long *V = nullptr, *F = nullptr;
+    unsigned long long *V = nullptr, *F = nullptr, *rec = nullptr;
     uint32_t *q = nullptr, *qp = nullptr, *qr = nullptr;
     BfsState *st = nullptr;
 };
@@ -411,8 +445,10 @@ static gb_info ms_workspace(gb_context *ctx, uint32_t n, MsWorkspace **out) {
     MsWorkspace &w = g_ms[ctx];
     if (w.n < n || !w.st) {
         dfree(ctx, w.V); dfree(ctx, w.F); dfree(ctx, w.q); dfree(ctx, w.qp); dfree(ctx, w.qr); dfree(ctx, w.st);
+        dfree(ctx, w.rec);
         w = MsWorkspace();
         GB_CHECK(dalloc_t(ctx, &w.V, (size_t)n + 1));
+        GB_CHECK(dalloc_t(ctx, &w.rec, 8ull * n + 8));
         GB_CHECK(dalloc_t(ctx, &w.F, 3ull * n + 3));
         GB_CHECK(dalloc_t(ctx, &w.q, 2ull * n + 2));
         GB_CHECK(dalloc_t(ctx, &w.qp, 2ull * n + 2));
@@ -431,6 +467,7 @@ void ms_workspace_release(gb_context *ctx) {
     if (it == g_ms.end()) return;
     MsWorkspace &w = it->second;
     dfree(ctx, w.V); dfree(ctx, w.F); dfree(ctx, w.q); dfree(ctx, w.qp); dfree(ctx, w.qr); dfree(ctx, w.st);
+    dfree(ctx, w.rec);
     g_ms.erase(it);
 }
 
@@ -447,6 +484,7 @@ gb_info msbfs_launch(gb_context *ctx, const gb_matrix *A, const uint32_t *d_srcs
     a.live = k >= 64 ? ~0ull : ((1ull << k) - 1);
     a.srcs = d_srcs;
     a.levels = levels;
+    a.rec = w->rec;
     a.rp_out = A->rowptr;
     a.ci_out = A->colidx;
     a.rp_in = A->has_csc ? A->colptr : nullptr;
