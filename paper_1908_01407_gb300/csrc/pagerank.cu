@@ -107,7 +107,7 @@ __device__ __forceinline__ void epilogue(const PrArgs &a, uint32_t i, float y, f
     if (!deg) dang += (double)p;
 }
 
-__global__ void __launch_bounds__(PR_BLOCK) k_pr_spmv(PrArgs a) {
+__global__ void __launch_bounds__(PR_BLOCK, 6) k_pr_spmv(PrArgs a) {
     // dynamic shared memory: s_rs[0] = start of the chunk's first row,
     // s_rs[r + 1] = end of its row r; gathered x values and previous ranks
     extern __shared__ __align__(16) unsigned char pr_smem[];
@@ -132,11 +132,24 @@ __global__ void __launch_bounds__(PR_BLOCK) k_pr_spmv(PrArgs a) {
     for (uint64_t c = D0; c < D1; c += PR_TILE) {
         const uint64_t ce = c + PR_TILE < D1 ? c + PR_TILE : D1;
         const uint32_t clen = (uint32_t)(ce - c);
-        // stage the row bounds of every row the chunk can reach (one coalesced load)
+        // stage the row bounds the chunk can reach, PR_BLOCK at a time, until a
+        // staged row end lies at or past the chunk's last nonzero: no row
+        // beyond it can end inside the chunk, so the merge searches never
+        // look further (a chunk of rows of ~30 entries needs one round instead
+        // of the clen + 1 bounds a chunk of empty rows would)
         const uint32_t avail = a.n - ic;
-        const uint32_t R = avail < clen + 1 ? avail : clen + 1;
-        for (uint32_t r = threadIdx.x; r <= R; r += PR_BLOCK) s_rs[r] = __ldg(&a.rp[ic + r]);
-        __syncthreads();
+        const uint32_t Rmax = avail < clen + 1 ? avail : clen + 1;
+        uint32_t R = Rmax;
+        for (uint32_t r0 = 0;; r0 += PR_BLOCK) {
+            const uint32_t r = r0 + threadIdx.x;
+            if (r <= Rmax) s_rs[r] = __ldg(&a.rp[ic + r]);
+            __syncthreads();
+            const uint32_t last = r0 + PR_BLOCK - 1 < Rmax ? r0 + PR_BLOCK - 1 : Rmax;
+            if (last == Rmax || (uint64_t)s_rs[last] >= kc + clen) {
+                R = last;
+                break;
+            }
+        }
         const uint32_t *s_re = s_rs + 1;
         const uint64_t nk_left = a.nnz - kc;
         const uint32_t bl = nk_left < clen ? (uint32_t)nk_left : clen;
