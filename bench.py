@@ -141,6 +141,25 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, ws):
+    """The slowest rank's value of x (timings are the maximum over ranks);
+    x itself when there is one rank. Collective over the default group."""
+    if ws == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gteps(ws, bfs_per_rank, m, seconds):
+    """GTEPS of the whole job: every replica traverses bfs_per_rank times
+    the m stored edges in `seconds` (the slowest rank's time)."""
+    return ws * bfs_per_rank * m / seconds / 1e9
+
+
 def make_inputs():
     import gen
     t = gen.rmat(SCALE, EF, seed=SEED)
@@ -262,12 +281,9 @@ def run_gbx(args):
     ctx.profile(False)
     clk = clocks.stop()
 
-    if ws > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(total_ms, ws)
     ms_per_step = total_ms / args.steps
-    value = ws * NSRC * m / (ms_per_step / 1e3) / 1e9
+    value = whole_job_gteps(ws, NSRC, m, ms_per_step / 1e3)
 
     # end to end through the C ABI with host buffers: one gb_bfs_batch call per step writes every
     # source's levels and parents to pinned host memory (each run's copy overlaps the next run)
@@ -277,11 +293,13 @@ def run_gbx(args):
     gb.bfs_batch(ctx, A, srcs_u[:2], lv_h[:2], pa_h[:2], desc=desc)
     torch.cuda.synchronize()
     e_steps = max(1, min(args.steps, 3))
+    if ws > 1:
+        dist.barrier()
     e0 = time.perf_counter()
     for _ in range(e_steps):
         gb.bfs_batch(ctx, A, srcs_u, lv_h, pa_h, desc=desc)
-    e2e_s = (time.perf_counter() - e0) / e_steps
-    e2e_val = NSRC * m / e2e_s / 1e9
+    e2e_s = max_over_ranks((time.perf_counter() - e0) / e_steps, ws)
+    e2e_val = whole_job_gteps(ws, NSRC, m, e2e_s)
     del lv_h, pa_h
 
     hbm, peak_kind = peaks()

@@ -1,0 +1,62 @@
+"""The N > 1 host path of the benchmark on CPU: world_size-2 gloo ranks
+(the benchmark runs one independent replica per GPU, no data-path
+collective; the ranks only agree on the slowest rank's time)."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+import bench
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, ws, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        # every rank reports its own step time; all of them get the slowest
+        t = bench.max_over_ranks(10.0 + 5.0 * rank, ws)
+        assert bench.dist_env() == (ws, rank, rank)
+        out.put((rank, t))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_agree_on_the_slowest_time():
+    ws, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_main, args=(r, ws, port, q)) for r in range(ws)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(90)
+    assert all(p.exitcode == 0 for p in procs), [p.exitcode for p in procs]
+    got = dict(q.get(timeout=5) for _ in range(ws))
+    assert got == {0: 15.0, 1: 15.0}
+
+
+def test_whole_job_value_counts_every_replica():
+    # 64 BFS of 128.3M edges in 10 ms on each of N replicas: N times one replica's rate
+    one = bench.whole_job_gteps(1, 64, 128_304_424, 0.010)
+    assert one == pytest.approx(64 * 128_304_424 / 0.010 / 1e9)
+    assert bench.whole_job_gteps(4, 64, 128_304_424, 0.010) == pytest.approx(4 * one)
+    assert bench.max_over_ranks(3.5, 1) == 3.5
+
+
+def test_reference_arm_prints_only_on_rank_zero(capsys, monkeypatch):
+    """Under torchrun the other ranks of the reference arm exit without work."""
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    args = type("A", (), {"steps": 1, "warmup": 0, "ref_sources": 1, "gpus": 2})()
+    bench.run_reference(args)
+    assert capsys.readouterr().out == ""
