@@ -285,12 +285,15 @@ def test_tc_rmat_s20_full_size(ctx):
 
 # ------------------------------------------------------- multi-source BFS
 @pytest.mark.parametrize("case,k", [("rmat14", 64), ("rmat14", 1), ("rmat13", 37), ("grid", 64), ("small", 5),
+                                    ("path", 9),
                                     ("rmat13", 150)])
 def test_bfs_multi_matches_independent_bfs(ctx, case, k):
     t = {"rmat14": lambda: gen.rmat(14, 16, seed=1),
          "rmat13": lambda: gen.rmat(13, 8, seed=8),
          "grid": lambda: gen.grid(60, 50, 0.1, seed=3),
-         "small": lambda: gen.from_edges(9, [(0, 1), (1, 2), (3, 4)])}[case]()
+         "small": lambda: gen.from_edges(9, [(0, 1), (1, 2), (3, 4)]),
+         # levels up to 699: the per-vertex level bytes hold levels below 254, later ones go to the output directly
+         "path": lambda: gen.from_edges(700, [(i, i + 1) for i in range(699)])}[case]()
     g = oracle.csr_from_tuples(t)
     A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, flags=gb.SYMMETRIC)
     rng = np.random.default_rng(k)
