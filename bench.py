@@ -305,6 +305,8 @@ def run_gbx(args):
     hbm, peak_kind = peaks()
     avg_kernel_ms = k_ms / max(k_n, 1)
     achieved = alg_per_bfs / (avg_kernel_ms / 1e3) / 1e9
+    traffic = recorded_traffic(BFS_PROFILE, BFS_KERNEL_SOURCES, args.beta or tuned_beta)
+    dram_achieved = traffic / (avg_kernel_ms / 1e3) / 1e9 if traffic else None
     line = {
         "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -314,9 +316,10 @@ def run_gbx(args):
                    "beta": args.beta or tuned_beta, "beta_from": "fixed" if args.beta else "autotuner"},
         "gpu_launches": int(args.steps * NSRC),
         "roofline": {"bound": "hbm", "kernel": "k_bfs", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "peak_kind": peak_kind,
-                     "traffic": recorded_traffic(BFS_PROFILE, BFS_KERNEL_SOURCES, args.beta or tuned_beta),
-                     "alg_bytes_per_launch": alg_per_bfs, "avg_launch_ms": avg_kernel_ms},
+                     "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": traffic,
+                     "alg_bytes_per_launch": alg_per_bfs, "avg_launch_ms": avg_kernel_ms,
+                     # the same launches by the DRAM bytes ncu counted (null without a matching capture)
+                     "dram_achieved": dram_achieved, "dram_frac": dram_achieved / hbm if dram_achieved else None},
         "e2e": {"value": e2e_val, "unit": "GTEPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": int(NSRC * 2 * 4 * n)},
         "clocks": clk,
@@ -360,6 +363,24 @@ def extra_rows(args, hbm):
     stream = torch.cuda.Stream()
     ctx = gb.Context(0)
     ctx.set_stream(stream)
+    # --- BFS on R-MAT s14 from its max-degree vertex (the graph is L2-resident:
+    # latency per BFS and per level, not bandwidth)
+    t = gen.rmat(14, 16, seed=1)
+    A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, flags=gb.SYMMETRIC)
+    rows, _ = A.extract_tuples()
+    deg = np.bincount(np.asarray(rows, dtype=np.int64), minlength=t.n)   # stored degrees
+    src = int(np.flatnonzero(deg == deg.max())[0])                        # lowest id on ties
+    lv = torch.empty(t.n, dtype=torch.int32, device="cuda")
+    pa = torch.empty(t.n, dtype=torch.int32, device="cuda")
+    _, _, st = gb.bfs(ctx, A, src, lv, pa, stats=True)
+    for _ in range(10):
+        gb.bfs(ctx, A, src, lv, pa, stats=False)
+    reps = 200
+    ms = cuda_time_ms(lambda: [gb.bfs(ctx, A, src, lv, pa, stats=False) for _ in range(reps)], stream)
+    out["bfs_s14"] = {"source": src, "us_per_bfs": 1e3 * ms / reps, "depth": st["depth"],
+                      "us_per_level": 1e3 * ms / reps / max(st["depth"], 1),
+                      "gteps": A.nvals / (ms / reps / 1e3) / 1e9}
+    A.free()
     # --- SSSP and PageRank on R-MAT s22 (weights uniform in [1, 255])
     t = gen.rmat(SCALE, EF, seed=SEED, wmax=255)
     A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, t.w, type_=gb.UINT32, flags=gb.SYMMETRIC)
