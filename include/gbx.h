@@ -288,14 +288,18 @@ gb_info gb_reduce_rows(gb_vector *w, const gb_vector *mask, gb_binop accum, gb_m
 #define GB_TRACE_LEVELS 32
 
 typedef struct {
-    uint32_t depth;              /* number of BFS levels expanded */
+    uint32_t depth;              /* 1 + the largest level; levels expanded = push_levels + pull_levels
+                                    (one fewer when the source's whole component was reached first) */
     uint32_t push_levels;
     uint32_t pull_levels;
     uint32_t status;             /* 0, or GB_TIMEOUT if a bounded device wait ran out */
     uint64_t vertices_reached;
     uint64_t edges_examined;     /* adjacency entries read (push and pull) */
     uint64_t frontier_edges;     /* sum of degrees of all frontiers */
-    uint64_t alg_bytes;          /* algorithmic bytes moved (see the design notes) */
+    uint64_t alg_bytes;          /* algorithmic bytes: 8 n (levels, parents) + per push level
+                                    8 |V_f| + 4 |E_f| + 12 |V_next|, per pull level min(n/8, 4 |C|)
+                                    + 8 (unvisited candidates of C) + 4 |E_examined| + 12 |V_next|,
+                                    C = the candidates the pull walks (gb_bfs) */
     /* per-level trace of the first GB_TRACE_LEVELS levels (gb_bfs, gb_bfs_multi) */
     uint32_t trace_len;
     uint32_t trace_dir[GB_TRACE_LEVELS];        /* 1 = push, 2 = pull */

@@ -6,7 +6,7 @@ paper: semirings and monoids (Section 3.1.3-3.1.4, Table 5), masking and its
 structural complement (Section 3.2.1), the descriptor (Table 6), and the
 operations of Table 7 (mxv, vxm, mxm, eWiseAdd, eWiseMult, reduce).
 
-Readings where the paper is silent (also listed in the design notes):
+Readings where the paper is silent:
 * accum: the paper ignores it (Section 3.6); here w = accum(w, t) on the
   positions the mask lets through, as the GraphBLAS C API defines it.
 * REPLACE: the paper leaves it out (Section 3.6); here positions outside the
