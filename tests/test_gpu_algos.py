@@ -177,9 +177,11 @@ def tc_pipeline(ctx, t):
     return A, B, L, new_id
 
 
-@pytest.mark.parametrize("case", ["k12", "wheel", "tree", "rmat12", "rmat14", "grid"])
+@pytest.mark.parametrize("case", ["k12", "wheel", "tree", "rmat12", "rmat14", "grid", "empty", "k3"])
 def test_tc_count_and_entries(ctx, case):
     t = {"k12": lambda: gen.from_edges(12, list(itertools.combinations(range(12), 2))),
+         "empty": lambda: gen.from_edges(6, []),                       # no entries in L at all
+         "k3": lambda: gen.from_edges(3, [(0, 1), (1, 2), (0, 2)]),     # one triangle, counted at one entry
          "wheel": lambda: gen.from_edges(10, [(0, i) for i in range(1, 10)] + [(i, i % 9 + 1) for i in range(1, 10)]),
          "tree": lambda: gen.from_edges(31, [(i, (i - 1) // 2) for i in range(1, 31)]),
          "rmat12": lambda: gen.rmat(12, 16, seed=4),

@@ -383,3 +383,33 @@ def test_bfs_stops_once_the_component_is_reached(ctx):
         assert len(st["trace"]) == st["depth"] - 1, (s, st["depth"], len(st["trace"]))
     d.free()
     A.free()
+
+
+def test_bfs_with_self_loops_and_a_directed_build(ctx):
+    """A matrix built from tuples with self-loops (no symmetric flag: CSR and
+    CSC): a self-loop never makes a vertex its own parent or moves its level,
+    in any direction; the component early stop still holds."""
+    rows = np.array([0, 0, 1, 1, 2, 2, 3, 3, 4, 5, 5, 6], np.uint32)
+    cols = np.array([0, 1, 0, 2, 1, 3, 2, 3, 4, 6, 5, 5], np.uint32)
+    n = 8
+    g = oracle.csr_build(n, rows, cols)
+    A = gb.Matrix.from_tuples(ctx, n, rows, cols)
+    for direction in (gb.AUTO, gb.PUSH, gb.PULL):
+        d = gb.Descriptor(direction=direction)
+        for src in (0, 3, 4, 5, 7):
+            lv, par, st = gb.bfs(ctx, A, src, desc=d)
+            torch.cuda.synchronize()
+            lv, par = lv.cpu().numpy(), par.cpu().numpy()
+            assert np.array_equal(lv, oracle.bfs(g, src)), (direction, src)
+            assert oracle.bfs_parent_violations(g, src, lv, par) == 0
+            assert par[src] == src
+        d.free()
+    A.free()
+
+
+def test_bfs_batch_single_vertex_graph(ctx):
+    t = gen.from_edges(1, [])
+    g, A = make(ctx, t)
+    lv, par = gb.bfs_batch(ctx, A, np.zeros(3, np.uint32), np.empty((3, 1), np.int32), np.empty((3, 1), np.int32))
+    assert lv.tolist() == [[0], [0], [0]] and par.tolist() == [[0], [0], [0]]
+    A.free()
