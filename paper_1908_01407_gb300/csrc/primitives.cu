@@ -270,11 +270,6 @@ __global__ void k_rowptr(const uint64_t *keys, const uint32_t *head, const uint3
     }
 }
 
-__global__ void k_fill_u32(uint32_t *p, uint64_t n, uint32_t v) {
-    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) p[i] = v;
-}
-
 inline unsigned nblk(uint64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
 }  // namespace
 
