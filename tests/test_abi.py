@@ -76,3 +76,20 @@ def test_teps_metric_matches_paper_table9():
     assert abs(got - want) / want < float(f["rel_tol"])
     got_t = gb.teps(float(f["edges"]), float(f["titan_runtime_ms"]) / 1e3) / 1e9
     assert abs(got_t - float(f["titan_gteps"])) / float(f["titan_gteps"]) < 0.005
+
+
+def test_every_entry_point_rejects_null_handles(L):
+    """Each call of the ABI, given NULL for every pointer and 0 for every
+    number, returns an error code (NULL_POINTER, or INVALID_VALUE where a
+    count of 0 is checked first) without touching a device or crashing."""
+    import ctypes as C
+    codes = {}
+    for name, argtypes in sorted(gb._SIGS.items()):
+        f = getattr(L, name)
+        args = [None if t in (C.c_void_p, C.c_char_p) or isinstance(t, type(C.POINTER(C.c_int)))
+                else t(0) for t in argtypes]
+        codes[name] = f(*args)
+    bad = {n: c for n, c in codes.items() if c not in (gb.NULL_POINTER, gb.INVALID_VALUE)}
+    assert not bad, bad
+    assert codes["gb_bfs_multi"] == gb.INVALID_VALUE          # k == 0 is checked before the handles
+    assert codes["gb_bfs_batch"] == gb.NULL_POINTER
