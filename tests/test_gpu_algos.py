@@ -405,3 +405,31 @@ def test_pagerank_and_delta_directed_matrix(ctx):
     assert abs(it - it_o) <= 2
     assert np.abs(got.astype(np.float64) - want).sum() <= 1e-5 + 10 * eps
     A.free()
+
+
+def test_tc_every_set_kind_on_disjoint_cliques(ctx):
+    """65 disjoint K_514 (33,410 vertices, all of degree 513, so the degree
+    relabel keeps every id and each L(i,j), j < i, lies inside one clique):
+    C(i,j) = i - j - 1, the clique's vertices between them, and the total is
+    65 * C(514, 3). Rows of vertices above 32,768 use the hash set (at most
+    512 entries) or the binary search in global memory (513 entries), the
+    others the bitmap, so all three kinds run, with and without C."""
+    m, c = 514, 65
+    iu, ju = np.triu_indices(m, 1)
+    base = (np.arange(c, dtype=np.int64) * m)[:, None]
+    a = (base + iu[None, :]).ravel().astype(np.uint32)
+    b = (base + ju[None, :]).ravel().astype(np.uint32)
+    n = m * c
+    A = gb.Matrix.from_tuples(ctx, n, np.concatenate([a, b]), np.concatenate([b, a]), flags=gb.SYMMETRIC)
+    B, new_id = A.degree_order()
+    assert np.array_equal(np.asarray(new_id), np.arange(n))
+    L = B.tril()
+    want = c * m * (m - 1) * (m - 2) // 6
+    assert gb.tc(ctx, L) == want
+    C = gb.Matrix(ctx, gb.UINT32, n, n)
+    assert gb.tc(ctx, L, C) == want
+    r, col, v = C.extract_tuples(with_vals=True)
+    assert len(v) == L.nvals
+    assert np.array_equal(v.astype(np.int64), r.astype(np.int64) - col.astype(np.int64) - 1)
+    for x in (A, B, L, C):
+        x.free()
