@@ -102,10 +102,12 @@ BFS_KERNEL_SOURCES = ["paper_1908_01407_gb300/csrc/bfs.cu", "paper_1908_01407_gb
 BFS_PROFILE = "profiles/k_bfs_rmat_s22.md"
 
 
-def code_digest(paths, root=ROOT):
-    """sha256 of the code of `paths` with comments and blank lines removed."""
+def code_digest(paths, root=None):
+    """sha256 of the code of `paths` (relative to root, default the
+    repository) with comments and blank lines removed."""
     import hashlib
     import re
+    root = ROOT if root is None else root
     h = hashlib.sha256()
     for p in paths:
         src = open(os.path.join(root, p)).read()

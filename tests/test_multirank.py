@@ -60,3 +60,27 @@ def test_reference_arm_prints_only_on_rank_zero(capsys, monkeypatch):
     args = type("A", (), {"steps": 1, "warmup": 0, "ref_sources": 1, "gpus": 2})()
     bench.run_reference(args)
     assert capsys.readouterr().out == ""
+
+
+def test_traffic_record_needs_the_same_code_and_threshold(tmp_path):
+    """The bench reports a kernel's DRAM bytes only from a capture of the same
+    code (a digest of its sources without comments) at the same push/pull
+    threshold."""
+    src = tmp_path / "k.cu"
+    src.write_text("// a comment\n__global__ void k() { int x = 1; }\n")
+    dig = bench.code_digest(["k.cu"], root=str(tmp_path))
+    prof = tmp_path / "p.md"
+    prof.write_text(f"traffic-record: kernel=k digest={dig} beta=24 bytes_per_launch=1000 launches=64\n"
+                    f"traffic-record: kernel=k digest={dig} beta=16 bytes_per_launch=900 launches=64\n")
+    old_root = bench.ROOT
+    try:
+        bench.ROOT = str(tmp_path)
+        assert bench.recorded_traffic("p.md", ["k.cu"], 24) == 1000.0
+        assert bench.recorded_traffic("p.md", ["k.cu"], 16) == 900.0
+        assert bench.recorded_traffic("p.md", ["k.cu"], 8) is None
+        src.write_text("// another comment\n__global__ void k() { int x = 1; }\n")   # comments do not count
+        assert bench.recorded_traffic("p.md", ["k.cu"], 24) == 1000.0
+        src.write_text("__global__ void k() { int x = 2; }\n")                        # code does
+        assert bench.recorded_traffic("p.md", ["k.cu"], 24) is None
+    finally:
+        bench.ROOT = old_root
