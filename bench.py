@@ -159,7 +159,8 @@ def max_over_ranks(x, ws):
 def whole_job_gteps(ws, bfs_per_rank, m, seconds):
     """GTEPS of the whole job: every replica traverses bfs_per_rank times
     the m stored edges in `seconds` (the slowest rank's time)."""
-    return ws * bfs_per_rank * m / seconds / 1e9
+    from paper_1908_01407_gb300.metrics import teps
+    return ws * bfs_per_rank * teps(m, seconds) / 1e9
 
 
 def make_inputs():
@@ -220,6 +221,7 @@ def cpu_baseline(t, srcs, budget_s):
 def run_gbx(args):
     import torch
     import paper_1908_01407_gb300 as gb
+    from paper_1908_01407_gb300.metrics import teps_undirected
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -232,7 +234,24 @@ def run_gbx(args):
     ctx = gb.Context(local)
     stream = torch.cuda.Stream(device=dev)
     ctx.set_stream(stream)
+    # matrix build (Table 4 build: tuples -> CSR, aliased CSC, live table, component sizes), timed twice:
+    # from tuples already resident on the device (the paper excludes uploads), and from host tuples
+    src_d = torch.from_numpy(t.src.view(np.int32)).to(dev)
+    dst_d = torch.from_numpy(t.dst.view(np.int32)).to(dev)
+    build_s = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        b0 = time.perf_counter()
+        A = gb.Matrix.from_tuples(ctx, t.n, src_d, dst_d, flags=gb.SYMMETRIC)
+        torch.cuda.synchronize()
+        build_s.append(time.perf_counter() - b0)
+        A.free()
+    del src_d, dst_d
+    torch.cuda.synchronize()
+    b0 = time.perf_counter()
     A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, flags=gb.SYMMETRIC)
+    torch.cuda.synchronize()
+    build_host_s = time.perf_counter() - b0
     n, m = A.nrows, A.nvals
     desc = gb.Descriptor(beta=args.beta) if args.beta else None
     levels = torch.empty(n, dtype=torch.int32, device=dev)
@@ -325,12 +344,20 @@ def run_gbx(args):
         "e2e": {"value": e2e_val, "unit": "GTEPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": int(NSRC * 2 * 4 * n)},
         "clocks": clk,
+        "build": {"ms_device_tuples": 1e3 * min(build_s), "ms_host_tuples": 1e3 * build_host_s,
+                  "what": "tuples -> sorted CSR (CSC aliased), live table, FastSV component sizes"},
         "bfs": {"median_depth": float(np.median(depth)), "mean_push_levels": float(np.mean(pushes)),
                 "mean_pull_levels": float(np.mean(pulls)), "ms_per_bfs": ms_per_step / NSRC,
-                "gteps_graph500": value / 2},
+                "gteps_graph500": ws * NSRC * teps_undirected(m, ms_per_step / 1e3) / 1e9},
     }
     if rank == 0 and not args.no_rows:
+        legs = OracleLegs() if not args.no_cpu_baseline else None
         line["rows"] = extra_rows(args, hbm)
+        if legs is not None:
+            legs.finish(line["rows"])
+    if rank == 0 and "rows" in line:
+        for k in [k for k in line["rows"] if k.startswith("_")]:
+            del line["rows"][k]
     if rank == 0 and not args.no_serving:
         line["serving"] = serving_bench(args)
     if rank == 0 and not args.no_cpu_baseline:
@@ -379,6 +406,7 @@ def extra_rows(args, hbm):
         gb.bfs(ctx, A, src, lv, pa, stats=False)
     reps = 200
     ms = cuda_time_ms(lambda: [gb.bfs(ctx, A, src, lv, pa, stats=False) for _ in range(reps)], stream)
+    out["_bfs_s14_levels"] = lv.cpu().numpy()
     out["bfs_s14"] = {"source": src, "us_per_bfs": 1e3 * ms / reps, "depth": st["depth"],
                       "us_per_level": 1e3 * ms / reps / max(st["depth"], 1),
                       "gteps": A.nvals / (ms / reps / 1e3) / 1e9}
@@ -389,29 +417,47 @@ def extra_rows(args, hbm):
     n, m = A.nrows, A.nvals
     srcs = gen.sources(t, 8, seed=SRC_SEED)
     dist = torch.empty(n, dtype=torch.int32, device="cuda")
-    for s in srcs[:2]:
-        gb.sssp(ctx, A, int(s), dist)
+    sssp_alg = []
+    for s in srcs:
+        sssp_alg.append(gb.sssp(ctx, A, int(s), dist, stats=True)[2]["alg_bytes"])
     iters = []
     def sssp_all():
         for s in srcs:
             _, it = gb.sssp(ctx, A, int(s), dist)
             iters.append(it)
+    ctx.profile(True)
     ms = cuda_time_ms(sssp_all, stream)
+    k_ms, k_n = ctx.profile_get("sssp")
+    ctx.profile(False)
+    k_avg = k_ms / max(k_n, 1)
+    a_sssp = float(np.mean(sssp_alg))
     out["sssp_s22"] = {"sources": len(srcs), "ms_per_sssp": ms / len(srcs), "gteps": len(srcs) * m / (ms / 1e3) / 1e9,
-                       "mean_iterations": float(np.mean(iters)), "cpu_baseline": None}
+                       "mean_iterations": float(np.mean(iters)),
+                       "roofline": {"bound": "hbm", "kernel": "k_relax", "alg_bytes_per_launch": a_sssp,
+                                    "avg_launch_ms": k_avg, "achieved": a_sssp / (k_avg / 1e3) / 1e9, "peak": hbm,
+                                    "unit": "GB/s", "frac": a_sssp / (k_avg / 1e3) / 1e9 / hbm}}
     rank = torch.empty(n, dtype=torch.float32, device="cuda")
     gb.pagerank(ctx, A, 0.85, 50, rank, residuals=False)
     ctx.profile(True)
     ms = cuda_time_ms(lambda: gb.pagerank(ctx, A, 0.85, 50, rank, residuals=False), stream)
     k_ms, k_n = ctx.profile_get("pagerank_spmv")
+    u_ms, u_n = ctx.profile_get("pagerank_update")
     ctx.profile(False)
-    it_ms = k_ms / max(k_n, 1)
+    spmv_ms = k_ms / max(k_n, 1)
+    upd_ms = u_ms / max(u_n, 1)
+    it_ms = ms / 50          # whole iterations (SpMV, the rows that cross tiles, update, reduction)
     bytes_iter = 4.0 * m + 20.0 * n
+    bytes_spmv = 4.0 * m + 8.0 * n   # column indices, x once, the row sums written
+    out["_pagerank_s22_rank"] = rank.cpu().numpy()
     out["pagerank_s22"] = {"iterations": 50, "ms_total": ms, "ms_per_iteration": it_ms,
+                           "ms_spmv_kernel": spmv_ms, "ms_update_kernel": upd_ms,
                            "gteps_per_iteration": m / (it_ms / 1e3) / 1e9,
-                           "roofline": {"bound": "hbm", "kernel": "k_pr_spmv", "alg_bytes_per_launch": bytes_iter,
-                                        "achieved": bytes_iter / (it_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-                                        "frac": bytes_iter / (it_ms / 1e3) / 1e9 / hbm}}
+                           "iteration_alg_bytes": bytes_iter,
+                           "iteration_frac": bytes_iter / (it_ms / 1e3) / 1e9 / hbm,
+                           "roofline": {"bound": "hbm", "kernel": "k_pr_tiles", "alg_bytes_per_launch": bytes_spmv,
+                                        "avg_launch_ms": spmv_ms,
+                                        "achieved": bytes_spmv / (spmv_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                                        "frac": bytes_spmv / (spmv_ms / 1e3) / 1e9 / hbm}}
     # --- adaptive PageRank (PageRankDelta): converged vertices masked out
     prd = {}
     for eps in (1e-4, 1e-5):
@@ -471,6 +517,99 @@ def extra_rows(args, hbm):
     return out
 
 
+def _timed(fn):
+    t0 = time.perf_counter()
+    r = fn()
+    return r, time.perf_counter() - t0
+
+
+class OracleLegs:
+    """The oracle, as it stands (plain single-threaded C), timed on the host
+    beside each GPU row on the same seeded input, and the FP32 PageRank's
+    error against the FP64 oracle. The long legs run in host threads (each
+    one C call at a time, the GIL released) while the GPU rows are measured:
+    SSSP s22 runs Dijkstra from the first of its 8 sources; PageRank s22 runs
+    all 50 FP64 iterations (also the reference of the error); TC s20 runs the
+    node iterator once; the grid runs queue BFS, Dijkstra and union-find once
+    each. BFS s14 runs after the GPU rows. Each leg uses one core."""
+
+    def __init__(self):
+        self.out = {}
+        self.threads = [threading.Thread(target=f, daemon=True)
+                        for f in (self._s22, self._tc, self._grid)]
+        for t in self.threads:
+            t.start()
+
+    def _s22(self):
+        import gen
+        import oracle
+        t = gen.rmat(SCALE, EF, seed=SEED, wmax=255)
+        g = oracle.csr_from_tuples(t)
+        srcs = gen.sources(t, 8, seed=SRC_SEED)
+        del t
+        _, dt = _timed(lambda: oracle.sssp(g, int(srcs[0])))
+        self.out["sssp_s22"] = {"value": g.m / dt / 1e9, "unit": "GTEPS", "ms_per_sssp": 1e3 * dt, "cores": 1,
+                                "kind": "oracle", "sample": "binary-heap Dijkstra from the first of the 8 sources"}
+        (p64, _), dt = _timed(lambda: oracle.pagerank(g, 0.85, 50))
+        self.out["pagerank_s22"] = {"value": 1e3 * dt / 50, "unit": "ms per iteration", "cores": 1, "kind": "oracle",
+                                    "sample": "FP64 power iteration, all 50 iterations"}
+        self.out["_p64"] = p64
+
+    def _tc(self):
+        import gen
+        import oracle
+        t = gen.rmat(20, 16, seed=4)
+        g = oracle.csr_from_tuples(t)
+        del t
+        cnt, dt = _timed(lambda: oracle.tc(g))
+        self.out["tc_s20"] = {"value": g.m / dt / 1e6, "unit": "MTEPS", "ms": 1e3 * dt, "cores": 1, "kind": "oracle",
+                              "sample": "node iterator over sorted adjacency, one count"}
+        self.out["_tc"] = cnt
+
+    def _grid(self):
+        import gen
+        import oracle
+        t = gen.grid(4096, 4096, 0.1, seed=3, wmax=1000)
+        g = oracle.csr_from_tuples(t)
+        src = gen.first_nonisolated(t)
+        del t
+        _, dt_b = _timed(lambda: oracle.bfs(g, src))
+        _, dt_s = _timed(lambda: oracle.sssp(g, src))
+        _, dt_c = _timed(lambda: oracle.cc(g))
+        self.out["grid_4096"] = {"bfs_ms": 1e3 * dt_b, "sssp_ms": 1e3 * dt_s, "cc_ms": 1e3 * dt_c, "cores": 1,
+                                 "kind": "oracle",
+                                 "sample": "queue BFS, binary-heap Dijkstra and union-find, one run each"}
+
+    def finish(self, rows):
+        """Joins the legs and adds them (and the output checks) to the GPU rows."""
+        import gen
+        import oracle
+        t = gen.rmat(14, 16, seed=1)
+        g = oracle.csr_from_tuples(t)
+        src = rows["bfs_s14"]["source"]
+        reps = 20
+        _, dt = _timed(lambda: [oracle.bfs(g, src) for _ in range(reps)])
+        rows["bfs_s14"]["cpu_baseline"] = {"value": 1e6 * dt / reps, "unit": "us per BFS", "cores": 1,
+                                           "kind": "oracle", "sample": f"{reps} queue BFS from the same source"}
+        rows["bfs_s14"]["levels_match_oracle"] = bool(np.array_equal(rows.pop("_bfs_s14_levels"),
+                                                                     oracle.bfs(g, src)))
+        for t in self.threads:
+            t.join()
+        for k in ("sssp_s22", "pagerank_s22", "tc_s20", "grid_4096"):
+            if k in self.out and k in rows:
+                rows[k]["cpu_baseline"] = dict(self.out[k], sample=self.out[k]["sample"] +
+                                               " (timed in a host thread while the GPU rows ran)")
+        if "_p64" in self.out and "_pagerank_s22_rank" in rows:
+            p64 = self.out["_p64"]
+            err = np.abs(rows.pop("_pagerank_s22_rank").astype(np.float64) - p64)
+            rows["pagerank_s22"]["error_vs_fp64_oracle"] = {
+                "l1": float(err.sum()), "max_abs": float(err.max()),
+                "max_rel": float((err / np.maximum(p64, 1e-300)).max()), "bound_l1": 1e-5}
+        if "_tc" in self.out and "tc_s20" in rows:
+            rows["tc_s20"]["count_matches_oracle"] = bool(self.out["_tc"] == rows["tc_s20"]["triangles"])
+        return rows
+
+
 def serving_bench(args):
     """Poisson stream of BFS/SSSP/PageRank (60/30/10) requests over 64
     R-MAT graphs of scales 12..20 (log-uniform, edge factor 16, weights in
@@ -513,7 +652,20 @@ def serving_bench(args):
         run_one(i)
         lat.append((time.perf_counter() - a) * 1e6)
     serial_s = time.perf_counter() - t0
-    serial = {"qps": N / serial_s, "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99))}
+    serial = {"qps": N / serial_s, "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+              "what": "service time of each request run alone, one after another"}
+    service_us = np.array(lat)
+
+    def serial_fifo(lam, nreq, seed):
+        """Latency of the one-at-a-time server under the same Poisson arrivals: a
+        FIFO queue whose service times are the measured ones, in request order."""
+        arr = np.cumsum(np.random.default_rng(seed).exponential(1.0 / lam, nreq)) * 1e6
+        done, out = 0.0, []
+        for i in range(nreq):
+            start = max(done, arr[i])
+            done = start + service_us[i % len(service_us)]
+            out.append(done - arr[i])
+        return float(np.percentile(out, 50)), float(np.percentile(out, 99))
     # served: Poisson arrivals at lam = load * serial capacity
     import threading
 
@@ -543,13 +695,25 @@ def serving_bench(args):
         return lam, st
 
     lam, st = run_served(args.serve_load, N, 6)
-    # latency against offered load (the first requests of the same stream)
+    # latency against offered load (the first requests of the same stream), served
+    # and one-at-a-time (FIFO over the measured service times, same arrivals)
     sweep = []
-    for load in (0.25, 0.5, 1.0, 2.0, 4.0):
+    for load in (0.25, 0.5, 0.75, 1.0, 1.5, 2.0, 3.0, 4.0):
         nreq = min(N, args.serve_sweep_requests)
         lam_s, st_s = run_served(load, nreq, 7)
+        s50, s99 = serial_fifo(lam_s, nreq, 7)
         sweep.append({"load": load, "offered_qps": lam_s, "qps": st_s["qps"], "p50_us": st_s["p50_us"],
-                      "p99_us": st_s["p99_us"], "requests": nreq})
+                      "p99_us": st_s["p99_us"], "serial_p50_us": s50, "serial_p99_us": s99, "requests": nreq})
+    target = args.serve_p99_target_ms * 1e3
+    ok_served = [p for p in sweep if p["p99_us"] <= target and p["qps"] >= 0.97 * p["offered_qps"]]
+    ok_serial = [p for p in sweep if p["serial_p99_us"] <= target and p["load"] < 1.0]
+    at_target = {"p99_target_ms": args.serve_p99_target_ms,
+                 "served_qps": max((p["qps"] for p in ok_served), default=None),
+                 "serial_qps": max((p["offered_qps"] for p in ok_serial), default=None),
+                 "what": "largest offered load of the sweep whose p99 stays under the target (served: "
+                         "and which is kept up with), and the same for the one-at-a-time server"}
+    if at_target["served_qps"] and at_target["serial_qps"]:
+        at_target["speedup"] = at_target["served_qps"] / at_target["serial_qps"]
     for A, _, _ in graphs:
         A.free()
     ctx.close()
@@ -557,7 +721,8 @@ def serving_bench(args):
             "offered_qps": lam, "served": {"qps": st["qps"], "p50_us": st["p50_us"], "p99_us": st["p99_us"],
                                            "batches": st["batches"], "bfs_batched": st["batched_bfs"],
                                            "slots": args.serve_slots},
-            "serial": serial, "speedup_qps": st["qps"] / serial["qps"], "load_sweep": sweep}
+            "serial": serial, "speedup_qps": st["qps"] / serial["qps"], "at_p99_target": at_target,
+            "load_sweep": sweep}
 
 
 def run_profile(args):
@@ -635,6 +800,8 @@ def main():
     ap.add_argument("--serve-load", type=float, default=2.0, help="offered load as a multiple of serial capacity")
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-window-us", type=int, default=300)
+    ap.add_argument("--serve-p99-target-ms", type=float, default=25.0,
+                    help="latency target of the queries/s-at-p99 figure")
     ap.add_argument("--serve-sweep-requests", type=int, default=800,
                     help="requests per point of the latency-vs-load sweep")
     ap.add_argument("--profile", choices=["bfs", "pr", "sssp", "msbfs", "tc", "prd", "fastsv", "gridbfs"], default=None,

@@ -126,6 +126,10 @@ gb_info gb_init(int device, gb_context **ctx);
 /* Orders all later work on `stream` (a cudaStream_t, e.g. torch's current
  * stream); NULL selects the legacy default stream. The stream is borrowed. */
 gb_info gb_context_set_stream(gb_context *ctx, void *stream);
+/* Waits for the context stream. Returns GB_TIMEOUT (once) if a BFS that
+ * was launched without waiting for it (gb_bfs with GB_DEVICE outputs and no
+ * stats) ran out of a bounded device wait since the last such report; its
+ * outputs are then undefined. */
 gb_info gb_context_synchronize(gb_context *ctx);
 /* Bytes held by the context's pool and its high-water mark. */
 gb_info gb_context_pool_stats(gb_context *ctx, uint64_t *held_bytes, uint64_t *peak_bytes);
@@ -316,7 +320,11 @@ typedef struct {
  * parents != NULL, a BFS-tree parent (parents[src] = src, unreachable -1).
  * A must be square and symmetric-or-CSC-built. levels/parents have nrows
  * entries in `mem`. stats may be NULL. desc: GB_DIRECTION, GB_SWITCH_BETA,
- * GB_SCHEDULE (a device that cannot co-schedule a cluster runs GB_SCHED_GRID). */
+ * GB_SCHEDULE (a device that cannot co-schedule a cluster runs GB_SCHED_GRID).
+ * With GB_HOST outputs or stats the call waits and returns GB_TIMEOUT if a
+ * bounded device wait ran out; with GB_DEVICE outputs and no stats it
+ * returns without waiting, and such a timeout is reported by the next
+ * gb_context_synchronize (the outputs are then undefined). */
 gb_info gb_bfs(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *levels, int32_t *parents,
                gb_mem mem, const gb_desc *desc, gb_bfs_stats *stats);
 /* k independent direction-optimised BFS runs (Algorithm 1, Section 7.1),
@@ -357,19 +365,24 @@ gb_info gb_bfs_autotune(gb_context *ctx, gb_matrix *A, const uint32_t *srcs, uin
  * pointers again for a symmetric graph, or NULL for push-only), and the
  * outputs levels[n] and parents[n] (parents may be NULL). colidx and rowidx
  * must start on a 16-byte boundary and stay readable for 16 bytes past
- * their last entry. All scratch lives in one array built into the library
- * (about 8.5 MB, enough for n <= GB_NOALLOC_MAX_VERTICES); each GPU that
- * loads the library holds it until the process exits. n above that limit:
- * GB_INVALID_VALUE. The first call on a device looks up the array's device
- * address (with that device current); make that first call before any
- * stream capture. Work is enqueued on `stream` (a cudaStream_t; NULL = the
- * legacy default stream) and the call returns without waiting. Every call
- * shares the one array and the array keeps the last call's contents:
- * calls whose work overlaps on the GPU (e.g. on different streams) race, so
- * order them on one stream or with events. */
+ * their last entry. status (a device int32, 4-byte aligned, may be NULL)
+ * receives the kernel's exit status when it finishes: 0, or GB_TIMEOUT if a
+ * bounded device wait ran out, in which case levels and parents are
+ * undefined; with status NULL such a timeout cannot be observed. All
+ * scratch lives in one array built into the library (about 8.5 MB, enough
+ * for n <= GB_NOALLOC_MAX_VERTICES); each GPU that loads the library holds
+ * it until the process exits. n above that limit: GB_INVALID_VALUE. The
+ * first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture. Work is
+ * enqueued on `stream` (a cudaStream_t; NULL = the legacy default stream)
+ * and the call returns without waiting. Every call shares the one array and
+ * the array keeps the last call's contents: calls whose work overlaps on
+ * the GPU (e.g. on different streams) race, so order them on one stream or
+ * with events. */
 #define GB_NOALLOC_MAX_VERTICES 262144u
 gb_info gb_bfs_noalloc(const uint32_t *rowptr, const uint32_t *colidx, const uint32_t *colptr, const uint32_t *rowidx,
-                       uint32_t n, uint64_t nnz, uint32_t src, int32_t *levels, int32_t *parents, void *stream);
+                       uint32_t n, uint64_t nnz, uint32_t src, int32_t *levels, int32_t *parents, int32_t *status,
+                       void *stream);
 /* Multi-source BFS as Boolean SpMM over 64-bit bit-packed frontiers
  * (Section 3.3 multi-nodeset traversal; Section 9 matrix direction
  * optimisation): k >= 1 sources, levels is k x nrows (row q = source q).
@@ -384,9 +397,15 @@ gb_info gb_bfs_multi(gb_context *ctx, const gb_matrix *A, const uint32_t *srcs, 
  * desc: GB_DIRECTION, GB_SWITCH_BETA, GB_SCHEDULE (GB_SCHED_CLUSTER relaxes
  * by push inside one thread-block cluster; GB_SCHED_AUTO and GB_SCHED_GRID
  * use the persistent grid kernel, which is faster wherever the frontiers of
- * improved vertices are large, as on the weighted 4096^2 grid). */
+ * improved vertices are large, as on the weighted 4096^2 grid). stats (may
+ * be NULL) receives, as for gb_bfs, the iterations (depth), push and pull
+ * iterations, frontier out-edges, the per-iteration trace and alg_bytes:
+ * 4 n value writes, per push iteration 8 per frontier vertex and 8 per
+ * frontier out-edge (index and weight), per pull iteration 4 (n + 1) row
+ * offsets + n / 8 frontier bits + 4 per stored entry (indices) + 4 per
+ * frontier out-edge (weights), and 4 per improved value. */
 gb_info gb_sssp(gb_context *ctx, const gb_matrix *A, uint32_t src, uint32_t *dist, gb_mem mem,
-                const gb_desc *desc, uint32_t *iterations);
+                const gb_desc *desc, uint32_t *iterations, gb_bfs_stats *stats);
 /* PageRank (Section 7.3), pull SpMV in FP32 with FP32 accumulation:
  * p0 = 1/n; p' = (1-damping)/n + damping * (sum_{j in N(i)} p(j)/deg(j)
  * + dangling/n), exactly `iters` iterations; the per-iteration L1 residual
@@ -402,13 +421,21 @@ gb_info gb_pagerank(gb_context *ctx, const gb_matrix *A, float damping, uint32_t
  * vertex is active or after max_iters iterations. rank[nrows] in `mem`;
  * iterations, residuals[max_iters] (L1 change per iteration, FP64) and
  * active[max_iters] (vertices updated per iteration) are host pointers and
- * may be NULL. Results are bit-reproducible. */
+ * may be NULL. Results are bit-reproducible. eps must be at least
+ * GB_PAGERANK_DELTA_MIN_EPS (GB_INVALID_VALUE below it, and for NaN): the
+ * FP32 values carry rounding of about 1e-6 relative after the summation of
+ * long rows, so a smaller threshold would be decided by that rounding
+ * rather than by eps. A negative eps never freezes a vertex (max_iters
+ * plain iterations). */
+#define GB_PAGERANK_DELTA_MIN_EPS 1e-5f
 gb_info gb_pagerank_delta(gb_context *ctx, const gb_matrix *A, float damping, float eps, uint32_t max_iters,
                           float *rank, gb_mem mem, uint32_t *iterations, double *residuals, uint32_t *active);
 /* Connected components (Section 7.4) by min-label propagation
  * (min.second mxv to a fixed point): labels[v] = smallest vertex id in v's
- * component. iterations may be NULL. */
-gb_info gb_cc(gb_context *ctx, const gb_matrix *A, uint32_t *labels, gb_mem mem, uint32_t *iterations);
+ * component. iterations and stats (as for gb_sssp, without weights) may be
+ * NULL. */
+gb_info gb_cc(gb_context *ctx, const gb_matrix *A, uint32_t *labels, gb_mem mem, uint32_t *iterations,
+              gb_bfs_stats *stats);
 /* Connected components by FastSV (Section 7.4: the paper's CC algorithm):
  * per iteration mngf = A min.second gf, stochastic hooking
  * f(f(u)) = min(f(f(u)), mngf(u)), aggressive hooking and shortcut

@@ -181,6 +181,27 @@ def pagerank_delta(g: CSR, alpha: float = 0.85, eps: float = 1e-6, max_iters: in
     return p, int(it), act[:it]
 
 
+def pagerank_residual(g: CSR, x, alpha: float = 0.85) -> float:
+    """L1 size of one more PageRank step from x, ||T(x) - x||_1, in FP64,
+    with T the recurrence of reading 5 (Section 7.3): T(x)(v) = (1-a)/n +
+    a * (sum over edges u -> v of x(u)/outdeg(u) + D(x)/n), D(x) the sum of x
+    over vertices without out-edges. g's rows are out-edges (for a
+    symmetric g they are the in-edges too, and the formula is the same).
+    T is an a-contraction in L1 (its linear part is column-stochastic), so
+    ||x - p*||_1 <= r(x) / (1 - a) for the fixed point p*: how far any
+    approximate PageRank vector is from p* is bounded by something computed
+    from the vector alone."""
+    x = np.asarray(x, dtype=np.float64)
+    n = g.n
+    outdeg = np.diff(g.rowptr).astype(np.int64)
+    share = np.where(outdeg > 0, x / np.maximum(outdeg, 1), 0.0)
+    u = np.repeat(np.arange(n, dtype=np.int64), outdeg)
+    pulled = np.bincount(g.colidx.astype(np.int64), weights=share[u], minlength=n)
+    dangling = x[outdeg == 0].sum()
+    tx = (1.0 - alpha) / n + alpha * (pulled + dangling / n)
+    return float(np.abs(tx - x).sum())
+
+
 def cc(g: CSR) -> np.ndarray:
     """uint32 component label = smallest vertex id of the component."""
     lab = np.empty(g.n, dtype=np.uint32)

@@ -126,11 +126,11 @@ _SIGS = {
     "gb_reduce_vector": [_P, _I, _I, _P], "gb_reduce_matrix": [_P, _I, _I, _P],
     "gb_reduce_rows": [_P, _P, _I, _I, _P, _P],
     "gb_bfs": [_P, _P, _U32, _P, _P, _I, _P, _P],
-    "gb_bfs_noalloc": [_P, _P, _P, _P, _U32, _U64, _U32, _P, _P, _P],
+    "gb_bfs_noalloc": [_P, _P, _P, _P, _U32, _U64, _U32, _P, _P, _P, _P],
     "gb_bfs_autotune": [_P, _P, _P, _U32, _P, _P], "gb_bfs_multi": [_P, _P, _P, _U32, _P, _I, _P, _P],
     "gb_bfs_batch": [_P, _P, _P, _U32, _P, _P, _I, _P],
-    "gb_sssp": [_P, _P, _U32, _P, _I, _P, _P], "gb_pagerank": [_P, _P, ctypes.c_float, _U32, _P, _P, _I],
-    "gb_cc": [_P, _P, _P, _I, _P], "gb_tc": [_P, _P, _P, _P],
+    "gb_sssp": [_P, _P, _U32, _P, _I, _P, _P, _P], "gb_pagerank": [_P, _P, ctypes.c_float, _U32, _P, _P, _I],
+    "gb_cc": [_P, _P, _P, _I, _P, _P], "gb_tc": [_P, _P, _P, _P],
     "gb_cc_fastsv": [_P, _P, _P, _I, _P],
     "gb_pagerank_delta": [_P, _P, ctypes.c_float, ctypes.c_float, _U32, _P, _I, _P, _P, _P],
     "gb_server_create": [_PP, _P, _P], "gb_server_add_graph": [_P, _P, _P], "gb_server_submit": [_P, _P, _P],
@@ -562,19 +562,33 @@ def bfs_autotune(ctx, A, srcs):
     return b.value, ms.value
 
 
-NOALLOC_MAX_VERTICES = 262144
+def _header_define(name: str) -> int:
+    """Value of a numeric #define of include/gbx.h (the one place a limit of
+    the C ABI is stated)."""
+    import re
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "gbx.h")
+    m = re.search(r"#define\s+" + name + r"\s+(\d+)u?", open(hdr).read())
+    if not m:
+        raise RuntimeError(f"{name} is not defined in {hdr}")
+    return int(m.group(1))
 
 
-def bfs_noalloc(rowptr, colidx, colptr, rowidx, n, nnz, src, levels, parents=None, stream=None):
+NOALLOC_MAX_VERTICES = _header_define("GB_NOALLOC_MAX_VERTICES")
+
+
+def bfs_noalloc(rowptr, colidx, colptr, rowidx, n, nnz, src, levels, parents=None, status=None, stream=None):
     """gb_bfs_noalloc: BFS with the library's built-in scratch (no device
     allocation on the call path). All arrays are CUDA tensors; colidx and
     rowidx must be 16-byte aligned and readable 16 bytes past their end.
+    status: an int32 CUDA tensor of one element (or None) that receives the
+    kernel's exit status (0, or GB_TIMEOUT when a bounded wait ran out).
     stream: a torch.cuda.Stream (default: the current stream)."""
     torch = _torch()
     if stream is None:
         stream = torch.cuda.current_stream()
-    ptrs = [x.data_ptr() if x is not None else None for x in (rowptr, colidx, colptr, rowidx, levels, parents)]
-    check(lib().gb_bfs_noalloc(ptrs[0], ptrs[1], ptrs[2], ptrs[3], n, nnz, src, ptrs[4], ptrs[5],
+    ptrs = [x.data_ptr() if x is not None else None
+            for x in (rowptr, colidx, colptr, rowidx, levels, parents, status)]
+    check(lib().gb_bfs_noalloc(ptrs[0], ptrs[1], ptrs[2], ptrs[3], n, nnz, src, ptrs[4], ptrs[5], ptrs[6],
                                ctypes.c_void_p(stream.cuda_stream)))
     return levels, parents
 
@@ -614,15 +628,18 @@ def bfs_multi(ctx, A, srcs, levels=None, desc=None, stats=True):
     return levels, (st.as_dict() if stats else None)
 
 
-def sssp(ctx, A, src, dist=None, desc=None):
+def sssp(ctx, A, src, dist=None, desc=None, stats=False):
+    """SSSP; returns (dist, iterations), or (dist, iterations, stats-dict)
+    with stats=True."""
     n = A.nrows
     if dist is None:
         torch = _torch()
         dist = torch.empty(n, dtype=torch.int32, device=f"cuda:{ctx.device}")
     pd, md = _out_mem(dist)
     it = ctypes.c_uint32()
-    check(lib().gb_sssp(ctx.h, A.h, src, pd, md, _h(desc), ctypes.byref(it)))
-    return dist, it.value
+    st = BfsStats()
+    check(lib().gb_sssp(ctx.h, A.h, src, pd, md, _h(desc), ctypes.byref(it), ctypes.byref(st) if stats else None))
+    return (dist, it.value, st.as_dict()) if stats else (dist, it.value)
 
 
 def pagerank(ctx, A, damping=0.85, iters=50, rank=None, residuals=True):
@@ -636,7 +653,7 @@ def pagerank(ctx, A, damping=0.85, iters=50, rank=None, residuals=True):
     return rank, (res[:iters] if res is not None else None)
 
 
-def pagerank_delta(ctx, A, damping=0.85, eps=1e-6, max_iters=100, rank=None):
+def pagerank_delta(ctx, A, damping=0.85, eps=1e-4, max_iters=100, rank=None):
     """Adaptive PageRank (PageRankDelta). Returns (rank, iterations,
     residuals[iterations], active[iterations])."""
     n = A.nrows
@@ -672,7 +689,7 @@ def cc(ctx, A, labels=None):
         labels = torch.empty(n, dtype=torch.int32, device=f"cuda:{ctx.device}")
     pl, ml = _out_mem(labels)
     it = ctypes.c_uint32()
-    check(lib().gb_cc(ctx.h, A.h, pl, ml, ctypes.byref(it)))
+    check(lib().gb_cc(ctx.h, A.h, pl, ml, ctypes.byref(it), None))
     return labels, it.value
 
 

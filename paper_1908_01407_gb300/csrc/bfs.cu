@@ -90,6 +90,135 @@ static __device__ __forceinline__ void flush_candidates(const uint32_t *sbuf, ui
     __syncwarp();
 }
 
+// Claims the found vertices of one lane slot across the warp: visited and
+// next-frontier bits with one atomicOr per run of lanes in the same word,
+// then level, parent and the out-degree count.
+static __device__ __forceinline__ void claim_found(const BfsArgs &a, uint32_t *Fn, int d, bool f, uint32_t v,
+                                                   uint32_t par, uint32_t dego, uint32_t &mycnt, uint32_t &mydeg) {
+    const uint32_t NONE = 0xffffffffu;
+    if (!__ballot_sync(0xffffffffu, f)) return;
+    uint32_t key = f ? (v >> 5) : NONE;
+    uint32_t bits = f ? 1u << (v & 31) : 0u;
+    if (run_or_head(key, bits) && f) {
+        atomicOr(&a.visited[key], bits);
+        atomicOr(&Fn[key], bits);
+    }
+    if (f) {
+        a.levels[v] = d + 1;
+        if (a.parents) a.parents[v] = (int32_t)par;
+        if (dego == NONE) dego = __ldg(&a.rp_out[v + 1]) - __ldg(&a.rp_out[v]);
+        mydeg += dego;
+        mycnt += 1;
+    }
+}
+
+// Adds this lane's candidate (when keep) to the warp's staged survivors, the
+// candidates a later pull walks; flushes first when they would not fit.
+static __device__ __forceinline__ void keep_candidate(uint32_t *sbuf, uint32_t &staged, uint32_t *Lout,
+                                                      unsigned int *lout_cnt, bool keep, uint32_t c) {
+    const uint32_t km = __ballot_sync(0xffffffffu, keep);
+    if (!km) return;
+    if (staged + __popc(km) > (uint32_t)STAGE_CAP) flush_candidates(sbuf, staged, Lout, lout_cnt);
+    if (keep) sbuf[staged + __popc(km & dev::lanemask_lt())] = c;
+    staged += __popc(km);
+    __syncwarp();
+}
+
+// Scans the rows of the last k (<= 32) entries of the warp's miss queue,
+// one per lane: in aligned 16-byte chunks for PULL_ROUNDS chunks, then
+// warp-cooperatively (32 entries per step), stopping at the first
+// in-neighbour on the frontier. A queued row had no frontier vertex in its
+// head: with the live table the head is not a row prefix, so the whole row
+// is scanned (its head entries again, harmlessly); without it the scan
+// starts after the four head entries.
+static __device__ void scan_misses(const BfsArgs &a, MissQueue &mq, uint32_t &nq, uint32_t k, const uint32_t *F,
+                                   uint32_t *Fn, int d, bool table, uint32_t *sbuf, uint32_t &staged,
+                                   uint32_t *Lout, unsigned int *lout_cnt, unsigned long long &exam,
+                                   unsigned long long &lefte, uint32_t &mycnt, uint32_t &mydeg) {
+    const uint32_t full = 0xffffffffu;
+    const uint32_t NONE = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint4 *ci4 = reinterpret_cast<const uint4 *>(a.ci_in);
+    const uint32_t q0 = nq - k;
+    uint32_t v = NONE, c = 0, len = 0, dego = 0;
+    if ((uint32_t)lane < k) {
+        v = mq.v[warp][q0 + lane];
+        c = mq.c[warp][q0 + lane];
+        len = mq.len[warp][q0 + lane];
+        dego = mq.deg[warp][q0 + lane];
+    }
+    __syncwarp();
+    nq = q0;
+    bool found = false;
+    uint32_t par = 0, p = 0, e = 0;
+    if (v != NONE) {
+        const uint32_t b = __ldg(&a.rp_in[v]);
+        p = table ? b : b + 4;
+        e = b + len;
+    }
+#pragma unroll 1
+    for (int r = 0; r < PULL_ROUNDS; ++r) {
+        const bool pend = p < e;
+        if (!__any_sync(full, pend)) break;
+        uint4 cw = make_uint4(0, 0, 0, 0);
+        if (pend) cw = ld_stream(&ci4[p >> 2]);
+        const uint32_t q = p & ~3u;
+        const uint32_t cc[4] = {cw.x, cw.y, cw.z, cw.w};
+        uint32_t f4[4];
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) {
+            const bool in = pend && q + k2 >= p && q + k2 < e;
+            f4[k2] = in ? ldcg(&F[cc[k2] >> 5]) : 0u;
+        }
+        if (pend) {
+            uint32_t stop = q + 4 < e ? q + 4 : e;
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) {
+                const uint32_t pos = q + k2;
+                if (!found && pos >= p && pos < e && ((f4[k2] >> (cc[k2] & 31)) & 1u)) {
+                    found = true;
+                    par = cc[k2];
+                    stop = pos + 1;
+                }
+            }
+            exam += stop - p;
+            p = found ? e : q + 4;
+        }
+    }
+    uint32_t coop = __ballot_sync(full, !found && p < e);
+    while (coop) {
+        const int l = __ffs(coop) - 1;
+        coop &= coop - 1;
+        const uint32_t pb = __shfl_sync(full, p, l);
+        const uint32_t pe = __shfl_sync(full, e, l);
+        bool got = false;
+        uint32_t gpar = 0;
+        for (uint32_t x0 = pb; x0 < pe; x0 += 32) {
+            const uint32_t x = x0 + lane;
+            uint32_t u = 0;
+            bool hit = false;
+            if (x < pe) {
+                u = ld_stream(&a.ci_in[x]);
+                hit = (ldcg(&F[u >> 5]) >> (u & 31)) & 1u;
+            }
+            const uint32_t hb = __ballot_sync(full, hit);
+            if (hb) {
+                const int f = __ffs(hb) - 1;
+                gpar = __shfl_sync(full, u, f);
+                got = true;
+                if (lane == 0) exam += (x0 - pb) + f + 1;
+                break;
+            }
+            if (lane == 0) exam += (pe - x0 < 32 ? pe - x0 : 32);
+        }
+        if (lane == l && got) { found = true; par = gpar; }
+    }
+    claim_found(a, Fn, d, found, v, par, dego, mycnt, mydeg);
+    const bool keep = v != NONE && !found;
+    if (keep) lefte += len;
+    keep_candidate(sbuf, staged, Lout, lout_cnt, keep, c);
+}
+
 // Pull over a list of candidates: for the first pull of a traversal every
 // vertex with an in-edge, afterwards the candidates the previous pull left
 // unvisited (a push may have claimed some since; their visited bit skips
@@ -102,17 +231,17 @@ static __device__ __forceinline__ void flush_candidates(const uint32_t *sbuf, ui
 // entries are then loaded together, the other two only where those missed
 // (two dependent memory steps for almost every vertex). Without the table a
 // candidate is a vertex and its head is the first four entries of its row,
-// read through the row pointers. Rows longer than four whose head has no
-// frontier vertex are scanned in aligned 16-byte chunks for PULL_ROUNDS
-// chunks, then warp-cooperatively (32 neighbours per step), with early exit.
-// Warps take groups of PULL_WPW * 32 consecutive candidates, each lane
-// PULL_WPW in flight. Found vertices set their visited and next-frontier
-// bits (one atomicOr per run of lanes in the same bitmap word); the others
-// are collected per warp in shared memory and appended to the next list
-// STAGE_CAP at a time. Pull writes the next frontier as a bitmap and only
-// counts it (vertices, out-edges); the list form is built when a push needs
-// it. It also counts the unvisited candidates it walked and sums the
-// in-degrees of those it leaves (what a later pull over them reads at most).
+// read through the row pointers. Warps take groups of PULL_WPW * 32
+// consecutive candidates, each lane PULL_WPW in flight. A candidate whose
+// head has no frontier vertex and whose row is longer than four goes to the
+// warp's miss queue, scanned 32 at a time (scan_misses). Found vertices set
+// their visited and next-frontier bits (one atomicOr per run of lanes in the
+// same bitmap word); the others are collected per warp in shared memory and
+// appended to the next list STAGE_CAP at a time. Pull writes the next
+// frontier as a bitmap and only counts it (vertices, out-edges); the list
+// form is built when a push needs it. It also counts the unvisited
+// candidates it walked and sums the in-degrees of those it leaves (what a
+// later pull over them reads at most).
 __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Lin, uint32_t nin, uint32_t *Lout,
                            unsigned int *lout_cnt, unsigned long long *examined, uint32_t *cnt_out,
                            uint32_t *deg_out, uint32_t *act_out, unsigned long long *left_edges) {
@@ -121,7 +250,6 @@ __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Li
     const uint32_t full = 0xffffffffu;
     const uint32_t NONE = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint4 *ci4 = reinterpret_cast<const uint4 *>(a.ci_in);
     const bool table = a.live_head != nullptr;
     constexpr uint32_t GROUP = PULL_WPW * 32;
     const uint32_t ngroups = (uint32_t)(((uint64_t)nin + GROUP - 1) / GROUP);
@@ -130,10 +258,13 @@ __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Li
     uint32_t mycnt = 0, mydeg = 0, myact = 0;
     uint32_t *sbuf = sm.stage.v[warp];   // this warp's candidates for the next list
     uint32_t staged = 0;
+    uint32_t nq = 0;                     // entries in this warp's miss queue
+    MissQueue &mq = sm.miss;
     static_assert(GROUP <= STAGE_CAP, "a group's candidates fit the staging row");
+    static_assert(31 + GROUP <= MISS_CAP, "a group's misses fit the queue");
     for (uint32_t g = blockIdx.x * WARPS + warp; g < ngroups; g += nwarps) {
-        uint32_t c[PULL_WPW], v[PULL_WPW], h[PULL_WPW][4], len[PULL_WPW], dego[PULL_WPW], b[PULL_WPW];
-        uint32_t par[PULL_WPW], p[PULL_WPW], e[PULL_WPW];
+        uint32_t c[PULL_WPW], v[PULL_WPW], h[PULL_WPW][4], len[PULL_WPW], dego[PULL_WPW];
+        uint32_t par[PULL_WPW];
         bool act[PULL_WPW], found[PULL_WPW];
 #pragma unroll
         for (int j = 0; j < PULL_WPW; ++j) {
@@ -144,7 +275,7 @@ __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Li
 #pragma unroll
         for (int j = 0; j < PULL_WPW; ++j) {
             v[j] = NONE;
-            len[j] = dego[j] = b[j] = 0;
+            len[j] = dego[j] = 0;
             h[j][0] = h[j][1] = h[j][2] = h[j][3] = NONE;
             if (c[j] != NONE) {
                 if (table) {
@@ -152,20 +283,17 @@ __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Li
                     const uint4 hh = ld_stream(&a.live_head[c[j]]);
                     h[j][0] = hh.x; h[j][1] = hh.y; h[j][2] = hh.z; h[j][3] = hh.w;
                     len[j] = ld_stream(&a.live_len[c[j]]);
-                    dego[j] = ld_stream(&a.live_deg[c[j]]);
+                    dego[j] = a.csr_is_csc ? len[j] : ld_stream(&a.live_deg[c[j]]);
                 } else {
                     v[j] = c[j];
-                    b[j] = __ldg(&a.rp_in[v[j]]);
-                    len[j] = __ldg(&a.rp_in[v[j] + 1]) - b[j];
+                    const uint32_t b = __ldg(&a.rp_in[v[j]]);
+                    len[j] = __ldg(&a.rp_in[v[j] + 1]) - b;
+                    dego[j] = a.csr_is_csc ? len[j] : NONE;   // read from the CSR once found
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if ((uint32_t)k < len[j]) h[j][k] = ld_stream(&a.ci_in[b + k]);
                 }
             }
-        }
-        if (!table) {
-#pragma unroll
-            for (int j = 0; j < PULL_WPW; ++j)
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if ((uint32_t)k < len[j]) h[j][k] = ld_stream(&a.ci_in[b[j] + k]);
         }
         // the visited word and the frontier words of the first two head
         // entries, together; the other two only where those did not hit
@@ -176,7 +304,6 @@ __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Li
 #pragma unroll
             for (int k = 0; k < 2; ++k) fw[j][k] = h[j][k] != NONE ? ldcg(&F[h[j][k] >> 5]) : 0u;
         }
-        bool more = false;
 #pragma unroll
         for (int j = 0; j < PULL_WPW; ++j) {
             act[j] = v[j] != NONE && !((vw[j] >> (v[j] & 31)) & 1u);
@@ -210,135 +337,31 @@ __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Li
                 ex = par[j] == h[j][0] ? 1 : 2;
             }
             if (act[j]) { exam += ex; ++myact; }
-            p[j] = e[j] = 0;
-            more |= act[j] && !found[j] && len[j] > 4;
-        }
-        // rows longer than four with no frontier vertex in their head
-        if (__any_sync(full, more)) {
-#pragma unroll
-            for (int j = 0; j < PULL_WPW; ++j) {
-                if (act[j] && !found[j] && len[j] > 4) {
-                    // the table's head is not a row prefix: scan the whole row
-                    // (its four head entries again, harmlessly); without the
-                    // table the head is the first four entries
-                    if (table) b[j] = __ldg(&a.rp_in[v[j]]);
-                    p[j] = table ? b[j] : b[j] + 4;
-                    e[j] = b[j] + len[j];
-                }
-            }
-#pragma unroll 1
-            for (int r = 0; r < PULL_ROUNDS; ++r) {
-                uint4 cw[PULL_WPW];
-                bool pend[PULL_WPW];
-#pragma unroll
-                for (int j = 0; j < PULL_WPW; ++j) {
-                    pend[j] = !found[j] && p[j] < e[j];
-                    if (pend[j]) cw[j] = ld_stream(&ci4[p[j] >> 2]);
-                }
-                uint32_t f4[PULL_WPW][4];
-#pragma unroll
-                for (int j = 0; j < PULL_WPW; ++j) {
-                    uint32_t q = p[j] & ~3u;
-                    uint32_t cc[4] = {cw[j].x, cw[j].y, cw[j].z, cw[j].w};
-#pragma unroll
-                    for (int k2 = 0; k2 < 4; ++k2) {
-                        bool in = pend[j] && q + k2 >= p[j] && q + k2 < e[j];
-                        f4[j][k2] = in ? ldcg(&F[cc[k2] >> 5]) : 0u;
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < PULL_WPW; ++j) {
-                    if (!pend[j]) continue;
-                    uint32_t q = p[j] & ~3u;
-                    uint32_t cc[4] = {cw[j].x, cw[j].y, cw[j].z, cw[j].w};
-                    uint32_t stop = q + 4 < e[j] ? q + 4 : e[j];
-#pragma unroll
-                    for (int k2 = 0; k2 < 4; ++k2) {
-                        uint32_t pos = q + k2;
-                        if (!found[j] && pos >= p[j] && pos < e[j] && ((f4[j][k2] >> (cc[k2] & 31)) & 1u)) {
-                            found[j] = true;
-                            par[j] = cc[k2];
-                            stop = pos + 1;
-                        }
-                    }
-                    exam += stop - p[j];
-                    p[j] = found[j] ? stop : q + 4;
-                }
-                bool any = false;
-#pragma unroll
-                for (int j = 0; j < PULL_WPW; ++j) any |= !found[j] && p[j] < e[j];
-                if (!__any_sync(full, any)) break;
-            }
-#pragma unroll
-            for (int j = 0; j < PULL_WPW; ++j) {
-                uint32_t coop = __ballot_sync(full, !found[j] && p[j] < e[j]);
-                while (coop) {
-                    int l = __ffs(coop) - 1;
-                    coop &= coop - 1;
-                    uint32_t pb = __shfl_sync(full, p[j], l);
-                    uint32_t pe = __shfl_sync(full, e[j], l);
-                    bool got = false;
-                    uint32_t gpar = 0;
-                    for (uint32_t q0 = pb; q0 < pe; q0 += 32) {
-                        uint32_t q = q0 + lane;
-                        uint32_t u = 0;
-                        bool hit = false;
-                        if (q < pe) {
-                            u = ld_stream(&a.ci_in[q]);
-                            hit = (ldcg(&F[u >> 5]) >> (u & 31)) & 1u;
-                        }
-                        uint32_t hb = __ballot_sync(full, hit);
-                        if (hb) {
-                            int f = __ffs(hb) - 1;
-                            gpar = __shfl_sync(full, u, f);
-                            got = true;
-                            if (lane == 0) exam += (q0 - pb) + f + 1;
-                            break;
-                        }
-                        if (lane == 0) exam += (pe - q0 < 32 ? pe - q0 : 32);
-                    }
-                    if (lane == l && got) { found[j] = true; par[j] = gpar; }
-                }
-            }
         }
 #pragma unroll
         for (int j = 0; j < PULL_WPW; ++j) {
-            const bool f = found[j];
-            if (__ballot_sync(full, f)) {
-                uint32_t key = f ? (v[j] >> 5) : NONE;
-                uint32_t bits = f ? 1u << (v[j] & 31) : 0u;
-                if (run_or_head(key, bits) && f) {
-                    atomicOr(&a.visited[key], bits);
-                    atomicOr(&Fn[key], bits);
-                }
-                if (f) {
-                    a.levels[v[j]] = d + 1;
-                    if (a.parents) a.parents[v[j]] = (int32_t)par[j];
-                    if (!table)
-                        dego[j] = a.csr_is_csc ? len[j] : __ldg(&a.rp_out[v[j] + 1]) - __ldg(&a.rp_out[v[j]]);
-                    mydeg += dego[j];
-                    mycnt += 1;
-                }
+            claim_found(a, Fn, d, found[j], v[j], par[j], dego[j], mycnt, mydeg);
+            // rows longer than four whose head missed: to the miss queue
+            const bool miss = act[j] && !found[j] && len[j] > 4;
+            const uint32_t mm = __ballot_sync(full, miss);
+            if (miss) {
+                const uint32_t at = nq + __popc(mm & dev::lanemask_lt());
+                mq.v[warp][at] = v[j];
+                mq.c[warp][at] = c[j];
+                mq.len[warp][at] = len[j];
+                mq.deg[warp][at] = dego[j];
             }
-        }
-        // candidates that stay unvisited (and can still be reached) go to the next list
-        uint32_t km[PULL_WPW], nkeep = 0;
-#pragma unroll
-        for (int j = 0; j < PULL_WPW; ++j) {
-            km[j] = __ballot_sync(full, act[j] && !found[j] && len[j] > 0);
-            nkeep += __popc(km[j]);
-        }
-        if (staged + nkeep > (uint32_t)STAGE_CAP) flush_candidates(sbuf, staged, Lout, lout_cnt);
-#pragma unroll
-        for (int j = 0; j < PULL_WPW; ++j) {
-            if ((km[j] >> lane) & 1u) {
-                sbuf[staged + __popc(km[j] & dev::lanemask_lt())] = c[j];
-                lefte += len[j];
-            }
-            staged += __popc(km[j]);
+            nq += __popc(mm);
+            // rows of at most four entries are done: unvisited ones stay candidates
+            const bool keep = act[j] && !found[j] && len[j] > 0 && len[j] <= 4;
+            if (keep) lefte += len[j];
+            keep_candidate(sbuf, staged, Lout, lout_cnt, keep, c[j]);
         }
         __syncwarp();
+        while (nq >= 32)
+            scan_misses(a, mq, nq, 32, F, Fn, d, table, sbuf, staged, Lout, lout_cnt, exam, lefte, mycnt, mydeg);
     }
+    if (nq) scan_misses(a, mq, nq, nq, F, Fn, d, table, sbuf, staged, Lout, lout_cnt, exam, lefte, mycnt, mydeg);
     flush_candidates(sbuf, staged, Lout, lout_cnt);
     *examined += exam;
     *cnt_out += mycnt;
@@ -403,7 +426,14 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
         __syncthreads();
         if (threadIdx.x == 0) res->t_entry = t_entry;
     }
-    bool ok = dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns);
+    bool ok;
+    if (a.withhold && blockIdx.x == 0 && gridDim.x > 1) {
+        // failure-path test: this block never arrives, so the bounded wait of
+        // the others runs out; it waits (bounded too) until they record it
+        ok = dev::wait_for_error(&st->err, 2 * a.timeout_ns);
+    } else {
+        ok = dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns);
+    }
     const uint64_t t_start = dev::globaltimer_ns();
     uint64_t reached = 0;
     // previous level's numbers for the algorithmic byte count
@@ -574,6 +604,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
             const int e = ld_relaxed_gpu_int_(&st->err);
             res->err = e;
             if (e && a.err_sticky) atomicMax(a.err_sticky, e);
+            if (a.status_out) *a.status_out = e;
             res->t_exit = dev::globaltimer_ns();
             st->err = 0;
             st->bar.count = 0;
@@ -671,6 +702,20 @@ static gb_info bfs_cluster_run(gb_context *ctx, const gb_matrix *A, uint32_t src
                               err_sticky);
 }
 
+// Failure-path test hook: when the environment variable
+// GBX_TEST_WITHHOLD_BARRIER_US is set to a positive number of microseconds,
+// BFS launches bound each grid-barrier wait by that much and block 0
+// withholds its arrival at the first barrier, so the wait of the other
+// blocks runs out (no fault, no hang) and the launch ends with GB_TIMEOUT.
+static uint64_t test_withhold_ns() {
+    const char *e = getenv("GBX_TEST_WITHHOLD_BARRIER_US");
+    if (!e || !*e) return 0;
+    long long us = atoll(e);
+    if (us <= 0) return 0;
+    if (us > 1000000) us = 1000000;
+    return (uint64_t)us * 1000ull;
+}
+
 gb_info bfs_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *levels, int32_t *parents,
                    const gb_desc *desc, BfsWorkspace *w, int grid_override, int *err_sticky = nullptr) {
     BfsArgs a;
@@ -704,7 +749,14 @@ gb_info bfs_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *l
     a.st = w->st;
     a.timeout_ns = 4000000000ull;
     a.total_limit_ns = 120000000000ull;
-    a.err_sticky = err_sticky;
+    // without a caller's word, a timeout is kept for gb_context_synchronize
+    a.err_sticky = err_sticky ? err_sticky : &w->st->sticky;
+    a.status_out = nullptr;
+    a.withhold = false;
+    if (const uint64_t t = test_withhold_ns()) {
+        a.timeout_ns = t;
+        a.withhold = true;
+    }
     int grid = w->grid;
     if (ctx->grid_limit > 0 && ctx->grid_limit < grid) grid = ctx->grid_limit;
     if (grid_override > 0 && grid_override < grid) grid = grid_override;
@@ -714,6 +766,26 @@ gb_info bfs_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *l
                                         ctx->stream));
     prof_end(ctx, span);
     return GB_SUCCESS;
+}
+
+// Reads and clears the context's sticky BFS status word (the largest exit
+// code of launches whose caller did not wait for them); GB_TIMEOUT if it
+// was set. Called by gb_context_synchronize.
+gb_info bfs_collect_status(gb_context *ctx) {
+    BfsState *st = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_ws_mu);
+        auto it = g_ws.find(ctx);
+        if (it == g_ws.end() || !it->second.st) return GB_SUCCESS;
+        st = it->second.st;
+    }
+    int e = 0;
+    GB_CUDA(cudaMemcpyAsync(&e, &st->sticky, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    GB_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (!e) return GB_SUCCESS;
+    GB_CUDA(cudaMemsetAsync(&st->sticky, 0, sizeof(int), ctx->stream));
+    GB_CUDA(cudaStreamSynchronize(ctx->stream));
+    return fail(GB_TIMEOUT, "a BFS launched without waiting for it ran out of a bounded device wait");
 }
 
 }  // namespace gbx
@@ -738,7 +810,7 @@ extern "C" gb_info gb_bfs(gb_context *ctx, const gb_matrix *A, uint32_t src, int
         }
     }
     const int sch = bfs_schedule(ctx, A, desc);
-    if (sch == GB_SCHED_CLUSTER) GB_CHECK(bfs_cluster_run(ctx, A, src, dl, dp, w));
+    if (sch == GB_SCHED_CLUSTER) GB_CHECK(bfs_cluster_run(ctx, A, src, dl, dp, w, &w->st->sticky));
     else GB_CHECK(bfs_launch(ctx, A, src, dl, dp, desc, w, 0));
     if (mem == GB_HOST) {
         GB_CUDA(cudaMemcpyAsync(levels, dl, (size_t)A->nrows * 4, cudaMemcpyDeviceToHost, ctx->stream));
@@ -746,7 +818,9 @@ extern "C" gb_info gb_bfs(gb_context *ctx, const gb_matrix *A, uint32_t src, int
     }
     if (sch == GB_SCHED_CLUSTER) {
         if (stats || mem == GB_HOST) {
-            GB_CHECK(bfs_cluster_result(ctx, w->cl_state, stats));
+            const gb_info r = bfs_cluster_result(ctx, w->cl_state, stats);
+            if (r == GB_TIMEOUT) (void)bfs_collect_status(ctx);   // reported here, not again
+            GB_CHECK(r);
             if (stats) stats->schedule = GB_SCHED_CLUSTER;
         }
         return GB_SUCCESS;
@@ -755,6 +829,9 @@ extern "C" gb_info gb_bfs(gb_context *ctx, const gb_matrix *A, uint32_t src, int
         BfsResult hs;
         GB_CUDA(cudaMemcpyAsync(&hs, &w->st->res, sizeof(BfsResult), cudaMemcpyDeviceToHost, ctx->stream));
         GB_CUDA(cudaStreamSynchronize(ctx->stream));
+        // this launch's status is in hs.err; its copy in the sticky word is
+        // reported here, not again by gb_context_synchronize
+        if (hs.err) (void)bfs_collect_status(ctx);
         if (stats) {
             stats->depth = hs.depth;
             stats->push_levels = hs.push_levels;
@@ -909,7 +986,7 @@ static __device__ __align__(256) unsigned char g_bfs_scratch[noalloc::BYTES];
 
 extern "C" gb_info gb_bfs_noalloc(const uint32_t *rowptr, const uint32_t *colidx, const uint32_t *colptr,
                                   const uint32_t *rowidx, uint32_t n, uint64_t nnz, uint32_t src, int32_t *levels,
-                                  int32_t *parents, void *stream) {
+                                  int32_t *parents, int32_t *status, void *stream) {
     using namespace gbx::noalloc;
     if (!rowptr || !colidx || !levels) return fail(GB_NULL_POINTER, "gb_bfs_noalloc: NULL argument");
     if ((colptr == nullptr) != (rowidx == nullptr))
@@ -921,6 +998,7 @@ extern "C" gb_info gb_bfs_noalloc(const uint32_t *rowptr, const uint32_t *colidx
     if (src >= n) return fail(GB_INVALID_INDEX, "gb_bfs_noalloc: source %u out of range", src);
     if (((uintptr_t)colidx & 15) || ((uintptr_t)rowidx & 15))
         return fail(GB_INVALID_VALUE, "gb_bfs_noalloc: colidx and rowidx must be 16-byte aligned");
+    if ((uintptr_t)status & 3) return fail(GB_INVALID_VALUE, "gb_bfs_noalloc: status must be 4-byte aligned");
     int dev = 0;
     GB_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= MAX_DEVICES) return fail(GB_INVALID_VALUE, "gb_bfs_noalloc: device %d unsupported", dev);
@@ -974,6 +1052,12 @@ extern "C" gb_info gb_bfs_noalloc(const uint32_t *rowptr, const uint32_t *colidx
     a.timeout_ns = 4000000000ull;
     a.total_limit_ns = 120000000000ull;
     a.err_sticky = nullptr;
+    a.status_out = status;   // the caller's word: 0 or GB_TIMEOUT once the kernel has finished
+    a.withhold = false;
+    if (const uint64_t t = test_withhold_ns()) {
+        a.timeout_ns = t;
+        a.withhold = true;
+    }
     // the kernel needs a zeroed working state; the last call's contents may remain
     GB_CUDA(cudaMemsetAsync(a.st, 0, sizeof(BfsState), s));
     void *args[] = {&a};

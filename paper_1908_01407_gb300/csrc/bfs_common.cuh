@@ -39,6 +39,9 @@ struct BfsState {
     unsigned int pad1;
     unsigned long long uedg[3];        // in-edges of the candidates a pull leaves, per pull slot
     unsigned long long uact[3];        // unvisited candidates a pull walked, per level slot
+    int sticky;                        // max of the exit codes of launches nobody has waited for yet
+                                       // (launches leave it as it is; gb_context_synchronize reads and clears it)
+    int pad2;
     BfsResult res;
 };
 
@@ -68,6 +71,8 @@ struct BfsArgs {
     uint64_t timeout_ns;       // bound on one grid-barrier wait
     uint64_t total_limit_ns;   // bound on the whole traversal
     int *err_sticky;           // optional: a nonzero exit status is also max-ed in here (batched runs)
+    int *status_out;           // optional: the exit status (0 or GB_TIMEOUT) is stored here by the last block
+    bool withhold;             // failure-path test: block 0 never arrives at the first grid barrier
 };
 
 }  // namespace gbx

@@ -189,6 +189,7 @@ int bits_for(uint64_t x);  // number of bits needed to represent values < x
 // and returns its slot (or -1); prof_end records the matching end event.
 int prof_begin(gb_context *ctx, const char *name);
 void bfs_workspace_release(gb_context *ctx);
+gb_info bfs_collect_status(gb_context *ctx);
 void ms_workspace_release(gb_context *ctx);
 void prof_end(gb_context *ctx, int slot);
 
@@ -290,6 +291,24 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *bar, unsigned int nblocks
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// Waits (thread 0 polls, the block follows) until *err is nonzero or
+// limit_ns has passed; in the second case it records GB_TIMEOUT itself.
+// Returns false: the caller has left the barrier protocol. Used only by the
+// failure-path test in which one block withholds its barrier arrival.
+__device__ __forceinline__ bool wait_for_error(int *err, uint64_t limit_ns) {
+    if (threadIdx.x == 0) {
+        const uint64_t t0 = globaltimer_ns();
+        while (ld_relaxed_gpu_int(err) == 0) {
+            if (globaltimer_ns() - t0 > limit_ns) {
+                atomicCAS(err, 0, (int)GB_TIMEOUT);
+                break;
+            }
+        }
+    }
+    __syncthreads();
+    return false;
 }
 
 }  // namespace dev

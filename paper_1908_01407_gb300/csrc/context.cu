@@ -202,8 +202,10 @@ gb_info gb_context_set_stream(gb_context *ctx, void *stream) {
 
 gb_info gb_context_synchronize(gb_context *ctx) {
     if (!ctx) return fail(GB_NULL_POINTER, "gb_context_synchronize: ctx is NULL");
+    GB_CUDA(cudaSetDevice(ctx->device));
     GB_CUDA(cudaStreamSynchronize(ctx->stream));
-    return GB_SUCCESS;
+    // a timeout of a BFS that was launched without waiting for it
+    return bfs_collect_status(ctx);
 }
 
 gb_info gb_context_pool_stats(gb_context *ctx, uint64_t *held, uint64_t *peak) {

@@ -36,8 +36,21 @@ struct Stage {
     uint32_t wdeg[WARPS];
     unsigned long long base;
 };
+// Per-warp queue of pull candidates whose row head had no frontier vertex:
+// they are scanned 32 at a time (one per lane), so a long row delays only
+// the misses batched with it, not every candidate of its group.
+constexpr int MISS_CAP = 96;   // fewer than 32 left over + a group of at most 64
+struct MissQueue {
+    uint32_t v[WARPS][MISS_CAP];     // vertex
+    uint32_t c[WARPS][MISS_CAP];     // candidate (the entry a later pull walks)
+    uint32_t len[WARPS][MISS_CAP];   // in-degree
+    uint32_t deg[WARPS][MISS_CAP];   // out-degree
+};
 struct Smem {
-    SmemPush push;
+    union {
+        SmemPush push;      // push levels
+        MissQueue miss;     // pull levels
+    };
     Stage stage;
     unsigned long long qs;
     unsigned long long ue;   // in-edges of the last pull's leftover candidates

@@ -280,6 +280,10 @@ extern "C" gb_info gb_pagerank_delta(gb_context *ctx, const gb_matrix *A, float 
     if (!A->built) return fail(GB_INVALID_VALUE, "gb_pagerank_delta: matrix not built");
     if (A->nrows != A->ncols) return fail(GB_DIMENSION_MISMATCH, "gb_pagerank_delta: matrix must be square");
     if (!(damping >= 0.f && damping <= 1.f)) return fail(GB_INVALID_VALUE, "gb_pagerank_delta: damping not in [0, 1]");
+    if (eps != eps || (eps >= 0.f && eps < GB_PAGERANK_DELTA_MIN_EPS))
+        return fail(GB_INVALID_VALUE,
+                    "gb_pagerank_delta: eps = %g is below the FP32 floor %g (a negative eps never freezes)",
+                    (double)eps, (double)GB_PAGERANK_DELTA_MIN_EPS);
     const uint32_t n = A->nrows;
     if (n == 0 || max_iters == 0) {
         if (iterations) *iterations = 0;

@@ -94,6 +94,9 @@ __device__ void relax_pull(const RelaxArgs &a, int d, uint32_t *cnt_out, uint32_
                 any |= pend[j];
             }
             if (!__any_sync(full, any)) break;
+            // indices and weights of a chunk load together: reading the weights only
+            // after the frontier test found a source would add a dependent DRAM step
+            // to every round, and in a pull (a dense frontier) most chunks hit anyway
             uint4 c[RPULL_WPW], wv[RPULL_WPW];
 #pragma unroll
             for (int j = 0; j < RPULL_WPW; ++j) {
@@ -234,6 +237,15 @@ __global__ void __launch_bounds__(BLOCK, 6) k_relax(RelaxArgs a) {
     bool ok = dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns);
     const uint64_t t_start = dev::globaltimer_ns();
     bool list_valid = !a.all_active;
+    // algorithmic bytes (thread 0 of block 0): the initial value writes, then
+    // per push 8 per frontier vertex (offsets), 8 (or 4 unweighted) per
+    // frontier out-edge (index, weight); per pull the full masked pass:
+    // 4 (n + 1) offsets, n / 8 frontier bits, 4 m indices, 4 per weight of an
+    // edge out of the frontier; per level 4 per value written (next frontier)
+    double alg = 4.0 * a.n;
+    uint32_t prev_cnt = 0;
+    uint64_t prev_fe = 0;
+    bool prev_pull = false;
     int d = 0;
     for (; ok; ++d) {
         if (threadIdx.x == 0)
@@ -244,6 +256,12 @@ __global__ void __launch_bounds__(BLOCK, 6) k_relax(RelaxArgs a) {
         __syncthreads();
         const uint32_t cnt = (uint32_t)(qs >> a.ebits);
         const uint64_t fe = qs & a.emask;
+        if (tid == 0 && d > 0) {
+            const double ew = a.weighted ? 4.0 : 0.0;
+            if (prev_pull) alg += 4.0 * (a.n + 1.0) + a.n / 8.0 + 4.0 * a.m + ew * prev_fe;
+            else alg += 8.0 * prev_cnt + (4.0 + ew) * prev_fe;
+            alg += 4.0 * cnt;
+        }
         if (cnt == 0) break;
         // guard: every value can decrease only finitely often; a wall-clock budget bounds the loop
         if (threadIdx.x == 0 && dev::globaltimer_ns() - t_start > a.total_limit_ns) atomicCAS(&st->err, 0, (int)GB_TIMEOUT);
@@ -259,6 +277,9 @@ __global__ void __launch_bounds__(BLOCK, 6) k_relax(RelaxArgs a) {
             res->frontier_edges += fe;
             st->qstate[(d + 2) % 3] = 0;
             st->cstate[(d + 2) % 3] = 0;
+            prev_cnt = cnt;
+            prev_fe = fe;
+            prev_pull = pull;
         }
         uint32_t *Fclr = a.front[(d + 2) % 3];
         for (uint64_t w = tid; w < a.nwords; w += nthreads) Fclr[w] = 0u;
@@ -300,6 +321,7 @@ __global__ void __launch_bounds__(BLOCK, 6) k_relax(RelaxArgs a) {
         res->depth = d;
         if (d < GBX_MAX_LEVEL_LOG) res->lv_ns[d] = dev::globaltimer_ns();
         res->t_begin = t_start;
+        res->alg_bytes = alg;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -328,7 +350,8 @@ gb_info sssp_cluster_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, u
 gb_info cluster_iterations(gb_context *ctx, const void *state, uint32_t *iterations);
 
 static gb_info relax_run(gb_context *ctx, const gb_matrix *A, bool weighted, uint32_t src, uint32_t *out, gb_mem mem,
-                         const gb_desc *desc, uint32_t *iterations, const char *who) {
+                         const gb_desc *desc, uint32_t *iterations, gb_bfs_stats *stats, const char *who) {
+    if (stats) memset(stats, 0, sizeof(*stats));
     if (!ctx || !A || !out) return fail(GB_NULL_POINTER, "%s: NULL argument", who);
     if (!A->built) return fail(GB_INVALID_VALUE, "%s: matrix not built", who);
     if (A->nrows != A->ncols) return fail(GB_DIMENSION_MISMATCH, "%s: matrix must be square", who);
@@ -370,7 +393,15 @@ static gb_info relax_run(gb_context *ctx, const gb_matrix *A, bool weighted, uin
         GB_CHECK(sssp_cluster_launch(ctx, A, src, a.val, stamp.as<uint32_t>(), q, q + A->nrows + 1, cl_state));
         if (mem == GB_HOST)
             GB_CUDA(cudaMemcpyAsync(out, a.val, (size_t)A->nrows * 4, cudaMemcpyDeviceToHost, ctx->stream));
-        return cluster_iterations(ctx, cl_state, iterations);
+        uint32_t it = 0;
+        const gb_info r = cluster_iterations(ctx, cl_state, &it);
+        if (iterations) *iterations = it;
+        if (stats) {
+            stats->depth = it;
+            stats->push_levels = it;
+            stats->schedule = GB_SCHED_CLUSTER;
+        }
+        return r;
     }
     for (int k = 0; k < 3; ++k) a.front[k] = front + (size_t)k * a.nwords;
     a.q[0] = q; a.q[1] = q + A->nrows + 1;
@@ -408,6 +439,24 @@ static gb_info relax_run(gb_context *ctx, const gb_matrix *A, bool weighted, uin
     if (mem == GB_HOST) GB_CUDA(cudaMemcpyAsync(out, a.val, (size_t)A->nrows * 4, cudaMemcpyDeviceToHost, ctx->stream));
     GB_CHECK(sync(ctx));
     if (iterations) *iterations = hs.depth;
+    if (stats) {
+        stats->depth = hs.depth;
+        stats->push_levels = hs.push_levels;
+        stats->pull_levels = hs.pull_levels;
+        stats->status = (uint32_t)hs.err;
+        stats->frontier_edges = hs.frontier_edges;
+        stats->alg_bytes = (uint64_t)hs.alg_bytes;
+        const uint32_t nl = hs.depth < GB_TRACE_LEVELS ? hs.depth : GB_TRACE_LEVELS;
+        stats->trace_len = nl;
+        for (uint32_t l = 0; l < nl; ++l) {
+            stats->trace_dir[l] = hs.dir_log[l];
+            stats->trace_vertices[l] = hs.lv_cnt[l];
+            stats->trace_edges[l] = hs.lv_fe[l];
+            const uint64_t t1 = (l + 1 < GBX_MAX_LEVEL_LOG) ? hs.lv_ns[l + 1] : hs.lv_ns[l];
+            stats->trace_us[l] = (float)((t1 - hs.lv_ns[l]) * 1e-3);
+        }
+        stats->schedule = GB_SCHED_GRID;
+    }
     if (hs.err) return fail(GB_TIMEOUT, "%s: a bounded device wait or the time budget ran out", who);
     return GB_SUCCESS;
 }
@@ -417,12 +466,13 @@ static gb_info relax_run(gb_context *ctx, const gb_matrix *A, bool weighted, uin
 extern "C" {
 
 gb_info gb_sssp(gb_context *ctx, const gb_matrix *A, uint32_t src, uint32_t *dist, gb_mem mem, const gb_desc *desc,
-                uint32_t *iterations) {
-    return relax_run(ctx, A, true, src, dist, mem, desc, iterations, "gb_sssp");
+                uint32_t *iterations, gb_bfs_stats *stats) {
+    return relax_run(ctx, A, true, src, dist, mem, desc, iterations, stats, "gb_sssp");
 }
 
-gb_info gb_cc(gb_context *ctx, const gb_matrix *A, uint32_t *labels, gb_mem mem, uint32_t *iterations) {
-    return relax_run(ctx, A, false, 0, labels, mem, nullptr, iterations, "gb_cc");
+gb_info gb_cc(gb_context *ctx, const gb_matrix *A, uint32_t *labels, gb_mem mem, uint32_t *iterations,
+              gb_bfs_stats *stats) {
+    return relax_run(ctx, A, false, 0, labels, mem, nullptr, iterations, stats, "gb_cc");
 }
 
 }  // extern "C"

@@ -11,8 +11,3 @@ def teps(m_stored: int, seconds: float) -> float:
 def teps_undirected(m_stored: int, seconds: float) -> float:
     """Graph500 convention: undirected edges (half the stored nonzeros)."""
     return (m_stored / 2) / seconds
-
-
-def harmonic_mean(xs):
-    xs = list(xs)
-    return len(xs) / sum(1.0 / x for x in xs)

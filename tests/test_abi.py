@@ -93,3 +93,16 @@ def test_every_entry_point_rejects_null_handles(L):
     assert not bad, bad
     assert codes["gb_bfs_multi"] == gb.INVALID_VALUE          # k == 0 is checked before the handles
     assert codes["gb_bfs_batch"] == gb.NULL_POINTER
+
+
+def test_noalloc_limit_of_the_library_is_the_headers(L):
+    """The scratch limit compiled into the library (its size check runs on
+    the host, before any device call) equals the GB_NOALLOC_MAX_VERTICES of
+    include/gbx.h, which the binding reads."""
+    src = open(os.path.join(ROOT, "include", "gbx.h")).read()
+    limit = int(re.search(r"#define\s+GB_NOALLOC_MAX_VERTICES\s+(\d+)u?", src).group(1))
+    assert gb.NOALLOC_MAX_VERTICES == limit
+    p = ctypes.c_void_p(4096)          # never dereferenced: the size check comes first
+    rc = L.gb_bfs_noalloc(p, p, p, p, limit + 1, 0, 0, p, None, None, None)
+    assert rc == gb.INVALID_VALUE
+    assert f"1..{limit}" in gb.last_error()

@@ -342,34 +342,67 @@ def test_sssp_single_cluster_schedule(ctx, case):
 
 
 # ------------------------------------------------------- adaptive PageRank
+PRD_EPS = (1e-5, 1e-4, 1e-3, 1e-2)   # the floor GB_PAGERANK_DELTA_MIN_EPS and up
+
+
+def prd_parity(g, got, want, alpha=0.85):
+    """The bar of adaptive PageRank (DESIGN reading 14). T, one step of the
+    PageRank recurrence, is an alpha-contraction in L1, so any vector x is
+    within r(x) / (1 - alpha) of the fixed point p*, r(x) = ||T(x) - x||_1
+    (computed by the oracle in FP64). Hence, exactly,
+        ||got - want||_1 <= (r(got) + r(want)) / (1 - alpha).
+    And the GPU's run must be converged as far as the oracle's run with the
+    same eps: the two apply one freeze rule to values that differ by FP32
+    rounding, so only vertices within that rounding of the threshold can
+    decide differently: r(got) <= 2 r(want) + 1e-6."""
+    r_got = oracle.pagerank_residual(g, got, alpha)
+    r_want = oracle.pagerank_residual(g, want, alpha)
+    l1 = np.abs(got.astype(np.float64) - want).sum()
+    # r is computed in FP64 as a sum of n differences of values near each other: its
+    # absolute error is at most about n * 2^-52 * max(p), allowed for by the last term
+    fp64 = 4 * g.n * 2.0 ** -52 * max(float(np.abs(want).max()), 1e-30) / (1 - alpha)
+    assert l1 <= (r_got + r_want) / (1 - alpha) * (1 + 1e-9) + fp64, (l1, r_got, r_want)
+    assert r_got <= 2 * r_want + 1e-6, (r_got, r_want)
+    return l1, r_got, r_want
+
+
 @pytest.mark.parametrize("case", ["rmat14", "grid", "star", "cycle", "dangling"])
 def test_pagerank_delta_vs_fp64_oracle(ctx, case):
-    """Adaptive PageRank against the FP64 oracle with the same eps. Both take
-    the freeze decision in FP32; they can differ only for vertices within
-    FP32 rounding of the threshold, and such a vertex moves values by about
-    eps * p, so L1 <= 1e-5 (the FP32 PageRank bound) + 10 * eps. eps stays
-    at 80 FP32 ulps (1e-5) or more: closer to FP32 resolution the rounding of
-    the GPU's FP32 values decides the threshold crossing, and a graph whose
-    vertices all freeze together (the star's leaves) can shift by several
-    iterations. Runs are bit-identical; iteration counts agree within 2."""
+    """Adaptive PageRank against the FP64 oracle with the same eps, for every
+    eps the API accepts from its floor up (GB_PAGERANK_DELTA_MIN_EPS = 1e-5;
+    below it the call is refused): the contraction bound of prd_parity, the
+    active counts never grow and start at n, iteration counts within 2, and
+    runs bit-identical."""
     t = {"rmat14": lambda: gen.rmat(14, 16, seed=21),
          "grid": lambda: gen.grid(100, 90, 0.1, seed=2),
          "star": lambda: gen.from_edges(6000, [(0, i) for i in range(1, 6000)]),   # a row past 4096: block row
          "cycle": lambda: gen.from_edges(97, [(i, (i + 1) % 97) for i in range(97)]),
          "dangling": lambda: gen.from_edges(50, [(0, 1), (1, 2), (2, 0), (3, 4), (2, 5)])}[case]()
     g, A = build(ctx, t, weights=False)
-    for eps in (1e-4, 1e-5):
+    for eps in PRD_EPS:
         want, it_o, act_o = oracle.pagerank_delta(g, 0.85, eps, 200)
         got = np.empty(t.n, np.float32)
         _, it, res, act = gb.pagerank_delta(ctx, A, 0.85, eps, 200, got)
         assert abs(it - it_o) <= 2
-        assert np.abs(got.astype(np.float64) - want).sum() <= 1e-5 + 10 * eps
+        prd_parity(g, got, want)
         again = np.empty(t.n, np.float32)
         gb.pagerank_delta(ctx, A, 0.85, eps, 200, again)
         assert np.array_equal(got.view(np.uint32), again.view(np.uint32))
         assert act[0] == t.n and np.all(np.diff(act.astype(np.int64)) <= 0)
         if case == "cycle":
             assert it == 1
+    A.free()
+
+
+def test_pagerank_delta_refuses_eps_below_its_floor(ctx):
+    t = gen.rmat(10, 8, seed=22)
+    g, A = build(ctx, t, weights=False)
+    got = np.empty(t.n, np.float32)
+    for eps in (0.0, 1e-6, 9.9e-6, float("nan")):
+        with pytest.raises(gb.GBError) as e:
+            gb.pagerank_delta(ctx, A, 0.85, eps, 50, got)
+        assert e.value.code == gb.INVALID_VALUE
+    gb.pagerank_delta(ctx, A, 0.85, 1e-5, 50, got)     # the floor itself is accepted
     A.free()
 
 
@@ -399,11 +432,11 @@ def test_pagerank_and_delta_directed_matrix(ctx):
     gb.pagerank(ctx, A, 0.85, 30, got, residuals=False)
     want, _ = oracle.pagerank(g, 0.85, 30, directed=True)
     assert np.abs(got.astype(np.float64) - want).sum() <= 1e-5
-    eps = 1e-5
-    want, it_o, _ = oracle.pagerank_delta(g, 0.85, eps, 200, directed=True)
-    _, it, _, _ = gb.pagerank_delta(ctx, A, 0.85, eps, 200, got)
-    assert abs(it - it_o) <= 2
-    assert np.abs(got.astype(np.float64) - want).sum() <= 1e-5 + 10 * eps
+    for eps in PRD_EPS:
+        want, it_o, _ = oracle.pagerank_delta(g, 0.85, eps, 200, directed=True)
+        _, it, _, _ = gb.pagerank_delta(ctx, A, 0.85, eps, 200, got)
+        assert abs(it - it_o) <= 2
+        prd_parity(g, got, want)
     A.free()
 
 
@@ -433,3 +466,35 @@ def test_tc_every_set_kind_on_disjoint_cliques(ctx):
     assert np.array_equal(v.astype(np.int64), r.astype(np.int64) - col.astype(np.int64) - 1)
     for x in (A, B, L, C):
         x.free()
+
+
+def test_sssp_stats_count_the_algorithmic_bytes_of_each_iteration(ctx):
+    """gb_sssp's stats: the iterations and the per-iteration trace, and the
+    algorithmic bytes recomputed on the host from that trace (4 n value
+    writes; per push 8 per frontier vertex + 8 per frontier out-edge; per
+    pull 4 (n + 1) + n / 8 + 4 m + 4 per frontier out-edge; 4 per improved
+    value) equal the kernel's count, while the distances match Dijkstra."""
+    t = gen.rmat(14, 16, seed=31, wmax=255)
+    g, A = build(ctx, t)
+    n, m = A.nrows, A.nvals
+    src = int(gen.sources(t, 1, seed=1)[0])
+    for direction in (gb.AUTO, gb.PUSH, gb.PULL):
+        d = gb.Descriptor(direction=direction)
+        dist = np.empty(n, np.uint32)
+        _, it, st = gb.sssp(ctx, A, src, dist, d, stats=True)
+        assert np.array_equal(dist, oracle.sssp(g, src))
+        assert st["depth"] == it == st["push_levels"] + st["pull_levels"] == len(st["trace"])
+        tr = st["trace"]
+        want = 4.0 * n
+        for k, lv in enumerate(tr):
+            nxt = tr[k + 1]["vertices"] if k + 1 < len(tr) else 0
+            if lv["dir"] == "pull":
+                want += 4.0 * (n + 1) + n / 8.0 + 4.0 * m + 4.0 * lv["edges"]
+            else:
+                want += 8.0 * lv["vertices"] + 8.0 * lv["edges"]
+            want += 4.0 * nxt
+        assert abs(st["alg_bytes"] - want) <= 2, (st["alg_bytes"], want)
+        if direction == gb.PULL:
+            assert st["push_levels"] == 0
+        d.free()
+    A.free()

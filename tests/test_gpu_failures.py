@@ -60,3 +60,35 @@ def test_server_wait_times_out_then_completes(ctx):
         assert r.status == gb.SUCCESS
     S.destroy()
     A.free()
+
+
+def test_bfs_timeout_without_waiting_is_reported_by_synchronize(ctx):
+    """gb_bfs with device outputs and no stats returns without waiting; when
+    its bounded barrier wait runs out (a test hook makes one block withhold
+    its arrival; no fault), the next synchronise reports GB_TIMEOUT once, a
+    waiting call reports it at once, and the context stays usable."""
+    import os
+    import torch
+    t = gen.rmat(12, 16, seed=24)
+    A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, flags=gb.SYMMETRIC)
+    g = oracle.csr_from_tuples(t)
+    s = int(gen.sources(t, 1, seed=1)[0])
+    lv = torch.empty(t.n, dtype=torch.int32, device="cuda")
+    ctx.synchronize()
+    os.environ["GBX_TEST_WITHHOLD_BARRIER_US"] = "2000"
+    try:
+        gb.bfs(ctx, A, s, lv, False, stats=False)          # does not wait
+        with pytest.raises(gb.GBError) as e:
+            ctx.synchronize()
+        assert e.value.code == gb.TIMEOUT
+        ctx.synchronize()                                   # reported once
+        with pytest.raises(gb.GBError) as e:                # a waiting call reports it itself
+            gb.bfs(ctx, A, s, lv, False, stats=True)
+        assert e.value.code == gb.TIMEOUT
+        ctx.synchronize()
+    finally:
+        del os.environ["GBX_TEST_WITHHOLD_BARRIER_US"]
+    _, _, st = gb.bfs(ctx, A, s, lv, False, stats=True)
+    assert st["status"] == 0
+    assert np.array_equal(lv.cpu().numpy(), oracle.bfs(g, s))
+    A.free()

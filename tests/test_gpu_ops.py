@@ -39,7 +39,29 @@ def rand_val(rng, t):
         return int(rng.integers(0, 20))
     if t == "int32":
         return int(rng.integers(-9, 10))
-    return float(rng.integers(-9, 10))
+    if t == "fp32":
+        return float(np.float32(rng.uniform(-9, 9)))   # a value FP32 holds exactly
+    return float(rng.uniform(-9, 9))
+
+
+# Floating-point outputs are compared with a bound derived from the
+# arithmetic, not a fixed tolerance. The oracle computes in double from
+# inputs the type holds exactly; the GPU computes in the type, in another
+# order. An output made of k terms a (x) b (a product or a sum, then the
+# add monoid over the terms) and an optional accumulated old value w has
+# every intermediate bounded by S = |w| + sum(|a||b| + |a| + |b|), and each
+# of its at most k + 2 rounded operations errs by at most u * S (u = 2^-24
+# for fp32, 2^-53 for fp64; a min/max only selects), so the GPU result is
+# within (k + 3) * u * S of the exact one, and the oracle's double result
+# within (k + 3) * 2^-53 * S of it.
+UNIT = {"fp32": 2.0 ** -24, "fp64": 2.0 ** -53}
+
+
+def float_bound(t, terms, w_old=0.0):
+    if t not in UNIT:
+        return 0.0
+    S = abs(float(w_old)) + sum(abs(float(a)) * abs(float(b)) + abs(float(a)) + abs(float(b)) for a, b in terms)
+    return (len(terms) + 3) * (UNIT[t] + 2.0 ** -53) * S
 
 
 def rand_dict(rng, n, k, t):
@@ -74,21 +96,23 @@ def gpu_mat(ctx, e, t, nr, nc, structural=False, flags=gb.BUILD_DEFAULT):
     return A
 
 
-def close(a, b, t):
+def close(a, b, t, tol=0.0):
+    if t == "fp32" and abs(b) > float(np.finfo(np.float32).max):
+        b = math.copysign(math.inf, b)              # the exact value overflows FP32
     if t in ("fp32", "fp64"):
         if math.isinf(a) or math.isinf(b):
             return a == b
-        return abs(a - b) <= 1e-5 * max(1.0, abs(b))
+        return abs(a - b) <= tol
     if t == "bool":
         return bool(a) == bool(b)
     return int(a) == int(b)
 
 
-def assert_vec(v, want: gbo.Vec):
+def assert_vec(v, want: gbo.Vec, tol=lambda i: 0.0):
     got = v.to_dict()
     assert set(got) == set(want.e), (sorted(set(got) ^ set(want.e))[:10])
     for i, x in want.e.items():
-        assert close(got[i], x, want.t), (i, got[i], x)
+        assert close(got[i], x, want.t, tol(i)), (i, got[i], x, tol(i))
 
 
 CASES = []
@@ -147,7 +171,11 @@ def test_mxv_vxm_all_semirings_masks_directions(ctx, sr, t):
             want = gbo.vxm(gbo.Vec(nout, t, wd), gbo.Vec(nout, mt, md) if md is not None else None, acc_op, sr,
                            gbo.Vec(nin, t, ud), Am, tran=tran, structural="structure" in mk, scmp="scmp" in mk,
                            replace=replace)
-        assert_vec(w, want)
+        def tol(i, E=E, ud=ud, wd=wd, out_rows=out_rows, accum=accum):
+            terms = [(a, ud[j]) for (r, c), a in E.items()
+                     for j in [c if out_rows else r] if (r if out_rows else c) == i and j in ud]
+            return float_bound(t, terms, wd.get(i, 0.0) if accum else 0.0)
+        assert_vec(w, want, tol)
         for x in (A, u, w, mask, d):
             if x is not None:
                 x.free()
@@ -220,21 +248,31 @@ def test_ewise_and_reduce(ctx, t):
                 g = gbo.ewise_add if add else gbo.ewise_mult
                 want = g(gbo.Vec(n, t, wd), gbo.Vec(n, "int32", md) if mk is not None else None, None, op,
                          gbo.Vec(n, t, ud), gbo.Vec(n, t, vd), structural=mk == gb.STRUCTURE, scmp=mk == gb.SCMP)
-                assert_vec(w, want)
+                assert_vec(w, want, lambda i: float_bound(t, [(ud.get(i, 0.0), vd.get(i, 0.0))]))
     for mon in MON:
         ud = rand_dict(rng, n, 40, t)
         got = gb.reduce_vector(gpu_vec(ctx, ud, t, n), MON[mon])
-        assert close(got, gbo.reduce_vector(t, mon, gbo.Vec(n, t, ud)), t)
+        # a reduction of k values: k - 1 rounded operations on partial results bounded by sum |x|
+        # (a product of k values is bounded by prod max(1, |x|) instead)
+        red = lambda vals: float_bound(t, [(1.0, 0.0)] * len(vals)) * (
+            float(np.prod([max(1.0, abs(x)) for x in vals])) if mon == "TIMES" else
+            sum(abs(x) for x in vals) / max(len(vals), 1) + 1.0) if t in UNIT else 0.0
+        assert close(got, gbo.reduce_vector(t, mon, gbo.Vec(n, t, ud)), t, red(list(ud.values())))
         got = gb.reduce_vector(gpu_vec(ctx, {}, t, n), MON[mon])
         assert close(got, gbo.reduce_vector(t, mon, gbo.Vec(n, t, {})), t)
         E = rand_mat(rng, 50, 70, 400, t)
         A = gpu_mat(ctx, E, t, 50, 70)
-        assert close(gb.reduce_matrix(A, MON[mon]), gbo.reduce_matrix(t, mon, gbo.Mat(50, 70, t, E)), t)
+        assert close(gb.reduce_matrix(A, MON[mon]), gbo.reduce_matrix(t, mon, gbo.Mat(50, 70, t, E)), t,
+                     red(list(E.values())))
         for tran in (False, True):
             nout = 70 if tran else 50
             w = gpu_vec(ctx, {}, t, nout)
             gb.reduce_rows(w, None, gb.NOP, MON[mon], A, gb.Descriptor(inp0=gb.TRAN if tran else 0))
-            assert_vec(w, gbo.reduce_rows(gbo.Vec(nout, t), None, None, mon, gbo.Mat(50, 70, t, E), tran=tran))
+            rows = {}
+            for (r, c), x in E.items():
+                rows.setdefault(c if tran else r, []).append(x)
+            assert_vec(w, gbo.reduce_rows(gbo.Vec(nout, t), None, None, mon, gbo.Mat(50, 70, t, E), tran=tran),
+                       lambda i: red(rows.get(i, [])))
 
 
 def test_reduce_accumulates_into_prior_value(ctx):
@@ -269,8 +307,16 @@ def test_mxm_masked(ctx, sr, t):
         r, c, v = C.extract_tuples(with_vals=True)
         got = {(int(i), int(j)): x.item() for i, j, x in zip(r, c, v)}
         assert set(got) == set(want.e)
+        At = {(j, i): v for (i, j), v in Ae.items()} if tran0 else Ae
+        Bt = {(j, i): v for (i, j), v in Be.items()} if tran1 else Be
+        Brow = {}
+        for (kk, j), b in Bt.items():
+            Brow.setdefault(kk, {})[j] = b
         for k, x in want.e.items():
-            assert close(got[k], x, t), (k, got[k], x)
+            i, j = k
+            terms = [(a, Brow[kk][j]) for (ii, kk), a in At.items() if ii == i and kk in Brow and j in Brow[kk]]
+            tol = float_bound(t, terms, Ce.get(k, 0.0) if acc_op else 0.0)
+            assert close(got[k], x, t, tol), (k, got[k], x, tol)
         for x in (A, B, M, C, d):
             x.free()
 

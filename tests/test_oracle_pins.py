@@ -372,6 +372,39 @@ def test_pagerank_directed_matches_dense_power_iteration():
         assert it == k and np.abs(q - y).sum() < 1e-12
 
 
+def test_pagerank_residual_is_the_dense_step_and_bounds_the_error():
+    """r(x) = ||T(x) - x||_1 against the dense Google matrix built
+    independently (symmetric and directed graphs, random x), against the C
+    oracle's logged change of each power-iteration step, and the contraction
+    bound ||x - p*||_1 <= r(x) / (1 - a) with p* from a dense solve."""
+    rng = np.random.default_rng(23)
+    edges, _ = small_edges(11, 0.3, 44)
+    sym = g_from_edges(11, edges + [(0, 10)])
+    r = rng.integers(0, 12, 30).astype(np.uint32)
+    c = rng.integers(0, 12, 30).astype(np.uint32)
+    keep = (r != c) & (r < 9)
+    dirg = oracle.csr_build(12, r[keep], c[keep])
+    for g in (sym, dirg):
+        G = google_matrix(g, 0.85)
+        for _ in range(3):
+            x = rng.random(g.n)
+            x /= x.sum()
+            assert abs(oracle.pagerank_residual(g, x, 0.85) - np.abs(G @ x - x).sum()) < 1e-14
+        M = np.eye(g.n) - G
+        M[-1, :] = 1.0
+        rhs = np.zeros(g.n)
+        rhs[-1] = 1.0
+        pstar = np.linalg.solve(M, rhs)
+        directed = g is dirg
+        _, log = oracle.pagerank(g, 0.85, 12, directed=directed)
+        for k in (1, 4, 11):
+            pk, _ = oracle.pagerank(g, 0.85, k, directed=directed)
+            rk = oracle.pagerank_residual(g, pk, 0.85)
+            assert abs(rk - log[k]) < 1e-14                   # the step the C oracle took next
+            assert np.abs(pk - pstar).sum() <= rk / 0.15 + 1e-14
+        assert oracle.pagerank_residual(g, pstar, 0.85) < 1e-14
+
+
 # ------------------------------------------------------------------- CC ---
 def test_cc_known_components_and_full_grid():
     edges = [(0, 3), (3, 7), (1, 2), (5, 6), (6, 8), (8, 5)]
