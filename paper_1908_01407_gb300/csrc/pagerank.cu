@@ -1,15 +1,25 @@
 // PageRank (Section 7.3), pull formulation, in FP32 with FP32 accumulation:
 //   p'(i) = (1 - a)/n + a * ( sum_{j in N(i)} p(j)/deg(j) + D/n ),
 // D = sum of p over vertices without edges (spread uniformly), p0 = 1/n,
-// a fixed number of iterations. The SpMV is merge-path load balanced
-// (Section 6.3.2; Merrill and Garland's 2-D diagonal split of row ends
-// against nonzeros): every block gets an equal share of the merged
-// sequence, so rows of any length cost the same per item. The update is
-// fused into the SpMV's row epilogue, which also writes x' = p'/deg for the
-// next iteration. Per-iteration L1 residual sum |p' - p| and the dangling
-// mass D are reduced in FP64 in a fixed order, as is the final
-// normalisation; no floating-point atomics are used, so a run is
-// bit-reproducible.
+// a fixed number of iterations.
+//
+// The SpMV y = A x (x = p/deg) splits the nonzeros, not the rows, evenly
+// (Section 6.3.2 balances SpMV by merge-path; here the split is over the
+// nonzeros alone, which rows of any length cross freely): every warp takes
+// tiles of 512 consecutive nonzeros, each lane 4 consecutive nonzeros of each
+// of the tile's four 128-nonzero sub-tiles, so a warp's column-index loads
+// are one contiguous 512-byte run per sub-tile and a lane has all 16 of its
+// x gathers in flight at once. A bit per nonzero marks the first entry of
+// each row (computed once per call), and a per-tile prefix of those bits
+// gives the rank of each row start; the k-th row start is row live[k] (the
+// ascending list of nonempty rows, which the matrix keeps). Within a tile
+// the rows are closed by a lane walk and a warp-level segmented scan (no
+// shared memory, no block barrier); a row that crosses tile ends is
+// finished by k_pr_span, which adds the tiles' partial sums in tile order.
+// A separate pass applies the update p' = base + a y, x' = p'/deg and
+// reduces the L1 residual sum |p' - p| and the dangling mass D in FP64 in a
+// fixed order. Every sum has one fixed order and no floating-point atomics
+// are used, so a run is bit-reproducible.
 #include "common.cuh"
 
 using namespace gbx;
@@ -18,288 +28,214 @@ namespace gbx {
 namespace {
 
 constexpr int PR_BLOCK = 256;
-constexpr int PR_IPT = 8;
-constexpr int PR_LOAD_BATCH = 8;
-constexpr int PR_TILE = PR_BLOCK * PR_IPT;
-constexpr int PR_RS_BYTES = ((PR_TILE + 2) * 4 + 15) / 16 * 16;
-constexpr int PR_SMEM_BYTES = PR_RS_BYTES + PR_IPT * PR_BLOCK * 4 + PR_TILE * 4;
+constexpr int PR_WARPS = PR_BLOCK / 32;
+constexpr uint32_t PR_SUB = 128;               // nonzeros per sub-tile (4 per lane)
+constexpr uint32_t PR_NSUB = 4;                // sub-tiles per tile
+constexpr uint32_t PR_TILE = PR_SUB * PR_NSUB; // nonzeros per warp tile
 
-struct PrRec {
-    uint32_t first_row;   // row finished by the block's first row end, if it began earlier
-    float first_val;
-    uint32_t last_row;    // row still open at the block's end
-    float last_val;
-    uint32_t flags;       // 1 = has a row end, 2 = starts mid-row, 4 = ends mid-row
-};
-
-struct PrArgs {
-    uint32_t n;
+struct TileArgs {
     uint64_t nnz;
-    const uint32_t *rp, *ci;      // rows = in-edges of each vertex
-    const uint32_t *rp_out;       // out-degrees
-    bool rows_are_out;            // rp is also the out-edge structure (symmetric matrix)
-    const float *x;               // p(j)/deg(j), 0 for deg(j) = 0
-    const float *p_old;
+    uint32_t ntiles;
+    const uint32_t *ci;       // column indices of the pulled rows (in-edges)
+    const uint32_t *flags;    // bit e: nonzero e is the first of its row
+    const uint32_t *trank;    // per tile: row starts before it
+    const uint32_t *live;     // k-th nonempty row
+    const float *x;           // p(j)/deg(j)
+    float *y;                 // row sums (rows never written stay 0)
+    float *pfirst;            // per tile: partial of the row open at its start (the whole tile without starts)
+    float *plast;             // per tile with a start: partial of the row open at its end
+    uint32_t *rlast;          // its rank
+    uint32_t *tflag;          // 1 if the tile holds a row start
+};
+
+// bit e of flags set where nonzero e starts its row
+__global__ void k_pr_flags(const uint32_t *rp, uint32_t n, uint32_t *flags) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t b = __ldg(&rp[i]);
+        if (b < __ldg(&rp[i + 1])) atomicOr(&flags[b >> 5], 1u << (b & 31));
+    }
+}
+
+// row starts per tile (16 flag words)
+__global__ void k_pr_tilecount(const uint32_t *flags, uint32_t nwords, uint32_t ntiles, uint32_t *cnt) {
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
+        uint32_t c = 0;
+        for (uint32_t w = t * (PR_TILE / 32); w < (t + 1) * (PR_TILE / 32) && w < nwords; ++w) c += __popc(flags[w]);
+        cnt[t] = c;
+    }
+}
+
+__global__ void __launch_bounds__(PR_BLOCK) k_pr_tiles(TileArgs a) {
+    const uint32_t full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nwarps = gridDim.x * PR_WARPS;
+    const uint4 *ci4 = reinterpret_cast<const uint4 *>(a.ci);
+    for (uint32_t t = blockIdx.x * PR_WARPS + (threadIdx.x >> 5); t < a.ntiles; t += nwarps) {
+        const uint64_t t0 = (uint64_t)t * PR_TILE;
+        // every load of the tile first: column indices and start bits, then the gathers
+        uint32_t col[PR_NSUB][4], fl[PR_NSUB];
+#pragma unroll
+        for (uint32_t k2 = 0; k2 < PR_NSUB; ++k2) {
+            const uint64_t e = t0 + k2 * PR_SUB + 4 * lane;
+            uint4 c4 = make_uint4(0, 0, 0, 0);
+            uint32_t f = 0;
+            if (e < a.nnz) {
+                c4 = __ldcs(&ci4[e >> 2]);   // the index array is padded: a partial last chunk is readable
+                f = (__ldg(&a.flags[e >> 5]) >> (e & 31)) & 0xfu;
+                const uint64_t left = a.nnz - e;
+                if (left < 4) f &= (1u << left) - 1u;
+            }
+            col[k2][0] = c4.x; col[k2][1] = c4.y; col[k2][2] = c4.z; col[k2][3] = c4.w;
+            fl[k2] = f;
+        }
+        float xv[PR_NSUB][4];
+#pragma unroll
+        for (uint32_t k2 = 0; k2 < PR_NSUB; ++k2)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint64_t e = t0 + k2 * PR_SUB + 4 * lane + j;
+                xv[k2][j] = e < a.nnz ? __ldg(&a.x[col[k2][j]]) : 0.f;
+            }
+        // sub-tiles in order; the row open across them is carried warp-wide
+        uint32_t R = __ldg(&a.trank[t]);   // rank of the next row start
+        float carry = 0.f;                 // partial sum of the open row
+        bool carry_in_tile = false;        // the open row began inside this tile
+#pragma unroll
+        for (uint32_t k2 = 0; k2 < PR_NSUB; ++k2) {
+            const uint32_t f = fl[k2];
+            const uint32_t nf = __popc(f);
+            uint32_t tot;
+            const uint32_t excl = dev::warp_exclusive_sum<uint32_t>(nf, &tot);
+            const uint32_t Rb = R + excl;
+            // lane walk: rows that start and end inside the lane's four entries are done here
+            float acc = 0.f, head = 0.f;
+            bool seen = false;
+            uint32_t r = Rb;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if ((f >> j) & 1u) {
+                    if (seen) {
+                        a.y[__ldg(&a.live[r])] = acc;
+                        ++r;
+                    } else {
+                        head = acc;
+                        seen = true;
+                    }
+                    acc = 0.f;
+                }
+                acc += xv[k2][j];
+            }
+            if (!seen) head = acc;   // no start in the lane: all of it continues the open row
+            // segmented inclusive scan over lanes of (value since the lane's last start, start seen)
+            float v = seen ? acc : head;
+            bool rs = seen;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float yv = __shfl_up_sync(full, v, o);
+                const bool yr = __shfl_up_sync(full, rs ? 1 : 0, o) != 0;
+                if (lane >= o && !rs) {
+                    v += yv;
+                    rs = yr;
+                }
+            }
+            // what flows into this lane from earlier lanes (and from the carry when none started)
+            const uint32_t starts = __ballot_sync(full, seen);
+            const bool started_before = (starts & dev::lanemask_lt()) != 0u;
+            float inflow = __shfl_up_sync(full, v, 1);
+            if (lane == 0) inflow = 0.f;
+            if (!started_before) inflow += carry;
+            if (seen) {
+                // the row this lane's first start closes: rank Rb - 1
+                const float total = inflow + head;
+                if (started_before || carry_in_tile) a.y[__ldg(&a.live[Rb - 1])] = total;
+                else a.pfirst[t] = total;   // it began before the tile: finished by k_pr_span
+            }
+            const float last = __shfl_sync(full, v, 31);
+            if (starts) {
+                carry = last;
+                carry_in_tile = true;
+            } else {
+                carry += last;
+            }
+            R += tot;
+        }
+        if (lane == 0) {
+            const bool any = R != __ldg(&a.trank[t]);
+            a.tflag[t] = any ? 1u : 0u;
+            if (any) {
+                a.plast[t] = carry;
+                a.rlast[t] = R - 1;
+            } else {
+                a.pfirst[t] = carry;
+            }
+        }
+    }
+}
+
+// rows that cross tile ends: the partial at the end of the tile where the
+// row starts, plus the partials of the following tiles up to the first one
+// that holds a row start, in tile order
+__global__ void __launch_bounds__(PR_BLOCK) k_pr_span(TileArgs a) {
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < a.ntiles; t += gridDim.x * blockDim.x) {
+        if (!a.tflag[t]) continue;
+        float total = a.plast[t];
+        for (uint32_t t2 = t + 1; t2 < a.ntiles; ++t2) {
+            total += a.pfirst[t2];
+            if (a.tflag[t2]) break;
+        }
+        a.y[__ldg(&a.live[a.rlast[t]])] = total;
+    }
+}
+
+struct UpdArgs {
+    uint32_t n;
+    const float *y, *p_old;
     float *p_new, *x_new;
-    const float *base;            // device scalar: (1-a)/n + a*D/n
+    const uint32_t *rp_out;   // out-degrees
+    const float *base;        // device scalar: (1-a)/n + a*D/n
     float alpha;
-    PrRec *rec;
-    double *part_res, *part_dang; // per block
-    uint32_t nblocks;
+    double *part_res, *part_dang;
 };
 
-// merge-path search: split of diagonal d between row ends a[] (absolute
-// offsets) and nonzero indices k0, k0+1, ...; returns x = rows consumed
-__device__ __forceinline__ uint32_t merge_search_smem(const uint32_t *a, uint32_t nrows, uint32_t k0, uint32_t nk,
-                                                      uint32_t d) {
-    uint32_t lo = d > nk ? d - nk : 0;
-    uint32_t hi = d < nrows ? d : nrows;
-    while (lo < hi) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (a[mid] <= k0 + d - mid - 1) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-// the same on the global row-end array rp[1..n] for an absolute diagonal,
-// done by the whole block (one probe per thread per round)
-__device__ uint32_t block_merge_search(const uint32_t *rp, uint32_t n, uint64_t nnz, uint64_t d) {
-    uint32_t lo = d > nnz ? (uint32_t)(d - nnz) : 0;
-    uint32_t hi = d < n ? (uint32_t)d : n;
-    // invariant: answer in [lo, hi]; predicate(x) = rp[x+1] <= d - x - 1 is monotone (true then false)
-    while (hi > lo) {
-        uint32_t span = hi - lo;
-        uint32_t step = (span + PR_BLOCK - 1) / PR_BLOCK;
-        uint32_t x = lo + threadIdx.x * step;
-        int ok = x < hi && (uint64_t)__ldg(&rp[x + 1]) + x + 1 <= d;
-        int c = __syncthreads_count(ok);
-        if (c == 0) { hi = lo; break; }
-        uint32_t last_ok = lo + (uint32_t)(c - 1) * step;   // predicate true here, maybe beyond
-        lo = last_ok + 1;
-        uint32_t nh = last_ok + step;
-        hi = nh < hi ? nh : hi;
-    }
-    return lo;
-}
-
-struct Seg {
-    int reset;   // thread (or prefix) contains a row end
-    float v;     // partial of the row open at its end
-};
-__device__ __forceinline__ Seg seg_op(Seg a, Seg b) {
-    Seg r;
-    r.reset = a.reset | b.reset;
-    r.v = b.reset ? b.v : a.v + b.v;
-    return r;
-}
-
-// row i is complete with sum y: write p'(i), x'(i) = p'(i)/deg(i), and add
-// to the residual and dangling partials. rowlen is row i's length in the
-// pulled structure; it is the out-degree when that structure is the CSR
-// itself (symmetric matrix), otherwise the out-degree is read from rp_out.
-__device__ __forceinline__ void epilogue(const PrArgs &a, uint32_t i, float y, float base, float p_old, uint32_t rowlen,
-                                         double &res, double &dang) {
-    float p = base + a.alpha * y;
-    uint32_t deg = a.rows_are_out ? rowlen : __ldg(&a.rp_out[i + 1]) - __ldg(&a.rp_out[i]);
-    a.p_new[i] = p;
-    a.x_new[i] = deg ? p / (float)deg : 0.f;
-    res += fabs((double)p - (double)p_old);
-    if (!deg) dang += (double)p;
-}
-
-__global__ void __launch_bounds__(PR_BLOCK, 6) k_pr_spmv(PrArgs a) {
-    // dynamic shared memory: s_rs[0] = start of the chunk's first row,
-    // s_rs[r + 1] = end of its row r; gathered x values and previous ranks
-    extern __shared__ __align__(16) unsigned char pr_smem[];
-    uint32_t *s_rs = reinterpret_cast<uint32_t *>(pr_smem);
-    float (*s_xv)[PR_BLOCK] = reinterpret_cast<float (*)[PR_BLOCK]>(pr_smem + PR_RS_BYTES);
-    float *s_sum = reinterpret_cast<float *>(pr_smem + PR_RS_BYTES + PR_IPT * PR_BLOCK * 4);   // finished rows
-    __shared__ Seg s_scan[PR_BLOCK / 32];
-    __shared__ uint32_t s_x[PR_BLOCK + 1];
-    __shared__ double s_red[2][PR_BLOCK / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint64_t total = (uint64_t)a.n + a.nnz;
-    const uint64_t D0 = total * blockIdx.x / gridDim.x, D1 = total * (blockIdx.x + 1) / gridDim.x;
+// p' = base + a y, x' = p'/deg; FP64 partial sums of |p' - p| and of the
+// dangling p', each block over a fixed contiguous range of rows
+__global__ void __launch_bounds__(PR_BLOCK) k_pr_update(UpdArgs a) {
+    __shared__ double s_red[2][PR_WARPS];
+    const uint64_t per = ((uint64_t)a.n + gridDim.x - 1) / gridDim.x;
+    const uint64_t b0 = per * blockIdx.x, b1 = b0 + per < a.n ? b0 + per : a.n;
     const float base = *a.base;
     double res = 0.0, dang = 0.0;
-    uint32_t i0 = block_merge_search(a.rp, a.n, a.nnz, D0);
-    uint32_t ic = i0;
-    uint64_t kc = D0 - i0;
-    const bool start_mid = i0 < a.n && kc > __ldg(&a.rp[i0]);
-    bool pending = start_mid;          // the first row end closes a row begun before D0
-    bool has_end = false;
-    Seg carry = {0, 0.f};
-    for (uint64_t c = D0; c < D1; c += PR_TILE) {
-        const uint64_t ce = c + PR_TILE < D1 ? c + PR_TILE : D1;
-        const uint32_t clen = (uint32_t)(ce - c);
-        // stage the row bounds the chunk can reach, PR_BLOCK at a time, until a
-        // staged row end lies at or past the chunk's last nonzero: no row
-        // beyond it can end inside the chunk, so the merge searches never
-        // look further (a chunk of rows of ~30 entries needs one round instead
-        // of the clen + 1 bounds a chunk of empty rows would)
-        const uint32_t avail = a.n - ic;
-        const uint32_t Rmax = avail < clen + 1 ? avail : clen + 1;
-        uint32_t R = Rmax;
-        for (uint32_t r0 = 0;; r0 += PR_BLOCK) {
-            const uint32_t r = r0 + threadIdx.x;
-            if (r <= Rmax) s_rs[r] = __ldg(&a.rp[ic + r]);
-            __syncthreads();
-            const uint32_t last = r0 + PR_BLOCK - 1 < Rmax ? r0 + PR_BLOCK - 1 : Rmax;
-            if (last == Rmax || (uint64_t)s_rs[last] >= kc + clen) {
-                R = last;
-                break;
-            }
-        }
-        const uint32_t *s_re = s_rs + 1;
-        const uint64_t nk_left = a.nnz - kc;
-        const uint32_t bl = nk_left < clen ? (uint32_t)nk_left : clen;
-        // one merge-path search per thread for the start of its items; the
-        // last thread also finds the chunk end; neighbours exchange them
-        uint32_t d0 = threadIdx.x * PR_IPT < clen ? threadIdx.x * PR_IPT : clen;
-        const uint32_t x0 = merge_search_smem(s_re, R, (uint32_t)kc, bl, d0);
-        s_x[threadIdx.x] = x0;
-        if (threadIdx.x == PR_BLOCK - 1) s_x[PR_BLOCK] = merge_search_smem(s_re, R, (uint32_t)kc, bl, clen);
-        __syncthreads();
-        const uint32_t nrows = s_x[PR_BLOCK];                  // row ends inside the chunk
-        const uint32_t nk = clen - nrows;
-        const uint32_t ie = ic + nrows;
-        uint32_t d1 = d0 + PR_IPT < clen ? d0 + PR_IPT : clen;
-        const uint32_t x1 = s_x[threadIdx.x + 1];
-        const uint32_t tk0 = (uint32_t)kc + (d0 - x0), tk1 = (uint32_t)kc + (d1 - x1);
-        // all loads of the thread at once: column indices, then the gathers,
-        // and the previous ranks of the rows it finishes
-#pragma unroll
-        for (int j0 = 0; j0 < PR_IPT; j0 += PR_LOAD_BATCH) {
-            float xv[PR_LOAD_BATCH];
-            uint32_t cidx[PR_LOAD_BATCH];
-#pragma unroll
-            for (int j = 0; j < PR_LOAD_BATCH; ++j) cidx[j] = tk0 + j0 + j < tk1 ? __ldcs(&a.ci[tk0 + j0 + j]) : 0u;
-#pragma unroll
-            for (int j = 0; j < PR_LOAD_BATCH; ++j) xv[j] = tk0 + j0 + j < tk1 ? __ldcg(&a.x[cidx[j]]) : 0.f;
-#pragma unroll
-            for (int j = 0; j < PR_LOAD_BATCH; ++j) s_xv[j0 + j][threadIdx.x] = xv[j];
-        }
-        // walk the items: a row end stores the row's sum (the first one
-        // also needs the partial sums of earlier threads, added after the scan)
-        uint32_t ti = x0, tk = tk0, jn = 0;
-        float sum = 0.f;
-        bool head = false;
-        float head_val = 0.f;
-        for (uint32_t d = d0; d < d1; ++d) {
-            if (ti < nrows && tk >= s_re[ti]) {
-                if (!head) { head = true; head_val = sum; }
-                else s_sum[ti] = sum;
-                sum = 0.f;
-                ++ti;
-            } else {
-                sum += s_xv[jn++][threadIdx.x];
-                ++tk;
-            }
-        }
-        // segmented scan over threads: carry into each thread
-        Seg me = {head ? 1 : 0, sum};
-        Seg incl = me;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            Seg y;
-            y.reset = __shfl_up_sync(0xffffffffu, incl.reset, o);
-            y.v = __shfl_up_sync(0xffffffffu, incl.v, o);
-            if (lane >= o) incl = seg_op(y, incl);
-        }
-        if (lane == 31) s_scan[warp] = incl;
-        __syncthreads();
-        Seg wpre = carry;                       // chunk carry-in, then earlier warps
-        Seg tot_all = carry;
-        bool any_head = false;
-#pragma unroll
-        for (int w = 0; w < PR_BLOCK / 32; ++w) {
-            Seg sw = s_scan[w];
-            if (w < warp) wpre = seg_op(wpre, sw);
-            tot_all = seg_op(tot_all, sw);
-            any_head |= sw.reset != 0;
-        }
-        Seg excl_lane;
-        excl_lane.reset = __shfl_up_sync(0xffffffffu, incl.reset, 1);
-        excl_lane.v = __shfl_up_sync(0xffffffffu, incl.v, 1);
-        Seg into = lane == 0 ? wpre : seg_op(wpre, excl_lane);
-        if (head) s_sum[x0] = into.v + head_val;
-        __syncthreads();
-        // epilogue over the chunk's finished rows [ic, ie): coalesced, one row per thread
-        const bool first_pending = pending && nrows > 0;   // row ic began before this block
-        for (uint32_t r = threadIdx.x; r < nrows; r += PR_BLOCK) {
-            float y = s_sum[r];
-            if (r == 0 && first_pending) {
-                a.rec[blockIdx.x].first_row = ic;
-                a.rec[blockIdx.x].first_val = y;
-            } else {
-                epilogue(a, ic + r, y, base, __ldg(&a.p_old[ic + r]), s_rs[r + 1] - s_rs[r], res, dang);
-            }
-        }
-        carry.reset = 0;
-        carry.v = tot_all.v;
-        if (any_head) { pending = false; has_end = true; }
-        ic = ie;
-        kc = kc + nk;
-        __syncthreads();   // the staged arrays and s_scan are rewritten by the next chunk
+    for (uint64_t i = b0 + threadIdx.x; i < b1; i += PR_BLOCK) {
+        const float p = base + a.alpha * a.y[i];
+        const uint32_t deg = __ldg(&a.rp_out[i + 1]) - __ldg(&a.rp_out[i]);
+        a.p_new[i] = p;
+        a.x_new[i] = deg ? p / (float)deg : 0.f;
+        res += fabs((double)p - (double)a.p_old[i]);
+        if (!deg) dang += (double)p;
     }
-    // block records
-    if (threadIdx.x == 0) {
-        uint32_t fl = (has_end ? 1u : 0u) | (start_mid ? 2u : 0u);
-        bool end_open = ic < a.n && kc > __ldg(&a.rp[ic]);
-        if (end_open) fl |= 4u;
-        PrRec &r = a.rec[blockIdx.x];
-        r.last_row = ic;
-        r.last_val = carry.v;
-        r.flags = fl;
-        if (!has_end) { r.first_row = i0; r.first_val = 0.f; }
-    }
-    // fixed-order block reduction of the FP64 partials
     res = dev::warp_sum<double>(res);
     dang = dev::warp_sum<double>(dang);
-    if (lane == 0) { s_red[0][warp] = res; s_red[1][warp] = dang; }
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s_red[0][warp] = res; s_red[1][warp] = dang; }
     __syncthreads();
     if (threadIdx.x == 0) {
         double r0 = 0, r1 = 0;
-        for (int w = 0; w < PR_BLOCK / 32; ++w) { r0 += s_red[0][w]; r1 += s_red[1][w]; }
+        for (int w = 0; w < PR_WARPS; ++w) { r0 += s_red[0][w]; r1 += s_red[1][w]; }
         a.part_res[blockIdx.x] = r0;
         a.part_dang[blockIdx.x] = r1;
     }
 }
 
-// One block: finishes the rows that cross block boundaries (walking
-// forward from the block where each one starts, summing in block order),
-// then reduces all FP64 partials in a fixed order into the residual and the
-// next iteration's dangling mass and base term.
-__global__ void __launch_bounds__(PR_BLOCK) k_pr_fix(PrArgs a, double *residual_out, double *dang_io, float *base_out,
-                                                    double *fix_res, double *fix_dang, int init) {
+// One block: the FP64 partials in a fixed order -> the iteration's residual,
+// the dangling mass D and the next base term (1-a)/n + a D/n.
+__global__ void __launch_bounds__(PR_BLOCK) k_pr_reduce(uint32_t n, float alpha, const double *part_res,
+                                                       const double *part_dang, uint32_t nparts,
+                                                       double *residual_out, float *base_out) {
     __shared__ double s[2][PR_BLOCK];
-    const float base = *a.base;
-    if (!init) {
-        for (uint32_t b = threadIdx.x; b < a.nblocks; b += PR_BLOCK) {
-            double r = 0, dn = 0;
-            const PrRec &rb = a.rec[b];
-            bool open = rb.flags & 4u;
-            bool starts_here = (rb.flags & 1u) || !(rb.flags & 2u);
-            if (open && starts_here) {
-                uint32_t row = rb.last_row;
-                float tot = rb.last_val;
-                for (uint32_t b2 = b + 1; b2 < a.nblocks; ++b2) {
-                    const PrRec &q = a.rec[b2];
-                    if (!(q.flags & 1u)) { tot += q.last_val; continue; }
-                    tot += q.first_val;
-                    break;
-                }
-                epilogue(a, row, tot, base, a.p_old[row], __ldg(&a.rp[row + 1]) - __ldg(&a.rp[row]), r, dn);
-            }
-            fix_res[b] = r;
-            fix_dang[b] = dn;
-        }
-        __syncthreads();
-    }
     double r0 = 0, r1 = 0;
-    for (uint32_t b = threadIdx.x; b < a.nblocks; b += PR_BLOCK) {
-        r0 += a.part_res[b] + (init ? 0.0 : fix_res[b]);
-        r1 += a.part_dang[b] + (init ? 0.0 : fix_dang[b]);
+    for (uint32_t b = threadIdx.x; b < nparts; b += PR_BLOCK) {
+        r0 += part_res[b];
+        r1 += part_dang[b];
     }
     s[0][threadIdx.x] = r0;
     s[1][threadIdx.x] = r1;
@@ -310,9 +246,8 @@ __global__ void __launch_bounds__(PR_BLOCK) k_pr_fix(PrArgs a, double *residual_
     }
     if (threadIdx.x == 0) {
         if (residual_out) *residual_out = s[0][0];
-        *dang_io = s[1][0];
-        double n = (double)a.n;
-        *base_out = (float)((1.0 - (double)a.alpha) / n + (double)a.alpha * s[1][0] / n);
+        const double nn = (double)n;
+        *base_out = (float)((1.0 - (double)alpha) / nn + (double)alpha * s[1][0] / nn);
     }
 }
 
@@ -376,65 +311,95 @@ extern "C" gb_info gb_pagerank(gb_context *ctx, const gb_matrix *A, float dampin
     if (!A->built) return fail(GB_INVALID_VALUE, "gb_pagerank: matrix not built");
     if (A->nrows != A->ncols) return fail(GB_DIMENSION_MISMATCH, "gb_pagerank: matrix must be square");
     if (!A->has_csc) return fail(GB_INVALID_VALUE, "gb_pagerank: needs the CSC copy (in-edges)");
+    if (!A->live_list) return fail(GB_INVALID_VALUE, "gb_pagerank: the matrix has no list of nonempty rows");
     if (!(damping >= 0.f && damping <= 1.f)) return fail(GB_INVALID_VALUE, "gb_pagerank: damping must be in [0, 1]");
     const uint32_t n = A->nrows;
     if (n == 0) return GB_SUCCESS;
     GB_CUDA(cudaSetDevice(ctx->device));
+    const uint64_t m = A->nvals;
+    const uint32_t ntiles = (uint32_t)((m + PR_TILE - 1) / PR_TILE);
+    const uint32_t nfw = (uint32_t)((m + 31) / 32);
     int occ = 0;
-    GB_CUDA(cudaFuncSetAttribute(k_pr_spmv, cudaFuncAttributeMaxDynamicSharedMemorySize, PR_SMEM_BYTES));
-    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pr_spmv, PR_BLOCK, PR_SMEM_BYTES));
-    uint64_t total = (uint64_t)n + A->nvals;
-    uint32_t G = (uint32_t)(occ * ctx->num_sms);
-    if (G < 1) G = 1;
-    // at least a few tiles of work per block
-    uint64_t maxg = total / (PR_TILE * 4) + 1;
-    if (G > maxg) G = (uint32_t)maxg;
-    Scratch p0(ctx), p1(ctx), x0(ctx), x1(ctx), rec(ctx), pres(ctx), pdang(ctx), fres(ctx), fdang(ctx), scal(ctx),
-        resid(ctx), outb(ctx);
+    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pr_tiles, PR_BLOCK, 0));
+    // a plain (not cooperative) launch: it needs no co-residency, so it takes the
+    // whole GPU even where a context's persistent kernels are capped, and the
+    // hardware interleaves its blocks with those of concurrent work
+    uint32_t G = (uint32_t)(occ > 0 ? occ : 1) * (uint32_t)ctx->num_sms;
+    const uint32_t need = (ntiles + PR_WARPS - 1) / PR_WARPS;
+    if (G > need) G = need > 0 ? need : 1;
+    const uint32_t UB = 1024;   // blocks of the update pass (fixed: the reduction order does not depend on the GPU)
+    Scratch p0(ctx), p1(ctx), x0(ctx), x1(ctx), yb(ctx), fl(ctx), tr(ctx), pf(ctx), pl(ctx), rl(ctx), tf(ctx),
+        pres(ctx), pdang(ctx), scal(ctx), resid(ctx), outb(ctx);
     GB_CHECK(p0.alloc((size_t)n * 4 + 16));
     GB_CHECK(p1.alloc((size_t)n * 4 + 16));
     GB_CHECK(x0.alloc((size_t)n * 4 + 16));
     GB_CHECK(x1.alloc((size_t)n * 4 + 16));
-    uint32_t nrec = G > 1024 ? G : 1024;
-    GB_CHECK(rec.alloc((size_t)nrec * sizeof(PrRec)));
-    GB_CHECK(pres.alloc((size_t)nrec * 8));
-    GB_CHECK(pdang.alloc((size_t)nrec * 8));
-    GB_CHECK(fres.alloc((size_t)nrec * 8));
-    GB_CHECK(fdang.alloc((size_t)nrec * 8));
+    GB_CHECK(yb.alloc((size_t)n * 4 + 16));
+    GB_CHECK(fl.alloc((size_t)nfw * 4 + 64));
+    GB_CHECK(tr.alloc((size_t)ntiles * 4 + 16));
+    GB_CHECK(pf.alloc((size_t)ntiles * 4 + 16));
+    GB_CHECK(pl.alloc((size_t)ntiles * 4 + 16));
+    GB_CHECK(rl.alloc((size_t)ntiles * 4 + 16));
+    GB_CHECK(tf.alloc((size_t)ntiles * 4 + 16));
+    GB_CHECK(pres.alloc((size_t)UB * 8));
+    GB_CHECK(pdang.alloc((size_t)UB * 8));
     GB_CHECK(scal.alloc(64));
     GB_CHECK(resid.alloc(((size_t)iters + 1) * 8));
     float *out = rank;
     if (mem == GB_HOST) { GB_CHECK(outb.alloc((size_t)n * 4 + 16)); out = outb.as<float>(); }
-    double *dang = scal.as<double>();
     float *base = reinterpret_cast<float *>(scal.as<char>() + 16);
-    PrArgs a;
-    a.n = n;
-    a.nnz = A->nvals;
-    a.rp = A->colptr;
-    a.ci = A->rowidx;
-    a.rp_out = A->rowptr;
-    a.rows_are_out = A->csc_alias;
-    a.alpha = damping;
-    a.rec = rec.as<PrRec>();
-    a.part_res = pres.as<double>();
-    a.part_dang = pdang.as<double>();
-    a.base = base;
+    // once per call: the row-start bits, their per-tile prefix, zero row sums
+    // (rows without in-edges are never written and keep y = 0)
+    GB_CHECK(memset_async(ctx, fl.p, 0, (size_t)nfw * 4 + 64));
+    GB_CHECK(memset_async(ctx, yb.p, 0, (size_t)n * 4 + 16));
+    k_pr_flags<<<1024, PR_BLOCK, 0, ctx->stream>>>(A->colptr, n, fl.as<uint32_t>());
+    if (ntiles) {
+        k_pr_tilecount<<<(ntiles + PR_BLOCK - 1) / PR_BLOCK < 4096 ? (ntiles + PR_BLOCK - 1) / PR_BLOCK : 4096,
+                         PR_BLOCK, 0, ctx->stream>>>(fl.as<uint32_t>(), nfw, ntiles, tr.as<uint32_t>());
+        GB_LAUNCH_CHECK();
+        GB_CHECK(scan_exclusive_u32(ctx, tr.as<uint32_t>(), tr.as<uint32_t>(), ntiles, nullptr));
+    }
     // init: p0, x0, D0 -> base
-    uint32_t ib = 1024;
-    k_pr_init<<<ib, PR_BLOCK, 0, ctx->stream>>>(n, A->rowptr, p0.as<float>(), x0.as<float>(), pdang.as<double>(),
-                                              pres.as<double>());
-    a.nblocks = ib;
-    k_pr_fix<<<1, PR_BLOCK, 0, ctx->stream>>>(a, nullptr, dang, base, fres.as<double>(), fdang.as<double>(), 1);
+    k_pr_init<<<UB, PR_BLOCK, 0, ctx->stream>>>(n, A->rowptr, p0.as<float>(), x0.as<float>(), pdang.as<double>(),
+                                             pres.as<double>());
+    k_pr_reduce<<<1, PR_BLOCK, 0, ctx->stream>>>(n, damping, pres.as<double>(), pdang.as<double>(), UB, nullptr, base);
     GB_LAUNCH_CHECK();
-    a.nblocks = G;
+    TileArgs ta;
+    ta.nnz = m;
+    ta.ntiles = ntiles;
+    ta.ci = A->rowidx;
+    ta.flags = fl.as<uint32_t>();
+    ta.trank = tr.as<uint32_t>();
+    ta.live = A->live_list;
+    ta.y = yb.as<float>();
+    ta.pfirst = pf.as<float>();
+    ta.plast = pl.as<float>();
+    ta.rlast = rl.as<uint32_t>();
+    ta.tflag = tf.as<uint32_t>();
+    UpdArgs ua;
+    ua.n = n;
+    ua.y = yb.as<float>();
+    ua.rp_out = A->rowptr;
+    ua.base = base;
+    ua.alpha = damping;
+    ua.part_res = pres.as<double>();
+    ua.part_dang = pdang.as<double>();
+    const uint32_t SB = (ntiles + PR_BLOCK - 1) / PR_BLOCK < 1024 ? (ntiles + PR_BLOCK - 1) / PR_BLOCK : 1024;
     float *pc = p0.as<float>(), *pn = p1.as<float>(), *xc = x0.as<float>(), *xn = x1.as<float>();
     for (uint32_t it = 0; it < iters; ++it) {
-        a.p_old = pc; a.x = xc; a.p_new = pn; a.x_new = xn;
-        int span = prof_begin(ctx, "pagerank_spmv");
-        k_pr_spmv<<<G, PR_BLOCK, PR_SMEM_BYTES, ctx->stream>>>(a);
+        ta.x = xc;
+        ua.p_old = pc; ua.p_new = pn; ua.x_new = xn;
+        if (ntiles) {
+            int span = prof_begin(ctx, "pagerank_spmv");
+            k_pr_tiles<<<G, PR_BLOCK, 0, ctx->stream>>>(ta);
+            prof_end(ctx, span);
+            k_pr_span<<<SB, PR_BLOCK, 0, ctx->stream>>>(ta);
+        }
+        int span = prof_begin(ctx, "pagerank_update");
+        k_pr_update<<<UB, PR_BLOCK, 0, ctx->stream>>>(ua);
         prof_end(ctx, span);
-        k_pr_fix<<<1, PR_BLOCK, 0, ctx->stream>>>(a, resid.as<double>() + it, dang, base, fres.as<double>(),
-                                                 fdang.as<double>(), 0);
+        k_pr_reduce<<<1, PR_BLOCK, 0, ctx->stream>>>(n, damping, pres.as<double>(), pdang.as<double>(), UB,
+                                                     resid.as<double>() + it, base);
         GB_LAUNCH_CHECK();
         float *t = pc; pc = pn; pn = t;
         t = xc; xc = xn; xn = t;

@@ -6,6 +6,7 @@
 // multi-source bit-frontier launch. A job is admitted only while its memory
 // estimate fits the HBM budget. Persistent kernels of concurrent slots are
 // given grids that fit on the GPU together, so their work overlaps.
+// A job that starts while no other job runs or waits gets the whole GPU.
 // Results stay on the device until fetched. Latency is measured from submit
 // to the moment the slot sees the job finish on the GPU.
 #include "common.cuh"
@@ -69,6 +70,7 @@ struct gb_server_t {
     uint64_t budget = 0, in_use = 0, peak = 0;
     uint64_t held = 0;             // bytes of finished, unfetched results (part of in_use)
     int running = 0;
+    int share = 0;                 // blocks of a persistent kernel when slots run together
     // statistics
     std::vector<double> lat;
     uint64_t submitted = 0, completed = 0, batches = 0, batched_bfs = 0;
@@ -149,6 +151,10 @@ void worker_loop(gb_server *S, int w) {
         S->in_use += need;
         S->peak = std::max(S->peak, S->in_use);
         S->running++;
+        // a job that starts with nothing else running or waiting takes the whole
+        // GPU; otherwise its persistent kernels get the share that lets every
+        // slot run at once
+        ctx->grid_limit = (S->running == 1 && S->pending.empty()) ? 0 : S->share;
         std::vector<uint32_t> srcs;
         for (uint64_t t : job) srcs.push_back(S->tickets[t].req.src);
         lk.unlock();
@@ -175,7 +181,7 @@ void worker_loop(gb_server *S, int w) {
                 if (st == GB_SUCCESS) st = sync(ctx);
             } else if (req.kind == GB_REQ_SSSP) {
                 uint32_t it = 0;
-                st = gb_sssp(ctx, A, req.src, (uint32_t *)res->dev, GB_DEVICE, nullptr, &it);
+                st = gb_sssp(ctx, A, req.src, (uint32_t *)res->dev, GB_DEVICE, nullptr, &it, nullptr);
             } else {
                 st = gb_pagerank(ctx, A, S->cfg.pagerank_damping, S->cfg.pagerank_iters, (float *)res->dev, nullptr,
                                  GB_DEVICE);
@@ -246,6 +252,7 @@ gb_info gb_server_create(gb_server **s, gb_context *ctx, const gb_server_cfg *cf
         wc->grid_limit = c.max_inflight > 1 ? grid_limit : 0;
         S->wctx.push_back(wc);
     }
+    S->share = c.max_inflight > 1 ? grid_limit : 0;
     for (uint32_t w = 0; w < c.max_inflight; ++w) S->workers.emplace_back(worker_loop, S, (int)w);
     *s = S;
     return GB_SUCCESS;
