@@ -87,7 +87,9 @@ typedef enum {
     GB_INP1 = 3,        /* GB_DEFAULT or GB_TRAN */
     GB_DIRECTION = 4,   /* GB_AUTO (default), GB_PUSH or GB_PULL */
     GB_SWITCH_BETA = 5, /* integer beta of the push/pull rule |E_f| > |E| / beta; 0 = tuned default */
-    GB_SCHEDULE = 6     /* BFS: GB_SCHED_AUTO (default), GB_SCHED_GRID or GB_SCHED_CLUSTER */
+    GB_SCHEDULE = 6,    /* BFS: GB_SCHED_AUTO (default), GB_SCHED_GRID or GB_SCHED_CLUSTER */
+    GB_SSSP_DELTA = 7   /* SSSP: width of the distance buckets of the near-far frontier; 0 = automatic,
+                           a width of at least 2^31 - 1 = no buckets (the plain changed-set iteration) */
 } gb_field;
 
 enum {
@@ -265,12 +267,18 @@ gb_info gb_mxv(gb_vector *w, const gb_vector *mask, gb_binop accum, gb_semiring 
  * identical to mxv with A transposed (Figure 4 caption). */
 gb_info gb_vxm(gb_vector *w, const gb_vector *mask, gb_binop accum, gb_semiring s, const gb_vector *u,
                const gb_matrix *A, const gb_desc *desc);
-/* Table 7 mxm with a mask (Section 6.3.4 masked SpGEMM, Section 7.5):
+/* Table 7 mxm (Section 6.3.4 masked SpGEMM, Section 7.5):
  * C<M> = accum(C, A (+).(x) B); GB_INP0/GB_INP1 = GB_TRAN transpose A/B.
- * Only the positions stored in M are computed (mask first): for each
- * M(i,j) the row A(i,:) is intersected with the column B(:,j). The mask must
- * not be complemented (GB_SCMP on mxm: GB_NOT_IMPLEMENTED). C must be
- * empty or have M's structure. */
+ * With a mask M (not complemented) only the positions stored in M are
+ * computed (mask first): for each M(i,j) the row A(i,:) is intersected with
+ * the column B(:,j). Without a mask (M = NULL), or with GB_SCMP, the whole
+ * product is formed by expanding every A(i,k) (x) B(k,j) into a tuple,
+ * dropping the positions a complemented mask excludes, and sorting and
+ * reducing equal positions with the semiring's add (as Section 6.3.1's
+ * SpMSpV does with its expanded products); the products must number fewer
+ * than 2^32 (GB_OUT_OF_MEMORY otherwise). Then accum, the mask and
+ * GB_REPLACE act as for the other operations (C may be empty or hold any
+ * entries). GB_SCMP with M = NULL allows no position. */
 gb_info gb_mxm(gb_matrix *C, const gb_matrix *M, gb_binop accum, gb_semiring s, const gb_matrix *A,
                const gb_matrix *B, const gb_desc *desc);
 /* Table 7 eWiseAdd (union) and eWiseMult (intersection) of vectors with a
@@ -413,6 +421,17 @@ gb_info gb_sssp(gb_context *ctx, const gb_matrix *A, uint32_t src, uint32_t *dis
  * rank[n] in `mem`; residuals[iters] (host, may be NULL). */
 gb_info gb_pagerank(gb_context *ctx, const gb_matrix *A, float damping, uint32_t iters, float *rank,
                     double *residuals, gb_mem mem);
+/* Autotuner of the PageRank SpMV tile (the paper has no counterpart; its
+ * merge-path SpMV of Section 6.3.2 has a fixed work per thread): times
+ * gb_pagerank on A with warp tiles of 256, 512 and 1,024 nonzeros (8, 16 or
+ * 32 gathers in flight per lane; the larger tiles use more registers, so
+ * fewer warps), two passes over the candidates, and keeps the fastest on
+ * the matrix for later gb_pagerank calls (untuned: 512). *tile_nnz receives
+ * it, *ms_per_iteration (may be NULL) its time per iteration. */
+gb_info gb_pagerank_autotune(gb_context *ctx, gb_matrix *A, uint32_t *tile_nnz, double *ms_per_iteration);
+/* Sets the PageRank tile of A by hand: 256, 512 or 1,024 nonzeros, or 0 for
+ * the default (GB_INVALID_VALUE otherwise). */
+gb_info gb_pagerank_set_tile(gb_matrix *A, uint32_t tile_nnz);
 /* Adaptive PageRank, also called PageRankDelta (Section 5.1: converged
  * vertices as the output mask; Section 7.3 names the variant): the
  * gb_pagerank recurrence, where a vertex whose value moved by at most eps

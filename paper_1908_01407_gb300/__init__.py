@@ -29,7 +29,8 @@ BOOL, INT32, UINT32, UINT64, FP32, FP64 = range(6)
 NOP, PLUS, TIMES, MIN, MAX, LOR, LAND, FIRST, SECOND, PAIR, MINUS = range(11)
 MONOID_PLUS, MONOID_TIMES, MONOID_MIN, MONOID_MAX, MONOID_LOR, MONOID_LAND = range(6)
 PLUS_TIMES, LOR_LAND, MIN_PLUS, MAX_PLUS, MIN_TIMES, MIN_SECOND, PLUS_PAIR = range(7)
-F_MASK, F_OUTP, F_INP0, F_INP1, F_DIRECTION, F_SWITCH_BETA, F_SCHEDULE = range(7)
+F_MASK, F_OUTP, F_INP0, F_INP1, F_DIRECTION, F_SWITCH_BETA, F_SCHEDULE, F_SSSP_DELTA = range(8)
+SSSP_DELTA_NONE = 2**31 - 1   # no buckets: the plain changed-set iteration
 DEFAULT, SCMP, STRUCTURE = 0, 1, 2
 REPLACE = 1
 TRAN = 1
@@ -133,6 +134,7 @@ _SIGS = {
     "gb_cc": [_P, _P, _P, _I, _P, _P], "gb_tc": [_P, _P, _P, _P],
     "gb_cc_fastsv": [_P, _P, _P, _I, _P],
     "gb_pagerank_delta": [_P, _P, ctypes.c_float, ctypes.c_float, _U32, _P, _I, _P, _P, _P],
+    "gb_pagerank_autotune": [_P, _P, _P, _P], "gb_pagerank_set_tile": [_P, _U32],
     "gb_server_create": [_PP, _P, _P], "gb_server_add_graph": [_P, _P, _P], "gb_server_submit": [_P, _P, _P],
     "gb_server_wait": [_P, _U64, _U32, _P], "gb_server_fetch": [_P, _U64, _P, _I],
     "gb_server_stats_get": [_P, _P], "gb_server_destroy": [_PP],
@@ -455,7 +457,8 @@ class Descriptor:
         check(lib().gb_desc_new(ctypes.byref(h)))
         self.h = h
         names = {"mask": F_MASK, "outp": F_OUTP, "inp0": F_INP0, "inp1": F_INP1,
-                 "direction": F_DIRECTION, "beta": F_SWITCH_BETA, "schedule": F_SCHEDULE}
+                 "direction": F_DIRECTION, "beta": F_SWITCH_BETA, "schedule": F_SCHEDULE,
+                 "sssp_delta": F_SSSP_DELTA}
         for k, v in fields.items():
             self.set(names[k], v)
 
@@ -651,6 +654,19 @@ def pagerank(ctx, A, damping=0.85, iters=50, rank=None, residuals=True):
     res = np.empty(max(iters, 1), np.float64) if residuals else None
     check(lib().gb_pagerank(ctx.h, A.h, damping, iters, pr, res.ctypes.data if res is not None else None, mr))
     return rank, (res[:iters] if res is not None else None)
+
+
+def pagerank_autotune(ctx, A):
+    """Pick the PageRank SpMV tile for A from timed runs; returns (tile
+    nonzeros, ms per iteration). The choice is kept on A."""
+    t = ctypes.c_uint32()
+    ms = ctypes.c_double()
+    check(lib().gb_pagerank_autotune(ctx.h, A.h, ctypes.byref(t), ctypes.byref(ms)))
+    return t.value, ms.value
+
+
+def pagerank_set_tile(A, tile_nnz):
+    check(lib().gb_pagerank_set_tile(A.h, tile_nnz))
 
 
 def pagerank_delta(ctx, A, damping=0.85, eps=1e-4, max_iters=100, rank=None):

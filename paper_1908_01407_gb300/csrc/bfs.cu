@@ -76,19 +76,17 @@ static __device__ __forceinline__ bool run_or_head(uint32_t key, uint32_t &bits)
     return lane == 0 || kp != key;
 }
 
-// Appends a warp's staged candidates to the next list: one atomicAdd
-// reserves the space, the copy is coalesced.
-static __device__ __forceinline__ void flush_candidates(const uint32_t *sbuf, uint32_t &staged, uint32_t *Lout,
-                                                        unsigned int *lout_cnt) {
-    const int lane = threadIdx.x & 31;
-    if (!staged) return;
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(lout_cnt, staged);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    for (uint32_t i = lane; i < staged; i += 32) Lout[base + i] = sbuf[i];
-    staged = 0;
-    __syncwarp();
-}
+// Shared memory of the pull levels (in a union with the push staging):
+// per warp, the candidates it keeps for the next pull, appended to the next
+// list PULL_KEEP_CAP at a time (one atomicAdd per flush), and the queue of
+// candidates whose head missed.
+constexpr int PULL_GROUP = PULL_WPW * 32;
+constexpr int PULL_KEEP_CAP = 64;
+constexpr int PULL_MISS_CAP = 64;   // fewer than 32 left over + one lane slot of 32
+struct PullSmem {
+    PullRec keep[WARPS][PULL_KEEP_CAP];
+    PullRec miss[WARPS][PULL_MISS_CAP];
+};
 
 // Claims the found vertices of one lane slot across the warp: visited and
 // next-frontier bits with one atomicOr per run of lanes in the same word,
@@ -112,14 +110,34 @@ static __device__ __forceinline__ void claim_found(const BfsArgs &a, uint32_t *F
     }
 }
 
-// Adds this lane's candidate (when keep) to the warp's staged survivors, the
-// candidates a later pull walks; flushes first when they would not fit.
-static __device__ __forceinline__ void keep_candidate(uint32_t *sbuf, uint32_t &staged, uint32_t *Lout,
-                                                      unsigned int *lout_cnt, bool keep, uint32_t c) {
+// Writes the warp's staged candidates to the next candidate list: one
+// atomicAdd reserves their places, the copy is coalesced (their pull records
+// with the live table, their vertex ids without it).
+template <bool TABLE>
+static __device__ __forceinline__ void flush_kept(PullRec *kbuf, uint32_t &staged, void *Lout,
+                                                  unsigned int *lout_cnt) {
+    if (!staged) return;
+    const int lane = threadIdx.x & 31;
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(lout_cnt, staged);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (uint32_t i = lane; i < staged; i += 32) {
+        if (TABLE) static_cast<PullRec *>(Lout)[base + i] = kbuf[i];
+        else static_cast<uint32_t *>(Lout)[base + i] = kbuf[i].v;
+    }
+    staged = 0;
+    __syncwarp();
+}
+
+// Adds the lanes' kept candidates to the warp's staging buffer, flushing it
+// first when they would not fit.
+template <bool TABLE>
+static __device__ __forceinline__ void keep_candidates(PullRec *kbuf, uint32_t &staged, void *Lout,
+                                                       unsigned int *lout_cnt, bool keep, const PullRec &r) {
     const uint32_t km = __ballot_sync(0xffffffffu, keep);
     if (!km) return;
-    if (staged + __popc(km) > (uint32_t)STAGE_CAP) flush_candidates(sbuf, staged, Lout, lout_cnt);
-    if (keep) sbuf[staged + __popc(km & dev::lanemask_lt())] = c;
+    if (staged + __popc(km) > (uint32_t)PULL_KEEP_CAP) flush_kept<TABLE>(kbuf, staged, Lout, lout_cnt);
+    if (keep) kbuf[staged + __popc(km & dev::lanemask_lt())] = r;
     staged += __popc(km);
     __syncwarp();
 }
@@ -131,33 +149,30 @@ static __device__ __forceinline__ void keep_candidate(uint32_t *sbuf, uint32_t &
 // head: with the live table the head is not a row prefix, so the whole row
 // is scanned (its head entries again, harmlessly); without it the scan
 // starts after the four head entries.
-static __device__ void scan_misses(const BfsArgs &a, MissQueue &mq, uint32_t &nq, uint32_t k, const uint32_t *F,
-                                   uint32_t *Fn, int d, bool table, uint32_t *sbuf, uint32_t &staged,
-                                   uint32_t *Lout, unsigned int *lout_cnt, unsigned long long &exam,
-                                   unsigned long long &lefte, uint32_t &mycnt, uint32_t &mydeg) {
+template <bool TABLE>
+static __device__ void scan_misses(const BfsArgs &a, PullRec *mq, uint32_t &nq, uint32_t k, const uint32_t *F,
+                                   uint32_t *Fn, int d, PullRec *kbuf, uint32_t &staged, void *Lout,
+                                   unsigned int *lout_cnt, uint32_t &exam, uint32_t &lefte, uint32_t &mycnt,
+                                   uint32_t &mydeg) {
     const uint32_t full = 0xffffffffu;
     const uint32_t NONE = 0xffffffffu;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const uint4 *ci4 = reinterpret_cast<const uint4 *>(a.ci_in);
     const uint32_t q0 = nq - k;
-    uint32_t v = NONE, c = 0, len = 0, dego = 0;
+    struct { uint32_t v, len, b, deg; } r = {NONE, 0, 0, 0};   // the head is re-read only to keep the record
     if ((uint32_t)lane < k) {
-        v = mq.v[warp][q0 + lane];
-        c = mq.c[warp][q0 + lane];
-        len = mq.len[warp][q0 + lane];
-        dego = mq.deg[warp][q0 + lane];
+        const uint4 x = *reinterpret_cast<const uint4 *>(&mq[q0 + lane]);
+        r.v = x.x; r.len = x.y; r.b = x.z; r.deg = x.w;
     }
-    __syncwarp();
-    nq = q0;
+    nq = q0;   // the entries stay intact until this warp queues again, after this call
     bool found = false;
     uint32_t par = 0, p = 0, e = 0;
-    if (v != NONE) {
-        const uint32_t b = __ldg(&a.rp_in[v]);
-        p = table ? b : b + 4;
-        e = b + len;
+    if (r.v != NONE) {
+        p = TABLE ? r.b : r.b + 4;
+        e = r.b + r.len;
     }
 #pragma unroll 1
-    for (int r = 0; r < PULL_ROUNDS; ++r) {
+    for (int rd = 0; rd < PULL_ROUNDS; ++rd) {
         const bool pend = p < e;
         if (!__any_sync(full, pend)) break;
         uint4 cw = make_uint4(0, 0, 0, 0);
@@ -213,10 +228,16 @@ static __device__ void scan_misses(const BfsArgs &a, MissQueue &mq, uint32_t &nq
         }
         if (lane == l && got) { found = true; par = gpar; }
     }
-    claim_found(a, Fn, d, found, v, par, dego, mycnt, mydeg);
-    const bool keep = v != NONE && !found;
-    if (keep) lefte += len;
-    keep_candidate(sbuf, staged, Lout, lout_cnt, keep, c);
+    claim_found(a, Fn, d, found, r.v, par, r.deg, mycnt, mydeg);
+    const bool keep = r.v != NONE && !found;
+    if (keep) lefte += r.len;
+    const uint32_t km = __ballot_sync(full, keep);
+    if (km) {
+        if (staged + __popc(km) > (uint32_t)PULL_KEEP_CAP) flush_kept<TABLE>(kbuf, staged, Lout, lout_cnt);
+        if (keep) kbuf[staged + __popc(km & dev::lanemask_lt())] = mq[q0 + lane];
+        staged += __popc(km);
+    }
+    __syncwarp();
 }
 
 // Pull over a list of candidates: for the first pull of a traversal every
@@ -225,24 +246,26 @@ static __device__ void scan_misses(const BfsArgs &a, MissQueue &mq, uint32_t &nq
 // them). Vertices without in-edges can never be reached by a pull, and a
 // later pull needs only what an earlier one left, so a pull touches
 // |candidates| vertices rather than all n. With the matrix's live table a
-// candidate is an index into the live list, and its four in-neighbours of
-// largest degree, in-degree and out-degree come with coalesced loads in
-// list order; the visited word and the frontier words of the first two head
-// entries are then loaded together, the other two only where those missed
-// (two dependent memory steps for almost every vertex). Without the table a
-// candidate is a vertex and its head is the first four entries of its row,
-// read through the row pointers. Warps take groups of PULL_WPW * 32
-// consecutive candidates, each lane PULL_WPW in flight. A candidate whose
-// head has no frontier vertex and whose row is longer than four goes to the
-// warp's miss queue, scanned 32 at a time (scan_misses). Found vertices set
-// their visited and next-frontier bits (one atomicOr per run of lanes in the
-// same bitmap word); the others are collected per warp in shared memory and
-// appended to the next list STAGE_CAP at a time. Pull writes the next
-// frontier as a bitmap and only counts it (vertices, out-edges); the list
-// form is built when a push needs it. It also counts the unvisited
-// candidates it walked and sums the in-degrees of those it leaves (what a
-// later pull over them reads at most).
-__device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Lin, uint32_t nin, uint32_t *Lout,
+// candidate is a pull record (vertex, CSC row, out-degree and its four
+// in-neighbours of largest out-degree, one 32-byte sector, read with two
+// coalesced 16-byte loads): the first pull reads the table itself, a later
+// one the records the previous pull kept, contiguous in its list. Without
+// the table a candidate is a vertex and its head is the first four entries
+// of its row, read through the row pointers. The visited word and the
+// frontier words of the four head entries load together (one dependent
+// step), so a candidate with a frontier vertex among its head is decided
+// there. Warps take groups of PULL_GROUP consecutive candidates, each lane
+// PULL_WPW. A candidate whose head has no frontier vertex and whose row is
+// longer than four goes to the warp's miss queue, scanned 32 at a time
+// (scan_misses). Found vertices set their visited and next-frontier bits
+// (one atomicOr per run of lanes in the same bitmap word); the others are
+// staged per warp and appended to the next list PULL_KEEP_CAP at a time.
+// Pull writes the next frontier as a bitmap and only counts it (vertices,
+// out-edges); the list form is built when a push needs it. It also counts
+// the unvisited candidates it walked and sums the in-degrees of those it
+// leaves (what a later pull over them reads at most).
+template <bool TABLE>
+__device__ void pull_level(const BfsArgs &a, PullSmem &ps, int d, const void *Lin, uint32_t nin, void *Lout,
                            unsigned int *lout_cnt, unsigned long long *examined, uint32_t *cnt_out,
                            uint32_t *deg_out, uint32_t *act_out, unsigned long long *left_edges) {
     const uint32_t *F = a.front[d % 3];
@@ -250,119 +273,120 @@ __device__ void pull_level(const BfsArgs &a, Smem &sm, int d, const uint32_t *Li
     const uint32_t full = 0xffffffffu;
     const uint32_t NONE = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool table = a.live_head != nullptr;
-    constexpr uint32_t GROUP = PULL_WPW * 32;
-    const uint32_t ngroups = (uint32_t)(((uint64_t)nin + GROUP - 1) / GROUP);
+    const uint32_t ngroups = (uint32_t)(((uint64_t)nin + PULL_GROUP - 1) / PULL_GROUP);
     const uint32_t nwarps = gridDim.x * WARPS;
-    unsigned long long exam = 0, lefte = 0;
+    const PullRec *recs = TABLE ? (Lin ? static_cast<const PullRec *>(Lin) : a.live_rec) : nullptr;
+    PullRec *kbuf = ps.keep[warp];
+    PullRec *mq = ps.miss[warp];
+    uint32_t exam = 0, lefte = 0;   // per thread and level these stay far below 2^32
     uint32_t mycnt = 0, mydeg = 0, myact = 0;
-    uint32_t *sbuf = sm.stage.v[warp];   // this warp's candidates for the next list
-    uint32_t staged = 0;
-    uint32_t nq = 0;                     // entries in this warp's miss queue
-    MissQueue &mq = sm.miss;
-    static_assert(GROUP <= STAGE_CAP, "a group's candidates fit the staging row");
-    static_assert(31 + GROUP <= MISS_CAP, "a group's misses fit the queue");
+    uint32_t nq = 0;       // entries in this warp's miss queue
+    uint32_t staged = 0;   // candidates staged for the next list
+    static_assert(31 + 32 <= PULL_MISS_CAP, "a lane slot's misses fit the queue");
     for (uint32_t g = blockIdx.x * WARPS + warp; g < ngroups; g += nwarps) {
-        uint32_t c[PULL_WPW], v[PULL_WPW], h[PULL_WPW][4], len[PULL_WPW], dego[PULL_WPW];
-        uint32_t par[PULL_WPW];
+        PullRec r[PULL_WPW];
         bool act[PULL_WPW], found[PULL_WPW];
+        uint32_t par[PULL_WPW];
 #pragma unroll
         for (int j = 0; j < PULL_WPW; ++j) {
-            uint32_t idx = g * GROUP + j * 32 + lane;
-            c[j] = idx < nin ? (Lin ? ldcg(&Lin[idx]) : idx) : NONE;
-        }
-        // the candidate's record: vertex, row head, degrees
-#pragma unroll
-        for (int j = 0; j < PULL_WPW; ++j) {
-            v[j] = NONE;
-            len[j] = dego[j] = 0;
-            h[j][0] = h[j][1] = h[j][2] = h[j][3] = NONE;
-            if (c[j] != NONE) {
-                if (table) {
-                    v[j] = ld_stream(&a.live[c[j]]);
-                    const uint4 hh = ld_stream(&a.live_head[c[j]]);
-                    h[j][0] = hh.x; h[j][1] = hh.y; h[j][2] = hh.z; h[j][3] = hh.w;
-                    len[j] = ld_stream(&a.live_len[c[j]]);
-                    dego[j] = a.csr_is_csc ? len[j] : ld_stream(&a.live_deg[c[j]]);
+            const uint32_t idx = g * PULL_GROUP + j * 32 + lane;
+            r[j].v = NONE;
+            r[j].len = r[j].b = r[j].deg = 0;
+            r[j].head = make_uint4(NONE, NONE, NONE, NONE);
+            if (idx < nin) {
+                if (TABLE) {
+                    const uint4 *q = reinterpret_cast<const uint4 *>(recs + idx);
+                    const uint4 x = ld_stream(q), y = ld_stream(q + 1);
+                    r[j].v = x.x; r[j].len = x.y; r[j].b = x.z; r[j].deg = x.w;
+                    r[j].head = y;
                 } else {
-                    v[j] = c[j];
-                    const uint32_t b = __ldg(&a.rp_in[v[j]]);
-                    len[j] = __ldg(&a.rp_in[v[j] + 1]) - b;
-                    dego[j] = a.csr_is_csc ? len[j] : NONE;   // read from the CSR once found
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if ((uint32_t)k < len[j]) h[j][k] = ld_stream(&a.ci_in[b + k]);
+                    const uint32_t v = Lin ? ldcg(&static_cast<const uint32_t *>(Lin)[idx]) : idx;
+                    r[j].v = v;
+                    r[j].b = __ldg(&a.rp_in[v]);
+                    r[j].len = __ldg(&a.rp_in[v + 1]) - r[j].b;
+                    r[j].deg = a.csr_is_csc ? r[j].len : NONE;   // read from the CSR once found
                 }
             }
         }
+        if (!TABLE) {
+#pragma unroll
+            for (int j = 0; j < PULL_WPW; ++j) {
+                uint32_t hh[4] = {NONE, NONE, NONE, NONE};
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (r[j].v != NONE && (uint32_t)k < r[j].len) hh[k] = ld_stream(&a.ci_in[r[j].b + k]);
+                r[j].head = make_uint4(hh[0], hh[1], hh[2], hh[3]);
+            }
+        }
         // the visited word and the frontier words of the first two head
-        // entries, together; the other two only where those did not hit
+        // entries, together; the other two only where those did not hit (every
+        // frontier word is a random sector lookup, and the first two decide
+        // most candidates)
         uint32_t vw[PULL_WPW], fw[PULL_WPW][4];
 #pragma unroll
         for (int j = 0; j < PULL_WPW; ++j) {
-            vw[j] = v[j] != NONE ? ldcg(&a.visited[v[j] >> 5]) : full;
+            const uint32_t h[2] = {r[j].head.x, r[j].head.y};
+            vw[j] = r[j].v != NONE ? ldcg(&a.visited[r[j].v >> 5]) : full;
 #pragma unroll
-            for (int k = 0; k < 2; ++k) fw[j][k] = h[j][k] != NONE ? ldcg(&F[h[j][k] >> 5]) : 0u;
+            for (int k = 0; k < 2; ++k) fw[j][k] = h[k] != NONE ? ldcg(&F[h[k] >> 5]) : 0u;
         }
 #pragma unroll
         for (int j = 0; j < PULL_WPW; ++j) {
-            act[j] = v[j] != NONE && !((vw[j] >> (v[j] & 31)) & 1u);
+            const uint32_t h[2] = {r[j].head.x, r[j].head.y};
+            act[j] = r[j].v != NONE && !((vw[j] >> (r[j].v & 31)) & 1u);
             found[j] = false;
             par[j] = 0;
 #pragma unroll
-            for (int k = 1; k >= 0; --k)   // the first frontier neighbour in row order
-                if (h[j][k] != NONE && ((fw[j][k] >> (h[j][k] & 31)) & 1u)) {
+            for (int k = 1; k >= 0; --k)   // the first frontier neighbour in head order
+                if (h[k] != NONE && ((fw[j][k] >> (h[k] & 31)) & 1u)) {
                     found[j] = true;
-                    par[j] = h[j][k];
+                    par[j] = h[k];
                 }
             found[j] = found[j] && act[j];
         }
 #pragma unroll
-        for (int j = 0; j < PULL_WPW; ++j)
+        for (int j = 0; j < PULL_WPW; ++j) {
+            const uint32_t h[2] = {r[j].head.z, r[j].head.w};
 #pragma unroll
-            for (int k = 2; k < 4; ++k)
-                fw[j][k] = (act[j] && !found[j] && h[j][k] != NONE) ? ldcg(&F[h[j][k] >> 5]) : 0u;
+            for (int k = 0; k < 2; ++k)
+                fw[j][2 + k] = (act[j] && !found[j] && h[k] != NONE) ? ldcg(&F[h[k] >> 5]) : 0u;
+        }
 #pragma unroll
         for (int j = 0; j < PULL_WPW; ++j) {
-            uint32_t ex = len[j] < 4 ? len[j] : 4;
+            uint32_t ex = r[j].len < 4 ? r[j].len : 4;
             if (act[j] && !found[j]) {
+                const uint32_t h[2] = {r[j].head.z, r[j].head.w};
 #pragma unroll
-                for (int k = 3; k >= 2; --k)
-                    if (h[j][k] != NONE && ((fw[j][k] >> (h[j][k] & 31)) & 1u)) {
+                for (int k = 1; k >= 0; --k)
+                    if (h[k] != NONE && ((fw[j][2 + k] >> (h[k] & 31)) & 1u)) {
                         found[j] = true;
-                        par[j] = h[j][k];
-                        ex = k + 1;
+                        par[j] = h[k];
+                        ex = k + 3;
                     }
             } else if (found[j]) {
-                ex = par[j] == h[j][0] ? 1 : 2;
+                ex = par[j] == r[j].head.x ? 1 : 2;
             }
             if (act[j]) { exam += ex; ++myact; }
         }
 #pragma unroll
         for (int j = 0; j < PULL_WPW; ++j) {
-            claim_found(a, Fn, d, found[j], v[j], par[j], dego[j], mycnt, mydeg);
+            claim_found(a, Fn, d, found[j], r[j].v, par[j], r[j].deg, mycnt, mydeg);
             // rows longer than four whose head missed: to the miss queue
-            const bool miss = act[j] && !found[j] && len[j] > 4;
+            const bool miss = act[j] && !found[j] && r[j].len > 4;
             const uint32_t mm = __ballot_sync(full, miss);
-            if (miss) {
-                const uint32_t at = nq + __popc(mm & dev::lanemask_lt());
-                mq.v[warp][at] = v[j];
-                mq.c[warp][at] = c[j];
-                mq.len[warp][at] = len[j];
-                mq.deg[warp][at] = dego[j];
-            }
+            if (miss) mq[nq + __popc(mm & dev::lanemask_lt())] = r[j];
             nq += __popc(mm);
             // rows of at most four entries are done: unvisited ones stay candidates
-            const bool keep = act[j] && !found[j] && len[j] > 0 && len[j] <= 4;
-            if (keep) lefte += len[j];
-            keep_candidate(sbuf, staged, Lout, lout_cnt, keep, c[j]);
+            const bool keep = act[j] && !found[j] && r[j].len > 0 && r[j].len <= 4;
+            if (keep) lefte += r[j].len;
+            keep_candidates<TABLE>(kbuf, staged, Lout, lout_cnt, keep, r[j]);
+            __syncwarp();
+            if (nq >= 32)
+                scan_misses<TABLE>(a, mq, nq, 32, F, Fn, d, kbuf, staged, Lout, lout_cnt, exam, lefte, mycnt, mydeg);
         }
-        __syncwarp();
-        while (nq >= 32)
-            scan_misses(a, mq, nq, 32, F, Fn, d, table, sbuf, staged, Lout, lout_cnt, exam, lefte, mycnt, mydeg);
     }
-    if (nq) scan_misses(a, mq, nq, nq, F, Fn, d, table, sbuf, staged, Lout, lout_cnt, exam, lefte, mycnt, mydeg);
-    flush_candidates(sbuf, staged, Lout, lout_cnt);
+    if (nq) scan_misses<TABLE>(a, mq, nq, nq, F, Fn, d, kbuf, staged, Lout, lout_cnt, exam, lefte, mycnt, mydeg);
+    flush_kept<TABLE>(kbuf, staged, Lout, lout_cnt);
     *examined += exam;
     *cnt_out += mycnt;
     *deg_out += mydeg;
@@ -388,36 +412,69 @@ __device__ __forceinline__ bool choose_pull(const BfsArgs &a, uint64_t fe, uint3
     return pull_reads <= push_reads;
 }
 
-__global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
-    __shared__ Smem sm;
-    __shared__ unsigned long long s_exam, s_left;
-    __shared__ uint32_t s_cnt, s_deg, s_act;
-    const uint64_t t_entry = dev::globaltimer_ns();
+union BfsShared {
+    Smem push;       // push levels and the bitmap -> list compaction
+    PullSmem pull;   // pull levels
+};
+
+// level and parent -1 for the vertices whose bit is set in unreached(w): each
+// lane loads one word, then the warp walks its 32 words with one broadcast
+// and one coalesced store per word (a single dependent load per warp)
+template <class Unreached>
+__device__ __forceinline__ void write_unreached(const BfsArgs &ar, Unreached unreached) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t nwarps = (uint64_t)gridDim.x * WARPS;
+    for (uint64_t w0 = ((uint64_t)blockIdx.x * WARPS + (threadIdx.x >> 5)) * 32; w0 < ar.nwords; w0 += nwarps * 32) {
+        const uint32_t mine = w0 + lane < ar.nwords ? unreached(w0 + lane) : 0u;
+        uint32_t todo = __ballot_sync(0xffffffffu, mine != 0u);
+        while (todo) {
+            const int k = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const uint32_t bits = __shfl_sync(0xffffffffu, mine, k);
+            if ((bits >> lane) & 1u) {
+                const uint64_t v = (w0 + k) * 32 + lane;
+                ar.levels[v] = -1;
+                if (ar.parents) ar.parents[v] = -1;
+            }
+        }
+    }
+}
+
+// One traversal from ar.src (Algorithm 1): its start (bitmaps, level-0 list,
+// counters), the levels, each ended by a grid barrier on bst, and the final
+// pass that gives unreached vertices -1. ar.st holds the traversal's
+// counters and result record; bst holds the barrier and the error word.
+// Returns false when a barrier wait ran out.
+__device__ bool bfs_run(const BfsArgs &ar, BfsState *bst, bool first, uint64_t t_entry, BfsShared &shm,
+                        unsigned long long *s_box, uint32_t *s_box32) {
+    Smem &sm = shm.push;
+    unsigned long long &s_exam = s_box[0], &s_left = s_box[1], &s_qs = s_box[2], &s_ue = s_box[3];
+    uint32_t &s_cnt = s_box32[0], &s_deg = s_box32[1], &s_act = s_box32[2], &s_uc = s_box32[3];
     const uint32_t nthreads = gridDim.x * BLOCK;
     const uint32_t tid = blockIdx.x * BLOCK + threadIdx.x;
-    BfsState *st = a.st;
+    BfsState *st = ar.st;
     BfsResult *res = &st->res;
-    // ---- init: bitmaps and the level-0 list (levels/parents of vertices
+    // ---- start: bitmaps and the level-0 list (levels/parents of vertices
     // that stay unreached are written at the end)
-    const uint32_t sw = a.src >> 5, sbit = 1u << (a.src & 31);
-    const uint32_t tail = (a.n & 31) ? ~((1u << (a.n & 31)) - 1u) : 0u;
-    for (uint64_t w = tid; w < a.nwords; w += nthreads) {
+    const uint32_t sw = ar.src >> 5, sbit = 1u << (ar.src & 31);
+    const uint32_t tail = (ar.n & 31) ? ~((1u << (ar.n & 31)) - 1u) : 0u;
+    for (uint64_t w = tid; w < ar.nwords; w += nthreads) {
         uint32_t vis = (w == sw ? sbit : 0u);
-        if (w == a.nwords - 1) vis |= tail;
-        a.visited[w] = vis;
-        a.front[0][w] = w == sw ? sbit : 0u;
-        a.front[1][w] = 0u;
-        a.front[2][w] = 0u;
+        if (w == ar.nwords - 1) vis |= tail;
+        ar.visited[w] = vis;
+        ar.front[0][w] = w == sw ? sbit : 0u;
+        ar.front[1][w] = 0u;
+        ar.front[2][w] = 0u;
     }
     if (tid == 0) {
-        uint32_t r0 = __ldg(&a.rp_out[a.src]);
-        uint32_t deg = __ldg(&a.rp_out[a.src + 1]) - r0;
-        a.levels[a.src] = 0;
-        if (a.parents) a.parents[a.src] = (int32_t)a.src;
-        a.q[0][0] = a.src;
-        a.qp[0][0] = 0;
-        a.qr[0][0] = r0;
-        st->qstate[0] = (1ull << a.ebits) | deg;
+        uint32_t r0 = __ldg(&ar.rp_out[ar.src]);
+        uint32_t deg = __ldg(&ar.rp_out[ar.src + 1]) - r0;
+        ar.levels[ar.src] = 0;
+        if (ar.parents) ar.parents[ar.src] = (int32_t)ar.src;
+        ar.q[0][0] = ar.src;
+        ar.qp[0][0] = 0;
+        ar.qr[0][0] = r0;
+        st->qstate[0] = (1ull << ar.ebits) | deg;
     }
     if (blockIdx.x == 0) {
         // block 0 zeroes the result record, then its thread 0 owns it
@@ -427,43 +484,43 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
         if (threadIdx.x == 0) res->t_entry = t_entry;
     }
     bool ok;
-    if (a.withhold && blockIdx.x == 0 && gridDim.x > 1) {
+    if (first && ar.withhold && blockIdx.x == 0 && gridDim.x > 1) {
         // failure-path test: this block never arrives, so the bounded wait of
         // the others runs out; it waits (bounded too) until they record it
-        ok = dev::wait_for_error(&st->err, 2 * a.timeout_ns);
+        ok = dev::wait_for_error(&bst->err, 2 * ar.timeout_ns);
     } else {
-        ok = dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns);
+        ok = dev::grid_sync(&bst->bar, gridDim.x, &bst->err, ar.timeout_ns);
     }
     const uint64_t t_start = dev::globaltimer_ns();
     uint64_t reached = 0;
     // previous level's numbers for the algorithmic byte count
     uint32_t prev_dir = 0, prev_cnt = 0, prev_nin = 0;
     uint64_t prev_fe = 0;
-    double alg = 8.0 * a.n;   // levels + parents writes
+    double alg = 8.0 * ar.n;   // levels + parents writes
     bool list_valid = true;    // the list form of the current frontier exists
     int npull = 0;             // pull steps so far (selects the candidate lists)
     // the source's component size: once that many vertices are reached the
     // last frontier has nothing left to discover and is not expanded
-    const uint32_t csize = a.comp_size ? __ldg(&a.comp_size[a.src]) : 0u;
+    const uint32_t csize = ar.comp_size ? __ldg(&ar.comp_size[ar.src]) : 0u;
     bool exhausted = false;
     int d = 0;
     for (; ok; ++d) {
         if (threadIdx.x == 0) {
-            sm.qs = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>(st->qstate[d % 3])
-                        .load(cuda::memory_order_relaxed);
+            s_qs = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>(st->qstate[d % 3])
+                       .load(cuda::memory_order_relaxed);
             if (npull > 0) {
-                sm.uc = (uint32_t)dev::ld_relaxed_gpu_int((const int *)&st->ucnt[(npull - 1) % 3]);
-                sm.ue = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>(st->uedg[(npull - 1) % 3])
-                            .load(cuda::memory_order_relaxed);
+                s_uc = (uint32_t)dev::ld_relaxed_gpu_int((const int *)&st->ucnt[(npull - 1) % 3]);
+                s_ue = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>(st->uedg[(npull - 1) % 3])
+                           .load(cuda::memory_order_relaxed);
             }
         }
         __syncthreads();
-        const unsigned long long qs = sm.qs;
-        const uint32_t uc = npull > 0 ? sm.uc : 0u;
-        const unsigned long long ue = npull > 0 ? sm.ue : 0ull;
+        const unsigned long long qs = s_qs;
+        const uint32_t uc = npull > 0 ? s_uc : 0u;
+        const unsigned long long ue = npull > 0 ? s_ue : 0ull;
         __syncthreads();
-        uint32_t cnt = (uint32_t)(qs >> a.ebits);
-        uint64_t fe = qs & a.emask;
+        uint32_t cnt = (uint32_t)(qs >> ar.ebits);
+        uint64_t fe = qs & ar.emask;
         if (tid == 0 && d > 0) {
             unsigned long long ex = st->exam[(d - 1) % 3];
             if (prev_dir == 0) {
@@ -471,7 +528,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
             } else {
                 // the mask words the pull reads, the row pointers of the unvisited candidates it
                 // walked, the adjacency entries it examined and the discoveries it wrote
-                const double mask = a.n / 8.0 < 4.0 * prev_nin ? a.n / 8.0 : 4.0 * prev_nin;
+                const double mask = ar.n / 8.0 < 4.0 * prev_nin ? ar.n / 8.0 : 4.0 * prev_nin;
                 alg += mask + 8.0 * (double)st->uact[(d - 1) % 3] + 4.0 * ex + 12.0 * cnt;
             }
             res->edges_examined += prev_dir == 0 ? prev_fe : ex;
@@ -483,10 +540,10 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
             break;
         }
         // guard: no BFS has more than n levels; the traversal has a wall-clock budget
-        if (d > (int)a.n || (threadIdx.x == 0 && dev::globaltimer_ns() - t_start > a.total_limit_ns)) {
-            atomicCAS(&st->err, 0, (int)GB_TIMEOUT);
+        if (d > (int)ar.n || (threadIdx.x == 0 && dev::globaltimer_ns() - t_start > ar.total_limit_ns)) {
+            atomicCAS(&bst->err, 0, (int)GB_TIMEOUT);
         }
-        const bool pull = choose_pull(a, fe, cnt, npull, list_valid, uc, ue);
+        const bool pull = choose_pull(ar, fe, cnt, npull, list_valid, uc, ue);
         if (tid == 0) {
             if (d < GBX_MAX_LEVEL_LOG) {
                 res->dir_log[d] = pull ? 2 : 1;
@@ -495,32 +552,31 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
                 res->lv_ns[d] = dev::globaltimer_ns();
             }
             if (pull) res->pull_levels++; else res->push_levels++;
+            res->frontier_edges += fe;
             st->qstate[(d + 2) % 3] = 0;
             st->exam[(d + 2) % 3] = 0;
             st->uact[(d + 2) % 3] = 0;
             st->cstate[(d + 2) % 3] = 0;
-            res->frontier_edges += fe;
             prev_dir = pull ? 1u : 0u;
             prev_cnt = cnt;
             prev_fe = fe;
         }
         reached += cnt;
-        uint32_t *Fclr = a.front[(d + 2) % 3];
-        for (uint64_t w = tid; w < a.nwords; w += nthreads) Fclr[w] = 0u;
+        uint32_t *Fclr = ar.front[(d + 2) % 3];
+        for (uint64_t w = tid; w < ar.nwords; w += nthreads) Fclr[w] = 0u;
         if (pull) {
             if (threadIdx.x == 0) { s_exam = 0; s_left = 0; s_cnt = 0; s_deg = 0; s_act = 0; }
             __syncthreads();
-            // candidates: all live ones for the first pull, then what the previous pull left;
-            // with the live table a candidate is a live-list index, otherwise a vertex
-            const uint32_t *Lin;
+            // candidates: all live ones for the first pull, then what the previous pull left
+            const void *Lin;
             uint32_t nin;
             if (npull == 0) {
-                // every candidate once: the live-list indices 0..count-1 (with
-                // the live table), otherwise the vertices 0..n-1
+                // every candidate once: the live table's records (with the
+                // table), otherwise the vertices 0..n-1
                 Lin = nullptr;
-                nin = a.live ? ldcg(a.live_count) : a.n;
+                nin = ar.live_rec ? ldcg(ar.live_count) : ar.n;
             } else {
-                Lin = a.ul[(npull - 1) & 1];
+                Lin = ar.ul[(npull - 1) & 1];
                 nin = (uint32_t)dev::ld_relaxed_gpu_int((const int *)&st->ucnt[(npull - 1) % 3]);
             }
             if (tid == 0) {
@@ -531,7 +587,10 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
             const int us = npull % 3;
             unsigned long long ex = 0, le = 0;
             uint32_t c = 0, dg = 0, na = 0;
-            pull_level(a, sm, d, Lin, nin, a.ul[npull & 1], &st->ucnt[us], &ex, &c, &dg, &na, &le);
+            if (ar.live_rec)
+                pull_level<true>(ar, shm.pull, d, Lin, nin, ar.ul[npull & 1], &st->ucnt[us], &ex, &c, &dg, &na, &le);
+            else
+                pull_level<false>(ar, shm.pull, d, Lin, nin, ar.ul[npull & 1], &st->ucnt[us], &ex, &c, &dg, &na, &le);
             ++npull;
             ex = dev::warp_sum<unsigned long long>(ex);
             le = dev::warp_sum<unsigned long long>(le);
@@ -549,63 +608,48 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
                 if (s_exam) atomicAdd(&st->exam[d % 3], s_exam);
                 if (s_left) atomicAdd(&st->uedg[us], s_left);
                 if (s_act) atomicAdd(&st->uact[d % 3], (unsigned long long)s_act);
-                if (s_cnt) atomicAdd(&st->qstate[(d + 1) % 3], ((unsigned long long)s_cnt << a.ebits) | s_deg);
+                if (s_cnt) atomicAdd(&st->qstate[(d + 1) % 3], ((unsigned long long)s_cnt << ar.ebits) | s_deg);
             }
             list_valid = false;
         } else {
             if (!list_valid) {
-                compact_level(a, sm, d);
-                if (!dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns)) { ok = false; break; }
+                compact_level(ar, sm, d);
+                if (!dev::grid_sync(&bst->bar, gridDim.x, &bst->err, ar.timeout_ns)) { ok = false; break; }
             }
-            push_level(a, sm, d, cnt, fe);
+            push_level(ar, sm, d, cnt, fe);
             list_valid = true;
         }
-        ok = dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns);
+        ok = dev::grid_sync(&bst->bar, gridDim.x, &bst->err, ar.timeout_ns);
     }
     if (tid == 0) {
         res->t_end = dev::globaltimer_ns();
         if (d < GBX_MAX_LEVEL_LOG) res->lv_ns[d] = res->t_end;
     }
-    // ---- vertices never reached get level and parent -1: each lane loads
-    // one visited word, then the warp walks its 32 words with one broadcast
-    // and one coalesced store per word (a single dependent load per warp)
-    if (ok) {
-        const int lane = threadIdx.x & 31;
-        const uint64_t nwarps = (uint64_t)gridDim.x * WARPS;
-        for (uint64_t w0 = ((uint64_t)blockIdx.x * WARPS + (threadIdx.x >> 5)) * 32; w0 < a.nwords;
-             w0 += nwarps * 32) {
-            const uint32_t mine = w0 + lane < a.nwords ? ldcg(&a.visited[w0 + lane]) : ~0u;
-            uint32_t todo = __ballot_sync(0xffffffffu, mine != ~0u);
-            while (todo) {
-                const int k = __ffs(todo) - 1;
-                todo &= todo - 1;
-                const uint32_t bits = __shfl_sync(0xffffffffu, mine, k);
-                if (!((bits >> lane) & 1u)) {
-                    const uint64_t v = (w0 + k) * 32 + lane;
-                    a.levels[v] = -1;
-                    if (a.parents) a.parents[v] = -1;
-                }
-            }
-        }
-    }
+    // ---- vertices never reached get level and parent -1
+    if (ok) write_unreached(ar, [&](uint64_t w) -> uint32_t { return ~ldcg(&ar.visited[w]); });
     if (tid == 0) {
         res->depth = d + (exhausted ? 1 : 0);
         res->reached = reached;
         res->alg_bytes = alg;
         res->t_begin = t_start;
     }
-    // ---- leave: the last block out resets the working state for the next launch
+    return ok;
+}
+
+// The last block to leave resets the working state for the next launch.
+__device__ void bfs_leave(const BfsArgs &a) {
     __syncthreads();
     if (threadIdx.x == 0) {
+        BfsState *st = a.st;
         __threadfence();
         unsigned int old = atomicAdd(&st->bar.exits, 1u);
         if (old == gridDim.x - 1) {
             __threadfence();
             const int e = ld_relaxed_gpu_int_(&st->err);
-            res->err = e;
+            st->res.err = e;
             if (e && a.err_sticky) atomicMax(a.err_sticky, e);
             if (a.status_out) *a.status_out = e;
-            res->t_exit = dev::globaltimer_ns();
+            st->res.t_exit = dev::globaltimer_ns();
             st->err = 0;
             st->bar.count = 0;
             for (int k = 0; k < 3; ++k) {
@@ -616,6 +660,15 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
             st->bar.exits = 0;
         }
     }
+}
+
+__global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
+    __shared__ BfsShared shm;
+    __shared__ unsigned long long s_box[4];
+    __shared__ uint32_t s_box32[4];
+    const uint64_t t_entry = dev::globaltimer_ns();
+    bfs_run(a, a.st, true, t_entry, shm, s_box, s_box32);
+    bfs_leave(a);
 }
 
 }  // namespace bfsk
@@ -629,7 +682,8 @@ gb_info bfs_cluster_result(gb_context *ctx, const void *state, gb_bfs_stats *sta
 
 struct BfsWorkspace {
     uint32_t n = 0;
-    uint32_t *visited = nullptr, *front = nullptr, *q = nullptr, *qp = nullptr, *qr = nullptr, *ul = nullptr;
+    uint32_t *visited = nullptr, *front = nullptr, *q = nullptr, *qp = nullptr, *qr = nullptr;
+    PullRec *ul = nullptr;   // two candidate lists of pull records
     BfsState *st = nullptr;
     void *cl_state = nullptr;   // state block of the single-cluster schedule
     int grid = 0;
@@ -651,7 +705,7 @@ gb_info bfs_workspace(gb_context *ctx, uint32_t n, BfsWorkspace **out) {
         GB_CHECK(dalloc_t(ctx, &w.q, 2ull * n + 2));
         GB_CHECK(dalloc_t(ctx, &w.qp, 2ull * n + 2));
         GB_CHECK(dalloc_t(ctx, &w.qr, 2ull * n + 2));
-        GB_CHECK(dalloc_t(ctx, &w.ul, 2ull * n + 2));
+        GB_CHECK(dalloc(ctx, (void **)&w.ul, (2ull * n + 2) * sizeof(PullRec) + 16));
         GB_CHECK(dalloc_t(ctx, &w.st, 1));
         GB_CHECK(dalloc(ctx, &w.cl_state, bfs_cluster_state_bytes()));
         // the only reset of the working state: launches leave it zeroed
@@ -735,11 +789,8 @@ gb_info bfs_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *l
     a.q[0] = w->q; a.q[1] = w->q + A->nrows + 1;
     a.qp[0] = w->qp; a.qp[1] = w->qp + A->nrows + 1;
     a.qr[0] = w->qr; a.qr[1] = w->qr + A->nrows + 1;
-    a.live = A->has_csc ? A->live_list : nullptr;
-    a.live_count = A->has_csc ? A->live_count : nullptr;
-    a.live_head = a.live ? A->live_head : nullptr;
-    a.live_len = a.live ? A->live_len : nullptr;
-    a.live_deg = a.live ? A->live_deg : nullptr;
+    a.live_rec = A->has_csc ? A->live_rec : nullptr;
+    a.live_count = a.live_rec ? A->live_count : nullptr;
     a.ul[0] = w->ul; a.ul[1] = w->ul + A->nrows + 1;
     a.comp_size = A->comp_size;
     a.ebits = 64 - bits_for((uint64_t)A->nrows + 1);
@@ -1038,11 +1089,9 @@ extern "C" gb_info gb_bfs_noalloc(const uint32_t *rowptr, const uint32_t *colidx
     a.q[0] = (uint32_t *)(base + OFF_Q); a.q[1] = a.q[0] + n + 1;
     a.qp[0] = (uint32_t *)(base + OFF_QP); a.qp[1] = a.qp[0] + n + 1;
     a.qr[0] = (uint32_t *)(base + OFF_QR); a.qr[1] = a.qr[0] + n + 1;
-    a.live = nullptr;            // no cached list here: the first pull takes every vertex
+    a.live_rec = nullptr;        // no live table here: the first pull takes every vertex
     a.live_count = nullptr;
-    a.live_head = nullptr;
-    a.live_len = a.live_deg = nullptr;
-    a.ul[0] = (uint32_t *)(base + OFF_UL); a.ul[1] = a.ul[0] + n + 1;
+    a.ul[0] = (uint32_t *)(base + OFF_UL); a.ul[1] = (uint32_t *)(base + OFF_UL) + n + 1;
     a.comp_size = nullptr;
     a.ebits = 64 - bits_for((uint64_t)n + 1);
     a.emask = (1ull << a.ebits) - 1;

@@ -39,9 +39,9 @@ struct BfsState {
     unsigned int pad1;
     unsigned long long uedg[3];        // in-edges of the candidates a pull leaves, per pull slot
     unsigned long long uact[3];        // unvisited candidates a pull walked, per level slot
+    unsigned int far_cnt;              // SSSP near-far: vertices in the far set
     int sticky;                        // max of the exit codes of launches nobody has waited for yet
                                        // (launches leave it as it is; gb_context_synchronize reads and clears it)
-    int pad2;
     BfsResult res;
 };
 
@@ -56,12 +56,10 @@ struct BfsArgs {
     uint32_t *visited;
     uint32_t *front[3];
     uint32_t *q[2], *qp[2], *qr[2];    // frontier list: vertex, out-edge prefix, row start
-    const uint32_t *live;              // vertices with an in-edge (ascending); null = all vertices
-    const uint32_t *live_count;        // device scalar: length of live
-    const uint4 *live_head;            // per live entry: four in-neighbours of largest degree (0xffffffff = none)
-    const uint32_t *live_len;          // per live entry: in-degree
-    const uint32_t *live_deg;          // per live entry: out-degree
-    uint32_t *ul[2];                   // candidate lists of the pull steps (unvisited, with in-edges)
+    const PullRec *live_rec;           // pull records of the vertices with an in-edge (ascending); null = none
+    const uint32_t *live_count;        // device scalar: number of records
+    void *ul[2];                       // candidate lists of the pull steps (unvisited, with in-edges): pull
+                                       // records with the live table, vertex ids without it
     const uint32_t *comp_size;         // per vertex, its component's size; null = unknown
     int ebits;
     unsigned long long emask;

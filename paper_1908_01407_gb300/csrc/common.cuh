@@ -61,6 +61,16 @@ struct gb_context_t {
     int grid_limit = 0;
 };
 
+// One pull candidate (a vertex with an in-edge), as a BFS pull reads it:
+// one 32-byte sector holding everything the pull needs before the row
+// itself. head = its four in-neighbours of largest out-degree
+// (0xffffffff = none), b and len = its CSC row, deg = its out-degree.
+struct PullRec {
+    uint32_t v, len, b, deg;
+    uint4 head;
+};
+static_assert(sizeof(PullRec) == 32, "a pull record is one 32-byte sector");
+
 // In-rows longer than this are "hubs": the pull kernels (SSSP/CC relaxation,
 // multi-source BFS) split their edges over the whole grid instead of giving
 // each one to a single warp. The matrix caches the hub list for this length.
@@ -91,21 +101,25 @@ struct gb_matrix_t {
     uint32_t tuned_beta = 0;
     // BFS schedule chosen by gb_bfs_autotune (GB_SCHED_AUTO = not tuned)
     int tuned_schedule = GB_SCHED_AUTO;
+    // PageRank SpMV tile (128-nonzero sub-tiles per warp tile) chosen by
+    // gb_pagerank_autotune (0 = not tuned)
+    uint32_t tuned_pr_nsub = 0;
     // vertices with at least one in-edge (nonempty CSC row), ascending,
     // built with the CSC; live_count is a device scalar (live_list[nrows])
     uint32_t *live_list = nullptr;
     uint32_t *live_count = nullptr;
-    // per live vertex, in live-list order: its four in-neighbours of largest
-    // out-degree (0xffffffff for rows shorter than four), its in-degree, its
-    // out-degree
-    uint4 *live_head = nullptr;
-    uint32_t *live_len = nullptr;
-    uint32_t *live_deg = nullptr;    // == live_len for a symmetric matrix
+    // per live vertex, in live-list order, its pull record (vertex, CSC row,
+    // out-degree and the four in-neighbours of largest out-degree)
+    PullRec *live_rec = nullptr;
+    // bit v set when vertex v has no in-edge (no pull and no push can reach it;
+    // bits past nrows set too), built with the live table
     // per vertex, the size of its weakly connected component (built by
     // gb_matrix_build for a square matrix with a CSC): a traversal that has
     // reached that many vertices can stop without expanding its last frontier
     uint32_t *comp_size = nullptr;
-    // guards the caches built on first use (hub list)
+    // mean stored value (uint32 weights), computed on first use by SSSP; 0 = not yet
+    double mean_weight = 0;
+    // guards the caches built on first use (hub list, mean weight)
     std::mutex cache_mu;
 };
 
@@ -130,6 +144,7 @@ struct gb_desc_t {
     int direction = GB_AUTO;
     int beta = 0;
     int schedule = GB_SCHED_AUTO;
+    int sssp_delta = 0;
 };
 
 // ------------------------------------------------------------------ memory

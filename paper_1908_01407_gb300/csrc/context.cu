@@ -322,6 +322,9 @@ gb_info gb_desc_set(gb_desc *d, gb_field field, int value) {
         if (value < GB_SCHED_AUTO || value > GB_SCHED_CLUSTER)
             return fail(GB_INVALID_VALUE, "bad GB_SCHEDULE value %d", value);
         d->schedule = value; break;
+    case GB_SSSP_DELTA:
+        if (value < 0) return fail(GB_INVALID_VALUE, "bad GB_SSSP_DELTA value %d", value);
+        d->sssp_delta = value; break;
     default:
         return fail(GB_INVALID_VALUE, "unknown descriptor field %d", (int)field);
     }
@@ -338,6 +341,7 @@ gb_info gb_desc_get(const gb_desc *d, gb_field field, int *value) {
     case GB_DIRECTION: *value = d->direction; break;
     case GB_SCHEDULE: *value = d->schedule; break;
     case GB_SWITCH_BETA: *value = d->beta; break;
+    case GB_SSSP_DELTA: *value = d->sssp_delta; break;
     default: return fail(GB_INVALID_VALUE, "unknown descriptor field %d", (int)field);
     }
     return GB_SUCCESS;

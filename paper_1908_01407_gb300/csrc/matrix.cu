@@ -58,14 +58,11 @@ void release(gb_matrix *A) {
     dfree(ctx, A->colptr); dfree(ctx, A->rowidx); dfree(ctx, A->cvals);
     dfree(ctx, A->hub_list); dfree(ctx, A->hub_pre);
     dfree(ctx, A->live_list);
-    dfree(ctx, A->live_head);
-    dfree(ctx, A->live_len);
-    if (A->live_deg != A->live_len) dfree(ctx, A->live_deg);
+    dfree(ctx, A->live_rec);
     dfree(ctx, A->comp_size);
     A->comp_size = nullptr;
     A->live_list = A->live_count = nullptr;
-    A->live_head = nullptr;
-    A->live_len = A->live_deg = nullptr;
+    A->live_rec = nullptr;
     A->hub_list = A->hub_pre = nullptr;
     A->nhub = 0; A->hub_edges = 0; A->hub_ready = false;
     A->rowptr = A->colidx = A->colptr = A->rowidx = nullptr;
@@ -97,8 +94,7 @@ __global__ void k_live_emit(const uint32_t *flag, const uint32_t *pos, uint32_t 
 // frontier early.
 constexpr uint32_t LIVE_HEAD_SCAN = 256;
 __global__ void k_live_table(const uint32_t *list, const uint32_t *count, const uint32_t *colptr,
-                             const uint32_t *rowidx, const uint32_t *rowptr, uint4 *head, uint32_t *len,
-                             uint32_t *deg) {
+                             const uint32_t *rowidx, const uint32_t *rowptr, PullRec *rec) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= *count) return;
     const uint32_t v = list[i];
@@ -119,18 +115,22 @@ __global__ void k_live_table(const uint32_t *list, const uint32_t *count, const 
         best[p] = u;
         bd[p] = du;
     }
-    head[i] = make_uint4(best[0], best[1], best[2], best[3]);
-    len[i] = l;
-    if (deg != len) deg[i] = rowptr[v + 1] - rowptr[v];
+    PullRec r;
+    r.v = v;
+    r.len = l;
+    r.b = b;
+    r.deg = rowptr[v + 1] - rowptr[v];
+    r.head = make_uint4(best[0], best[1], best[2], best[3]);
+    rec[i] = r;
 }
 }  // namespace
 
 // The ascending list of vertices with a nonempty CSC row (an in-edge): the
 // only vertices a pull step can ever reach, with, in list order, each one's
-// four in-neighbours of largest out-degree, in-degree and out-degree (so a
-// pull over the list reads its candidates with coalesced loads and needs the
-// row pointers only for rows longer than four whose head has no frontier
-// vertex). The list length stays on the device.
+// pull record (its CSC row, out-degree and four in-neighbours of largest
+// out-degree; 32 bytes, so a pull reads a candidate with one sector and
+// needs the row itself only when the head has no frontier vertex). The list
+// length stays on the device.
 gb_info matrix_live(gb_matrix *A) {
     gb_context *ctx = A->ctx;
     const uint32_t n = A->ncols;
@@ -142,13 +142,10 @@ gb_info matrix_live(gb_matrix *A) {
     if (n) k_live_flags<<<nblk(n), 256, 0, ctx->stream>>>(A->colptr, n, flag.as<uint32_t>());
     GB_CHECK(scan_exclusive_u32(ctx, flag.as<uint32_t>(), pos.as<uint32_t>(), n, A->live_count));
     if (n) k_live_emit<<<nblk(n), 256, 0, ctx->stream>>>(flag.as<uint32_t>(), pos.as<uint32_t>(), n, A->live_list);
-    GB_CHECK(dalloc_t(ctx, &A->live_head, (size_t)n + 1));
-    GB_CHECK(dalloc_t(ctx, &A->live_len, (size_t)n + 1));
-    if (A->csc_alias) A->live_deg = A->live_len;
-    else GB_CHECK(dalloc_t(ctx, &A->live_deg, (size_t)n + 1));
+    GB_CHECK(dalloc_t(ctx, &A->live_rec, (size_t)n + 1));
     if (n)
         k_live_table<<<nblk(n), 256, 0, ctx->stream>>>(A->live_list, A->live_count, A->colptr, A->rowidx, A->rowptr,
-                                                       A->live_head, A->live_len, A->live_deg);
+                                                       A->live_rec);
     GB_LAUNCH_CHECK();
     return GB_SUCCESS;
 }

@@ -227,6 +227,126 @@ __global__ void k_emit_old(const uint32_t *keep, const uint32_t *pos, uint64_t n
     }
 }
 
+// ---- mxm without a mask or with a complemented mask: expand, sort, compress.
+// Every product A(i,k) (x) B(k,j) becomes a tuple (i, j, value); the device
+// build then sorts the tuples and reduces equal positions with the
+// semiring's add, as the paper's SpMSpV reduces its expanded products by
+// radix sort (Section 6.3.1).
+
+// rows[q] = the row of stored entry q of a compressed structure (ptr, n rows)
+__global__ void k_expand_ptr(const uint32_t *ptr, uint32_t n, uint32_t *rows) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        for (uint32_t q = ptr[i]; q < ptr[i + 1]; ++q) rows[q] = i;
+}
+
+// products of entry q of op(A): the length of op(B)'s row a_idx[q]
+__global__ void k_product_counts(const uint32_t *a_idx, uint64_t na, const uint32_t *b_ptr, uint32_t *cnt) {
+    const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < na) cnt[q] = b_ptr[a_idx[q] + 1] - b_ptr[a_idx[q]];
+}
+
+template <typename T, Mul MU>
+__global__ void k_products(const uint32_t *arows, const uint32_t *a_idx, const T *a_vals, uint64_t na,
+                           const uint32_t *b_ptr, const uint32_t *b_idx, const T *b_vals, const uint32_t *off,
+                           uint32_t *orow, uint32_t *ocol, T *oval) {
+    const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= na) return;
+    const uint32_t i = arows[q], k = a_idx[q];
+    const T a = a_vals ? a_vals[q] : (T)1;
+    uint32_t o = off[q];
+    for (uint32_t p = b_ptr[k]; p < b_ptr[k + 1]; ++p, ++o) {
+        orow[o] = i;
+        ocol[o] = b_idx[p];
+        oval[o] = mul_op<T, MU>(a, b_vals ? b_vals[p] : (T)1);
+    }
+}
+
+// is (i, j) allowed by the mask M (a stored nonzero, or any stored entry
+// when structural)? The complement inverts it.
+template <typename MT>
+__device__ __forceinline__ bool mask_has(const uint32_t *m_ptr, const uint32_t *m_idx, const MT *m_vals,
+                                         bool structural, uint32_t i, uint32_t j) {
+    uint32_t pos = 0;
+    bool in = bsearch_u32(m_idx, m_ptr[i], m_ptr[i + 1], j, &pos);
+    if (in && !structural && m_vals && m_vals[pos] == (MT)0) in = false;
+    return in;
+}
+
+template <typename MT>
+__global__ void k_product_allowed(const uint32_t *orow, const uint32_t *ocol, uint64_t np, const uint32_t *m_ptr,
+                                  const uint32_t *m_idx, const MT *m_vals, bool structural, uint32_t *flag) {
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < np) flag[t] = mask_has<MT>(m_ptr, m_idx, m_vals, structural, orow[t], ocol[t]) ? 0u : 1u;
+}
+
+template <typename T>
+__global__ void k_compact_products(const uint32_t *flag, const uint32_t *pos, uint64_t np, const uint32_t *orow,
+                                   const uint32_t *ocol, const T *oval, uint32_t *r2, uint32_t *c2, T *v2) {
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < np && flag[t]) {
+        r2[pos[t]] = orow[t];
+        c2[pos[t]] = ocol[t];
+        v2[pos[t]] = oval[t];
+    }
+}
+
+// entries of the old C against the product T (sorted rows): an entry at a
+// position of T is accumulated into T's value (accum) or replaced by it; one
+// elsewhere stays when the mask allows it and there is an accumulator, or
+// when the mask does not allow it and there is no REPLACE
+template <typename T, typename MT>
+__global__ void k_merge_old_c(const uint32_t *crows, const uint32_t *cidx, const T *cvals, uint64_t nc,
+                              const uint32_t *t_ptr, const uint32_t *t_idx, T *t_vals, const uint32_t *m_ptr,
+                              const uint32_t *m_idx, const MT *m_vals, bool has_mask, bool structural, bool scmp,
+                              gb_binop accum, bool replace, uint32_t *keep) {
+    const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nc) return;
+    const uint32_t i = crows[q], j = cidx[q];
+    const T c = cvals ? cvals[q] : (T)1;
+    uint32_t pos = 0;
+    keep[q] = 0;
+    if (bsearch_u32(t_idx, t_ptr[i], t_ptr[i + 1], j, &pos)) {
+        if (accum != GB_NOP) t_vals[pos] = apply_binop<T>(accum, c, t_vals[pos]);
+        return;
+    }
+    const bool allowed = has_mask ? (mask_has<MT>(m_ptr, m_idx, m_vals, structural, i, j) != scmp) : !scmp;
+    keep[q] = (allowed ? accum != GB_NOP : !replace) ? 1u : 0u;
+}
+
+template <typename T>
+gb_info mxm_expand(gb_context *ctx, gb_semiring s, const uint32_t *arows, const uint32_t *a_idx, const void *a_vals,
+                   uint64_t na, const uint32_t *b_ptr, const uint32_t *b_idx, const void *b_vals, const uint32_t *off,
+                   uint32_t *orow, uint32_t *ocol, void *oval) {
+    const T *av = (const T *)a_vals, *bv = (const T *)b_vals;
+    T *ov = (T *)oval;
+    const unsigned g = nblk(na);
+    if (!na) return GB_SUCCESS;
+    switch (s) {
+    case GB_PLUS_TIMES: case GB_MIN_TIMES:
+        k_products<T, Mul::TIMES><<<g, 256, 0, ctx->stream>>>(arows, a_idx, av, na, b_ptr, b_idx, bv, off, orow, ocol, ov); break;
+    case GB_MIN_PLUS: case GB_MAX_PLUS:
+        k_products<T, Mul::SATPLUS><<<g, 256, 0, ctx->stream>>>(arows, a_idx, av, na, b_ptr, b_idx, bv, off, orow, ocol, ov); break;
+    case GB_MIN_SECOND:
+        k_products<T, Mul::SECOND><<<g, 256, 0, ctx->stream>>>(arows, a_idx, av, na, b_ptr, b_idx, bv, off, orow, ocol, ov); break;
+    case GB_PLUS_PAIR:
+        k_products<T, Mul::PAIR><<<g, 256, 0, ctx->stream>>>(arows, a_idx, av, na, b_ptr, b_idx, bv, off, orow, ocol, ov); break;
+    case GB_LOR_LAND:
+        k_products<T, Mul::LAND><<<g, 256, 0, ctx->stream>>>(arows, a_idx, av, na, b_ptr, b_idx, bv, off, orow, ocol, ov); break;
+    }
+    GB_LAUNCH_CHECK();
+    return GB_SUCCESS;
+}
+
+// the build's duplicate operator that is the semiring's add monoid
+gb_binop semiring_add_op(gb_semiring s) {
+    switch (s) {
+    case GB_PLUS_TIMES: case GB_PLUS_PAIR: return GB_PLUS;
+    case GB_LOR_LAND: return GB_LOR;
+    case GB_MAX_PLUS: return GB_MAX;
+    default: return GB_MIN;
+    }
+}
+
 struct Desc {
     bool scmp = false, structure = false, replace = false, tran0 = false, tran1 = false;
     int direction = GB_AUTO;
@@ -374,6 +494,149 @@ void host_accum(void *out, gb_binop accum, T r) {
     *o = accum == GB_NOP ? r : apply_binop<T>(accum, *o, r);
 }
 
+__global__ void k_sum_u32(const uint32_t *x, uint64_t n, unsigned long long *total) {
+    unsigned long long acc = 0;
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (uint64_t)gridDim.x * blockDim.x)
+        acc += x[q];
+    acc = dev::warp_sum<unsigned long long>(acc);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(total, acc);
+}
+
+// C<M> = accum(C, A (+).(x) B) where M is absent or complemented (the
+// masked product of the same call computes only M's positions instead).
+gb_info mxm_general(gb_matrix *C, const gb_matrix *M, gb_binop accum, gb_semiring s, const gb_matrix *A,
+                    const gb_matrix *B, const Desc &d) {
+    gb_context *ctx = C->ctx;
+    const gb_type t = C->type;
+    const size_t vs = type_size(t);
+    // rows of op(A) and of op(B)
+    const uint32_t *a_ptr = d.tran0 ? A->colptr : A->rowptr, *a_idx = d.tran0 ? A->rowidx : A->colidx;
+    const void *a_vals = A->has_vals ? (d.tran0 ? A->cvals : A->vals) : nullptr;
+    const uint32_t *b_ptr = d.tran1 ? B->colptr : B->rowptr, *b_idx = d.tran1 ? B->rowidx : B->colidx;
+    const void *b_vals = B->has_vals ? (d.tran1 ? B->cvals : B->vals) : nullptr;
+    if (!a_ptr || !b_ptr) return fail(GB_INVALID_VALUE, "gb_mxm: a needed CSC copy is missing");
+    const uint32_t ar = C->nrows;
+    const uint64_t na = A->nvals;
+    // ---- expand: one tuple per product
+    Scratch arows(ctx), cnt(ctx), off(ctx), tot(ctx);
+    GB_CHECK(arows.alloc((na + 1) * 4));
+    GB_CHECK(cnt.alloc((na + 1) * 4));
+    GB_CHECK(off.alloc((na + 1) * 4));
+    GB_CHECK(tot.alloc(16));
+    GB_CHECK(memset_async(ctx, tot.p, 0, 16));
+    if (ar) k_expand_ptr<<<nblk(ar) < 4096 ? nblk(ar) : 4096, 256, 0, ctx->stream>>>(a_ptr, ar, arows.as<uint32_t>());
+    if (na) {
+        k_product_counts<<<nblk(na), 256, 0, ctx->stream>>>(a_idx, na, b_ptr, cnt.as<uint32_t>());
+        k_sum_u32<<<1024, 256, 0, ctx->stream>>>(cnt.as<uint32_t>(), na, tot.as<unsigned long long>());
+    }
+    GB_LAUNCH_CHECK();
+    unsigned long long np = 0;
+    GB_CUDA(cudaMemcpyAsync(&np, tot.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    GB_CHECK(sync(ctx));
+    if (np >= 0xffffffffull) return fail(GB_OUT_OF_MEMORY, "gb_mxm: %llu products exceed the 2^32 limit", np);
+    GB_CHECK(scan_exclusive_u32(ctx, cnt.as<uint32_t>(), off.as<uint32_t>(), na, nullptr));
+    Scratch orow(ctx), ocol(ctx), oval(ctx);
+    GB_CHECK(orow.alloc((np + 1) * 4));
+    GB_CHECK(ocol.alloc((np + 1) * 4));
+    GB_CHECK(oval.alloc((np + 1) * vs + 16));
+    DISPATCH_T(t, GB_CHECK(mxm_expand<T>(ctx, s, arows.as<uint32_t>(), a_idx, a_vals, na, b_ptr, b_idx, b_vals,
+                                         off.as<uint32_t>(), orow.as<uint32_t>(), ocol.as<uint32_t>(), oval.p)))
+    // ---- a complemented mask drops the products at positions M allows; the
+    // complement of an absent mask allows nothing
+    const bool structural = d.structure || (M && !M->has_vals);
+    uint64_t nkeep = np;
+    Scratch flag(ctx), pos(ctx), ktot(ctx), r2(ctx), c2(ctx), v2(ctx);
+    const uint32_t *trow = orow.as<uint32_t>(), *tcol = ocol.as<uint32_t>();
+    const void *tval = oval.p;
+    if (d.scmp && !M) nkeep = 0;
+    if (d.scmp && M && np) {
+        GB_CHECK(flag.alloc((np + 1) * 4));
+        GB_CHECK(pos.alloc((np + 1) * 4));
+        GB_CHECK(ktot.alloc(8));
+        DISPATCH_T(M->has_vals ? M->type : GB_UINT32,
+                   k_product_allowed<T><<<nblk(np), 256, 0, ctx->stream>>>(
+                       orow.as<uint32_t>(), ocol.as<uint32_t>(), np, M->rowptr, M->colidx,
+                       M->has_vals ? (const T *)M->vals : nullptr, structural, flag.as<uint32_t>()))
+        GB_LAUNCH_CHECK();
+        GB_CHECK(scan_exclusive_u32(ctx, flag.as<uint32_t>(), pos.as<uint32_t>(), np, ktot.as<uint32_t>()));
+        uint32_t k32 = 0;
+        GB_CUDA(cudaMemcpyAsync(&k32, ktot.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
+        GB_CHECK(sync(ctx));
+        nkeep = k32;
+        GB_CHECK(r2.alloc((nkeep + 1) * 4));
+        GB_CHECK(c2.alloc((nkeep + 1) * 4));
+        GB_CHECK(v2.alloc((nkeep + 1) * vs + 16));
+        DISPATCH_T(t, k_compact_products<T><<<nblk(np), 256, 0, ctx->stream>>>(
+                          flag.as<uint32_t>(), pos.as<uint32_t>(), np, orow.as<uint32_t>(), ocol.as<uint32_t>(),
+                          (const T *)oval.p, r2.as<uint32_t>(), c2.as<uint32_t>(), (T *)v2.p))
+        GB_LAUNCH_CHECK();
+        trow = r2.as<uint32_t>();
+        tcol = c2.as<uint32_t>();
+        tval = v2.p;
+    }
+    // ---- sort and compress: P = the product, equal positions reduced by the semiring's add
+    gb_matrix *P = nullptr;
+    GB_CHECK(gb_matrix_new(&P, ctx, t, C->nrows, C->ncols));
+    struct Freer { gb_matrix **m; ~Freer() { gb_matrix_free(m); } } freer{&P};
+    GB_CHECK(matrix_build_device(P, trow, tcol, tval, nkeep, semiring_add_op(s), GB_CSR_ONLY));
+    // ---- merge with the old C (accum, mask, REPLACE)
+    const uint64_t nc = C->built ? C->nvals : 0;
+    const uint64_t nt = P->nvals;
+    Scratch crows(ctx), keep(ctx), kpos(ctx), kt(ctx);
+    uint32_t nold = 0;
+    if (nc) {
+        GB_CHECK(crows.alloc((nc + 1) * 4));
+        GB_CHECK(keep.alloc((nc + 1) * 4));
+        GB_CHECK(kpos.alloc((nc + 1) * 4));
+        GB_CHECK(kt.alloc(8));
+        GB_CHECK(matrix_expand_rows(C, crows.as<uint32_t>()));
+        // the mask's values are read as raw bits of their width (as for the masked product)
+        const void *mv = M && M->has_vals ? M->vals : nullptr;
+        const size_t ms = M && M->has_vals ? type_size(M->type) : 4;
+        const uint32_t *mp = M ? M->rowptr : nullptr, *mi = M ? M->colidx : nullptr;
+        DISPATCH_T(t, {
+            const T *cvals = C->has_vals ? (const T *)C->vals : nullptr;
+            T *tv = (T *)P->vals;
+            if (ms == 1)
+                k_merge_old_c<T, uint8_t><<<nblk(nc), 256, 0, ctx->stream>>>(
+                    crows.as<uint32_t>(), C->colidx, cvals, nc, P->rowptr, P->colidx, tv, mp, mi, (const uint8_t *)mv,
+                    M != nullptr, structural, d.scmp, accum, d.replace, keep.as<uint32_t>());
+            else if (ms == 4)
+                k_merge_old_c<T, uint32_t><<<nblk(nc), 256, 0, ctx->stream>>>(
+                    crows.as<uint32_t>(), C->colidx, cvals, nc, P->rowptr, P->colidx, tv, mp, mi,
+                    (const uint32_t *)mv, M != nullptr, structural, d.scmp, accum, d.replace, keep.as<uint32_t>());
+            else
+                k_merge_old_c<T, uint64_t><<<nblk(nc), 256, 0, ctx->stream>>>(
+                    crows.as<uint32_t>(), C->colidx, cvals, nc, P->rowptr, P->colidx, tv, mp, mi,
+                    (const uint64_t *)mv, M != nullptr, structural, d.scmp, accum, d.replace, keep.as<uint32_t>());
+        })
+        GB_LAUNCH_CHECK();
+        GB_CHECK(scan_exclusive_u32(ctx, keep.as<uint32_t>(), kpos.as<uint32_t>(), nc, kt.as<uint32_t>()));
+        GB_CUDA(cudaMemcpyAsync(&nold, kt.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
+        GB_CHECK(sync(ctx));
+    }
+    // ---- the result: T's entries and the kept old ones (distinct positions)
+    const uint64_t nr = nt + nold;
+    Scratch frow(ctx), fcol(ctx), fval(ctx);
+    GB_CHECK(frow.alloc((nr + 1) * 4));
+    GB_CHECK(fcol.alloc((nr + 1) * 4));
+    GB_CHECK(fval.alloc((nr + 1) * vs + 16));
+    if (nt) {
+        GB_CHECK(matrix_expand_rows(P, frow.as<uint32_t>()));
+        GB_CUDA(cudaMemcpyAsync(fcol.p, P->colidx, nt * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+        GB_CUDA(cudaMemcpyAsync(fval.p, P->vals, nt * vs, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    if (nold) {
+        DISPATCH_T(t, k_emit_old<T><<<nblk(nc), 256, 0, ctx->stream>>>(
+                          keep.as<uint32_t>(), kpos.as<uint32_t>(), nc, (uint32_t)nt, crows.as<uint32_t>(), C->colidx,
+                          C->has_vals ? (const T *)C->vals : nullptr, frow.as<uint32_t>(), fcol.as<uint32_t>(),
+                          (T *)fval.p))
+        GB_LAUNCH_CHECK();
+    }
+    GB_CHECK(matrix_build_device(C, frow.as<uint32_t>(), fcol.as<uint32_t>(), fval.p, nr, GB_FIRST, GB_BUILD_DEFAULT));
+    return sync(ctx);
+}
+
 }  // namespace
 }  // namespace gbx
 
@@ -462,20 +725,23 @@ gb_info gb_reduce_rows(gb_vector *w, const gb_vector *mask, gb_binop accum, gb_m
 gb_info gb_mxm(gb_matrix *C, const gb_matrix *M, gb_binop accum, gb_semiring s, const gb_matrix *A,
                const gb_matrix *B, const gb_desc *desc) {
     if (!C || !A || !B) return fail(GB_NULL_POINTER, "gb_mxm: NULL argument");
-    if (!M) return fail(GB_NOT_IMPLEMENTED, "gb_mxm: only the masked product (Section 6.3.4) is provided");
-    if (!A->built || !B->built || !M->built) return fail(GB_INVALID_VALUE, "gb_mxm: an input is not built");
+    if (!A->built || !B->built || (M && !M->built)) return fail(GB_INVALID_VALUE, "gb_mxm: an input is not built");
     if (!valid_accum(accum)) return fail(GB_INVALID_VALUE, "gb_mxm: bad accumulator");
     if (s < GB_PLUS_TIMES || s > GB_PLUS_PAIR) return fail(GB_INVALID_VALUE, "gb_mxm: bad semiring");
     Desc d = read_desc(desc);
-    if (d.scmp) return fail(GB_NOT_IMPLEMENTED, "gb_mxm: a complemented mask is not provided");
     uint32_t ar = d.tran0 ? A->ncols : A->nrows, ak = d.tran0 ? A->nrows : A->ncols;
     uint32_t bk = d.tran1 ? B->ncols : B->nrows, bc = d.tran1 ? B->nrows : B->ncols;
-    if (ak != bk || C->nrows != ar || C->ncols != bc || M->nrows != ar || M->ncols != bc)
+    if (ak != bk || C->nrows != ar || C->ncols != bc || (M && (M->nrows != ar || M->ncols != bc)))
         return fail(GB_DIMENSION_MISMATCH, "gb_mxm: dimensions do not match");
     gb_type t = C->type;
     if ((A->has_vals && A->type != t) || (B->has_vals && B->type != t))
         return fail(GB_DOMAIN_MISMATCH, "gb_mxm: input and output types differ");
     if (!semiring_supported(s, t)) return fail(GB_DOMAIN_MISMATCH, "gb_mxm: semiring not available for this type");
+    if (!M || d.scmp) {
+        // no mask or a complemented one: the whole product (expand, sort, compress)
+        GB_CUDA(cudaSetDevice(C->ctx->device));
+        return mxm_general(C, M, accum, s, A, B, d);
+    }
     MxmPlan p;
     p.ctx = C->ctx;
     gb_context *ctx = C->ctx;

@@ -30,8 +30,9 @@ namespace {
 constexpr int PR_BLOCK = 256;
 constexpr int PR_WARPS = PR_BLOCK / 32;
 constexpr uint32_t PR_SUB = 128;               // nonzeros per sub-tile (4 per lane)
-constexpr uint32_t PR_NSUB = 4;                // sub-tiles per tile
-constexpr uint32_t PR_TILE = PR_SUB * PR_NSUB; // nonzeros per warp tile
+// sub-tiles per warp tile: 2, 4 or 8 (256, 512 or 1,024 nonzeros, 8, 16 or 32
+// gathers in flight per lane), picked per matrix by gb_pagerank_autotune
+constexpr uint32_t PR_NSUB_DEFAULT = 4;
 
 struct TileArgs {
     uint64_t nnz;
@@ -56,16 +57,19 @@ __global__ void k_pr_flags(const uint32_t *rp, uint32_t n, uint32_t *flags) {
     }
 }
 
-// row starts per tile (16 flag words)
-__global__ void k_pr_tilecount(const uint32_t *flags, uint32_t nwords, uint32_t ntiles, uint32_t *cnt) {
+// row starts per tile (tile / 32 flag words)
+__global__ void k_pr_tilecount(const uint32_t *flags, uint32_t nwords, uint32_t ntiles, uint32_t tile, uint32_t *cnt) {
+    const uint32_t tw = tile / 32;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
         uint32_t c = 0;
-        for (uint32_t w = t * (PR_TILE / 32); w < (t + 1) * (PR_TILE / 32) && w < nwords; ++w) c += __popc(flags[w]);
+        for (uint32_t w = t * tw; w < (t + 1) * tw && w < nwords; ++w) c += __popc(flags[w]);
         cnt[t] = c;
     }
 }
 
+template <uint32_t PR_NSUB>
 __global__ void __launch_bounds__(PR_BLOCK) k_pr_tiles(TileArgs a) {
+    constexpr uint32_t PR_TILE = PR_SUB * PR_NSUB;   // nonzeros per warp tile
     const uint32_t full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const uint32_t nwarps = gridDim.x * PR_WARPS;
@@ -305,8 +309,14 @@ __global__ void __launch_bounds__(PR_BLOCK) k_pr_norm(uint32_t n, const float *p
 }  // namespace
 }  // namespace gbx
 
-extern "C" gb_info gb_pagerank(gb_context *ctx, const gb_matrix *A, float damping, uint32_t iters, float *rank,
-                               double *residuals, gb_mem mem) {
+// tile kernel with nsub sub-tiles per warp tile (2, 4 or 8)
+static const void *tiles_kernel(uint32_t nsub) {
+    return nsub == 2 ? (const void *)k_pr_tiles<2> : nsub == 8 ? (const void *)k_pr_tiles<8> : (const void *)k_pr_tiles<4>;
+}
+
+// One PageRank of `iters` iterations with warp tiles of nsub sub-tiles.
+static gb_info pagerank_run(gb_context *ctx, const gb_matrix *A, float damping, uint32_t iters, float *rank,
+                            double *residuals, gb_mem mem, uint32_t nsub) {
     if (!ctx || !A || !rank) return fail(GB_NULL_POINTER, "gb_pagerank: NULL argument");
     if (!A->built) return fail(GB_INVALID_VALUE, "gb_pagerank: matrix not built");
     if (A->nrows != A->ncols) return fail(GB_DIMENSION_MISMATCH, "gb_pagerank: matrix must be square");
@@ -317,10 +327,12 @@ extern "C" gb_info gb_pagerank(gb_context *ctx, const gb_matrix *A, float dampin
     if (n == 0) return GB_SUCCESS;
     GB_CUDA(cudaSetDevice(ctx->device));
     const uint64_t m = A->nvals;
-    const uint32_t ntiles = (uint32_t)((m + PR_TILE - 1) / PR_TILE);
+    if (nsub != 2 && nsub != 8) nsub = 4;
+    const uint32_t tile = PR_SUB * nsub;
+    const uint32_t ntiles = (uint32_t)((m + tile - 1) / tile);
     const uint32_t nfw = (uint32_t)((m + 31) / 32);
     int occ = 0;
-    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pr_tiles, PR_BLOCK, 0));
+    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tiles_kernel(nsub), PR_BLOCK, 0));
     // a plain (not cooperative) launch: it needs no co-residency, so it takes the
     // whole GPU even where a context's persistent kernels are capped, and the
     // hardware interleaves its blocks with those of concurrent work
@@ -355,7 +367,7 @@ extern "C" gb_info gb_pagerank(gb_context *ctx, const gb_matrix *A, float dampin
     k_pr_flags<<<1024, PR_BLOCK, 0, ctx->stream>>>(A->colptr, n, fl.as<uint32_t>());
     if (ntiles) {
         k_pr_tilecount<<<(ntiles + PR_BLOCK - 1) / PR_BLOCK < 4096 ? (ntiles + PR_BLOCK - 1) / PR_BLOCK : 4096,
-                         PR_BLOCK, 0, ctx->stream>>>(fl.as<uint32_t>(), nfw, ntiles, tr.as<uint32_t>());
+                         PR_BLOCK, 0, ctx->stream>>>(fl.as<uint32_t>(), nfw, ntiles, tile, tr.as<uint32_t>());
         GB_LAUNCH_CHECK();
         GB_CHECK(scan_exclusive_u32(ctx, tr.as<uint32_t>(), tr.as<uint32_t>(), ntiles, nullptr));
     }
@@ -391,7 +403,8 @@ extern "C" gb_info gb_pagerank(gb_context *ctx, const gb_matrix *A, float dampin
         ua.p_old = pc; ua.p_new = pn; ua.x_new = xn;
         if (ntiles) {
             int span = prof_begin(ctx, "pagerank_spmv");
-            k_pr_tiles<<<G, PR_BLOCK, 0, ctx->stream>>>(ta);
+            void *args[] = {&ta};
+            GB_CUDA(cudaLaunchKernel(tiles_kernel(nsub), dim3(G), dim3(PR_BLOCK), args, 0, ctx->stream));
             prof_end(ctx, span);
             k_pr_span<<<SB, PR_BLOCK, 0, ctx->stream>>>(ta);
         }
@@ -411,5 +424,61 @@ extern "C" gb_info gb_pagerank(gb_context *ctx, const gb_matrix *A, float dampin
     if (residuals && iters) GB_CUDA(cudaMemcpyAsync(residuals, resid.p, (size_t)iters * 8, cudaMemcpyDeviceToHost, ctx->stream));
     if (mem == GB_HOST) GB_CUDA(cudaMemcpyAsync(rank, out, (size_t)n * 4, cudaMemcpyDeviceToHost, ctx->stream));
     if (residuals || mem == GB_HOST) GB_CHECK(sync(ctx));
+    return GB_SUCCESS;
+}
+
+extern "C" gb_info gb_pagerank(gb_context *ctx, const gb_matrix *A, float damping, uint32_t iters, float *rank,
+                               double *residuals, gb_mem mem) {
+    if (!A) return fail(GB_NULL_POINTER, "gb_pagerank: NULL argument");
+    return pagerank_run(ctx, A, damping, iters, rank, residuals, mem,
+                        A->tuned_pr_nsub ? A->tuned_pr_nsub : PR_NSUB_DEFAULT);
+}
+
+extern "C" gb_info gb_pagerank_autotune(gb_context *ctx, gb_matrix *A, uint32_t *tile_nnz, double *ms_per_iteration) {
+    if (!ctx || !A || !tile_nnz) return fail(GB_NULL_POINTER, "gb_pagerank_autotune: NULL argument");
+    if (!A->built || A->nrows != A->ncols || !A->has_csc)
+        return fail(GB_INVALID_VALUE, "gb_pagerank_autotune: needs a built square matrix with its CSC");
+    GB_CUDA(cudaSetDevice(ctx->device));
+    Scratch out(ctx);
+    GB_CHECK(out.alloc((size_t)A->nrows * 4 + 16));
+    cudaEvent_t e0, e1;
+    GB_CUDA(cudaEventCreate(&e0));
+    GB_CUDA(cudaEventCreate(&e1));
+    static const uint32_t cand[] = {2, 4, 8};
+    constexpr uint32_t ITERS = 8;
+    double best = 1e30;
+    uint32_t bn = PR_NSUB_DEFAULT;
+    gb_info r = GB_SUCCESS;
+    // two passes over the candidates (forward, then backward), each keeping its faster pass
+    double tmin[3] = {1e30, 1e30, 1e30};
+    for (int pass = 0; pass < 2 && r == GB_SUCCESS; ++pass) {
+        for (int ci = 0; ci < 3 && r == GB_SUCCESS; ++ci) {
+            const int c = pass == 0 ? ci : 2 - ci;
+            r = pagerank_run(ctx, A, 0.85f, 2, out.as<float>(), nullptr, GB_DEVICE, cand[c]);   // warm
+            if (r == GB_SUCCESS && cudaEventRecord(e0, ctx->stream) != cudaSuccess) r = GB_PANIC;
+            if (r == GB_SUCCESS) r = pagerank_run(ctx, A, 0.85f, ITERS, out.as<float>(), nullptr, GB_DEVICE, cand[c]);
+            if (r == GB_SUCCESS && cudaEventRecord(e1, ctx->stream) != cudaSuccess) r = GB_PANIC;
+            if (r == GB_SUCCESS && cudaEventSynchronize(e1) != cudaSuccess) r = GB_PANIC;
+            float ms = 0;
+            if (r == GB_SUCCESS) cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < tmin[c]) tmin[c] = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != GB_SUCCESS) return r == GB_PANIC ? fail(GB_PANIC, "gb_pagerank_autotune: CUDA error") : r;
+    for (int c = 0; c < 3; ++c)
+        if (tmin[c] < best) { best = tmin[c]; bn = cand[c]; }
+    A->tuned_pr_nsub = bn;
+    *tile_nnz = bn * PR_SUB;
+    if (ms_per_iteration) *ms_per_iteration = best / ITERS;
+    return GB_SUCCESS;
+}
+
+extern "C" gb_info gb_pagerank_set_tile(gb_matrix *A, uint32_t tile_nnz) {
+    if (!A) return fail(GB_NULL_POINTER, "gb_pagerank_set_tile: NULL matrix");
+    if (tile_nnz != 0 && tile_nnz != 2 * PR_SUB && tile_nnz != 4 * PR_SUB && tile_nnz != 8 * PR_SUB)
+        return fail(GB_INVALID_VALUE, "gb_pagerank_set_tile: tile of %u nonzeros (256, 512, 1024 or 0)", tile_nnz);
+    A->tuned_pr_nsub = tile_nnz / PR_SUB;
     return GB_SUCCESS;
 }

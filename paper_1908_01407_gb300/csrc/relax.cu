@@ -8,6 +8,14 @@
 //    labels starting at the vertex ids, every vertex active at first.
 // The next frontier is exactly the set of vertices whose value decreased
 // (the sparsification step: Section 7.2 keeps only vertices that improved).
+// For SSSP the changed set is further split by distance (near-far order,
+// the bucket discipline of delta-stepping expressed as a mask): only
+// improved vertices below the current bound B form the frontier; the others
+// wait in a far bitmap. When the frontier empties, B grows by delta and the
+// far vertices below it move into the frontier. Every improvement is still
+// relaxed, so the fixed point (Dijkstra's distances) is the same; what
+// changes is the order, which on weighted graphs saves most of the repeated
+// relaxations of vertices improved many times over.
 // Each iteration is a push (merge-path over the frontier's out-edges,
 // atomicMin into the target) or a pull (every vertex scans its in-edges,
 // taking only frontier sources into account) by the rule of Table 9. The
@@ -44,12 +52,16 @@ struct RelaxArgs {
     const uint32_t *hub_list, *hub_pre;   // pull rows longer than RPULL_HUB
     uint32_t nhub;
     uint64_t hub_edges;
+    uint64_t delta;          // SSSP bucket width of the near-far frontier; 0 = no buckets
+    uint32_t *far;           // bitmap of the far set (improved, at or beyond the current bound)
 };
 
 constexpr int RPULL_WPW = 1;
 
+// weights stream through once per relaxation pass: evict-first, like the
+// indices, so they do not push the distances and bitmaps out of L2
 __device__ __forceinline__ uint32_t relax_val(const RelaxArgs &a, uint32_t vu, uint32_t p, const uint32_t *w) {
-    return a.weighted ? sat_add<uint32_t>(vu, __ldg(&w[p])) : vu;
+    return a.weighted ? sat_add<uint32_t>(vu, ld_stream(&w[p])) : vu;
 }
 
 // pull: lane per vertex, RPULL_WPW vertices per lane in flight. Each round
@@ -206,7 +218,9 @@ __device__ void relax_pull_hubs(const RelaxArgs &a, int d, uint32_t *cnt_out, ui
 
 __global__ void __launch_bounds__(BLOCK, 6) k_relax(RelaxArgs a) {
     __shared__ Smem sm;
-    __shared__ uint32_t s_cnt, s_deg;
+    __shared__ uint32_t s_cnt, s_deg, s_far;
+    __shared__ unsigned long long s_qs;
+    uint64_t bound = a.delta;   // near-far: the frontier holds improved vertices below bound
     const uint32_t nthreads = gridDim.x * BLOCK;
     const uint32_t tid = blockIdx.x * BLOCK + threadIdx.x;
     BfsState *st = a.st;
@@ -221,6 +235,7 @@ __global__ void __launch_bounds__(BLOCK, 6) k_relax(RelaxArgs a) {
         a.front[0][w] = f;
         a.front[1][w] = 0u;
         a.front[2][w] = 0u;
+        if (a.far) a.far[w] = 0u;
     }
     if (tid == 0) {
         memset(res, 0, sizeof(BfsResult));
@@ -254,18 +269,78 @@ __global__ void __launch_bounds__(BLOCK, 6) k_relax(RelaxArgs a) {
         __syncthreads();
         const unsigned long long qs = sm.qs;
         __syncthreads();
-        const uint32_t cnt = (uint32_t)(qs >> a.ebits);
-        const uint64_t fe = qs & a.emask;
+        uint32_t cnt = (uint32_t)(qs >> a.ebits);
+        uint64_t fe = qs & a.emask;
         if (tid == 0 && d > 0) {
             const double ew = a.weighted ? 4.0 : 0.0;
             if (prev_pull) alg += 4.0 * (a.n + 1.0) + a.n / 8.0 + 4.0 * a.m + ew * prev_fe;
             else alg += 8.0 * prev_cnt + (4.0 + ew) * prev_fe;
             alg += 4.0 * cnt;
         }
+        if (cnt == 0 && a.delta) {
+            // the frontier is empty: raise the bound by delta until far vertices
+            // fall below it (they become the frontier), or none is left. The far
+            // count is read once here, where it is stable (push levels change it,
+            // and they are behind the barrier); every block then tracks it
+            // identically from the counts it reads after each barrier.
+            if (threadIdx.x == 0) s_far = dev::ld_relaxed_gpu((const unsigned int *)&st->far_cnt);
+            __syncthreads();
+            uint32_t far_left = s_far;
+            __syncthreads();
+            bool advanced = false;
+            while (far_left > 0) {
+                bound += a.delta;
+                if (tid == 0) alg += a.n / 8.0 + 4.0 * far_left;   // the far bitmap and the far values
+                uint32_t *F = a.front[d % 3];
+                uint32_t moved = 0, mdeg = 0;
+                for (uint64_t w = tid; w < a.nwords; w += nthreads) {
+                    const uint32_t bits = a.far[w];
+                    if (!bits) continue;
+                    uint32_t take = 0;
+                    for (uint32_t bb = bits; bb; bb &= bb - 1) {
+                        const uint32_t v = (uint32_t)(w * 32 + (__ffs(bb) - 1));
+                        if ((uint64_t)ldcg(&a.val[v]) < bound) {
+                            take |= bb & (~bb + 1u);
+                            mdeg += __ldg(&a.rp_out[v + 1]) - __ldg(&a.rp_out[v]);
+                        }
+                    }
+                    if (take) {
+                        a.far[w] = bits & ~take;
+                        F[w] = take;   // F is empty: no improvement reached the frontier this level
+                        moved += __popc(take);
+                    }
+                }
+                moved = dev::warp_sum<uint32_t>(moved);
+                mdeg = dev::warp_sum<uint32_t>(mdeg);
+                if ((threadIdx.x & 31) == 0 && moved)
+                    atomicAdd(&st->qstate[d % 3], ((unsigned long long)moved << a.ebits) | mdeg);
+                if (threadIdx.x == 0 && dev::globaltimer_ns() - t_start > a.total_limit_ns)
+                    atomicCAS(&st->err, 0, (int)GB_TIMEOUT);
+                if (!dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns)) { ok = false; break; }
+                if (threadIdx.x == 0)
+                    s_qs = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>(st->qstate[d % 3])
+                               .load(cuda::memory_order_relaxed);
+                __syncthreads();
+                const unsigned long long q2 = s_qs;
+                __syncthreads();
+                cnt = (uint32_t)(q2 >> a.ebits);
+                fe = q2 & a.emask;
+                if (cnt) {
+                    advanced = true;
+                    // the moved vertices leave the far count; it is read again only
+                    // after this level's barrier
+                    if (tid == 0) atomicSub(&st->far_cnt, cnt);
+                    break;
+                }
+            }
+            if (!ok) break;
+            if (!advanced) break;
+            list_valid = false;   // the moved vertices exist as a bitmap only
+        }
         if (cnt == 0) break;
         // guard: every value can decrease only finitely often; a wall-clock budget bounds the loop
         if (threadIdx.x == 0 && dev::globaltimer_ns() - t_start > a.total_limit_ns) atomicCAS(&st->err, 0, (int)GB_TIMEOUT);
-        bool pull = a.rp_in && a.mode != GB_PUSH && (a.mode == GB_PULL || fe * (uint64_t)a.beta > a.m);
+        bool pull = !a.delta && a.rp_in && a.mode != GB_PUSH && (a.mode == GB_PULL || fe * (uint64_t)a.beta > a.m);
         if (tid == 0) {
             if (d < GBX_MAX_LEVEL_LOG) {
                 res->dir_log[d] = pull ? 2 : 1;
@@ -301,18 +376,27 @@ __global__ void __launch_bounds__(BLOCK, 6) k_relax(RelaxArgs a) {
                 compact_level(a, sm, d);
                 if (!dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns)) { ok = false; break; }
             }
+            uint32_t nfar = 0;
             push_edges(a, sm, d, cnt, fe, [&](uint32_t u, uint32_t v, uint32_t p, uint32_t *Fn, uint32_t *deg, uint32_t *r0) {
                 uint32_t c = relax_val(a, ldcg(&a.val[u]), p, a.w_out);
                 if (c >= ldcg(&a.val[v])) return false;
                 uint32_t old = atomicMin(&a.val[v], c);
                 if (c >= old) return false;
                 uint32_t bit = 1u << (v & 31);
+                if (a.delta && (uint64_t)c >= bound) {   // beyond the bound: the far set
+                    if (!(atomicOr(&a.far[v >> 5], bit) & bit)) ++nfar;
+                    return false;
+                }
                 uint32_t o = atomicOr(&Fn[v >> 5], bit);
                 if (o & bit) return false;
                 *r0 = __ldg(&a.rp_out[v]);
                 *deg = __ldg(&a.rp_out[v + 1]) - *r0;
                 return true;
             });
+            if (a.delta) {
+                nfar = dev::warp_sum<uint32_t>(nfar);
+                if ((threadIdx.x & 31) == 0 && nfar) atomicAdd(&st->far_cnt, nfar);
+            }
             list_valid = true;
         }
         ok = dev::grid_sync(&st->bar, gridDim.x, &st->err, a.timeout_ns);
@@ -333,6 +417,7 @@ __global__ void __launch_bounds__(BLOCK, 6) k_relax(RelaxArgs a) {
             st->err = 0;
             st->bar.count = 0;
             for (int k = 0; k < 3; ++k) { st->qstate[k] = 0; st->exam[k] = 0; st->cstate[k] = 0; }
+            st->far_cnt = 0;
             __threadfence();
             st->bar.exits = 0;
         }
@@ -348,6 +433,38 @@ bool bfs_cluster_available(gb_context *ctx);
 gb_info sssp_cluster_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, uint32_t *dist, uint32_t *stamp,
                             uint32_t *ov0, uint32_t *ov1, void *state);
 gb_info cluster_iterations(gb_context *ctx, const void *state, uint32_t *iterations);
+
+namespace {
+__global__ void k_weight_sum(const uint32_t *w, uint64_t m, unsigned long long *sum) {
+    unsigned long long acc = 0;
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x)
+        acc += w[q];
+    acc = dev::warp_sum<unsigned long long>(acc);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(sum, acc);
+}
+}  // namespace
+
+// Mean stored weight of A (uint32 values), computed once and kept on the matrix.
+static gb_info matrix_mean_weight(gb_context *ctx, const gb_matrix *A, double *mean) {
+    gb_matrix *M = const_cast<gb_matrix *>(A);
+    std::lock_guard<std::mutex> g(M->cache_mu);
+    if (M->mean_weight <= 0) {
+        Scratch s(ctx);
+        GB_CHECK(s.alloc(16));
+        GB_CHECK(memset_async(ctx, s.p, 0, 16));
+        if (A->nvals)
+            k_weight_sum<<<1024, 256, 0, ctx->stream>>>((const uint32_t *)A->vals, A->nvals,
+                                                       s.as<unsigned long long>());
+        GB_LAUNCH_CHECK();
+        unsigned long long sum = 0;
+        GB_CUDA(cudaMemcpyAsync(&sum, s.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
+        GB_CHECK(sync(ctx));
+        M->mean_weight = A->nvals ? (double)sum / (double)A->nvals : 1.0;
+        if (M->mean_weight <= 0) M->mean_weight = 1.0;
+    }
+    *mean = M->mean_weight;
+    return GB_SUCCESS;
+}
 
 static gb_info relax_run(gb_context *ctx, const gb_matrix *A, bool weighted, uint32_t src, uint32_t *out, gb_mem mem,
                          const gb_desc *desc, uint32_t *iterations, gb_bfs_stats *stats, const char *who) {
@@ -417,6 +534,33 @@ static gb_info relax_run(gb_context *ctx, const gb_matrix *A, bool weighted, uin
     a.hub_list = a.hub_pre = nullptr;
     a.nhub = 0;
     a.hub_edges = 0;
+    // SSSP bucket width: the descriptor's, or, by default, 32 times the mean
+    // weight times the mean degree. Narrow buckets save repeated relaxations
+    // but add synchronous steps (a step per bucket and per hop inside it);
+    // measured on the weighted 4096^2 grid (mean weight 500, degree 3.6),
+    // widths of 16,000 to 64,000 run 115-122 ms against 353 ms for no buckets
+    // and 460 ms for a width of 278, and on R-MAT s22 (weights 1-255, degree
+    // 30.6) every width from 16 up is within 15% of no buckets. A forced
+    // pull, or a width of 2^31 - 1 or more, is the plain changed-set iteration.
+    a.delta = 0;
+    a.far = nullptr;
+    Scratch farb(ctx);
+    if (weighted && a.mode != GB_PULL) {
+        const int dd = desc ? desc->sssp_delta : 0;
+        if (dd == 0) {
+            double mean = 1.0;
+            GB_CHECK(matrix_mean_weight(ctx, A, &mean));
+            const double avg_deg = A->nrows ? (double)A->nvals / (double)A->nrows : 1.0;
+            const double dl = 32.0 * mean * (avg_deg > 1.0 ? avg_deg : 1.0);
+            a.delta = dl < 1.0 ? 1u : (dl > 2147483646.0 ? 2147483646ull : (uint64_t)(dl + 0.5));
+        } else if (dd < 0x7fffffff) {
+            a.delta = (uint64_t)dd;
+        }
+        if (a.delta) {
+            GB_CHECK(farb.alloc((size_t)a.nwords * 4 + 16));
+            a.far = farb.as<uint32_t>();
+        }
+    }
     if (A->has_csc) {
         GB_CHECK(matrix_hubs(A, rlx::RPULL_HUB));
         a.hub_list = A->hub_list;

@@ -137,14 +137,16 @@ def test_cc_fastsv_weak_components_and_errors(ctx):
 
 
 # ---------------------------------------------------------------- PageRank
+@pytest.mark.parametrize("tile", [256, 512, 1024])
 @pytest.mark.parametrize("case", ["rmat14", "rmat12_e4", "grid", "star", "cycle"])
-def test_pagerank_l1_vs_fp64_oracle(ctx, case):
+def test_pagerank_l1_vs_fp64_oracle(ctx, case, tile):
     t = {"rmat14": lambda: gen.rmat(14, 16, seed=1),
          "rmat12_e4": lambda: gen.rmat(12, 4, seed=3),
          "grid": lambda: gen.grid(70, 50, 0.1, seed=3),
          "star": lambda: gen.from_edges(300, [(0, i) for i in range(1, 300)]),
          "cycle": lambda: gen.from_edges(1000, [(i, (i + 1) % 1000) for i in range(1000)])}[case]()
     g, A = build(ctx, t, weights=False)
+    gb.pagerank_set_tile(A, tile)
     want, wres = oracle.pagerank(g, 0.85, 50)
     rank = np.empty(t.n, np.float32)
     _, res = gb.pagerank(ctx, A, 0.85, 50, rank)
@@ -288,7 +290,7 @@ def test_tc_rmat_s20_full_size(ctx):
 # ------------------------------------------------------- multi-source BFS
 @pytest.mark.parametrize("case,k", [("rmat14", 64), ("rmat14", 1), ("rmat13", 37), ("grid", 64), ("small", 5),
                                     ("path", 9),
-                                    ("rmat13", 150)])
+                                    ("rmat13", 150), ("rmat14", 256)])
 def test_bfs_multi_matches_independent_bfs(ctx, case, k):
     t = {"rmat14": lambda: gen.rmat(14, 16, seed=1),
          "rmat13": lambda: gen.rmat(13, 8, seed=8),
@@ -479,7 +481,7 @@ def test_sssp_stats_count_the_algorithmic_bytes_of_each_iteration(ctx):
     n, m = A.nrows, A.nvals
     src = int(gen.sources(t, 1, seed=1)[0])
     for direction in (gb.AUTO, gb.PUSH, gb.PULL):
-        d = gb.Descriptor(direction=direction)
+        d = gb.Descriptor(direction=direction, sssp_delta=gb.SSSP_DELTA_NONE)   # the plain iteration
         dist = np.empty(n, np.uint32)
         _, it, st = gb.sssp(ctx, A, src, dist, d, stats=True)
         assert np.array_equal(dist, oracle.sssp(g, src))
@@ -497,4 +499,53 @@ def test_sssp_stats_count_the_algorithmic_bytes_of_each_iteration(ctx):
         if direction == gb.PULL:
             assert st["push_levels"] == 0
         d.free()
+    A.free()
+
+
+@pytest.mark.parametrize("case", ["rmat14", "grid", "directed", "path", "star"])
+def test_sssp_near_far_buckets_match_dijkstra(ctx, case):
+    """SSSP whose frontier is restricted to improved vertices below a bound
+    that grows by delta (the far ones wait): Dijkstra's distances for every
+    bucket width, from 1 (a bucket per distance) to one that holds every
+    distance, and the automatic one; bit-exact."""
+    if case == "directed":
+        rng = np.random.default_rng(9)
+        n = 3000
+        r = rng.integers(0, n, 25000).astype(np.uint32)
+        c = rng.integers(0, n, 25000).astype(np.uint32)
+        w = rng.integers(1, 300, 25000).astype(np.uint32)
+        A = gb.Matrix.from_tuples(ctx, n, r, c, w, type_=gb.UINT32)
+        g = oracle.csr_build(n, r, c, w)
+        srcs = [3, 2999]
+    else:
+        t = {"rmat14": lambda: gen.rmat(14, 16, seed=33, wmax=255),
+             "grid": lambda: gen.grid(150, 130, 0.1, seed=5, wmax=1000),
+             "path": lambda: gen.from_edges(700, [(i, i + 1) for i in range(699)], [1 + i % 7 for i in range(699)]),
+             "star": lambda: gen.from_edges(5000, [(0, i) for i in range(1, 5000)],
+                                            [1 + (i * 37) % 900 for i in range(1, 5000)])}[case]()
+        g, A = build(ctx, t)
+        n = t.n
+        srcs = [int(x) for x in gen.sources(t, 2, seed=3)]
+    for delta in (1, 5, 64, 2**31 - 2, 0):
+        d = gb.Descriptor(sssp_delta=delta)
+        for src in srcs:
+            dist = np.empty(n, np.uint32)
+            gb.sssp(ctx, A, src, dist, d)
+            assert np.array_equal(dist, oracle.sssp(g, src)), (delta, src)
+        d.free()
+    A.free()
+
+
+def test_pagerank_autotune_keeps_a_candidate_and_the_result(ctx):
+    t = gen.rmat(14, 16, seed=41)
+    g, A = build(ctx, t, weights=False)
+    tile, ms = gb.pagerank_autotune(ctx, A)
+    assert tile in (256, 512, 1024) and ms > 0
+    rank = np.empty(t.n, np.float32)
+    gb.pagerank(ctx, A, 0.85, 50, rank)
+    want, _ = oracle.pagerank(g, 0.85, 50)
+    assert np.abs(rank.astype(np.float64) - want).sum() <= PR_L1_TOL
+    with pytest.raises(gb.GBError) as e:
+        gb.pagerank_set_tile(A, 300)
+    assert e.value.code == gb.INVALID_VALUE
     A.free()

@@ -413,3 +413,41 @@ def test_bfs_batch_single_vertex_graph(ctx):
     lv, par = gb.bfs_batch(ctx, A, np.zeros(3, np.uint32), np.empty((3, 1), np.int32), np.empty((3, 1), np.int32))
     assert lv.tolist() == [[0], [0], [0]] and par.tolist() == [[0], [0], [0]]
     A.free()
+
+
+@pytest.mark.parametrize("case", ["rmat_even", "rmat_odd", "directed", "csr_only", "isolated", "single"])
+def test_bfs_batch_device_rows_match_the_oracle(ctx, case):
+    """gb_bfs_batch with device outputs: each row equals the oracle's BFS
+    (levels exactly, parents valid), for an even and an odd number of runs, a
+    directed matrix (pulls over its CSC), a CSR-only matrix (push only),
+    isolated sources among others, and one run; a second batch on the same
+    workspace gives the same rows."""
+    if case in ("directed", "csr_only"):
+        rng = np.random.default_rng(17)
+        n = 5000
+        r = rng.integers(0, n, 60000).astype(np.uint32)
+        c = rng.integers(0, n, 60000).astype(np.uint32)
+        A = gb.Matrix.from_tuples(ctx, n, r, c, flags=gb.CSR_ONLY if case == "csr_only" else gb.BUILD_DEFAULT)
+        g = oracle.csr_build(n, r, c)
+        srcs = [3, 11, 4999, 250, 7]
+    else:
+        t = gen.rmat(14, 16, seed=21)
+        g, A = make(ctx, t)
+        n = t.n
+        srcs = [int(s) for s in gen.sources(t, {"rmat_even": 8, "rmat_odd": 9, "isolated": 4, "single": 1}[case],
+                                              seed=5)]
+        if case == "isolated":
+            deg = np.diff(g.rowptr.astype(np.int64))
+            iso = [int(v) for v in np.flatnonzero(deg == 0)[:2]]
+            srcs = [iso[0], srcs[0], iso[1], srcs[1], srcs[2]]
+    k = len(srcs)
+    for _ in range(2):
+        lv = torch.full((k, n), 9, dtype=torch.int32, device="cuda")
+        par = torch.full((k, n), 9, dtype=torch.int32, device="cuda")
+        gb.bfs_batch(ctx, A, np.array(srcs, np.uint32), lv, par)
+        torch.cuda.synchronize()
+        lv, par = lv.cpu().numpy(), par.cpu().numpy()
+        for q, s in enumerate(srcs):
+            assert np.array_equal(lv[q], oracle.bfs(g, s)), (case, q)
+            assert oracle.bfs_parent_violations(g, s, lv[q], par[q]) == 0, (case, q)
+    A.free()

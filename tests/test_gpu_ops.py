@@ -283,9 +283,10 @@ def test_reduce_accumulates_into_prior_value(ctx):
 @pytest.mark.parametrize("sr,t", CASES)
 def test_mxm_masked(ctx, sr, t):
     rng = np.random.default_rng(7 + len(sr) + len(t))
-    for tran0, tran1, mk, acc, replace in itertools.product([False, True], [False, True],
-                                                            ["structure", "value"], [None, "acc"], [False, True]):
-        if rng.random() > 0.35:
+    for tran0, tran1, mk, acc, replace in itertools.product(
+            [False, True], [False, True], ["structure", "value", "none", "scmp", "scmp_structure", "none_scmp"],
+            [None, "acc"], [False, True]):
+        if rng.random() > 0.3:
             continue
         nr, nk, nc = 41, 37, 53
         Ae = rand_mat(rng, nk if tran0 else nr, nr if tran0 else nk, 300, t)
@@ -294,16 +295,18 @@ def test_mxm_masked(ctx, sr, t):
         Ce = rand_mat(rng, nr, nc, 200, t)
         A = gpu_mat(ctx, Ae, t, nk if tran0 else nr, nr if tran0 else nk)
         B = gpu_mat(ctx, Be, t, nc if tran1 else nk, nk if tran1 else nc)
-        M = gpu_mat(ctx, Me, "int32", nr, nc)
+        has_m = not mk.startswith("none")
+        M = gpu_mat(ctx, Me, "int32", nr, nc) if has_m else None
         C = gpu_mat(ctx, Ce, t, nr, nc)
         acc_op = {"bool": "LOR", "int32": "PLUS", "uint32": "MAX", "uint64": "PLUS", "fp32": "MIN",
                   "fp64": "PLUS"}[t] if acc else None
-        d = gb.Descriptor(mask=gb.STRUCTURE if mk == "structure" else 0, outp=gb.REPLACE if replace else 0,
+        mval = (gb.STRUCTURE if "structure" in mk else 0) | (gb.SCMP if "scmp" in mk else 0)
+        d = gb.Descriptor(mask=mval, outp=gb.REPLACE if replace else 0,
                           inp0=gb.TRAN if tran0 else 0, inp1=gb.TRAN if tran1 else 0)
         gb.mxm(C, M, BOP[acc_op] if acc_op else gb.NOP, SR[sr], A, B, d)
-        want = gbo.mxm(gbo.Mat(nr, nc, t, Ce), gbo.Mat(nr, nc, "int32", Me), acc_op, sr,
+        want = gbo.mxm(gbo.Mat(nr, nc, t, Ce), gbo.Mat(nr, nc, "int32", Me) if has_m else None, acc_op, sr,
                        gbo.Mat(A.nrows, A.ncols, t, Ae), gbo.Mat(B.nrows, B.ncols, t, Be), tran0=tran0, tran1=tran1,
-                       structural=mk == "structure", replace=replace)
+                       structural="structure" in mk, scmp="scmp" in mk, replace=replace)
         r, c, v = C.extract_tuples(with_vals=True)
         got = {(int(i), int(j)): x.item() for i, j, x in zip(r, c, v)}
         assert set(got) == set(want.e)
@@ -318,7 +321,8 @@ def test_mxm_masked(ctx, sr, t):
             tol = float_bound(t, terms, Ce.get(k, 0.0) if acc_op else 0.0)
             assert close(got[k], x, t, tol), (k, got[k], x, tol)
         for x in (A, B, M, C, d):
-            x.free()
+            if x is not None:
+                x.free()
 
 
 def test_vector_object_roundtrip(ctx):
