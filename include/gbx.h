@@ -421,17 +421,30 @@ gb_info gb_sssp(gb_context *ctx, const gb_matrix *A, uint32_t src, uint32_t *dis
  * rank[n] in `mem`; residuals[iters] (host, may be NULL). */
 gb_info gb_pagerank(gb_context *ctx, const gb_matrix *A, float damping, uint32_t iters, float *rank,
                     double *residuals, gb_mem mem);
-/* Autotuner of the PageRank SpMV tile (the paper has no counterpart; its
+/* Autotuner of the PageRank SpMV layout (the paper has no counterpart; its
  * merge-path SpMV of Section 6.3.2 has a fixed work per thread): times
  * gb_pagerank on A with warp tiles of 256, 512 and 1,024 nonzeros (8, 16 or
  * 32 gathers in flight per lane; the larger tiles use more registers, so
- * fewer warps), two passes over the candidates, and keeps the fastest on
- * the matrix for later gb_pagerank calls (untuned: 512). *tile_nnz receives
- * it, *ms_per_iteration (may be NULL) its time per iteration. */
-gb_info gb_pagerank_autotune(gb_context *ctx, gb_matrix *A, uint32_t *tile_nnz, double *ms_per_iteration);
+ * fewer warps) on A as stored, and with tiles of 256 and 512 on a copy of A
+ * whose vertices are renamed by decreasing out-degree, where every block
+ * stages the ranks of the first 16,384 or 32,768 vertices (the most
+ * referenced ones) in shared memory; two passes over the candidates. The
+ * fastest is kept on A for later gb_pagerank calls (untuned: 512 as
+ * stored); the copy stays on A while it is chosen (nnz + 2n words more).
+ * *tile_nnz receives the tile, *degree_order (may be NULL) 1 if the copy
+ * won, *staged_ranks (may be NULL) the staged count (0 as stored),
+ * *ms_per_iteration (may be NULL) the time per iteration. The result is
+ * the same PageRank either way, up to the order of the FP32 row sums. */
+gb_info gb_pagerank_autotune(gb_context *ctx, gb_matrix *A, uint32_t *tile_nnz, int32_t *degree_order,
+                             uint32_t *staged_ranks, double *ms_per_iteration);
 /* Sets the PageRank tile of A by hand: 256, 512 or 1,024 nonzeros, or 0 for
  * the default (GB_INVALID_VALUE otherwise). */
 gb_info gb_pagerank_set_tile(gb_matrix *A, uint32_t tile_nnz);
+/* Sets the PageRank vertex order of A by hand: 0 = as stored, 1 = the
+ * degree-ordered copy (built at the next gb_pagerank; a 1,024-nonzero tile
+ * runs as 512 there) with staged_ranks ranks in shared memory (a multiple
+ * of 1,024 up to 57,344; 0 = 32,768). GB_INVALID_VALUE otherwise. */
+gb_info gb_pagerank_set_order(gb_matrix *A, int32_t degree_order, uint32_t staged_ranks);
 /* Adaptive PageRank, also called PageRankDelta (Section 5.1: converged
  * vertices as the output mask; Section 7.3 names the variant): the
  * gb_pagerank recurrence, where a vertex whose value moved by at most eps

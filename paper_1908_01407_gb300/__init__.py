@@ -134,7 +134,8 @@ _SIGS = {
     "gb_cc": [_P, _P, _P, _I, _P, _P], "gb_tc": [_P, _P, _P, _P],
     "gb_cc_fastsv": [_P, _P, _P, _I, _P],
     "gb_pagerank_delta": [_P, _P, ctypes.c_float, ctypes.c_float, _U32, _P, _I, _P, _P, _P],
-    "gb_pagerank_autotune": [_P, _P, _P, _P], "gb_pagerank_set_tile": [_P, _U32],
+    "gb_pagerank_autotune": [_P, _P, _P, _P, _P, _P], "gb_pagerank_set_tile": [_P, _U32],
+    "gb_pagerank_set_order": [_P, _I, _U32],
     "gb_server_create": [_PP, _P, _P], "gb_server_add_graph": [_P, _P, _P], "gb_server_submit": [_P, _P, _P],
     "gb_server_wait": [_P, _U64, _U32, _P], "gb_server_fetch": [_P, _U64, _P, _I],
     "gb_server_stats_get": [_P, _P], "gb_server_destroy": [_PP],
@@ -657,16 +658,25 @@ def pagerank(ctx, A, damping=0.85, iters=50, rank=None, residuals=True):
 
 
 def pagerank_autotune(ctx, A):
-    """Pick the PageRank SpMV tile for A from timed runs; returns (tile
-    nonzeros, ms per iteration). The choice is kept on A."""
+    """Pick the PageRank SpMV layout for A from timed runs; returns (tile
+    nonzeros, degree order 0/1, staged ranks, ms per iteration). The choice
+    is kept on A."""
     t = ctypes.c_uint32()
+    o = ctypes.c_int32()
+    k = ctypes.c_uint32()
     ms = ctypes.c_double()
-    check(lib().gb_pagerank_autotune(ctx.h, A.h, ctypes.byref(t), ctypes.byref(ms)))
-    return t.value, ms.value
+    check(lib().gb_pagerank_autotune(ctx.h, A.h, ctypes.byref(t), ctypes.byref(o), ctypes.byref(k), ctypes.byref(ms)))
+    return t.value, o.value, k.value, ms.value
 
 
 def pagerank_set_tile(A, tile_nnz):
     check(lib().gb_pagerank_set_tile(A.h, tile_nnz))
+
+
+def pagerank_set_order(A, degree_order, staged_ranks=0):
+    """0: PageRank runs on A as stored; 1: on its degree-ordered copy with
+    staged_ranks ranks in shared memory (0 = the default)."""
+    check(lib().gb_pagerank_set_order(A.h, degree_order, staged_ranks))
 
 
 def pagerank_delta(ctx, A, damping=0.85, eps=1e-4, max_iters=100, rank=None):

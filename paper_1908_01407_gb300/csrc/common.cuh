@@ -104,6 +104,14 @@ struct gb_matrix_t {
     // PageRank SpMV tile (128-nonzero sub-tiles per warp tile) chosen by
     // gb_pagerank_autotune (0 = not tuned)
     uint32_t tuned_pr_nsub = 0;
+    // PageRank vertex order: 1 = run on a copy renamed by decreasing
+    // out-degree (pr_view, with pr_new_id[v] the new name of v), whose
+    // most-referenced ranks fit in shared memory; 0 = as stored. Chosen by
+    // gb_pagerank_autotune or set by hand; the copy is built on first use.
+    int pr_order = 0;
+    uint32_t pr_staged = 0;           // ranks staged in shared memory (0 = the default)
+    gb_matrix_t *pr_view = nullptr;
+    uint32_t *pr_new_id = nullptr;
     // vertices with at least one in-edge (nonempty CSC row), ascending,
     // built with the CSC; live_count is a device scalar (live_list[nrows])
     uint32_t *live_list = nullptr;
@@ -111,8 +119,6 @@ struct gb_matrix_t {
     // per live vertex, in live-list order, its pull record (vertex, CSC row,
     // out-degree and the four in-neighbours of largest out-degree)
     PullRec *live_rec = nullptr;
-    // bit v set when vertex v has no in-edge (no pull and no push can reach it;
-    // bits past nrows set too), built with the live table
     // per vertex, the size of its weakly connected component (built by
     // gb_matrix_build for a square matrix with a CSC): a traversal that has
     // reached that many vertices can stop without expanding its last frontier

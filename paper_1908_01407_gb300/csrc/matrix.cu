@@ -61,6 +61,9 @@ void release(gb_matrix *A) {
     dfree(ctx, A->live_rec);
     dfree(ctx, A->comp_size);
     A->comp_size = nullptr;
+    if (A->pr_view) gb_matrix_free(&A->pr_view);
+    dfree(ctx, A->pr_new_id);
+    A->pr_new_id = nullptr;
     A->live_list = A->live_count = nullptr;
     A->live_rec = nullptr;
     A->hub_list = A->hub_pre = nullptr;

@@ -20,6 +20,20 @@
 // reduces the L1 residual sum |p' - p| and the dangling mass D in FP64 in a
 // fixed order. Every sum has one fixed order and no floating-point atomics
 // are used, so a run is bit-reproducible.
+//
+// The gathers x[j] are the SpMV's limit: one random 4-byte load per
+// nonzero, and the L1 looks up one cache line per cycle, so a warp's
+// 32 gathers to 32 lines take 32 cycles however few bytes they move. On a
+// graph with a skewed degree distribution the run can instead use a copy
+// of the matrix with the vertices renamed by decreasing out-degree: the
+// ranks of the first 32,768 vertices, which then take about half of the
+// references (52% of the nonzeros of an R-MAT graph with 4M vertices), are
+// staged in shared memory by every block and gathered from there, and only
+// the rest go through the L1. Staging more leaves too little L1 for the
+// rest (57,344 ranks, 224 KB, ran slower than none). The ranks are renamed
+// back in the final normalisation. Each warp loads its next tile's column
+// indices while it gathers and sums the current one, so the DRAM latency of
+// the index stream is hidden behind the gathers.
 #include "common.cuh"
 
 using namespace gbx;
@@ -33,6 +47,13 @@ constexpr uint32_t PR_SUB = 128;               // nonzeros per sub-tile (4 per l
 // sub-tiles per warp tile: 2, 4 or 8 (256, 512 or 1,024 nonzeros, 8, 16 or 32
 // gathers in flight per lane), picked per matrix by gb_pagerank_autotune
 constexpr uint32_t PR_NSUB_DEFAULT = 4;
+// the kernel that stages ranks in shared memory: 1,024-thread blocks that
+// share up to 224 KB of them (tiles of 256 or 512 nonzeros: within 64
+// registers a thread). Fewer staged ranks leave more of the SM's 256 KB of
+// L1 + shared memory to the L1 (and room for a second block).
+constexpr int PR_HUB_BLOCK = 1024;
+constexpr uint32_t PR_HUB_MAX = 57344;
+constexpr uint32_t PR_HUB_DEFAULT = 32768;
 
 struct TileArgs {
     uint64_t nnz;
@@ -40,14 +61,19 @@ struct TileArgs {
     const uint32_t *ci;       // column indices of the pulled rows (in-edges)
     const uint32_t *flags;    // bit e: nonzero e is the first of its row
     const uint32_t *trank;    // per tile: row starts before it
-    const uint32_t *live;     // k-th nonempty row
+    const uint32_t *live;     // k-th nonempty row (null: row k, the nonempty rows come first)
     const float *x;           // p(j)/deg(j)
+    uint32_t nhub;            // x[0, nhub) is staged in shared memory (a multiple of 4; 0 = none)
     float *y;                 // row sums (rows never written stay 0)
     float *pfirst;            // per tile: partial of the row open at its start (the whole tile without starts)
     float *plast;             // per tile with a start: partial of the row open at its end
     uint32_t *rlast;          // its rank
     uint32_t *tflag;          // 1 if the tile holds a row start
 };
+
+__device__ __forceinline__ uint32_t row_of(const TileArgs &a, uint32_t r) {
+    return a.live ? __ldg(&a.live[r]) : r;
+}
 
 // bit e of flags set where nonzero e starts its row
 __global__ void k_pr_flags(const uint32_t *rp, uint32_t n, uint32_t *flags) {
@@ -67,20 +93,29 @@ __global__ void k_pr_tilecount(const uint32_t *flags, uint32_t nwords, uint32_t 
     }
 }
 
-template <uint32_t PR_NSUB>
-__global__ void __launch_bounds__(PR_BLOCK) k_pr_tiles(TileArgs a) {
+template <uint32_t PR_NSUB, bool HUB>
+__global__ void __launch_bounds__(HUB ? PR_HUB_BLOCK : PR_BLOCK) k_pr_tiles(TileArgs a) {
     constexpr uint32_t PR_TILE = PR_SUB * PR_NSUB;   // nonzeros per warp tile
+    constexpr uint32_t WARPS = (HUB ? PR_HUB_BLOCK : PR_BLOCK) / 32;
+    extern __shared__ float4 s_hub4[];
+    const float *s_hub = reinterpret_cast<const float *>(s_hub4);
+    if (HUB) {
+        // x of the first nhub vertices, once per block (x is padded past n to a multiple of 4)
+        const float4 *x4 = reinterpret_cast<const float4 *>(a.x);
+        for (uint32_t i = threadIdx.x; i < a.nhub / 4; i += blockDim.x) s_hub4[i] = __ldg(&x4[i]);
+        __syncthreads();
+    }
     const uint32_t full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const uint32_t nwarps = gridDim.x * PR_WARPS;
+    const uint32_t nwarps = gridDim.x * WARPS;
     const uint4 *ci4 = reinterpret_cast<const uint4 *>(a.ci);
-    for (uint32_t t = blockIdx.x * PR_WARPS + (threadIdx.x >> 5); t < a.ntiles; t += nwarps) {
-        const uint64_t t0 = (uint64_t)t * PR_TILE;
-        // every load of the tile first: column indices and start bits, then the gathers
-        uint32_t col[PR_NSUB][4], fl[PR_NSUB];
+    // a tile's own loads: column indices, start bits and the rank of its first row start
+    uint32_t col[PR_NSUB][4], fl[PR_NSUB], rank0 = 0;
+    auto load_tile = [&](uint32_t tt, uint32_t (&c)[PR_NSUB][4], uint32_t (&fo)[PR_NSUB], uint32_t &r0) {
+        const uint64_t b = (uint64_t)tt * PR_TILE;
 #pragma unroll
         for (uint32_t k2 = 0; k2 < PR_NSUB; ++k2) {
-            const uint64_t e = t0 + k2 * PR_SUB + 4 * lane;
+            const uint64_t e = b + k2 * PR_SUB + 4 * lane;
             uint4 c4 = make_uint4(0, 0, 0, 0);
             uint32_t f = 0;
             if (e < a.nnz) {
@@ -89,24 +124,38 @@ __global__ void __launch_bounds__(PR_BLOCK) k_pr_tiles(TileArgs a) {
                 const uint64_t left = a.nnz - e;
                 if (left < 4) f &= (1u << left) - 1u;
             }
-            col[k2][0] = c4.x; col[k2][1] = c4.y; col[k2][2] = c4.z; col[k2][3] = c4.w;
-            fl[k2] = f;
+            c[k2][0] = c4.x; c[k2][1] = c4.y; c[k2][2] = c4.z; c[k2][3] = c4.w;
+            fo[k2] = f;
         }
+        r0 = __ldg(&a.trank[tt]);
+    };
+    uint32_t t = blockIdx.x * WARPS + (threadIdx.x >> 5);
+    if (t < a.ntiles) load_tile(t, col, fl, rank0);
+    for (; t < a.ntiles; t += nwarps) {
+        const uint64_t t0 = (uint64_t)t * PR_TILE;
+        // the gathers of this tile, then the loads of the warp's next tile,
+        // which stream from DRAM while the gathers and the row sums run
         float xv[PR_NSUB][4];
 #pragma unroll
         for (uint32_t k2 = 0; k2 < PR_NSUB; ++k2)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const uint64_t e = t0 + k2 * PR_SUB + 4 * lane + j;
-                xv[k2][j] = e < a.nnz ? __ldg(&a.x[col[k2][j]]) : 0.f;
+                const uint32_t c = col[k2][j];
+                xv[k2][j] = e >= a.nnz ? 0.f : (HUB && c < a.nhub) ? s_hub[c] : __ldg(&a.x[c]);
             }
+        const uint32_t R0 = rank0;
+        uint32_t R = R0;                   // rank of the next row start
+        uint32_t fthis[PR_NSUB];
+#pragma unroll
+        for (uint32_t k2 = 0; k2 < PR_NSUB; ++k2) fthis[k2] = fl[k2];
+        if (t + nwarps < a.ntiles) load_tile(t + nwarps, col, fl, rank0);
         // sub-tiles in order; the row open across them is carried warp-wide
-        uint32_t R = __ldg(&a.trank[t]);   // rank of the next row start
         float carry = 0.f;                 // partial sum of the open row
         bool carry_in_tile = false;        // the open row began inside this tile
 #pragma unroll
         for (uint32_t k2 = 0; k2 < PR_NSUB; ++k2) {
-            const uint32_t f = fl[k2];
+            const uint32_t f = fthis[k2];
             const uint32_t nf = __popc(f);
             uint32_t tot;
             const uint32_t excl = dev::warp_exclusive_sum<uint32_t>(nf, &tot);
@@ -119,7 +168,7 @@ __global__ void __launch_bounds__(PR_BLOCK) k_pr_tiles(TileArgs a) {
             for (int j = 0; j < 4; ++j) {
                 if ((f >> j) & 1u) {
                     if (seen) {
-                        a.y[__ldg(&a.live[r])] = acc;
+                        a.y[row_of(a, r)] = acc;
                         ++r;
                     } else {
                         head = acc;
@@ -151,7 +200,7 @@ __global__ void __launch_bounds__(PR_BLOCK) k_pr_tiles(TileArgs a) {
             if (seen) {
                 // the row this lane's first start closes: rank Rb - 1
                 const float total = inflow + head;
-                if (started_before || carry_in_tile) a.y[__ldg(&a.live[Rb - 1])] = total;
+                if (started_before || carry_in_tile) a.y[row_of(a, Rb - 1)] = total;
                 else a.pfirst[t] = total;   // it began before the tile: finished by k_pr_span
             }
             const float last = __shfl_sync(full, v, 31);
@@ -164,7 +213,7 @@ __global__ void __launch_bounds__(PR_BLOCK) k_pr_tiles(TileArgs a) {
             R += tot;
         }
         if (lane == 0) {
-            const bool any = R != __ldg(&a.trank[t]);
+            const bool any = R != R0;
             a.tflag[t] = any ? 1u : 0u;
             if (any) {
                 a.plast[t] = carry;
@@ -178,16 +227,31 @@ __global__ void __launch_bounds__(PR_BLOCK) k_pr_tiles(TileArgs a) {
 
 // rows that cross tile ends: the partial at the end of the tile where the
 // row starts, plus the partials of the following tiles up to the first one
-// that holds a row start, in tile order
+// that holds a row start, in tile order. The flags and partials are read 8
+// tiles at a time: a row of 100,000 nonzeros crosses hundreds of tiles.
 __global__ void __launch_bounds__(PR_BLOCK) k_pr_span(TileArgs a) {
+    constexpr uint32_t R = 8;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < a.ntiles; t += gridDim.x * blockDim.x) {
         if (!a.tflag[t]) continue;
         float total = a.plast[t];
-        for (uint32_t t2 = t + 1; t2 < a.ntiles; ++t2) {
-            total += a.pfirst[t2];
-            if (a.tflag[t2]) break;
+        bool done = false;
+        for (uint32_t t2 = t + 1; !done && t2 < a.ntiles; t2 += R) {
+            uint32_t f[R];
+            float pf[R];
+#pragma unroll
+            for (uint32_t k = 0; k < R; ++k) {
+                const bool in = t2 + k < a.ntiles;
+                f[k] = in ? a.tflag[t2 + k] : 1u;
+                pf[k] = in ? a.pfirst[t2 + k] : 0.f;
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < R; ++k) {
+                if (done) break;
+                if (t2 + k < a.ntiles) total += pf[k];
+                done = f[k] != 0u;
+            }
         }
-        a.y[__ldg(&a.live[a.rlast[t]])] = total;
+        a.y[row_of(a, a.rlast[t])] = total;
     }
 }
 
@@ -199,12 +263,42 @@ struct UpdArgs {
     const float *base;        // device scalar: (1-a)/n + a*D/n
     float alpha;
     double *part_res, *part_dang;
+    uint32_t *done;           // blocks finished (the last one reduces, then resets it)
+    double *residual_out;     // this iteration's residual
+    float *base_out;          // the next iteration's base term (read by every block first)
 };
 
+// One block of PR_BLOCK threads: the FP64 partials in a fixed order -> the
+// residual, the dangling mass D and the next base term (1-a)/n + a D/n.
+__device__ void reduce_parts(uint32_t n, float alpha, const double *part_res, const double *part_dang,
+                             uint32_t nparts, double *residual_out, float *base_out, double (*s)[PR_BLOCK]) {
+    double r0 = 0, r1 = 0;
+    for (uint32_t b = threadIdx.x; b < nparts; b += PR_BLOCK) {
+        r0 += __ldcg(&part_res[b]);
+        r1 += __ldcg(&part_dang[b]);
+    }
+    s[0][threadIdx.x] = r0;
+    s[1][threadIdx.x] = r1;
+    __syncthreads();
+    for (int st = PR_BLOCK / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) { s[0][threadIdx.x] += s[0][threadIdx.x + st]; s[1][threadIdx.x] += s[1][threadIdx.x + st]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (residual_out) *residual_out = s[0][0];
+        const double nn = (double)n;
+        *base_out = (float)((1.0 - (double)alpha) / nn + (double)alpha * s[1][0] / nn);
+    }
+}
+
 // p' = base + a y, x' = p'/deg; FP64 partial sums of |p' - p| and of the
-// dangling p', each block over a fixed contiguous range of rows
+// dangling p', each block over a fixed contiguous range of rows. The block
+// that finishes last adds the partials up (reduce_parts): the order of that
+// sum does not depend on which block it is.
 __global__ void __launch_bounds__(PR_BLOCK) k_pr_update(UpdArgs a) {
     __shared__ double s_red[2][PR_WARPS];
+    __shared__ double s_fin[2][PR_BLOCK];
+    __shared__ bool s_last;
     const uint64_t per = ((uint64_t)a.n + gridDim.x - 1) / gridDim.x;
     const uint64_t b0 = per * blockIdx.x, b1 = b0 + per < a.n ? b0 + per : a.n;
     const float base = *a.base;
@@ -227,32 +321,22 @@ __global__ void __launch_bounds__(PR_BLOCK) k_pr_update(UpdArgs a) {
         for (int w = 0; w < PR_WARPS; ++w) { r0 += s_red[0][w]; r1 += s_red[1][w]; }
         a.part_res[blockIdx.x] = r0;
         a.part_dang[blockIdx.x] = r1;
+        __threadfence();
+        s_last = atomicAdd(a.done, 1u) == gridDim.x - 1;
     }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    reduce_parts(a.n, a.alpha, a.part_res, a.part_dang, gridDim.x, a.residual_out, a.base_out, s_fin);
+    if (threadIdx.x == 0) *a.done = 0u;
 }
 
-// One block: the FP64 partials in a fixed order -> the iteration's residual,
-// the dangling mass D and the next base term (1-a)/n + a D/n.
+// One block: reduce_parts of the initial dangling mass
 __global__ void __launch_bounds__(PR_BLOCK) k_pr_reduce(uint32_t n, float alpha, const double *part_res,
                                                        const double *part_dang, uint32_t nparts,
                                                        double *residual_out, float *base_out) {
     __shared__ double s[2][PR_BLOCK];
-    double r0 = 0, r1 = 0;
-    for (uint32_t b = threadIdx.x; b < nparts; b += PR_BLOCK) {
-        r0 += part_res[b];
-        r1 += part_dang[b];
-    }
-    s[0][threadIdx.x] = r0;
-    s[1][threadIdx.x] = r1;
-    __syncthreads();
-    for (int st = PR_BLOCK / 2; st > 0; st >>= 1) {
-        if (threadIdx.x < st) { s[0][threadIdx.x] += s[0][threadIdx.x + st]; s[1][threadIdx.x] += s[1][threadIdx.x + st]; }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        if (residual_out) *residual_out = s[0][0];
-        const double nn = (double)n;
-        *base_out = (float)((1.0 - (double)alpha) / nn + (double)alpha * s[1][0] / nn);
-    }
+    reduce_parts(n, alpha, part_res, part_dang, nparts, residual_out, base_out, s);
 }
 
 // p0 = 1/n, x0 = p0/deg; per-block dangling mass
@@ -292,8 +376,9 @@ __global__ void __launch_bounds__(PR_BLOCK) k_pr_sum(uint32_t n, const float *p,
     if (threadIdx.x == 0) part[blockIdx.x] = s[0];
 }
 
+// out[v] = p[new_id[v]] / S (new_id null: the identity)
 __global__ void __launch_bounds__(PR_BLOCK) k_pr_norm(uint32_t n, const float *p, const double *part, uint32_t nparts,
-                                                     float *out) {
+                                                     const uint32_t *new_id, float *out) {
     __shared__ double s_tot;
     if (threadIdx.x == 0) {
         double t = 0;
@@ -303,20 +388,49 @@ __global__ void __launch_bounds__(PR_BLOCK) k_pr_norm(uint32_t n, const float *p
     __syncthreads();
     const double inv = 1.0 / s_tot;
     for (uint32_t i = blockIdx.x * PR_BLOCK + threadIdx.x; i < n; i += gridDim.x * PR_BLOCK)
-        out[i] = (float)((double)p[i] * inv);
+        out[i] = (float)((double)p[new_id ? __ldg(&new_id[i]) : i] * inv);
 }
 
 }  // namespace
 }  // namespace gbx
 
-// tile kernel with nsub sub-tiles per warp tile (2, 4 or 8)
-static const void *tiles_kernel(uint32_t nsub) {
-    return nsub == 2 ? (const void *)k_pr_tiles<2> : nsub == 8 ? (const void *)k_pr_tiles<8> : (const void *)k_pr_tiles<4>;
+// tile kernel with nsub sub-tiles per warp tile (2, 4 or 8), staging ranks in
+// shared memory or not (nsub 2 or 4 there)
+static const void *tiles_kernel(uint32_t nsub, bool hub) {
+    if (hub) return nsub == 2 ? (const void *)k_pr_tiles<2, true> : (const void *)k_pr_tiles<4, true>;
+    return nsub == 2 ? (const void *)k_pr_tiles<2, false>
+                     : nsub == 8 ? (const void *)k_pr_tiles<8, false> : (const void *)k_pr_tiles<4, false>;
 }
 
-// One PageRank of `iters` iterations with warp tiles of nsub sub-tiles.
+// The copy of A with vertices renamed by decreasing out-degree (ties by
+// lower id), built on first use and kept on A with the renaming.
+static gb_info pagerank_view(const gb_matrix *Ac) {
+    gb_matrix *A = const_cast<gb_matrix *>(Ac);
+    std::lock_guard<std::mutex> lock(A->cache_mu);
+    if (A->pr_view) return GB_SUCCESS;
+    gb_context *ctx = A->ctx;
+    gb_matrix *B = nullptr;
+    uint32_t *nid = nullptr;
+    GB_CHECK(gb_matrix_new(&B, ctx, A->type, A->nrows, A->ncols));
+    gb_info r = dalloc_t(ctx, &nid, (size_t)A->nrows + 1);
+    if (r == GB_SUCCESS) r = gb_matrix_degree_order(B, A, nid, GB_DEVICE);
+    if (r != GB_SUCCESS) {
+        gb_matrix_free(&B);
+        dfree(ctx, nid);
+        return r;
+    }
+    // the copy serves PageRank alone: the BFS pull records are not kept
+    dfree(ctx, B->live_rec);
+    B->live_rec = nullptr;
+    A->pr_view = B;
+    A->pr_new_id = nid;
+    return GB_SUCCESS;
+}
+
+// One PageRank of `iters` iterations with warp tiles of nsub sub-tiles, on A
+// as stored (order 0) or on its degree-ordered copy with staged ranks (1).
 static gb_info pagerank_run(gb_context *ctx, const gb_matrix *A, float damping, uint32_t iters, float *rank,
-                            double *residuals, gb_mem mem, uint32_t nsub) {
+                            double *residuals, gb_mem mem, uint32_t nsub, int order, uint32_t staged) {
     if (!ctx || !A || !rank) return fail(GB_NULL_POINTER, "gb_pagerank: NULL argument");
     if (!A->built) return fail(GB_INVALID_VALUE, "gb_pagerank: matrix not built");
     if (A->nrows != A->ncols) return fail(GB_DIMENSION_MISMATCH, "gb_pagerank: matrix must be square");
@@ -326,18 +440,35 @@ static gb_info pagerank_run(gb_context *ctx, const gb_matrix *A, float damping, 
     const uint32_t n = A->nrows;
     if (n == 0) return GB_SUCCESS;
     GB_CUDA(cudaSetDevice(ctx->device));
-    const uint64_t m = A->nvals;
+    const gb_matrix *M = A;               // the matrix the iterations run on
+    const uint32_t *new_id = nullptr;     // its renaming of A's vertices
+    if (order) {
+        GB_CHECK(pagerank_view(A));
+        M = A->pr_view;
+        new_id = A->pr_new_id;
+    }
+    const uint64_t m = M->nvals;
     if (nsub != 2 && nsub != 8) nsub = 4;
+    const bool hub = order != 0;
+    if (hub && nsub == 8) nsub = 4;
     const uint32_t tile = PR_SUB * nsub;
     const uint32_t ntiles = (uint32_t)((m + tile - 1) / tile);
     const uint32_t nfw = (uint32_t)((m + 31) / 32);
+    // x is padded to n + 4 floats, so nhub rounded up to a multiple of 4 stays inside it
+    if (staged == 0 || staged > PR_HUB_MAX) staged = PR_HUB_DEFAULT;
+    const uint32_t nhub = hub ? (((n + 3u) & ~3u) < staged ? ((n + 3u) & ~3u) : staged) : 0u;
+    const int block = hub ? PR_HUB_BLOCK : PR_BLOCK;
+    const size_t smem = (size_t)nhub * 4;
+    const void *kern = tiles_kernel(nsub, hub);
+    if (hub) GB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(PR_HUB_MAX * 4)));
     int occ = 0;
-    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tiles_kernel(nsub), PR_BLOCK, 0));
+    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem));
     // a plain (not cooperative) launch: it needs no co-residency, so it takes the
     // whole GPU even where a context's persistent kernels are capped, and the
     // hardware interleaves its blocks with those of concurrent work
     uint32_t G = (uint32_t)(occ > 0 ? occ : 1) * (uint32_t)ctx->num_sms;
-    const uint32_t need = (ntiles + PR_WARPS - 1) / PR_WARPS;
+    const uint32_t wpb = (uint32_t)block / 32;
+    const uint32_t need = (ntiles + wpb - 1) / wpb;
     if (G > need) G = need > 0 ? need : 1;
     const uint32_t UB = 1024;   // blocks of the update pass (fixed: the reduction order does not depend on the GPU)
     Scratch p0(ctx), p1(ctx), x0(ctx), x1(ctx), yb(ctx), fl(ctx), tr(ctx), pf(ctx), pl(ctx), rl(ctx), tf(ctx),
@@ -360,11 +491,16 @@ static gb_info pagerank_run(gb_context *ctx, const gb_matrix *A, float damping, 
     float *out = rank;
     if (mem == GB_HOST) { GB_CHECK(outb.alloc((size_t)n * 4 + 16)); out = outb.as<float>(); }
     float *base = reinterpret_cast<float *>(scal.as<char>() + 16);
+    uint32_t *done = reinterpret_cast<uint32_t *>(scal.as<char>() + 32);
     // once per call: the row-start bits, their per-tile prefix, zero row sums
-    // (rows without in-edges are never written and keep y = 0)
+    // (rows without in-edges are never written and keep y = 0), and zero x
+    // padding (staged with the ranks, never gathered)
     GB_CHECK(memset_async(ctx, fl.p, 0, (size_t)nfw * 4 + 64));
     GB_CHECK(memset_async(ctx, yb.p, 0, (size_t)n * 4 + 16));
-    k_pr_flags<<<1024, PR_BLOCK, 0, ctx->stream>>>(A->colptr, n, fl.as<uint32_t>());
+    GB_CHECK(memset_async(ctx, x0.p, 0, (size_t)n * 4 + 16));
+    GB_CHECK(memset_async(ctx, x1.p, 0, (size_t)n * 4 + 16));
+    GB_CHECK(memset_async(ctx, scal.p, 0, 64));
+    k_pr_flags<<<1024, PR_BLOCK, 0, ctx->stream>>>(M->colptr, n, fl.as<uint32_t>());
     if (ntiles) {
         k_pr_tilecount<<<(ntiles + PR_BLOCK - 1) / PR_BLOCK < 4096 ? (ntiles + PR_BLOCK - 1) / PR_BLOCK : 4096,
                          PR_BLOCK, 0, ctx->stream>>>(fl.as<uint32_t>(), nfw, ntiles, tile, tr.as<uint32_t>());
@@ -372,17 +508,20 @@ static gb_info pagerank_run(gb_context *ctx, const gb_matrix *A, float damping, 
         GB_CHECK(scan_exclusive_u32(ctx, tr.as<uint32_t>(), tr.as<uint32_t>(), ntiles, nullptr));
     }
     // init: p0, x0, D0 -> base
-    k_pr_init<<<UB, PR_BLOCK, 0, ctx->stream>>>(n, A->rowptr, p0.as<float>(), x0.as<float>(), pdang.as<double>(),
+    k_pr_init<<<UB, PR_BLOCK, 0, ctx->stream>>>(n, M->rowptr, p0.as<float>(), x0.as<float>(), pdang.as<double>(),
                                              pres.as<double>());
     k_pr_reduce<<<1, PR_BLOCK, 0, ctx->stream>>>(n, damping, pres.as<double>(), pdang.as<double>(), UB, nullptr, base);
     GB_LAUNCH_CHECK();
     TileArgs ta;
     ta.nnz = m;
     ta.ntiles = ntiles;
-    ta.ci = A->rowidx;
+    ta.ci = M->rowidx;
     ta.flags = fl.as<uint32_t>();
     ta.trank = tr.as<uint32_t>();
-    ta.live = A->live_list;
+    // in the degree-ordered copy of a symmetric matrix the vertices with
+    // edges come first, so the k-th nonempty row is row k
+    ta.live = (order && M->csc_alias) ? nullptr : M->live_list;
+    ta.nhub = nhub;
     ta.y = yb.as<float>();
     ta.pfirst = pf.as<float>();
     ta.plast = pl.as<float>();
@@ -391,35 +530,36 @@ static gb_info pagerank_run(gb_context *ctx, const gb_matrix *A, float damping, 
     UpdArgs ua;
     ua.n = n;
     ua.y = yb.as<float>();
-    ua.rp_out = A->rowptr;
+    ua.rp_out = M->rowptr;
     ua.base = base;
     ua.alpha = damping;
     ua.part_res = pres.as<double>();
     ua.part_dang = pdang.as<double>();
+    ua.done = done;
+    ua.base_out = base;
     const uint32_t SB = (ntiles + PR_BLOCK - 1) / PR_BLOCK < 1024 ? (ntiles + PR_BLOCK - 1) / PR_BLOCK : 1024;
     float *pc = p0.as<float>(), *pn = p1.as<float>(), *xc = x0.as<float>(), *xn = x1.as<float>();
     for (uint32_t it = 0; it < iters; ++it) {
         ta.x = xc;
         ua.p_old = pc; ua.p_new = pn; ua.x_new = xn;
+        ua.residual_out = resid.as<double>() + it;
         if (ntiles) {
             int span = prof_begin(ctx, "pagerank_spmv");
             void *args[] = {&ta};
-            GB_CUDA(cudaLaunchKernel(tiles_kernel(nsub), dim3(G), dim3(PR_BLOCK), args, 0, ctx->stream));
+            GB_CUDA(cudaLaunchKernel(kern, dim3(G), dim3(block), args, smem, ctx->stream));
             prof_end(ctx, span);
             k_pr_span<<<SB, PR_BLOCK, 0, ctx->stream>>>(ta);
         }
         int span = prof_begin(ctx, "pagerank_update");
         k_pr_update<<<UB, PR_BLOCK, 0, ctx->stream>>>(ua);
         prof_end(ctx, span);
-        k_pr_reduce<<<1, PR_BLOCK, 0, ctx->stream>>>(n, damping, pres.as<double>(), pdang.as<double>(), UB,
-                                                     resid.as<double>() + it, base);
         GB_LAUNCH_CHECK();
         float *t = pc; pc = pn; pn = t;
         t = xc; xc = xn; xn = t;
     }
-    // final normalisation in FP64
+    // final normalisation in FP64, back to A's vertex names
     k_pr_sum<<<1024, PR_BLOCK, 0, ctx->stream>>>(n, pc, pres.as<double>());
-    k_pr_norm<<<1024, PR_BLOCK, 0, ctx->stream>>>(n, pc, pres.as<double>(), 1024, out);
+    k_pr_norm<<<1024, PR_BLOCK, 0, ctx->stream>>>(n, pc, pres.as<double>(), 1024, new_id, out);
     GB_LAUNCH_CHECK();
     if (residuals && iters) GB_CUDA(cudaMemcpyAsync(residuals, resid.p, (size_t)iters * 8, cudaMemcpyDeviceToHost, ctx->stream));
     if (mem == GB_HOST) GB_CUDA(cudaMemcpyAsync(rank, out, (size_t)n * 4, cudaMemcpyDeviceToHost, ctx->stream));
@@ -431,10 +571,11 @@ extern "C" gb_info gb_pagerank(gb_context *ctx, const gb_matrix *A, float dampin
                                double *residuals, gb_mem mem) {
     if (!A) return fail(GB_NULL_POINTER, "gb_pagerank: NULL argument");
     return pagerank_run(ctx, A, damping, iters, rank, residuals, mem,
-                        A->tuned_pr_nsub ? A->tuned_pr_nsub : PR_NSUB_DEFAULT);
+                        A->tuned_pr_nsub ? A->tuned_pr_nsub : PR_NSUB_DEFAULT, A->pr_order, A->pr_staged);
 }
 
-extern "C" gb_info gb_pagerank_autotune(gb_context *ctx, gb_matrix *A, uint32_t *tile_nnz, double *ms_per_iteration) {
+extern "C" gb_info gb_pagerank_autotune(gb_context *ctx, gb_matrix *A, uint32_t *tile_nnz, int32_t *degree_order,
+                                        uint32_t *staged_ranks, double *ms_per_iteration) {
     if (!ctx || !A || !tile_nnz) return fail(GB_NULL_POINTER, "gb_pagerank_autotune: NULL argument");
     if (!A->built || A->nrows != A->ncols || !A->has_csc)
         return fail(GB_INVALID_VALUE, "gb_pagerank_autotune: needs a built square matrix with its CSC");
@@ -444,19 +585,30 @@ extern "C" gb_info gb_pagerank_autotune(gb_context *ctx, gb_matrix *A, uint32_t 
     cudaEvent_t e0, e1;
     GB_CUDA(cudaEventCreate(&e0));
     GB_CUDA(cudaEventCreate(&e1));
-    static const uint32_t cand[] = {2, 4, 8};
+    // (sub-tiles, order, staged ranks): the tiles as stored, and on the
+    // degree-ordered copy the tiles that fit the staged-rank kernel's
+    // register budget with 16,384 and 32,768 staged ranks (64 or 128 KB:
+    // the larger sets leave too little L1 for the other gathers)
+    static const uint32_t cand_nsub[] = {2, 4, 8, 2, 4, 2, 4};
+    static const int cand_order[] = {0, 0, 0, 1, 1, 1, 1};
+    static const uint32_t cand_staged[] = {0, 0, 0, 16384, 16384, 32768, 32768};
+    constexpr int NC = 7;
     constexpr uint32_t ITERS = 8;
     double best = 1e30;
-    uint32_t bn = PR_NSUB_DEFAULT;
+    int bc = 1;
     gb_info r = GB_SUCCESS;
     // two passes over the candidates (forward, then backward), each keeping its faster pass
-    double tmin[3] = {1e30, 1e30, 1e30};
+    double tmin[NC];
+    for (int c = 0; c < NC; ++c) tmin[c] = 1e30;
     for (int pass = 0; pass < 2 && r == GB_SUCCESS; ++pass) {
-        for (int ci = 0; ci < 3 && r == GB_SUCCESS; ++ci) {
-            const int c = pass == 0 ? ci : 2 - ci;
-            r = pagerank_run(ctx, A, 0.85f, 2, out.as<float>(), nullptr, GB_DEVICE, cand[c]);   // warm
+        for (int ci = 0; ci < NC && r == GB_SUCCESS; ++ci) {
+            const int c = pass == 0 ? ci : NC - 1 - ci;
+            r = pagerank_run(ctx, A, 0.85f, 2, out.as<float>(), nullptr, GB_DEVICE, cand_nsub[c], cand_order[c],
+                                 cand_staged[c]);   // warm
             if (r == GB_SUCCESS && cudaEventRecord(e0, ctx->stream) != cudaSuccess) r = GB_PANIC;
-            if (r == GB_SUCCESS) r = pagerank_run(ctx, A, 0.85f, ITERS, out.as<float>(), nullptr, GB_DEVICE, cand[c]);
+            if (r == GB_SUCCESS)
+                r = pagerank_run(ctx, A, 0.85f, ITERS, out.as<float>(), nullptr, GB_DEVICE, cand_nsub[c], cand_order[c],
+                                 cand_staged[c]);
             if (r == GB_SUCCESS && cudaEventRecord(e1, ctx->stream) != cudaSuccess) r = GB_PANIC;
             if (r == GB_SUCCESS && cudaEventSynchronize(e1) != cudaSuccess) r = GB_PANIC;
             float ms = 0;
@@ -467,10 +619,20 @@ extern "C" gb_info gb_pagerank_autotune(gb_context *ctx, gb_matrix *A, uint32_t 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (r != GB_SUCCESS) return r == GB_PANIC ? fail(GB_PANIC, "gb_pagerank_autotune: CUDA error") : r;
-    for (int c = 0; c < 3; ++c)
-        if (tmin[c] < best) { best = tmin[c]; bn = cand[c]; }
-    A->tuned_pr_nsub = bn;
-    *tile_nnz = bn * PR_SUB;
+    for (int c = 0; c < NC; ++c)
+        if (tmin[c] < best) { best = tmin[c]; bc = c; }
+    A->tuned_pr_nsub = cand_nsub[bc];
+    A->pr_order = cand_order[bc];
+    A->pr_staged = cand_staged[bc];
+    if (!A->pr_order && A->pr_view) {   // the copy is not used: give its memory back
+        std::lock_guard<std::mutex> lock(A->cache_mu);
+        gb_matrix_free(&A->pr_view);
+        dfree(ctx, A->pr_new_id);
+        A->pr_new_id = nullptr;
+    }
+    *tile_nnz = cand_nsub[bc] * PR_SUB;
+    if (degree_order) *degree_order = cand_order[bc];
+    if (staged_ranks) *staged_ranks = cand_order[bc] ? cand_staged[bc] : 0u;
     if (ms_per_iteration) *ms_per_iteration = best / ITERS;
     return GB_SUCCESS;
 }
@@ -480,5 +642,17 @@ extern "C" gb_info gb_pagerank_set_tile(gb_matrix *A, uint32_t tile_nnz) {
     if (tile_nnz != 0 && tile_nnz != 2 * PR_SUB && tile_nnz != 4 * PR_SUB && tile_nnz != 8 * PR_SUB)
         return fail(GB_INVALID_VALUE, "gb_pagerank_set_tile: tile of %u nonzeros (256, 512, 1024 or 0)", tile_nnz);
     A->tuned_pr_nsub = tile_nnz / PR_SUB;
+    return GB_SUCCESS;
+}
+
+extern "C" gb_info gb_pagerank_set_order(gb_matrix *A, int32_t degree_order, uint32_t staged_ranks) {
+    if (!A) return fail(GB_NULL_POINTER, "gb_pagerank_set_order: NULL matrix");
+    if (degree_order != 0 && degree_order != 1)
+        return fail(GB_INVALID_VALUE, "gb_pagerank_set_order: %d (0 = as stored, 1 = degree order)", (int)degree_order);
+    if (staged_ranks % 1024 != 0 || staged_ranks > PR_HUB_MAX)
+        return fail(GB_INVALID_VALUE, "gb_pagerank_set_order: %u staged ranks (a multiple of 1,024 up to %u, 0 = default)",
+                    staged_ranks, PR_HUB_MAX);
+    A->pr_order = degree_order;
+    A->pr_staged = staged_ranks;
     return GB_SUCCESS;
 }

@@ -137,16 +137,23 @@ def test_cc_fastsv_weak_components_and_errors(ctx):
 
 
 # ---------------------------------------------------------------- PageRank
+@pytest.mark.parametrize("order", [0, 1, 57344])
 @pytest.mark.parametrize("tile", [256, 512, 1024])
-@pytest.mark.parametrize("case", ["rmat14", "rmat12_e4", "grid", "star", "cycle"])
-def test_pagerank_l1_vs_fp64_oracle(ctx, case, tile):
+@pytest.mark.parametrize("case", ["rmat14", "rmat17", "rmat12_e4", "grid", "star", "cycle"])
+def test_pagerank_l1_vs_fp64_oracle(ctx, case, tile, order):
+    """order 1 runs on the degree-ordered copy with the default 32,768
+    staged ranks, 57344 with the largest staged set: below that many
+    vertices every rank is staged; R-MAT scale 17 (131,072) also gathers
+    the rest from global memory."""
     t = {"rmat14": lambda: gen.rmat(14, 16, seed=1),
+         "rmat17": lambda: gen.rmat(17, 16, seed=4),
          "rmat12_e4": lambda: gen.rmat(12, 4, seed=3),
          "grid": lambda: gen.grid(70, 50, 0.1, seed=3),
          "star": lambda: gen.from_edges(300, [(0, i) for i in range(1, 300)]),
          "cycle": lambda: gen.from_edges(1000, [(i, (i + 1) % 1000) for i in range(1000)])}[case]()
     g, A = build(ctx, t, weights=False)
     gb.pagerank_set_tile(A, tile)
+    gb.pagerank_set_order(A, 1 if order else 0, order if order > 1 else 0)
     want, wres = oracle.pagerank(g, 0.85, 50)
     rank = np.empty(t.n, np.float32)
     _, res = gb.pagerank(ctx, A, 0.85, 50, rank)
@@ -160,9 +167,11 @@ def test_pagerank_l1_vs_fp64_oracle(ctx, case, tile):
     A.free()
 
 
-def test_pagerank_is_bit_reproducible(ctx):
-    t = gen.rmat(13, 16, seed=5)
+@pytest.mark.parametrize("order", [0, 1])
+def test_pagerank_is_bit_reproducible(ctx, order):
+    t = gen.rmat(17, 8, seed=5)
     g, A = build(ctx, t, weights=False)
+    gb.pagerank_set_order(A, order)
     r1 = np.empty(t.n, np.float32)
     r2 = np.empty(t.n, np.float32)
     gb.pagerank(ctx, A, 0.85, 20, r1)
@@ -245,9 +254,11 @@ def test_sssp_pagerank_rmat_s22_full_size(ctx):
     got, _ = sssp_gpu(ctx, A, s)
     assert np.array_equal(got, oracle.sssp(g, s))
     rank = np.empty(t.n, np.float32)
-    gb.pagerank(ctx, A, 0.85, 50, rank)
     want, _ = oracle.pagerank(g, 0.85, 50)
-    assert np.abs(rank.astype(np.float64) - want).sum() <= PR_L1_TOL
+    for order in (0, 1):     # as stored, and the degree-ordered copy with staged ranks
+        gb.pagerank_set_order(A, order)
+        gb.pagerank(ctx, A, 0.85, 50, rank)
+        assert np.abs(rank.astype(np.float64) - want).sum() <= PR_L1_TOL, order
     A.free()
 
 
@@ -431,9 +442,11 @@ def test_pagerank_and_delta_directed_matrix(ctx):
     A = gb.Matrix.from_tuples(ctx, n, r, c)
     g = oracle.csr_build(n, r, c)
     got = np.empty(n, np.float32)
-    gb.pagerank(ctx, A, 0.85, 30, got, residuals=False)
     want, _ = oracle.pagerank(g, 0.85, 30, directed=True)
-    assert np.abs(got.astype(np.float64) - want).sum() <= 1e-5
+    for order in (0, 1):     # the degree order is by out-degree: the CSC's column references
+        gb.pagerank_set_order(A, order)
+        gb.pagerank(ctx, A, 0.85, 30, got, residuals=False)
+        assert np.abs(got.astype(np.float64) - want).sum() <= 1e-5, order
     for eps in PRD_EPS:
         want, it_o, _ = oracle.pagerank_delta(g, 0.85, eps, 200, directed=True)
         _, it, _, _ = gb.pagerank_delta(ctx, A, 0.85, eps, 200, got)
@@ -539,8 +552,12 @@ def test_sssp_near_far_buckets_match_dijkstra(ctx, case):
 def test_pagerank_autotune_keeps_a_candidate_and_the_result(ctx):
     t = gen.rmat(14, 16, seed=41)
     g, A = build(ctx, t, weights=False)
-    tile, ms = gb.pagerank_autotune(ctx, A)
-    assert tile in (256, 512, 1024) and ms > 0
+    tile, order, staged, ms = gb.pagerank_autotune(ctx, A)
+    assert tile in (256, 512, 1024) and order in (0, 1) and ms > 0
+    if order == 1:
+        assert tile in (256, 512) and staged in (16384, 32768)
+    else:
+        assert staged == 0
     rank = np.empty(t.n, np.float32)
     gb.pagerank(ctx, A, 0.85, 50, rank)
     want, _ = oracle.pagerank(g, 0.85, 50)
@@ -548,4 +565,8 @@ def test_pagerank_autotune_keeps_a_candidate_and_the_result(ctx):
     with pytest.raises(gb.GBError) as e:
         gb.pagerank_set_tile(A, 300)
     assert e.value.code == gb.INVALID_VALUE
+    for bad in ((2, 0), (1, 1000), (1, 58368)):
+        with pytest.raises(gb.GBError) as e:
+            gb.pagerank_set_order(A, *bad)
+        assert e.value.code == gb.INVALID_VALUE
     A.free()
