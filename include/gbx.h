@@ -417,7 +417,9 @@ gb_info gb_sssp(gb_context *ctx, const gb_matrix *A, uint32_t src, uint32_t *dis
 /* PageRank (Section 7.3), pull SpMV in FP32 with FP32 accumulation:
  * p0 = 1/n; p' = (1-damping)/n + damping * (sum_{j in N(i)} p(j)/deg(j)
  * + dangling/n), exactly `iters` iterations; the per-iteration L1 residual
- * sum|p'-p| and the final normalisation are reduced in FP64.
+ * sum|p'-p| and the dangling mass are reduced in FP64 over FP32 sums of 4
+ * consecutive vertices, the final normalisation in FP64. The result is
+ * bit-reproducible run to run (fixed summation orders, no float atomics).
  * rank[n] in `mem`; residuals[iters] (host, may be NULL). */
 gb_info gb_pagerank(gb_context *ctx, const gb_matrix *A, float damping, uint32_t iters, float *rank,
                     double *residuals, gb_mem mem);

@@ -15,10 +15,10 @@
 // ascending list of nonempty rows, which the matrix keeps). Within a tile
 // the rows are closed by a lane walk and a warp-level segmented scan (no
 // shared memory, no block barrier); a row that crosses tile ends is
-// finished by k_pr_span, which adds the tiles' partial sums in tile order.
+// finished by k_pr_span, which adds the tiles' partial sums.
 // A separate pass applies the update p' = base + a y, x' = p'/deg and
-// reduces the L1 residual sum |p' - p| and the dangling mass D in FP64 in a
-// fixed order. Every sum has one fixed order and no floating-point atomics
+// reduces the L1 residual sum |p' - p| and the dangling mass D (FP32 over
+// 4 consecutive rows, FP64 above that) in a fixed order. Every sum has one fixed order and no floating-point atomics
 // are used, so a run is bit-reproducible.
 //
 // The gathers x[j] are the SpMV's limit: one random 4-byte load per
@@ -225,33 +225,74 @@ __global__ void __launch_bounds__(HUB ? PR_HUB_BLOCK : PR_BLOCK) k_pr_tiles(Tile
     }
 }
 
-// rows that cross tile ends: the partial at the end of the tile where the
-// row starts, plus the partials of the following tiles up to the first one
-// that holds a row start, in tile order. The flags and partials are read 8
-// tiles at a time: a row of 100,000 nonzeros crosses hundreds of tiles.
-__global__ void __launch_bounds__(PR_BLOCK) k_pr_span(TileArgs a) {
-    constexpr uint32_t R = 8;
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < a.ntiles; t += gridDim.x * blockDim.x) {
-        if (!a.tflag[t]) continue;
-        float total = a.plast[t];
-        bool done = false;
-        for (uint32_t t2 = t + 1; !done && t2 < a.ntiles; t2 += R) {
-            uint32_t f[R];
-            float pf[R];
+// Rows that cross tile ends: the partial at the end of the tile t where
+// the row starts, plus the partials of the following tiles up to the first
+// one that holds a row start (or the last tile). The first SB blocks take
+// a thread per tile and read the next SPAN_SHORT tiles' flags and partials
+// at once, adding them in tile order; a row that runs on past those (a row
+// of thousands of nonzeros, hundreds of tiles for the largest) is left to
+// the warps of the other blocks, a warp per row from the list
+// k_pr_long_spans made: each lane adds every 32nd partial after t in tile
+// order, the lanes' sums are added by a fixed shuffle tree, then the
+// partial of t.
+constexpr uint32_t SPAN_SHORT = 8;
+
+// has tile t a row start (t < ntiles - 1)
+__device__ __forceinline__ bool tile_has_start(const uint32_t *trank, uint32_t t) {
+    return __ldg(&trank[t + 1]) > __ldg(&trank[t]);
+}
+
+// once per call: (t, t2) for every row that starts in tile t and crosses
+// more than SPAN_SHORT tiles after it, t2 its last tile
+__global__ void k_pr_long_spans(const uint32_t *trank, uint32_t ntiles, uint2 *list, uint32_t *count) {
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
+        if ((uint64_t)t + SPAN_SHORT + 1 >= ntiles || !tile_has_start(trank, t)) continue;
+        bool closed = false;
+        for (uint32_t k = 1; k <= SPAN_SHORT && !closed; ++k) closed = tile_has_start(trank, t + k);
+        if (closed) continue;
+        uint32_t t2 = t + SPAN_SHORT + 1;
+        while (t2 < ntiles - 1 && !tile_has_start(trank, t2)) ++t2;
+        list[atomicAdd(count, 1u)] = make_uint2(t, t2);
+    }
+}
+
+__global__ void __launch_bounds__(PR_BLOCK) k_pr_span(TileArgs a, uint32_t short_blocks, const uint2 *long_list,
+                                                     const uint32_t *long_count) {
+    if (blockIdx.x < short_blocks) {
+        for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < a.ntiles; t += short_blocks * blockDim.x) {
+            if (!a.tflag[t]) continue;
+            uint32_t f[SPAN_SHORT];
+            float pf[SPAN_SHORT];
 #pragma unroll
-            for (uint32_t k = 0; k < R; ++k) {
-                const bool in = t2 + k < a.ntiles;
-                f[k] = in ? a.tflag[t2 + k] : 1u;
-                pf[k] = in ? a.pfirst[t2 + k] : 0.f;
+            for (uint32_t k = 0; k < SPAN_SHORT; ++k) {
+                const bool in = (uint64_t)t + 1 + k < a.ntiles;
+                f[k] = in ? a.tflag[t + 1 + k] : 1u;
+                pf[k] = in ? a.pfirst[t + 1 + k] : 0.f;
             }
+            float total = a.plast[t];
+            bool done = false;
 #pragma unroll
-            for (uint32_t k = 0; k < R; ++k) {
+            for (uint32_t k = 0; k < SPAN_SHORT; ++k) {
                 if (done) break;
-                if (t2 + k < a.ntiles) total += pf[k];
+                if ((uint64_t)t + 1 + k < a.ntiles) total += pf[k];
                 done = f[k] != 0u;
             }
+            if (!done && (uint64_t)t + SPAN_SHORT + 1 < a.ntiles) continue;   // a long row
+            a.y[row_of(a, a.rlast[t])] = total;
         }
-        a.y[row_of(a, a.rlast[t])] = total;
+        return;
+    }
+    const uint32_t nlong = *long_count;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t w0 = (blockIdx.x - short_blocks) * PR_WARPS + (threadIdx.x >> 5);
+    const uint32_t nw = (gridDim.x - short_blocks) * PR_WARPS;
+    for (uint32_t e = w0; e < nlong; e += nw) {
+        const uint2 sp = long_list[e];
+        float acc = 0.f;
+        for (uint32_t k = sp.x + 1 + lane; k <= sp.y; k += 32) acc += a.pfirst[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) a.y[row_of(a, a.rlast[sp.x])] = a.plast[sp.x] + acc;
     }
 }
 
@@ -291,25 +332,83 @@ __device__ void reduce_parts(uint32_t n, float alpha, const double *part_res, co
     }
 }
 
-// p' = base + a y, x' = p'/deg; FP64 partial sums of |p' - p| and of the
-// dangling p', each block over a fixed contiguous range of rows. The block
+// p' = base + a y, x' = p'/deg; partial sums of |p' - p| and of the
+// dangling p' (FP32 over 4 consecutive rows, FP64 above that), each block
+// over a fixed contiguous range of rows. The block
 // that finishes last adds the partials up (reduce_parts): the order of that
 // sum does not depend on which block it is.
 __global__ void __launch_bounds__(PR_BLOCK) k_pr_update(UpdArgs a) {
     __shared__ double s_red[2][PR_WARPS];
     __shared__ double s_fin[2][PR_BLOCK];
     __shared__ bool s_last;
-    const uint64_t per = ((uint64_t)a.n + gridDim.x - 1) / gridDim.x;
-    const uint64_t b0 = per * blockIdx.x, b1 = b0 + per < a.n ? b0 + per : a.n;
+    // each block a range of a multiple of 4 rows; each thread takes 4
+    // consecutive rows per group with 16-byte loads and stores (the vectors
+    // and the row offsets start 256-byte aligned), and loads G groups
+    // before it computes any
+    constexpr int G = 2;
+    const uint64_t per = (((uint64_t)a.n + gridDim.x - 1) / gridDim.x + 3) & ~3ull;
+    const uint64_t b0 = per * blockIdx.x < a.n ? per * blockIdx.x : a.n;
+    const uint64_t b1 = b0 + per < a.n ? b0 + per : a.n;
     const float base = *a.base;
     double res = 0.0, dang = 0.0;
-    for (uint64_t i = b0 + threadIdx.x; i < b1; i += PR_BLOCK) {
-        const float p = base + a.alpha * a.y[i];
-        const uint32_t deg = __ldg(&a.rp_out[i + 1]) - __ldg(&a.rp_out[i]);
-        a.p_new[i] = p;
-        a.x_new[i] = deg ? p / (float)deg : 0.f;
-        res += fabs((double)p - (double)a.p_old[i]);
-        if (!deg) dang += (double)p;
+    for (uint64_t i0 = b0 + 4 * threadIdx.x; i0 < b1; i0 += 4 * PR_BLOCK * G) {
+        float yv[G][4], po[G][4];
+        uint32_t rp[G][5];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const uint64_t i = i0 + (uint64_t)g * 4 * PR_BLOCK;
+            if (i + 4 <= b1) {
+                const float4 y4 = __ldg(reinterpret_cast<const float4 *>(a.y + i));
+                const float4 o4 = __ldg(reinterpret_cast<const float4 *>(a.p_old + i));
+                const uint4 r4 = __ldg(reinterpret_cast<const uint4 *>(a.rp_out + i));
+                yv[g][0] = y4.x; yv[g][1] = y4.y; yv[g][2] = y4.z; yv[g][3] = y4.w;
+                po[g][0] = o4.x; po[g][1] = o4.y; po[g][2] = o4.z; po[g][3] = o4.w;
+                rp[g][0] = r4.x; rp[g][1] = r4.y; rp[g][2] = r4.z; rp[g][3] = r4.w;
+                rp[g][4] = __ldg(&a.rp_out[i + 4]);
+            } else {
+                // a ragged end: rows past b1 read nothing; rp[j] is row i+j's
+                // offset for every j up to the row count (b1 <= n, so i+j <= n)
+#pragma unroll
+                for (int j = 0; j < 5; ++j) {
+                    const bool in = i + j < b1;
+                    if (j < 4) {
+                        yv[g][j] = in ? __ldg(&a.y[i + j]) : 0.f;
+                        po[g][j] = in ? __ldg(&a.p_old[i + j]) : 0.f;
+                    }
+                    rp[g][j] = i + j <= b1 ? __ldg(&a.rp_out[i + j]) : 0u;
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const uint64_t i = i0 + (uint64_t)g * 4 * PR_BLOCK;
+            float pn[4], xn[4];
+            // the group's 4 terms in FP32, the group sums in FP64 (FP64 is
+            // slow on this part: one FP64 add per group, not per row)
+            float rg = 0.f, dg = 0.f;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t deg = rp[g][j + 1] - rp[g][j];
+                const float p = base + a.alpha * yv[g][j];
+                pn[j] = p;
+                xn[j] = deg ? p / (float)deg : 0.f;
+                if (i + j < b1) {
+                    rg += fabsf(p - po[g][j]);
+                    if (!deg) dg += p;
+                }
+            }
+            res += (double)rg;
+            dang += (double)dg;
+            if (i + 4 <= b1) {
+                *reinterpret_cast<float4 *>(a.p_new + i) = make_float4(pn[0], pn[1], pn[2], pn[3]);
+                *reinterpret_cast<float4 *>(a.x_new + i) = make_float4(xn[0], xn[1], xn[2], xn[3]);
+            } else {
+                for (int j = 0; j < 4 && i + j < b1; ++j) {
+                    a.p_new[i + j] = pn[j];
+                    a.x_new[i + j] = xn[j];
+                }
+            }
+        }
     }
     res = dev::warp_sum<double>(res);
     dang = dev::warp_sum<double>(dang);
@@ -472,7 +571,7 @@ static gb_info pagerank_run(gb_context *ctx, const gb_matrix *A, float damping, 
     if (G > need) G = need > 0 ? need : 1;
     const uint32_t UB = 1024;   // blocks of the update pass (fixed: the reduction order does not depend on the GPU)
     Scratch p0(ctx), p1(ctx), x0(ctx), x1(ctx), yb(ctx), fl(ctx), tr(ctx), pf(ctx), pl(ctx), rl(ctx), tf(ctx),
-        pres(ctx), pdang(ctx), scal(ctx), resid(ctx), outb(ctx);
+        pres(ctx), pdang(ctx), scal(ctx), resid(ctx), outb(ctx), lsp(ctx);
     GB_CHECK(p0.alloc((size_t)n * 4 + 16));
     GB_CHECK(p1.alloc((size_t)n * 4 + 16));
     GB_CHECK(x0.alloc((size_t)n * 4 + 16));
@@ -484,6 +583,8 @@ static gb_info pagerank_run(gb_context *ctx, const gb_matrix *A, float damping, 
     GB_CHECK(pl.alloc((size_t)ntiles * 4 + 16));
     GB_CHECK(rl.alloc((size_t)ntiles * 4 + 16));
     GB_CHECK(tf.alloc((size_t)ntiles * 4 + 16));
+    // each long row takes more than SPAN_SHORT tiles of its own
+    GB_CHECK(lsp.alloc(((size_t)ntiles / SPAN_SHORT + 1) * sizeof(uint2)));
     GB_CHECK(pres.alloc((size_t)UB * 8));
     GB_CHECK(pdang.alloc((size_t)UB * 8));
     GB_CHECK(scal.alloc(64));
@@ -492,6 +593,7 @@ static gb_info pagerank_run(gb_context *ctx, const gb_matrix *A, float damping, 
     if (mem == GB_HOST) { GB_CHECK(outb.alloc((size_t)n * 4 + 16)); out = outb.as<float>(); }
     float *base = reinterpret_cast<float *>(scal.as<char>() + 16);
     uint32_t *done = reinterpret_cast<uint32_t *>(scal.as<char>() + 32);
+    uint32_t *nlong = reinterpret_cast<uint32_t *>(scal.as<char>() + 48);
     // once per call: the row-start bits, their per-tile prefix, zero row sums
     // (rows without in-edges are never written and keep y = 0), and zero x
     // padding (staged with the ranks, never gathered)
@@ -506,6 +608,9 @@ static gb_info pagerank_run(gb_context *ctx, const gb_matrix *A, float damping, 
                          PR_BLOCK, 0, ctx->stream>>>(fl.as<uint32_t>(), nfw, ntiles, tile, tr.as<uint32_t>());
         GB_LAUNCH_CHECK();
         GB_CHECK(scan_exclusive_u32(ctx, tr.as<uint32_t>(), tr.as<uint32_t>(), ntiles, nullptr));
+        k_pr_long_spans<<<(ntiles + PR_BLOCK - 1) / PR_BLOCK < 1024 ? (ntiles + PR_BLOCK - 1) / PR_BLOCK : 1024,
+                          PR_BLOCK, 0, ctx->stream>>>(tr.as<uint32_t>(), ntiles, lsp.as<uint2>(), nlong);
+        GB_LAUNCH_CHECK();
     }
     // init: p0, x0, D0 -> base
     k_pr_init<<<UB, PR_BLOCK, 0, ctx->stream>>>(n, M->rowptr, p0.as<float>(), x0.as<float>(), pdang.as<double>(),
@@ -538,6 +643,7 @@ static gb_info pagerank_run(gb_context *ctx, const gb_matrix *A, float damping, 
     ua.done = done;
     ua.base_out = base;
     const uint32_t SB = (ntiles + PR_BLOCK - 1) / PR_BLOCK < 1024 ? (ntiles + PR_BLOCK - 1) / PR_BLOCK : 1024;
+    const uint32_t LB = 256;   // blocks for the long rows (a warp each)
     float *pc = p0.as<float>(), *pn = p1.as<float>(), *xc = x0.as<float>(), *xn = x1.as<float>();
     for (uint32_t it = 0; it < iters; ++it) {
         ta.x = xc;
@@ -548,7 +654,9 @@ static gb_info pagerank_run(gb_context *ctx, const gb_matrix *A, float damping, 
             void *args[] = {&ta};
             GB_CUDA(cudaLaunchKernel(kern, dim3(G), dim3(block), args, smem, ctx->stream));
             prof_end(ctx, span);
-            k_pr_span<<<SB, PR_BLOCK, 0, ctx->stream>>>(ta);
+            int sspan = prof_begin(ctx, "pagerank_span");
+            k_pr_span<<<SB + LB, PR_BLOCK, 0, ctx->stream>>>(ta, SB, lsp.as<uint2>(), nlong);
+            prof_end(ctx, sspan);
         }
         int span = prof_begin(ctx, "pagerank_update");
         k_pr_update<<<UB, PR_BLOCK, 0, ctx->stream>>>(ua);
