@@ -526,6 +526,32 @@ def extra_rows(args, hbm):
     gb.cc_fastsv(ctx, A, d)
     ms = cuda_time_ms(lambda: its.append(gb.cc_fastsv(ctx, A, d)[1]), stream)
     g_out.update({"cc_fastsv_ms": ms, "cc_fastsv_iterations": its[0]})
+    # the barrier-free schedule: SSSP by distance buckets, BFS and min-label
+    # components in one phase; each checked against its synchronous result
+    da = gb.Descriptor(schedule=gb.SCHED_ASYNC)
+    ref = torch.empty_like(d)
+    gb.sssp(ctx, A, src, ref)
+    _, it_a, st_a = gb.sssp(ctx, A, src, d, da, stats=True)
+    ms = cuda_time_ms(lambda: gb.sssp(ctx, A, src, d, da), stream)
+    ab = st_a["alg_bytes"]
+    g_out["async"] = {
+        "sssp_ms": ms, "sssp_buckets": it_a, "sssp_relaxations_per_vertex": st_a["vertices_reached"] / t.n,
+        "sssp_matches_sync": bool(torch.equal(d, ref)),
+        "sssp_roofline": {"bound": "hbm", "kernel": "k_async<SSSP>", "alg_bytes_per_launch": ab,
+                          "achieved": ab / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                          "frac": ab / (ms / 1e3) / 1e9 / hbm}}
+    gb.bfs(ctx, A, src, lvg, False, stats=False)
+    ref.copy_(lvg)
+    _, _, st_b = gb.bfs(ctx, A, src, lvg, pag, desc=da)
+    ms = cuda_time_ms(lambda: gb.bfs(ctx, A, src, lvg, pag, desc=da, stats=False), stream)
+    g_out["async"].update({"bfs_ms": ms, "bfs_relaxations_per_vertex": st_b["vertices_reached"] / t.n,
+                           "bfs_matches_sync": bool(torch.equal(lvg, ref))})
+    gb.cc_fastsv(ctx, A, ref)
+    _, st_c = gb.cc_async(ctx, A, d, stats=True)
+    ms = cuda_time_ms(lambda: gb.cc_async(ctx, A, d), stream)
+    g_out["async"].update({"cc_ms": ms, "cc_relaxations_per_vertex": st_c["vertices_reached"] / t.n,
+                           "cc_matches_fastsv": bool(torch.equal(d, ref))})
+    da.free()
     out["grid_4096"] = g_out
     A.free()
     ctx.close()

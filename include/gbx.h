@@ -87,7 +87,7 @@ typedef enum {
     GB_INP1 = 3,        /* GB_DEFAULT or GB_TRAN */
     GB_DIRECTION = 4,   /* GB_AUTO (default), GB_PUSH or GB_PULL */
     GB_SWITCH_BETA = 5, /* integer beta of the push/pull rule |E_f| > |E| / beta; 0 = tuned default */
-    GB_SCHEDULE = 6,    /* BFS: GB_SCHED_AUTO (default), GB_SCHED_GRID or GB_SCHED_CLUSTER */
+    GB_SCHEDULE = 6,    /* BFS, SSSP: GB_SCHED_AUTO (default), GB_SCHED_GRID, GB_SCHED_CLUSTER or GB_SCHED_ASYNC */
     GB_SSSP_DELTA = 7   /* SSSP: width of the distance buckets of the near-far frontier; 0 = automatic,
                            a width of at least 2^31 - 1 = no buckets (the plain changed-set iteration) */
 } gb_field;
@@ -101,9 +101,13 @@ enum {
     /* GB_SCHEDULE values. GRID: one persistent cooperative kernel over the
      * whole GPU, push or pull per level. CLUSTER: the whole traversal in one
      * thread-block cluster (push only, levels separated by the cluster
-     * barrier; for graphs of high diameter). AUTO: what gb_bfs_autotune
-     * chose for the matrix, GRID if it was not tuned. */
-    GB_SCHED_AUTO = 0, GB_SCHED_GRID = 1, GB_SCHED_CLUSTER = 2
+     * barrier; for graphs of high diameter). ASYNC: no level barriers at
+     * all: one persistent launch relaxes (value, vertex) work items through a
+     * ring that warps poll, until no item is in flight (the asynchronous
+     * execution model of Section 9; for graphs of high diameter; gb_bfs,
+     * gb_sssp; gb_cc_async is the components form). AUTO: what
+     * gb_bfs_autotune chose for the matrix, GRID if it was not tuned. */
+    GB_SCHED_AUTO = 0, GB_SCHED_GRID = 1, GB_SCHED_CLUSTER = 2, GB_SCHED_ASYNC = 3
 };
 
 /* Matrix build flags. */
@@ -320,7 +324,14 @@ typedef struct {
     float trace_us[GB_TRACE_LEVELS];            /* level duration (device clock) */
     float init_us;                              /* kernel entry to the start of level 0 */
     float final_us;                             /* end of the last level to the kernel's exit */
-    uint32_t schedule;                          /* GB_SCHED_GRID or GB_SCHED_CLUSTER: the kernel that ran */
+    uint32_t schedule;                          /* GB_SCHED_GRID, GB_SCHED_CLUSTER or GB_SCHED_ASYNC: the kernel
+                                                   that ran. With GB_SCHED_ASYNC there are no levels: depth =
+                                                   push_levels = distance buckets (1 without buckets),
+                                                   vertices_reached = work items relaxed (stale ones not
+                                                   counted), edges_examined = frontier_edges = out-edges
+                                                   relaxed, alg_bytes = 4 n + 12 per item + 4 per edge (8 with
+                                                   weights) + 4 per improvement + 8 per ring entry read,
+                                                   final_us = device time of the traversal, no trace */
 } gb_bfs_stats;
 
 /* Direction-optimised BFS (Algorithm 1, Section 7.1): levels[v] = hop count
@@ -328,7 +339,9 @@ typedef struct {
  * parents != NULL, a BFS-tree parent (parents[src] = src, unreachable -1).
  * A must be square and symmetric-or-CSC-built. levels/parents have nrows
  * entries in `mem`. stats may be NULL. desc: GB_DIRECTION, GB_SWITCH_BETA,
- * GB_SCHEDULE (a device that cannot co-schedule a cluster runs GB_SCHED_GRID).
+ * GB_SCHEDULE (a device that cannot co-schedule a cluster runs GB_SCHED_GRID;
+ * GB_SCHED_ASYNC computes the levels without level barriers and then each
+ * parent as the smallest in-neighbour one level up, and always waits).
  * With GB_HOST outputs or stats the call waits and returns GB_TIMEOUT if a
  * bounded device wait ran out; with GB_DEVICE outputs and no stats it
  * returns without waiting, and such a timeout is reported by the next
@@ -403,9 +416,12 @@ gb_info gb_bfs_multi(gb_context *ctx, const gb_matrix *A, const uint32_t *srcs, 
  * the vertices whose distance changed. A holds uint32 weights. dist[v] =
  * shortest distance (UINT32_MAX unreachable). iterations may be NULL.
  * desc: GB_DIRECTION, GB_SWITCH_BETA, GB_SCHEDULE (GB_SCHED_CLUSTER relaxes
- * by push inside one thread-block cluster; GB_SCHED_AUTO and GB_SCHED_GRID
- * use the persistent grid kernel, which is faster wherever the frontiers of
- * improved vertices are large, as on the weighted 4096^2 grid). stats (may
+ * by push inside one thread-block cluster; GB_SCHED_ASYNC relaxes without
+ * any barrier inside a distance bucket (GB_SSSP_DELTA wide, the automatic
+ * width when 0, one bucket for a width >= 2^31 - 1), one grid barrier pair
+ * per bucket, the fastest on graphs of high diameter such as the weighted
+ * 4096^2 grid; GB_SCHED_AUTO and GB_SCHED_GRID use the persistent grid
+ * kernel with one barrier per iteration). stats (may
  * be NULL) receives, as for gb_bfs, the iterations (depth), push and pull
  * iterations, frontier out-edges, the per-iteration trace and alg_bytes:
  * 4 n value writes, per push iteration 8 per frontier vertex and 8 per
@@ -470,6 +486,14 @@ gb_info gb_pagerank_delta(gb_context *ctx, const gb_matrix *A, float damping, fl
  * NULL. */
 gb_info gb_cc(gb_context *ctx, const gb_matrix *A, uint32_t *labels, gb_mem mem, uint32_t *iterations,
               gb_bfs_stats *stats);
+/* Connected components by min-label propagation without level barriers
+ * (the asynchronous execution model of Section 9; the fixed point of
+ * gb_cc, so labels[v] = smallest vertex id in v's component, bit-identical
+ * to gb_cc): every vertex starts as a work item (label, vertex), and a
+ * persistent launch relaxes items through a ring that warps poll until none
+ * is in flight. Uses the out-edges (CSR): for a symmetric A these are the
+ * components. stats (may be NULL) as for gb_sssp with GB_SCHED_ASYNC. */
+gb_info gb_cc_async(gb_context *ctx, const gb_matrix *A, uint32_t *labels, gb_mem mem, gb_bfs_stats *stats);
 /* Connected components by FastSV (Section 7.4: the paper's CC algorithm):
  * per iteration mngf = A min.second gf, stochastic hooking
  * f(f(u)) = min(f(f(u)), mngf(u)), aggressive hooking and shortcut

@@ -35,7 +35,7 @@ DEFAULT, SCMP, STRUCTURE = 0, 1, 2
 REPLACE = 1
 TRAN = 1
 AUTO, PUSH, PULL = 0, 1, 2
-SCHED_AUTO, SCHED_GRID, SCHED_CLUSTER = 0, 1, 2
+SCHED_AUTO, SCHED_GRID, SCHED_CLUSTER, SCHED_ASYNC = 0, 1, 2, 3
 BUILD_DEFAULT, SYMMETRIC, CSR_ONLY = 0, 1, 2
 REQ_BFS, REQ_SSSP, REQ_PAGERANK = 0, 1, 2
 
@@ -132,7 +132,7 @@ _SIGS = {
     "gb_bfs_batch": [_P, _P, _P, _U32, _P, _P, _I, _P],
     "gb_sssp": [_P, _P, _U32, _P, _I, _P, _P, _P], "gb_pagerank": [_P, _P, ctypes.c_float, _U32, _P, _P, _I],
     "gb_cc": [_P, _P, _P, _I, _P, _P], "gb_tc": [_P, _P, _P, _P],
-    "gb_cc_fastsv": [_P, _P, _P, _I, _P],
+    "gb_cc_fastsv": [_P, _P, _P, _I, _P], "gb_cc_async": [_P, _P, _P, _I, _P],
     "gb_pagerank_delta": [_P, _P, ctypes.c_float, ctypes.c_float, _U32, _P, _I, _P, _P, _P],
     "gb_pagerank_autotune": [_P, _P, _P, _P, _P, _P], "gb_pagerank_set_tile": [_P, _U32],
     "gb_pagerank_set_order": [_P, _I, _U32],
@@ -717,6 +717,19 @@ def cc(ctx, A, labels=None):
     it = ctypes.c_uint32()
     check(lib().gb_cc(ctx.h, A.h, pl, ml, ctypes.byref(it), None))
     return labels, it.value
+
+
+def cc_async(ctx, A, labels=None, stats=False):
+    """Connected components by min-label propagation without level
+    barriers; returns labels, or (labels, stats-dict) with stats=True."""
+    n = A.nrows
+    if labels is None:
+        torch = _torch()
+        labels = torch.empty(n, dtype=torch.int32, device=f"cuda:{ctx.device}")
+    pl, ml = _out_mem(labels)
+    st = BfsStats()
+    check(lib().gb_cc_async(ctx.h, A.h, pl, ml, ctypes.byref(st) if stats else None))
+    return (labels, st.as_dict()) if stats else labels
 
 
 def tc(ctx, L, C=None):

@@ -673,6 +673,10 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
 
 }  // namespace bfsk
 
+// the barrier-free schedule (async_relax.cu)
+gb_info async_relax_run(gb_context *ctx, const gb_matrix *A, int kind, uint32_t src, uint32_t *out,
+                        uint32_t *parents, uint64_t delta, gb_bfs_stats *stats, const char *who);
+
 // the single-cluster schedule (bfs_cluster.cu)
 bool bfs_cluster_available(gb_context *ctx);
 gb_info bfs_cluster_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *levels, int32_t *parents,
@@ -859,6 +863,16 @@ extern "C" gb_info gb_bfs(gb_context *ctx, const gb_matrix *A, uint32_t src, int
             GB_CHECK(tp.alloc((size_t)A->nrows * 4));
             dp = tp.as<int32_t>();
         }
+    }
+    if (desc && desc->schedule == GB_SCHED_ASYNC) {
+        GB_CHECK(async_relax_run(ctx, A, 1, src, (uint32_t *)dl, (uint32_t *)dp, 0, stats, "gb_bfs"));
+        if (mem == GB_HOST) {
+            GB_CUDA(cudaMemcpyAsync(levels, dl, (size_t)A->nrows * 4, cudaMemcpyDeviceToHost, ctx->stream));
+            if (parents)
+                GB_CUDA(cudaMemcpyAsync(parents, dp, (size_t)A->nrows * 4, cudaMemcpyDeviceToHost, ctx->stream));
+            GB_CHECK(sync(ctx));
+        }
+        return GB_SUCCESS;
     }
     const int sch = bfs_schedule(ctx, A, desc);
     if (sch == GB_SCHED_CLUSTER) GB_CHECK(bfs_cluster_run(ctx, A, src, dl, dp, w, &w->st->sticky));

@@ -319,7 +319,7 @@ gb_info gb_desc_set(gb_desc *d, gb_field field, int value) {
         if (value < 0) return fail(GB_INVALID_VALUE, "bad GB_SWITCH_BETA value %d", value);
         d->beta = value; break;
     case GB_SCHEDULE:
-        if (value < GB_SCHED_AUTO || value > GB_SCHED_CLUSTER)
+        if (value < GB_SCHED_AUTO || value > GB_SCHED_ASYNC)
             return fail(GB_INVALID_VALUE, "bad GB_SCHEDULE value %d", value);
         d->schedule = value; break;
     case GB_SSSP_DELTA:
