@@ -120,10 +120,11 @@ def code_digest(paths, root=None):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(profile, sources, beta=None):
+def recorded_traffic(profile, sources, beta=None, shape=None):
     """DRAM bytes per launch from a profile summary's `traffic-record` line
-    for this push/pull threshold, or None when the kernel's code changed
-    since that capture or no capture used this threshold."""
+    for this push/pull threshold and tile shape ("pull width,blocks per SM"),
+    or None when the kernel's code changed since that capture or no capture
+    used this threshold and shape."""
     try:
         text = open(os.path.join(ROOT, profile)).read()
     except OSError:
@@ -131,7 +132,8 @@ def recorded_traffic(profile, sources, beta=None):
     for line in text.splitlines():
         if line.startswith("traffic-record:"):
             kv = dict(x.split("=", 1) for x in line.split(":", 1)[1].split())
-            if kv.get("digest") == code_digest(sources) and (beta is None or kv.get("beta") == str(beta)):
+            if kv.get("digest") == code_digest(sources) and (beta is None or kv.get("beta") == str(beta)) \
+                    and (shape is None or kv.get("shape", "2,0") == shape):
                 return float(kv["bytes_per_launch"])
     return None
 
@@ -262,6 +264,9 @@ def run_gbx(args):
     if not args.beta:
         import gen
         tuned_beta, _ = gb.bfs_autotune(ctx, A, gen.sources(t, 64, seed=99))
+    if args.bfs_shape:
+        gb.bfs_set_shape(A, *[int(x) for x in args.bfs_shape.split(",")])
+    pull_width, per_sm = gb.bfs_get_shape(A)
 
     # untimed pass with statistics: algorithmic bytes and levels per source
     alg, depth, pushes, pulls = [], [], [], []
@@ -322,13 +327,22 @@ def run_gbx(args):
         gb.bfs_batch(ctx, A, srcs_u, lv_h, pa_h, desc=desc)
     e2e_s = max_over_ranks((time.perf_counter() - e0) / e_steps, ws)
     e2e_val = whole_job_gteps(ws, NSRC, m, e2e_s)
-    del lv_h, pa_h
+    # the plain device-to-host copy rate into the same pinned buffer (context
+    # for the end-to-end figure, which the copies bound)
+    src_d = torch.empty_like(lv_h, device=dev)
+    lv_h.copy_(src_d, non_blocking=True)
+    torch.cuda.synchronize()
+    c0 = time.perf_counter()
+    lv_h.copy_(src_d, non_blocking=True)
+    torch.cuda.synchronize()
+    d2h_gbps = lv_h.numel() * 4 / (time.perf_counter() - c0) / 1e9
+    del lv_h, pa_h, src_d
 
     hbm, peak_kind = peaks()
     avg_kernel_ms = k_ms / max(k_n, 1)          # one launch = one traversal
     alg_per_launch = alg_per_bfs
     achieved = alg_per_launch / (avg_kernel_ms / 1e3) / 1e9
-    traffic = recorded_traffic(BFS_PROFILE, BFS_KERNEL_SOURCES, args.beta or tuned_beta)
+    traffic = recorded_traffic(BFS_PROFILE, BFS_KERNEL_SOURCES, args.beta or tuned_beta, f"{pull_width},{per_sm}")
     dram_achieved = traffic / (avg_kernel_ms / 1e3) / 1e9 if traffic else None
     line = {
         "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
@@ -336,14 +350,16 @@ def run_gbx(args):
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "m_stored": m, "sources": NSRC, "l2": "inputs_larger_than_l2",
                    "parallelism": f"replicas{ws}" if ws > 1 else "single",
-                   "beta": args.beta or tuned_beta, "beta_from": "fixed" if args.beta else "autotuner"},
+                   "beta": args.beta or tuned_beta, "beta_from": "fixed" if args.beta else "autotuner",
+                   "bfs_tile": {"pull_candidates_per_lane": pull_width, "blocks_per_sm": per_sm or "all that fit",
+                                "from": "fixed" if args.bfs_shape else ("autotuner" if not args.beta else "default")}},
         "gpu_launches": int(args.steps * NSRC),
-        "roofline": {"bound": "hbm", "kernel": "k_bfs", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+        "roofline": {"bound": "hbm", "kernel": f"k_bfs<{pull_width}>", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": traffic,
                      "alg_bytes_per_launch": alg_per_launch, "avg_launch_ms": avg_kernel_ms,
                      # the same launches by the DRAM bytes ncu counted (null without a matching capture)
                      "dram_achieved": dram_achieved, "dram_frac": dram_achieved / hbm if dram_achieved else None},
-        "e2e": {"value": e2e_val, "unit": "GTEPS", "h2d_bytes_per_step": 0,
+        "e2e": {"value": e2e_val, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_copy_gbps": d2h_gbps,
                 "d2h_bytes_per_step": int(NSRC * 2 * 4 * n)},
         "clocks": clk,
         "build": {"ms_device_tuples": 1e3 * min(build_s), "ms_host_tuples": 1e3 * build_host_s,
@@ -484,11 +500,21 @@ def extra_rows(args, hbm):
                                "row_updates_vs_plain_50": float(act.sum()) / (50.0 * n)}
     out["pagerank_delta_s22"] = prd
     # --- multi-source BFS: the 64 benchmark sources in one bit-frontier launch
-    bsrcs = gen.sources(t, NSRC, seed=SRC_SEED)
-    lv = torch.empty((NSRC, n), dtype=torch.int32, device="cuda")
-    gb.bfs_multi(ctx, A, bsrcs, lv, stats=False)
-    ms = cuda_time_ms(lambda: gb.bfs_multi(ctx, A, bsrcs, lv, stats=False), stream)
-    out["bfs_multi64_s22"] = {"ms_per_batch": ms, "gteps": NSRC * m / (ms / 1e3) / 1e9}
+    # (one 64-bit word of source bits per vertex), then 256 distinct sources
+    # of the same seeded stream in one launch (four words per vertex)
+    for k_ms in (NSRC, 256):
+        bsrcs = gen.sources(t, k_ms, seed=SRC_SEED)
+        lv = torch.empty((k_ms, n), dtype=torch.int32, device="cuda")
+        _, st_ms = gb.bfs_multi(ctx, A, bsrcs, lv)
+        ms = cuda_time_ms(lambda: gb.bfs_multi(ctx, A, bsrcs, lv, stats=False), stream)
+        ab = st_ms["alg_bytes"]
+        out[f"bfs_multi{k_ms}_s22"] = {
+            "ms_per_batch": ms, "us_per_source": 1e3 * ms / k_ms, "gteps": k_ms * m / (ms / 1e3) / 1e9,
+            "levels": st_ms["depth"], "push_levels": st_ms["push_levels"], "pull_levels": st_ms["pull_levels"],
+            "roofline": {"bound": "hbm", "kernel": f"k_msbfs<{(k_ms + 63) // 64}>", "alg_bytes_per_launch": ab,
+                         "achieved": ab / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": ab / (ms / 1e3) / 1e9 / hbm}}
+        del lv
     A.free()
     del t
     # --- triangle counting on R-MAT s20 (degree ordered, L = tril)
@@ -779,7 +805,16 @@ def run_profile(args):
     kind = args.profile
     ctx = gb.Context(0)
     k = args.profile_launches
-    if kind == "gridbfs":
+    if kind == "async":
+        side = args.profile_grid
+        t = gen.grid(side, side, 0.1, seed=3, wmax=1000)
+        A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, t.w, type_=gb.UINT32, flags=gb.SYMMETRIC)
+        src = gen.first_nonisolated(t)
+        dist = torch.empty(t.n, dtype=torch.int32, device="cuda")
+        d = gb.Descriptor(schedule=gb.SCHED_ASYNC)
+        for _ in range(k):
+            gb.sssp(ctx, A, src, dist, d)
+    elif kind == "gridbfs":
         t = gen.grid(4096, 4096, 0.1, seed=3)
         A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, flags=gb.SYMMETRIC)
         src = gen.first_nonisolated(t)
@@ -808,12 +843,16 @@ def run_profile(args):
         out = torch.empty(t.n * (NSRC if kind == "msbfs" else 1), dtype=torch.int32, device="cuda")
         out2 = torch.empty(t.n, dtype=torch.int32, device="cuda")
         desc = gb.Descriptor(beta=args.beta) if args.beta else None
+        if args.bfs_shape:
+            gb.bfs_set_shape(A, *[int(x) for x in args.bfs_shape.split(",")])
         if kind == "pr":
             gb.pagerank_set_tile(A, args.pr_tile)
             gb.pagerank_set_order(A, args.pr_order, args.pr_staged)
+        alg = []
         for i in range(k):
             if kind == "bfs":
-                gb.bfs(ctx, A, int(srcs[i]), out, out2, desc=desc, stats=True)
+                _, _, st = gb.bfs(ctx, A, int(srcs[i]), out, out2, desc=desc, stats=True)
+                alg.append(st["alg_bytes"])
             elif kind == "sssp":
                 gb.sssp(ctx, A, int(srcs[i]), out)
             elif kind == "msbfs":
@@ -824,6 +863,8 @@ def run_profile(args):
                 gb.pagerank_delta(ctx, A, 0.85, 1e-4, 200, out.view(torch.float32))
     torch.cuda.synchronize()
     ctx.close()
+    if kind == "bfs":
+        print(json.dumps({"alg_bytes_per_launch": alg}))
     print(f"profile run done: {kind} x{k}")
 
 
@@ -834,6 +875,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbx", choices=["gbx", "reference"])
     ap.add_argument("--beta", type=int, default=0)
+    ap.add_argument("--bfs-shape", default="",
+                    help="BFS tile shape 'pull width,blocks per SM' (default: the autotuner's, or 2,0 with --beta)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-sources", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -848,7 +891,8 @@ def main():
                     help="latency target of the queries/s-at-p99 figure")
     ap.add_argument("--serve-sweep-requests", type=int, default=800,
                     help="requests per point of the latency-vs-load sweep")
-    ap.add_argument("--profile", choices=["bfs", "pr", "sssp", "msbfs", "tc", "prd", "fastsv", "gridbfs"], default=None,
+    ap.add_argument("--profile", choices=["bfs", "pr", "sssp", "msbfs", "tc", "prd", "fastsv", "gridbfs", "async"],
+                    default=None,
                     help="short fixed run of one kernel for ncu")
     ap.add_argument("--profile-launches", type=int, default=3)
     ap.add_argument("--pr-tile", type=int, default=256, help="PageRank tile of the profiled run (256, 512, 1024)")
@@ -856,6 +900,8 @@ def main():
                     help="PageRank vertex order of the profiled run (1: the degree-ordered copy)")
     ap.add_argument("--pr-staged", type=int, default=0,
                     help="ranks staged in shared memory in the profiled run (degree order; 0 = default)")
+    ap.add_argument("--profile-grid", type=int, default=4096,
+                    help="side of the grid of the profiled barrier-free SSSP (async)")
     ap.add_argument("--profile-scale", type=int, default=SCALE,
                     help="R-MAT scale of the profiled workload (smaller for a first pass-count check)")
     args = ap.parse_args()

@@ -374,6 +374,19 @@ gb_info gb_bfs_batch(gb_context *ctx, const gb_matrix *A, const uint32_t *srcs, 
  * the paper's beta = 10). *best_ms (may be NULL) = mean ms per BFS at it. */
 gb_info gb_bfs_autotune(gb_context *ctx, gb_matrix *A, const uint32_t *srcs, uint32_t k, uint32_t *best_beta,
                         double *best_ms);
+/* BFS tile shape of the persistent grid kernel (its pull walks candidates
+ * in groups of 32 x pull_width, each lane pull_width of them with their
+ * loads in flight together; its launch fills blocks_per_sm blocks of 256
+ * threads on every SM). gb_bfs_autotune times pull widths {1, 2, 4} x
+ * {2, 3, 4} blocks per SM at the threshold it chose and keeps the fastest
+ * on the matrix; gb_bfs_set_shape sets them by hand (pull_width 0, 1, 2 or
+ * 4, 0 = the default 2; blocks_per_sm 0..4, 0 = as many as fit, else
+ * GB_INVALID_VALUE). The outputs of a BFS do not depend on the shape. The
+ * paper fixes its kernels' launch shapes (Section 6); tuning them per graph
+ * is this library's. gb_bfs_get_shape reports the pull width in effect and
+ * the blocks per SM (0 = as many as fit). */
+gb_info gb_bfs_set_shape(gb_matrix *A, uint32_t pull_width, uint32_t blocks_per_sm);
+gb_info gb_bfs_get_shape(const gb_matrix *A, uint32_t *pull_width, uint32_t *blocks_per_sm);
 /* BFS that allocates no device memory (the paper has no counterpart; it is
  * an extra for callers that cannot allocate on the call path: a process
  * whose device memory belongs to another allocator such as a framework's
@@ -407,9 +420,14 @@ gb_info gb_bfs_noalloc(const uint32_t *rowptr, const uint32_t *colidx, const uin
 /* Multi-source BFS as Boolean SpMM over 64-bit bit-packed frontiers
  * (Section 3.3 multi-nodeset traversal; Section 9 matrix direction
  * optimisation): k >= 1 sources, levels is k x nrows (row q = source q).
- * One launch serves up to 64 sources; more are served by consecutive
- * launches of 64 (the statistics then sum or maximise over them, the trace
- * is the first launch's). */
+ * One launch serves up to 256 sources: each vertex carries one 64-bit word
+ * of frontier bits per 64 sources (1, 2 or 4 words for up to 64, 128 or 256
+ * sources), and every level chooses push (SpMM from the frontier rows) or
+ * pull (the masked product over the rows some search has not reached, with
+ * the early exit once all searches are covered) for all of them at once.
+ * More than 256 sources are served by consecutive launches of 256 (the
+ * statistics then sum or maximise over them, the trace is the first
+ * launch's). */
 gb_info gb_bfs_multi(gb_context *ctx, const gb_matrix *A, const uint32_t *srcs, uint32_t k, int32_t *levels,
                      gb_mem mem, const gb_desc *desc, gb_bfs_stats *stats);
 /* SSSP (Section 7.2): adaptive Bellman-Ford by min.plus mxv restricted to

@@ -128,7 +128,8 @@ _SIGS = {
     "gb_reduce_rows": [_P, _P, _I, _I, _P, _P],
     "gb_bfs": [_P, _P, _U32, _P, _P, _I, _P, _P],
     "gb_bfs_noalloc": [_P, _P, _P, _P, _U32, _U64, _U32, _P, _P, _P, _P],
-    "gb_bfs_autotune": [_P, _P, _P, _U32, _P, _P], "gb_bfs_multi": [_P, _P, _P, _U32, _P, _I, _P, _P],
+    "gb_bfs_autotune": [_P, _P, _P, _U32, _P, _P], "gb_bfs_set_shape": [_P, _U32, _U32],
+    "gb_bfs_get_shape": [_P, _P, _P], "gb_bfs_multi": [_P, _P, _P, _U32, _P, _I, _P, _P],
     "gb_bfs_batch": [_P, _P, _P, _U32, _P, _P, _I, _P],
     "gb_sssp": [_P, _P, _U32, _P, _I, _P, _P, _P], "gb_pagerank": [_P, _P, ctypes.c_float, _U32, _P, _P, _I],
     "gb_cc": [_P, _P, _P, _I, _P, _P], "gb_tc": [_P, _P, _P, _P],
@@ -553,6 +554,20 @@ def bfs(ctx, A, src, levels=None, parents=None, desc=None, stats=True):
     st = BfsStats()
     check(lib().gb_bfs(ctx.h, A.h, src, pl, pp, ml, _h(desc), ctypes.byref(st) if stats else None))
     return levels, parents, (st.as_dict() if stats else None)
+
+
+def bfs_set_shape(A, pull_width=0, blocks_per_sm=0):
+    """BFS tile shape of A: pull candidates per lane (0 = default, 1, 2, 4)
+    and blocks per SM (0 = as many as fit, 1..4)."""
+    check(lib().gb_bfs_set_shape(A.h, pull_width, blocks_per_sm))
+
+
+def bfs_get_shape(A):
+    """(pull width in effect, blocks per SM or 0 = as many as fit) of A."""
+    w = ctypes.c_uint32()
+    b = ctypes.c_uint32()
+    check(lib().gb_bfs_get_shape(A.h, ctypes.byref(w), ctypes.byref(b)))
+    return w.value, b.value
 
 
 def bfs_autotune(ctx, A, srcs):

@@ -80,7 +80,6 @@ static __device__ __forceinline__ bool run_or_head(uint32_t key, uint32_t &bits)
 // per warp, the candidates it keeps for the next pull, appended to the next
 // list PULL_KEEP_CAP at a time (one atomicAdd per flush), and the queue of
 // candidates whose head missed.
-constexpr int PULL_GROUP = PULL_WPW * 32;
 constexpr int PULL_KEEP_CAP = 64;
 constexpr int PULL_MISS_CAP = 64;   // fewer than 32 left over + one lane slot of 32
 struct PullSmem {
@@ -254,8 +253,8 @@ static __device__ void scan_misses(const BfsArgs &a, PullRec *mq, uint32_t &nq, 
 // of its row, read through the row pointers. The visited word and the
 // frontier words of the four head entries load together (one dependent
 // step), so a candidate with a frontier vertex among its head is decided
-// there. Warps take groups of PULL_GROUP consecutive candidates, each lane
-// PULL_WPW. A candidate whose head has no frontier vertex and whose row is
+// there. Warps take groups of 32 WPW consecutive candidates, each lane
+// WPW (a tile shape the autotuner picks per matrix: 1, 2 or 4). A candidate whose head has no frontier vertex and whose row is
 // longer than four goes to the warp's miss queue, scanned 32 at a time
 // (scan_misses). Found vertices set their visited and next-frontier bits
 // (one atomicOr per run of lanes in the same bitmap word); the others are
@@ -264,7 +263,7 @@ static __device__ void scan_misses(const BfsArgs &a, PullRec *mq, uint32_t &nq, 
 // out-edges); the list form is built when a push needs it. It also counts
 // the unvisited candidates it walked and sums the in-degrees of those it
 // leaves (what a later pull over them reads at most).
-template <bool TABLE>
+template <bool TABLE, int WPW>
 __device__ void pull_level(const BfsArgs &a, PullSmem &ps, int d, const void *Lin, uint32_t nin, void *Lout,
                            unsigned int *lout_cnt, unsigned long long *examined, uint32_t *cnt_out,
                            uint32_t *deg_out, uint32_t *act_out, unsigned long long *left_edges) {
@@ -273,7 +272,7 @@ __device__ void pull_level(const BfsArgs &a, PullSmem &ps, int d, const void *Li
     const uint32_t full = 0xffffffffu;
     const uint32_t NONE = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t ngroups = (uint32_t)(((uint64_t)nin + PULL_GROUP - 1) / PULL_GROUP);
+    const uint32_t ngroups = (uint32_t)(((uint64_t)nin + (WPW * 32) - 1) / (WPW * 32));
     const uint32_t nwarps = gridDim.x * WARPS;
     const PullRec *recs = TABLE ? (Lin ? static_cast<const PullRec *>(Lin) : a.live_rec) : nullptr;
     PullRec *kbuf = ps.keep[warp];
@@ -284,12 +283,12 @@ __device__ void pull_level(const BfsArgs &a, PullSmem &ps, int d, const void *Li
     uint32_t staged = 0;   // candidates staged for the next list
     static_assert(31 + 32 <= PULL_MISS_CAP, "a lane slot's misses fit the queue");
     for (uint32_t g = blockIdx.x * WARPS + warp; g < ngroups; g += nwarps) {
-        PullRec r[PULL_WPW];
-        bool act[PULL_WPW], found[PULL_WPW];
-        uint32_t par[PULL_WPW];
+        PullRec r[WPW];
+        bool act[WPW], found[WPW];
+        uint32_t par[WPW];
 #pragma unroll
-        for (int j = 0; j < PULL_WPW; ++j) {
-            const uint32_t idx = g * PULL_GROUP + j * 32 + lane;
+        for (int j = 0; j < WPW; ++j) {
+            const uint32_t idx = g * (WPW * 32) + j * 32 + lane;
             r[j].v = NONE;
             r[j].len = r[j].b = r[j].deg = 0;
             r[j].head = make_uint4(NONE, NONE, NONE, NONE);
@@ -310,7 +309,7 @@ __device__ void pull_level(const BfsArgs &a, PullSmem &ps, int d, const void *Li
         }
         if (!TABLE) {
 #pragma unroll
-            for (int j = 0; j < PULL_WPW; ++j) {
+            for (int j = 0; j < WPW; ++j) {
                 uint32_t hh[4] = {NONE, NONE, NONE, NONE};
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
@@ -322,16 +321,16 @@ __device__ void pull_level(const BfsArgs &a, PullSmem &ps, int d, const void *Li
         // entries, together; the other two only where those did not hit (every
         // frontier word is a random sector lookup, and the first two decide
         // most candidates)
-        uint32_t vw[PULL_WPW], fw[PULL_WPW][4];
+        uint32_t vw[WPW], fw[WPW][4];
 #pragma unroll
-        for (int j = 0; j < PULL_WPW; ++j) {
+        for (int j = 0; j < WPW; ++j) {
             const uint32_t h[2] = {r[j].head.x, r[j].head.y};
             vw[j] = r[j].v != NONE ? ldcg(&a.visited[r[j].v >> 5]) : full;
 #pragma unroll
             for (int k = 0; k < 2; ++k) fw[j][k] = h[k] != NONE ? ldcg(&F[h[k] >> 5]) : 0u;
         }
 #pragma unroll
-        for (int j = 0; j < PULL_WPW; ++j) {
+        for (int j = 0; j < WPW; ++j) {
             const uint32_t h[2] = {r[j].head.x, r[j].head.y};
             act[j] = r[j].v != NONE && !((vw[j] >> (r[j].v & 31)) & 1u);
             found[j] = false;
@@ -345,14 +344,14 @@ __device__ void pull_level(const BfsArgs &a, PullSmem &ps, int d, const void *Li
             found[j] = found[j] && act[j];
         }
 #pragma unroll
-        for (int j = 0; j < PULL_WPW; ++j) {
+        for (int j = 0; j < WPW; ++j) {
             const uint32_t h[2] = {r[j].head.z, r[j].head.w};
 #pragma unroll
             for (int k = 0; k < 2; ++k)
                 fw[j][2 + k] = (act[j] && !found[j] && h[k] != NONE) ? ldcg(&F[h[k] >> 5]) : 0u;
         }
 #pragma unroll
-        for (int j = 0; j < PULL_WPW; ++j) {
+        for (int j = 0; j < WPW; ++j) {
             uint32_t ex = r[j].len < 4 ? r[j].len : 4;
             if (act[j] && !found[j]) {
                 const uint32_t h[2] = {r[j].head.z, r[j].head.w};
@@ -369,7 +368,7 @@ __device__ void pull_level(const BfsArgs &a, PullSmem &ps, int d, const void *Li
             if (act[j]) { exam += ex; ++myact; }
         }
 #pragma unroll
-        for (int j = 0; j < PULL_WPW; ++j) {
+        for (int j = 0; j < WPW; ++j) {
             claim_found(a, Fn, d, found[j], r[j].v, par[j], r[j].deg, mycnt, mydeg);
             // rows longer than four whose head missed: to the miss queue
             const bool miss = act[j] && !found[j] && r[j].len > 4;
@@ -445,6 +444,7 @@ __device__ __forceinline__ void write_unreached(const BfsArgs &ar, Unreached unr
 // pass that gives unreached vertices -1. ar.st holds the traversal's
 // counters and result record; bst holds the barrier and the error word.
 // Returns false when a barrier wait ran out.
+template <int WPW>
 __device__ bool bfs_run(const BfsArgs &ar, BfsState *bst, bool first, uint64_t t_entry, BfsShared &shm,
                         unsigned long long *s_box, uint32_t *s_box32) {
     Smem &sm = shm.push;
@@ -588,9 +588,11 @@ __device__ bool bfs_run(const BfsArgs &ar, BfsState *bst, bool first, uint64_t t
             unsigned long long ex = 0, le = 0;
             uint32_t c = 0, dg = 0, na = 0;
             if (ar.live_rec)
-                pull_level<true>(ar, shm.pull, d, Lin, nin, ar.ul[npull & 1], &st->ucnt[us], &ex, &c, &dg, &na, &le);
+                pull_level<true, WPW>(ar, shm.pull, d, Lin, nin, ar.ul[npull & 1], &st->ucnt[us], &ex, &c, &dg, &na,
+                                      &le);
             else
-                pull_level<false>(ar, shm.pull, d, Lin, nin, ar.ul[npull & 1], &st->ucnt[us], &ex, &c, &dg, &na, &le);
+                pull_level<false, WPW>(ar, shm.pull, d, Lin, nin, ar.ul[npull & 1], &st->ucnt[us], &ex, &c, &dg, &na,
+                                       &le);
             ++npull;
             ex = dev::warp_sum<unsigned long long>(ex);
             le = dev::warp_sum<unsigned long long>(le);
@@ -662,13 +664,22 @@ __device__ void bfs_leave(const BfsArgs &a) {
     }
 }
 
-__global__ void __launch_bounds__(BLOCK, 4) k_bfs(BfsArgs a) {
+// WPW: pull candidates per lane in flight (a tile shape tuned per matrix)
+template <int WPW>
+__global__ void __launch_bounds__(BLOCK, WPW == 4 ? 3 : 4) k_bfs(BfsArgs a) {
     __shared__ BfsShared shm;
     __shared__ unsigned long long s_box[4];
     __shared__ uint32_t s_box32[4];
     const uint64_t t_entry = dev::globaltimer_ns();
-    bfs_run(a, a.st, true, t_entry, shm, s_box, s_box32);
+    bfs_run<WPW>(a, a.st, true, t_entry, shm, s_box, s_box32);
     bfs_leave(a);
+}
+
+// the k_bfs instance for a pull width (1, 2 or 4; anything else: the default)
+static const void *bfs_kernel(uint32_t wpw) {
+    if (wpw == 1) return (const void *)k_bfs<1>;
+    if (wpw == 4) return (const void *)k_bfs<4>;
+    return (const void *)k_bfs<PULL_WPW>;
 }
 
 }  // namespace bfsk
@@ -690,8 +701,12 @@ struct BfsWorkspace {
     PullRec *ul = nullptr;   // two candidate lists of pull records
     BfsState *st = nullptr;
     void *cl_state = nullptr;   // state block of the single-cluster schedule
-    int grid = 0;
+    int grid = 0;               // blocks of the default k_bfs at full occupancy
+    int occ[3] = {0, 0, 0};     // resident blocks per SM of k_bfs<1>, <2>, <4>
 };
+
+// index of a pull width in BfsWorkspace::occ
+static int wpw_slot(uint32_t wpw) { return wpw == 1 ? 0 : (wpw == 4 ? 2 : 1); }
 
 static std::mutex g_ws_mu;
 static std::unordered_map<gb_context *, BfsWorkspace> g_ws;
@@ -717,10 +732,13 @@ gb_info bfs_workspace(gb_context *ctx, uint32_t n, BfsWorkspace **out) {
         w.n = n;
     }
     if (!w.grid) {
-        int occ = 0;
-        GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bfsk::k_bfs, bfsk::BLOCK, 0));
-        if (occ < 1) return fail(GB_PANIC, "BFS kernel cannot be resident");
-        w.grid = occ * ctx->num_sms;
+        const uint32_t widths[3] = {1, 2, 4};
+        for (int i = 0; i < 3; ++i) {
+            GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&w.occ[i], bfsk::bfs_kernel(widths[i]),
+                                                                  bfsk::BLOCK, 0));
+            if (w.occ[i] < 1) return fail(GB_PANIC, "BFS kernel cannot be resident");
+        }
+        w.grid = w.occ[wpw_slot(0)] * ctx->num_sms;
     }
     *out = &w;
     return GB_SUCCESS;
@@ -812,12 +830,16 @@ gb_info bfs_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *l
         a.timeout_ns = t;
         a.withhold = true;
     }
-    int grid = w->grid;
+    // the matrix's tile shape: pull width (kernel instance) and blocks per SM
+    const uint32_t wpw = A->bfs_pull_width;
+    int per_sm = w->occ[wpw_slot(wpw)];
+    if (A->bfs_blocks_per_sm > 0 && (int)A->bfs_blocks_per_sm < per_sm) per_sm = (int)A->bfs_blocks_per_sm;
+    int grid = per_sm * ctx->num_sms;
     if (ctx->grid_limit > 0 && ctx->grid_limit < grid) grid = ctx->grid_limit;
     if (grid_override > 0 && grid_override < grid) grid = grid_override;
     void *args[] = {&a};
     int span = prof_begin(ctx, "bfs");
-    GB_CUDA(cudaLaunchCooperativeKernel((const void *)bfsk::k_bfs, dim3(grid), dim3(bfsk::BLOCK), args, 0,
+    GB_CUDA(cudaLaunchCooperativeKernel(bfsk::bfs_kernel(wpw), dim3(grid), dim3(bfsk::BLOCK), args, 0,
                                         ctx->stream));
     prof_end(ctx, span);
     return GB_SUCCESS;
@@ -1076,7 +1098,7 @@ extern "C" gb_info gb_bfs_noalloc(const uint32_t *rowptr, const uint32_t *colidx
             cudaError_t e = cudaGetSymbolAddress(&p, g_bfs_scratch);
             if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_bfs_scratch)", __FILE__, __LINE__);
             int occ = 0, sms = 0;
-            GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bfsk::k_bfs, bfsk::BLOCK, 0));
+            GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bfsk::bfs_kernel(0), bfsk::BLOCK, 0));
             GB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
             if (occ < 1) return fail(GB_PANIC, "gb_bfs_noalloc: BFS kernel cannot be resident");
             D->base = (unsigned char *)p;
@@ -1124,7 +1146,7 @@ extern "C" gb_info gb_bfs_noalloc(const uint32_t *rowptr, const uint32_t *colidx
     // the kernel needs a zeroed working state; the last call's contents may remain
     GB_CUDA(cudaMemsetAsync(a.st, 0, sizeof(BfsState), s));
     void *args[] = {&a};
-    GB_CUDA(cudaLaunchCooperativeKernel((const void *)bfsk::k_bfs, dim3(D->grid), dim3(bfsk::BLOCK), args, 0, s));
+    GB_CUDA(cudaLaunchCooperativeKernel(bfsk::bfs_kernel(0), dim3(D->grid), dim3(bfsk::BLOCK), args, 0, s));
     return GB_SUCCESS;
 }
 
@@ -1152,6 +1174,10 @@ extern "C" gb_info gb_bfs_autotune(gb_context *ctx, gb_matrix *A, const uint32_t
     gb_desc d;
     double tmin[NC];
     for (int c = 0; c < NC; ++c) tmin[c] = 1e30;
+    // the threshold is tuned with the default tile shape, the shape at the
+    // chosen threshold
+    A->bfs_pull_width = 0;
+    A->bfs_blocks_per_sm = 0;
     // two passes over the candidates, forward then backward, keeping each
     // candidate's faster pass (so a slow drift of the clock favours none)
     for (int pass = 0; pass < 2; ++pass) {
@@ -1179,6 +1205,45 @@ extern "C" gb_info gb_bfs_autotune(gb_context *ctx, gb_matrix *A, const uint32_t
     uint32_t bb = 10;
     for (int c = 0; c < NC; ++c)
         if (tmin[c] < best) { best = tmin[c]; bb = cand[c]; }
+    // tile shape at that threshold: pull candidates per lane in flight x
+    // blocks per SM, timed the same way (two passes, the faster kept); the
+    // default shape's time is the threshold pass's
+    {
+        static const uint32_t widths[] = {1, 2, 4};
+        static const uint32_t per_sm[] = {2, 3, 4};
+        constexpr int NS = 9;
+        double ts[NS];
+        for (int c = 0; c < NS; ++c) ts[c] = 1e30;
+        d.beta = (int)bb;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int ci = 0; ci < NS; ++ci) {
+                const int c = pass == 0 ? ci : NS - 1 - ci;
+                A->bfs_pull_width = widths[c / 3];
+                A->bfs_blocks_per_sm = per_sm[c % 3];
+                gb_info r = bfs_launch(ctx, A, srcs[0], lv.as<int32_t>(), pa.as<int32_t>(), &d, w, 0);
+                if (r == GB_SUCCESS) r = cudaEventRecord(e0, ctx->stream) == cudaSuccess ? GB_SUCCESS : GB_PANIC;
+                for (uint32_t q = 0; q < k && r == GB_SUCCESS; ++q)
+                    r = bfs_launch(ctx, A, srcs[q], lv.as<int32_t>(), pa.as<int32_t>(), &d, w, 0);
+                if (r == GB_SUCCESS && cudaEventRecord(e1, ctx->stream) != cudaSuccess) r = GB_PANIC;
+                if (r == GB_SUCCESS && cudaEventSynchronize(e1) != cudaSuccess) r = GB_PANIC;
+                if (r != GB_SUCCESS) {
+                    A->bfs_pull_width = 0;
+                    A->bfs_blocks_per_sm = 0;
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return r == GB_PANIC ? fail(GB_PANIC, "gb_bfs_autotune: CUDA error") : r;
+                }
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < ts[c]) ts[c] = ms;
+            }
+        }
+        uint32_t bw = 0, bp = 0;
+        for (int c = 0; c < NS; ++c)
+            if (ts[c] < best) { best = ts[c]; bw = widths[c / 3]; bp = per_sm[c % 3]; }
+        A->bfs_pull_width = bw;
+        A->bfs_blocks_per_sm = bp;
+    }
     // the single-cluster schedule, timed the same way (two passes)
     int sched = GB_SCHED_GRID;
     if (bfs_cluster_available(ctx)) {
@@ -1225,5 +1290,23 @@ extern "C" gb_info gb_bfs_autotune(gb_context *ctx, gb_matrix *A, const uint32_t
     A->tuned_beta = bb;
     *best_beta = bb;
     if (best_ms) *best_ms = best / k;
+    return GB_SUCCESS;
+}
+
+extern "C" gb_info gb_bfs_set_shape(gb_matrix *A, uint32_t pull_width, uint32_t blocks_per_sm) {
+    if (!A) return fail(GB_NULL_POINTER, "gb_bfs_set_shape: NULL matrix");
+    if (pull_width != 0 && pull_width != 1 && pull_width != 2 && pull_width != 4)
+        return fail(GB_INVALID_VALUE, "gb_bfs_set_shape: pull width %u is not 0, 1, 2 or 4", pull_width);
+    if (blocks_per_sm > 4)
+        return fail(GB_INVALID_VALUE, "gb_bfs_set_shape: %u blocks per SM (at most 4)", blocks_per_sm);
+    A->bfs_pull_width = pull_width;
+    A->bfs_blocks_per_sm = blocks_per_sm;
+    return GB_SUCCESS;
+}
+
+extern "C" gb_info gb_bfs_get_shape(const gb_matrix *A, uint32_t *pull_width, uint32_t *blocks_per_sm) {
+    if (!A || !pull_width || !blocks_per_sm) return fail(GB_NULL_POINTER, "gb_bfs_get_shape: NULL argument");
+    *pull_width = A->bfs_pull_width ? A->bfs_pull_width : (uint32_t)bfsk::PULL_WPW;
+    *blocks_per_sm = A->bfs_blocks_per_sm;
     return GB_SUCCESS;
 }

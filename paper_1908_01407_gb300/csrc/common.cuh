@@ -101,6 +101,10 @@ struct gb_matrix_t {
     uint32_t tuned_beta = 0;
     // BFS schedule chosen by gb_bfs_autotune (GB_SCHED_AUTO = not tuned)
     int tuned_schedule = GB_SCHED_AUTO;
+    // BFS tile shape (gb_bfs_autotune or gb_bfs_set_shape; 0 = the default):
+    // pull candidates per lane in flight (1, 2, 4) and blocks per SM (1..4)
+    uint32_t bfs_pull_width = 0;
+    uint32_t bfs_blocks_per_sm = 0;
     // PageRank SpMV tile (128-nonzero sub-tiles per warp tile) chosen by
     // gb_pagerank_autotune (0 = not tuned)
     uint32_t tuned_pr_nsub = 0;

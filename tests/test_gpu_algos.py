@@ -301,8 +301,13 @@ def test_tc_rmat_s20_full_size(ctx):
 # ------------------------------------------------------- multi-source BFS
 @pytest.mark.parametrize("case,k", [("rmat14", 64), ("rmat14", 1), ("rmat13", 37), ("grid", 64), ("small", 5),
                                     ("path", 9),
-                                    ("rmat13", 150), ("rmat14", 256)])
+                                    ("rmat13", 150), ("rmat14", 256), ("rmat14", 100), ("grid", 128),
+                                    ("grid", 200), ("path", 130), ("small", 65), ("rmat13", 300)])
 def test_bfs_multi_matches_independent_bfs(ctx, case, k):
+    """k BFS as one Boolean SpMM over bit-packed frontiers: 64 sources per
+    word of source bits, one launch for up to 256 (one, two or four words
+    per vertex), consecutive launches beyond; every row equals the oracle's
+    queue BFS from that source, in push, pull and automatic direction."""
     t = {"rmat14": lambda: gen.rmat(14, 16, seed=1),
          "rmat13": lambda: gen.rmat(13, 8, seed=8),
          "grid": lambda: gen.grid(60, 50, 0.1, seed=3),
@@ -319,6 +324,8 @@ def test_bfs_multi_matches_independent_bfs(ctx, case, k):
         _, st = gb.bfs_multi(ctx, A, srcs, lv, gb.Descriptor(direction=direction))
         assert np.array_equal(lv, want), direction
         assert st["status"] == 0
+        if k <= 256:   # one launch: one direction per expanded level
+            assert st["push_levels"] + st["pull_levels"] <= st["depth"]
     A.free()
 
 

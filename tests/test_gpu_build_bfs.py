@@ -191,8 +191,40 @@ def test_bfs_autotune_picks_a_candidate_and_keeps_results(ctx):
     g, A = make(ctx, t)
     beta, ms = gb.bfs_autotune(ctx, A, gen.sources(t, 4, seed=99))
     assert beta in (4, 6, 8, 10, 12, 16, 20, 24, 32, 48, 64, 96, 128, 192, 256) and ms > 0
+    w, b = gb.bfs_get_shape(A)
+    assert w in (1, 2, 4) and b in (0, 2, 3, 4)
     for s in gen.sources(t, 4, seed=1):
-        check_bfs(ctx, g, A, int(s))          # default descriptor: the tuned beta
+        check_bfs(ctx, g, A, int(s))          # default descriptor: the tuned beta and shape
+    A.free()
+
+
+@pytest.mark.parametrize("case", ["rmat14", "grid", "layered"])
+def test_bfs_every_tile_shape_matches_the_oracle(ctx, case):
+    """Every tile shape the autotuner can pick (pull candidates per lane x
+    blocks per SM), with the default descriptor and forced pull: levels
+    bit-exact, parents valid."""
+    if case == "layered":
+        t, src0 = layered_graph()
+    else:
+        t = {"rmat14": lambda: gen.rmat(14, 16, seed=3), "grid": lambda: gen.grid(70, 61, 0.1, seed=2)}[case]()
+        src0 = int(gen.sources(t, 1, seed=5)[0])
+    g, A = make(ctx, t)
+    srcs = [src0] + [int(s) for s in gen.sources(t, 2, seed=7)]
+    pull = gb.Descriptor(direction=gb.PULL)
+    for w in (1, 2, 4):
+        for b in (0, 1, 2, 3, 4):
+            gb.bfs_set_shape(A, w, b)
+            assert gb.bfs_get_shape(A) == (w, b)
+            for s in srcs:
+                check_bfs(ctx, g, A, s)
+                check_bfs(ctx, g, A, s, pull)
+    gb.bfs_set_shape(A, 0, 0)
+    assert gb.bfs_get_shape(A) == (2, 0)
+    for bad in ((3, 0), (8, 0), (2, 5)):
+        with pytest.raises(gb.GBError) as e:
+            gb.bfs_set_shape(A, *bad)
+        assert e.value.code == gb.INVALID_VALUE
+    pull.free()
     A.free()
 
 
