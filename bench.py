@@ -120,11 +120,13 @@ def code_digest(paths, root=None):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(profile, sources, beta=None, shape=None):
+def recorded_traffic(profile, sources, beta=None, shape=None, alg_per_launch=None):
     """DRAM bytes per launch from a profile summary's `traffic-record` line
     for this push/pull threshold and tile shape ("pull width,blocks per SM"),
     or None when the kernel's code changed since that capture or no capture
-    used this threshold and shape."""
+    used this threshold and shape. A record of a sample of the sources that
+    also gives the sample's mean algorithmic bytes (alg_per_launch=) is
+    scaled to the caller's mean algorithmic bytes per launch."""
     try:
         text = open(os.path.join(ROOT, profile)).read()
     except OSError:
@@ -134,7 +136,10 @@ def recorded_traffic(profile, sources, beta=None, shape=None):
             kv = dict(x.split("=", 1) for x in line.split(":", 1)[1].split())
             if kv.get("digest") == code_digest(sources) and (beta is None or kv.get("beta") == str(beta)) \
                     and (shape is None or kv.get("shape", "2,0") == shape):
-                return float(kv["bytes_per_launch"])
+                t = float(kv["bytes_per_launch"])
+                if "alg_per_launch" in kv and alg_per_launch:
+                    t *= alg_per_launch / float(kv["alg_per_launch"])
+                return t
     return None
 
 
@@ -342,7 +347,8 @@ def run_gbx(args):
     avg_kernel_ms = k_ms / max(k_n, 1)          # one launch = one traversal
     alg_per_launch = alg_per_bfs
     achieved = alg_per_launch / (avg_kernel_ms / 1e3) / 1e9
-    traffic = recorded_traffic(BFS_PROFILE, BFS_KERNEL_SOURCES, args.beta or tuned_beta, f"{pull_width},{per_sm}")
+    traffic = recorded_traffic(BFS_PROFILE, BFS_KERNEL_SOURCES, args.beta or tuned_beta, f"{pull_width},{per_sm}",
+                               alg_per_launch)
     dram_achieved = traffic / (avg_kernel_ms / 1e3) / 1e9 if traffic else None
     line = {
         "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,

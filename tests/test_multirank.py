@@ -84,3 +84,23 @@ def test_traffic_record_needs_the_same_code_and_threshold(tmp_path):
         assert bench.recorded_traffic("p.md", ["k.cu"], 24) is None
     finally:
         bench.ROOT = old_root
+
+
+def test_traffic_record_of_a_sample_scales_by_algorithmic_bytes(tmp_path):
+    """A record taken on a sample of the sources, with the tile shape it ran
+    and the sample's mean algorithmic bytes, is scaled to the bench's mean
+    algorithmic bytes, and matches only its own shape."""
+    src = tmp_path / "k.cu"
+    src.write_text("__global__ void k() {}\n")
+    dig = bench.code_digest(["k.cu"], root=str(tmp_path))
+    (tmp_path / "p.md").write_text(
+        f"traffic-record: kernel=k digest={dig} beta=16 shape=1,4 bytes_per_launch=150 alg_per_launch=100 "
+        f"launches=8\n")
+    old_root = bench.ROOT
+    try:
+        bench.ROOT = str(tmp_path)
+        assert bench.recorded_traffic("p.md", ["k.cu"], 16, "1,4", 110.0) == pytest.approx(165.0)
+        assert bench.recorded_traffic("p.md", ["k.cu"], 16, "1,4") == 150.0
+        assert bench.recorded_traffic("p.md", ["k.cu"], 16, "2,0", 110.0) is None
+    finally:
+        bench.ROOT = old_root
