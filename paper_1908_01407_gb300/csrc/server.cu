@@ -5,8 +5,9 @@
 // every other pending BFS on the same graph up to 64, packed into one
 // multi-source bit-frontier launch. A job is admitted only while its memory
 // estimate fits the HBM budget. Persistent kernels of concurrent slots are
-// given grids that fit on the GPU together, so their work overlaps.
-// A job that starts while no other job runs or waits gets the whole GPU.
+// given grids that split the GPU between the jobs running or waiting when
+// they start, so their work overlaps; a job that starts while no other job
+// runs or waits gets the whole GPU.
 // Results stay on the device until fetched. Latency is measured from submit
 // to the moment the slot sees the job finish on the GPU.
 #include "common.cuh"
@@ -152,9 +153,14 @@ void worker_loop(gb_server *S, int w) {
         S->peak = std::max(S->peak, S->in_use);
         S->running++;
         // a job that starts with nothing else running or waiting takes the whole
-        // GPU; otherwise its persistent kernels get the share that lets every
-        // slot run at once
-        ctx->grid_limit = (S->running == 1 && S->pending.empty()) ? 0 : S->share;
+        // GPU; otherwise its persistent kernels get an equal part of it for the
+        // jobs running or waiting now (4 blocks per SM split between them), never
+        // less than the share that lets every slot run at once. A long job that
+        // overlaps one other thus keeps half the GPU, not an eighth of it.
+        {
+            const int conc = std::min(S->running + (int)S->pending.size(), (int)S->cfg.max_inflight);
+            ctx->grid_limit = conc <= 1 ? 0 : std::max(S->share, 4 * S->ctx->num_sms / conc);
+        }
         std::vector<uint32_t> srcs;
         for (uint64_t t : job) srcs.push_back(S->tickets[t].req.src);
         lk.unlock();
