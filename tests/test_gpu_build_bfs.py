@@ -447,13 +447,14 @@ def test_bfs_batch_single_vertex_graph(ctx):
     A.free()
 
 
-@pytest.mark.parametrize("case", ["rmat_even", "rmat_odd", "directed", "csr_only", "isolated", "single"])
+@pytest.mark.parametrize("case", ["rmat_even", "rmat_odd", "directed", "csr_only", "isolated", "single", "many"])
 def test_bfs_batch_device_rows_match_the_oracle(ctx, case):
     """gb_bfs_batch with device outputs: each row equals the oracle's BFS
     (levels exactly, parents valid), for an even and an odd number of runs, a
     directed matrix (pulls over its CSC), a CSR-only matrix (push only),
-    isolated sources among others, and one run; a second batch on the same
-    workspace gives the same rows."""
+    isolated sources among others, one run, and 75 runs with repeated and
+    isolated sources; a second batch on the same workspace gives the same
+    rows."""
     if case in ("directed", "csr_only"):
         rng = np.random.default_rng(17)
         n = 5000
@@ -466,8 +467,12 @@ def test_bfs_batch_device_rows_match_the_oracle(ctx, case):
         t = gen.rmat(14, 16, seed=21)
         g, A = make(ctx, t)
         n = t.n
-        srcs = [int(s) for s in gen.sources(t, {"rmat_even": 8, "rmat_odd": 9, "isolated": 4, "single": 1}[case],
-                                              seed=5)]
+        srcs = [int(s) for s in gen.sources(t, {"rmat_even": 8, "rmat_odd": 9, "isolated": 4, "single": 1,
+                                                 "many": 65}[case], seed=5)]
+        if case == "many":
+            deg = np.diff(g.rowptr.astype(np.int64))
+            iso = [int(v) for v in np.flatnonzero(deg == 0)[:5]]
+            srcs = srcs[:30] + iso + srcs[:5] + srcs[30:]
         if case == "isolated":
             deg = np.diff(g.rowptr.astype(np.int64))
             iso = [int(v) for v in np.flatnonzero(deg == 0)[:2]]
