@@ -855,7 +855,9 @@ def run_profile(args):
         srcs = gen.sources(t, NSRC, seed=SRC_SEED)
         A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, t.w if kind == "sssp" else None, type_=gb.UINT32,
                                   flags=gb.SYMMETRIC)
-        out = torch.empty(t.n * (NSRC if kind == "msbfs" else 1), dtype=torch.int32, device="cuda")
+        if kind == "msbfs":
+            srcs = gen.sources(t, args.ms_sources, seed=SRC_SEED)
+        out = torch.empty(t.n * (len(srcs) if kind == "msbfs" else 1), dtype=torch.int32, device="cuda")
         out2 = torch.empty(t.n, dtype=torch.int32, device="cuda")
         desc = gb.Descriptor(beta=args.beta) if args.beta else None
         if args.bfs_shape:
@@ -872,7 +874,7 @@ def run_profile(args):
             elif kind == "sssp":
                 gb.sssp(ctx, A, int(srcs[i]), out)
             elif kind == "msbfs":
-                gb.bfs_multi(ctx, A, srcs, out.view(NSRC, t.n), stats=False)
+                gb.bfs_multi(ctx, A, srcs, out.view(len(srcs), t.n), stats=False)
             elif kind == "pr":
                 gb.pagerank(ctx, A, 0.85, 2, out.view(torch.float32), residuals=False)
             elif kind == "prd":
@@ -912,6 +914,8 @@ def main():
                     default=None,
                     help="short fixed run of one kernel for ncu")
     ap.add_argument("--profile-launches", type=int, default=3)
+    ap.add_argument("--ms-sources", type=int, default=NSRC,
+                    help="sources of the profiled multi-source BFS (up to 256 share one launch)")
     ap.add_argument("--pr-tile", type=int, default=256, help="PageRank tile of the profiled run (256, 512, 1024)")
     ap.add_argument("--pr-order", type=int, default=0,
                     help="PageRank vertex order of the profiled run (1: the degree-ordered copy)")
