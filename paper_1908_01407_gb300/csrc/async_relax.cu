@@ -35,6 +35,8 @@
 // one barrier pair per distance bucket instead of one per hop.
 // Every wait is bounded: a wait that runs out sets GB_TIMEOUT and every warp
 // leaves.
+#include <cstdlib>
+
 #include "common.cuh"
 #include "types.cuh"
 
@@ -504,6 +506,15 @@ gb_info async_relax_run(gb_context *ctx, const gb_matrix *A, int kind, uint32_t 
     a.local = 1;
     a.wait_ns = 4000000000ull;
     a.total_limit_ns = 60000000000ull;
+    // failure-path test: GBX_TEST_ASYNC_LIMIT_US bounds the whole traversal by
+    // that many microseconds (1 us .. 1 s), so its bounded waits run out
+    if (const char *e = getenv("GBX_TEST_ASYNC_LIMIT_US")) {
+        long long us = atoll(e);
+        if (us > 0) {
+            if (us > 1000000) us = 1000000;
+            a.total_limit_ns = (uint64_t)us * 1000ull;
+        }
+    }
     const void *fn = kind == K_SSSP ? (const void *)k_async<K_SSSP>
                      : kind == K_BFS ? (const void *)k_async<K_BFS> : (const void *)k_async<K_CC>;
     int occ = 0;

@@ -92,3 +92,35 @@ def test_bfs_timeout_without_waiting_is_reported_by_synchronize(ctx):
     assert st["status"] == 0
     assert np.array_equal(lv.cpu().numpy(), oracle.bfs(g, s))
     A.free()
+
+
+def test_barrier_free_traversal_timeout_is_reported_and_the_next_run_is_correct(ctx):
+    """The barrier-free schedule bounds its whole traversal (and every wait
+    in it); a test hook shrinks that bound to a few microseconds, so the run
+    stops with GB_TIMEOUT (no fault, no hang), and the next run on the same
+    context, with its own fresh ring and state, gives Dijkstra's distances
+    and the union-find labels."""
+    import os
+    t = gen.grid(400, 400, 0.1, seed=6, wmax=1000)
+    g = oracle.csr_from_tuples(t)
+    A = gb.Matrix.from_tuples(ctx, t.n, t.src, t.dst, t.w, type_=gb.UINT32, flags=gb.SYMMETRIC)
+    src = gen.first_nonisolated(t)
+    d = gb.Descriptor(schedule=gb.SCHED_ASYNC)
+    dist = np.empty(t.n, np.uint32)
+    lab = np.empty(t.n, np.uint32)
+    os.environ["GBX_TEST_ASYNC_LIMIT_US"] = "5"
+    try:
+        with pytest.raises(gb.GBError) as e:
+            gb.sssp(ctx, A, src, dist, d)
+        assert e.value.code == gb.TIMEOUT
+        with pytest.raises(gb.GBError) as e:
+            gb.cc_async(ctx, A, lab)
+        assert e.value.code == gb.TIMEOUT
+    finally:
+        del os.environ["GBX_TEST_ASYNC_LIMIT_US"]
+    gb.sssp(ctx, A, src, dist, d)
+    assert np.array_equal(dist, oracle.sssp(g, src))
+    gb.cc_async(ctx, A, lab)
+    assert np.array_equal(lab, oracle.cc(g))
+    d.free()
+    A.free()
