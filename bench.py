@@ -555,7 +555,8 @@ def extra_rows(args, hbm):
     _, _, st = gb.bfs(ctx, A, src, lvg, pag)
     ms = cuda_time_ms(lambda: gb.bfs(ctx, A, src, lvg, pag, stats=False), stream)
     g_out = {"bfs_ms": ms, "bfs_levels": st["depth"], "bfs_us_per_level": 1e3 * ms / max(st["depth"], 1),
-             "bfs_schedule": "cluster" if st["schedule"] == gb.SCHED_CLUSTER else "grid", "bfs_beta": beta_g}
+             "bfs_schedule": {gb.SCHED_CLUSTER: "cluster", gb.SCHED_ASYNC: "async"}.get(st["schedule"], "grid"),
+             "bfs_beta": beta_g}
     d = torch.empty(t.n, dtype=torch.int32, device="cuda")
     its = []
     ms = cuda_time_ms(lambda: its.append(gb.sssp(ctx, A, src, d)[1]), stream)

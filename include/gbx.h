@@ -106,7 +106,7 @@ enum {
      * ring that warps poll, until no item is in flight (the asynchronous
      * execution model of Section 9; for graphs of high diameter; gb_bfs,
      * gb_sssp; gb_cc_async is the components form). AUTO: what
-     * gb_bfs_autotune chose for the matrix, GRID if it was not tuned. */
+     * gb_bfs_autotune chose for the matrix (BFS), GRID if it was not tuned. */
     GB_SCHED_AUTO = 0, GB_SCHED_GRID = 1, GB_SCHED_CLUSTER = 2, GB_SCHED_ASYNC = 3
 };
 
@@ -325,10 +325,12 @@ typedef struct {
     float init_us;                              /* kernel entry to the start of level 0 */
     float final_us;                             /* end of the last level to the kernel's exit */
     uint32_t schedule;                          /* GB_SCHED_GRID, GB_SCHED_CLUSTER or GB_SCHED_ASYNC: the kernel
-                                                   that ran. With GB_SCHED_ASYNC there are no levels: depth =
-                                                   push_levels = distance buckets (1 without buckets),
-                                                   vertices_reached = work items relaxed (stale ones not
-                                                   counted), edges_examined = frontier_edges = out-edges
+                                                   that ran. With GB_SCHED_ASYNC there are no levels:
+                                                   push_levels = distance buckets (1 without buckets), depth =
+                                                   the same for SSSP and components and 1 + the largest level
+                                                   for BFS, vertices_reached = work items relaxed (stale ones
+                                                   not counted) for SSSP and components and the vertices
+                                                   reached for BFS, edges_examined = frontier_edges = out-edges
                                                    relaxed, alg_bytes = 4 n + 12 per item + 4 per edge (8 with
                                                    weights) + 4 per improvement + 8 per ring entry read,
                                                    final_us = device time of the traversal, no trace */
@@ -367,9 +369,9 @@ gb_info gb_bfs_batch(gb_context *ctx, const gb_matrix *A, const uint32_t *srcs, 
  * given sources (host array) for each beta in {4, 6, 8, 10, 12, 16, 20, 24,
  * 32, 48, 64, 96, 128, 192, 256}, timed with CUDA events in two passes over
  * the candidates (forward, then backward; each keeps its faster pass), and
- * stores the fastest beta on the matrix; the single-cluster schedule is
- * timed the same way and kept for the matrix when it is faster still
- * (graphs of high diameter). Later gb_bfs calls
+ * stores the fastest beta on the matrix; the single-cluster and the
+ * barrier-free schedules are timed the same way and kept for the matrix when
+ * faster still (graphs of high diameter). Later gb_bfs calls
  * whose descriptor leaves GB_SWITCH_BETA at 0 use it (untuned matrices use
  * the paper's beta = 10). *best_ms (may be NULL) = mean ms per BFS at it. */
 gb_info gb_bfs_autotune(gb_context *ctx, gb_matrix *A, const uint32_t *srcs, uint32_t k, uint32_t *best_beta,

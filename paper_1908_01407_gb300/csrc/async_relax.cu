@@ -64,6 +64,7 @@ struct AState {
     unsigned long long items, stale, edges, updates;
     unsigned int phases, pad;
     unsigned long long t_begin, t_end;
+    unsigned int reached, maxlev;      // BFS: vertices reached, largest level (the parent pass)
 };
 
 struct AArgs {
@@ -448,21 +449,28 @@ __global__ void __launch_bounds__(ABLOCK, 4) k_async(AArgs a) {
 // with level(v) = level(u) + 1, parent(v) = the smallest such u (any of them
 // is a valid BFS-tree parent; the smallest makes the output deterministic).
 // A thread per vertex; rows longer than 32 are walked by the whole warp.
+// Also counts the vertices reached and the largest level (par == null: the
+// count only).
 __global__ void k_async_parents(const uint32_t *rp, const uint32_t *ci, uint32_t n, const uint32_t *lv,
-                                uint32_t *par, uint32_t src) {
+                                uint32_t *par, uint32_t src, AState *st) {
     const uint32_t full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
+    uint32_t reached = 0, maxlev = 0;
     for (uint64_t u0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); u0 < n; u0 += nth) {
         const uint64_t u = u0 + lane;
         uint32_t lu = UINT32_MAX, b = 0, e = 0;
         if (u < n) {
             lu = __ldcg(&lv[u]);
             if (lu != UINT32_MAX) {
-                b = __ldg(&rp[u]);
-                e = __ldg(&rp[u + 1]);
+                ++reached;
+                maxlev = lu > maxlev ? lu : maxlev;
+                if (par) {
+                    b = __ldg(&rp[u]);
+                    e = __ldg(&rp[u + 1]);
+                }
             }
-            if (u == src) par[u] = src;
+            if (par && u == src) par[u] = src;
         }
         if (e - b <= 32) {
             for (uint32_t p = b; p < e; ++p) {
@@ -482,6 +490,12 @@ __global__ void k_async_parents(const uint32_t *rp, const uint32_t *ci, uint32_t
                 if (v != src && __ldcg(&lv[v]) == pl + 1u) atomicMin(&par[v], pu);
             }
         }
+    }
+    reached = dev::warp_sum<uint32_t>(reached);
+    maxlev = __reduce_max_sync(full, maxlev);
+    if (lane == 0) {
+        if (reached) atomicAdd(&st->reached, reached);
+        atomicMax(&st->maxlev, maxlev);
     }
 }
 
@@ -543,9 +557,10 @@ gb_info async_relax_run(gb_context *ctx, const gb_matrix *A, int kind, uint32_t 
     int span = prof_begin(ctx, who);
     GB_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(ABLOCK), args, 0, ctx->stream));
     GB_LAUNCH_CHECK();
-    if (kind == K_BFS && parents) {
-        GB_CUDA(cudaMemsetAsync(parents, 0xff, (size_t)n * 4, ctx->stream));
-        k_async_parents<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(A->rowptr, A->colidx, n, out, parents, src);
+    if (kind == K_BFS && (parents || stats)) {
+        if (parents) GB_CUDA(cudaMemsetAsync(parents, 0xff, (size_t)n * 4, ctx->stream));
+        k_async_parents<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(A->rowptr, A->colidx, n, out, parents, src,
+                                                                   a.st);
         GB_LAUNCH_CHECK();
     }
     prof_end(ctx, span);
@@ -554,10 +569,10 @@ gb_info async_relax_run(gb_context *ctx, const gb_matrix *A, int kind, uint32_t 
     GB_CHECK(sync(ctx));
     if (stats) {
         memset(stats, 0, sizeof(*stats));
-        stats->depth = hs.phases;
+        stats->depth = kind == K_BFS ? hs.maxlev + 1 : hs.phases;
         stats->push_levels = hs.phases;
         stats->status = (uint32_t)hs.err;
-        stats->vertices_reached = hs.items;
+        stats->vertices_reached = kind == K_BFS ? hs.reached : hs.items;
         stats->edges_examined = hs.edges;
         stats->frontier_edges = hs.edges;
         // 4 n value writes; per vertex relaxed 8 (row bounds) + 4 (its value);

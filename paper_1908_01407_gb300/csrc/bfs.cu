@@ -769,6 +769,7 @@ void bfs_workspace_release(gb_context *ctx) {
 static int bfs_schedule(gb_context *ctx, const gb_matrix *A, const gb_desc *desc) {
     int sch = (desc && desc->schedule != GB_SCHED_AUTO) ? desc->schedule : A->tuned_schedule;
     if (sch == GB_SCHED_CLUSTER && !bfs_cluster_available(ctx)) sch = GB_SCHED_GRID;
+    if (sch == GB_SCHED_ASYNC) return GB_SCHED_ASYNC;
     return sch == GB_SCHED_CLUSTER ? GB_SCHED_CLUSTER : GB_SCHED_GRID;
 }
 
@@ -886,7 +887,7 @@ extern "C" gb_info gb_bfs(gb_context *ctx, const gb_matrix *A, uint32_t src, int
             dp = tp.as<int32_t>();
         }
     }
-    if (desc && desc->schedule == GB_SCHED_ASYNC) {
+    if (bfs_schedule(ctx, A, desc) == GB_SCHED_ASYNC) {
         GB_CHECK(async_relax_run(ctx, A, 1, src, (uint32_t *)dl, (uint32_t *)dp, 0, stats, "gb_bfs"));
         if (mem == GB_HOST) {
             GB_CUDA(cudaMemcpyAsync(levels, dl, (size_t)A->nrows * 4, cudaMemcpyDeviceToHost, ctx->stream));
@@ -998,6 +999,8 @@ extern "C" gb_info gb_bfs_batch(gb_context *ctx, const gb_matrix *A, const uint3
     GB_CHECK(memset_async(ctx, eb.p, 0, sizeof(int)));
     int *err = eb.as<int>();
     auto run = [&](uint32_t q, int32_t *dl, int32_t *dp) -> gb_info {
+        if (sch == GB_SCHED_ASYNC)
+            return async_relax_run(ctx, A, 1, srcs[q], (uint32_t *)dl, (uint32_t *)dp, 0, nullptr, "gb_bfs_batch");
         if (sch == GB_SCHED_CLUSTER) return bfs_cluster_run(ctx, A, srcs[q], dl, dp, w, err);
         return bfs_launch(ctx, A, srcs[q], dl, dp, desc, w, 0, err);
     };
@@ -1283,6 +1286,31 @@ extern "C" gb_info gb_bfs_autotune(gb_context *ctx, gb_matrix *A, const uint32_t
             if (ms < tcl) tcl = ms;
         }
         if (tcl < best) { best = tcl; sched = GB_SCHED_CLUSTER; }
+    }
+    // the barrier-free schedule (levels by unit-weight relaxation, then the
+    // parents), timed the same way after one untimed run and a hopeless check
+    {
+        double ta = 1e30;
+        bool hopeless = false;
+        for (int pass = 0; pass < 3 && !hopeless; ++pass) {
+            const uint32_t kk = pass == 0 ? 1u : k;
+            gb_info r = cudaEventRecord(e0, ctx->stream) == cudaSuccess ? GB_SUCCESS : GB_PANIC;
+            for (uint32_t q = 0; q < kk && r == GB_SUCCESS; ++q)
+                r = async_relax_run(ctx, A, 1, srcs[q], lv.as<uint32_t>(), pa.as<uint32_t>(), 0, nullptr,
+                                    "gb_bfs_autotune");
+            if (r == GB_SUCCESS && cudaEventRecord(e1, ctx->stream) != cudaSuccess) r = GB_PANIC;
+            if (r == GB_SUCCESS && cudaEventSynchronize(e1) != cudaSuccess) r = GB_PANIC;
+            if (r != GB_SUCCESS) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return r == GB_PANIC ? fail(GB_PANIC, "gb_bfs_autotune: CUDA error") : r;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (pass == 0) hopeless = (double)ms > 4.0 * best / k;   // the first run also warms the schedule up
+            else if (ms < ta) ta = ms;
+        }
+        if (ta < best) { best = ta; sched = GB_SCHED_ASYNC; }
     }
     A->tuned_schedule = sched;
     cudaEventDestroy(e0);

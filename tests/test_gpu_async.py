@@ -67,6 +67,8 @@ def test_async_bfs_levels_and_parents(ctx, case):
         _, _, st = gb.bfs(ctx, A, src, lv, par, desc=d)
         want = oracle.bfs(g, src)
         assert np.array_equal(lv, want), (case, src)
+        assert st["schedule"] == gb.SCHED_ASYNC and st["status"] == 0
+        assert st["depth"] == int(want.max()) + 1 and st["vertices_reached"] == int((want >= 0).sum())
         assert oracle.bfs_parent_violations(g, src, lv, par) == 0
         # each parent is the smallest in-neighbour one level up
         rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(g.rowptr.astype(np.int64)))

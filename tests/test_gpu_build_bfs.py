@@ -295,14 +295,15 @@ def test_bfs_single_cluster_schedule(ctx, case):
     A.free()
 
 
-def test_bfs_autotune_chooses_cluster_for_a_long_path(ctx):
-    """A 3000-vertex path has 3000 levels of one vertex each: the cluster
-    schedule wins and becomes the matrix's default."""
+def test_bfs_autotune_chooses_a_high_diameter_schedule_for_a_long_path(ctx):
+    """A 3000-vertex path has 3000 levels of one vertex each: the cluster or
+    the barrier-free schedule wins over the persistent grid and becomes the
+    matrix's default; the results and the statistics are the same."""
     t = gen.from_edges(3000, [(i, i + 1) for i in range(2999)])
     g, A = make(ctx, t)
     gb.bfs_autotune(ctx, A, np.array([0, 1500], np.uint32))
     st = check_bfs(ctx, g, A, 0)
-    assert st["schedule"] == gb.SCHED_CLUSTER
+    assert st["schedule"] in (gb.SCHED_CLUSTER, gb.SCHED_ASYNC)
     d = gb.Descriptor(schedule=gb.SCHED_GRID)      # the descriptor overrides the tuned choice
     st = check_bfs(ctx, g, A, 0, d)
     assert st["schedule"] == gb.SCHED_GRID
@@ -310,7 +311,7 @@ def test_bfs_autotune_chooses_cluster_for_a_long_path(ctx):
     A.free()
 
 
-@pytest.mark.parametrize("schedule", [gb.SCHED_GRID, gb.SCHED_CLUSTER])
+@pytest.mark.parametrize("schedule", [gb.SCHED_GRID, gb.SCHED_CLUSTER, gb.SCHED_ASYNC])
 @pytest.mark.parametrize("out", ["pinned", "numpy", "device", "levels_only"])
 def test_bfs_batch_rows_match_the_oracle(ctx, schedule, out):
     """gb_bfs_batch: row q is the BFS from source q (levels exactly, parents a
