@@ -317,53 +317,44 @@ __device__ void pull_level(const BfsArgs &a, PullSmem &ps, int d, const void *Li
                 r[j].head = make_uint4(hh[0], hh[1], hh[2], hh[3]);
             }
         }
-        // the visited word and the frontier words of the first two head
-        // entries, together; the other two only where those did not hit (every
-        // frontier word is a random sector lookup, and the first two decide
-        // most candidates)
+        // the visited word and the frontier word of the first head entry
+        // (the in-neighbour of largest out-degree) together; the other three
+        // only where it missed. Every frontier word is a random sector lookup
+        // and the lookups' rate bounds a wide pull, so each candidate asks for
+        // as few as decide it.
         uint32_t vw[WPW], fw[WPW][4];
 #pragma unroll
         for (int j = 0; j < WPW; ++j) {
-            const uint32_t h[2] = {r[j].head.x, r[j].head.y};
             vw[j] = r[j].v != NONE ? ldcg(&a.visited[r[j].v >> 5]) : full;
-#pragma unroll
-            for (int k = 0; k < 2; ++k) fw[j][k] = h[k] != NONE ? ldcg(&F[h[k] >> 5]) : 0u;
+            fw[j][0] = r[j].head.x != NONE ? ldcg(&F[r[j].head.x >> 5]) : 0u;
         }
 #pragma unroll
         for (int j = 0; j < WPW; ++j) {
-            const uint32_t h[2] = {r[j].head.x, r[j].head.y};
             act[j] = r[j].v != NONE && !((vw[j] >> (r[j].v & 31)) & 1u);
-            found[j] = false;
-            par[j] = 0;
-#pragma unroll
-            for (int k = 1; k >= 0; --k)   // the first frontier neighbour in head order
-                if (h[k] != NONE && ((fw[j][k] >> (h[k] & 31)) & 1u)) {
-                    found[j] = true;
-                    par[j] = h[k];
-                }
-            found[j] = found[j] && act[j];
+            found[j] = act[j] && r[j].head.x != NONE && ((fw[j][0] >> (r[j].head.x & 31)) & 1u);
+            par[j] = found[j] ? r[j].head.x : 0u;
         }
 #pragma unroll
         for (int j = 0; j < WPW; ++j) {
-            const uint32_t h[2] = {r[j].head.z, r[j].head.w};
+            const uint32_t h[3] = {r[j].head.y, r[j].head.z, r[j].head.w};
 #pragma unroll
-            for (int k = 0; k < 2; ++k)
-                fw[j][2 + k] = (act[j] && !found[j] && h[k] != NONE) ? ldcg(&F[h[k] >> 5]) : 0u;
+            for (int k = 0; k < 3; ++k)
+                fw[j][1 + k] = (act[j] && !found[j] && h[k] != NONE) ? ldcg(&F[h[k] >> 5]) : 0u;
         }
 #pragma unroll
         for (int j = 0; j < WPW; ++j) {
             uint32_t ex = r[j].len < 4 ? r[j].len : 4;
             if (act[j] && !found[j]) {
-                const uint32_t h[2] = {r[j].head.z, r[j].head.w};
+                const uint32_t h[3] = {r[j].head.y, r[j].head.z, r[j].head.w};
 #pragma unroll
-                for (int k = 1; k >= 0; --k)
-                    if (h[k] != NONE && ((fw[j][2 + k] >> (h[k] & 31)) & 1u)) {
+                for (int k = 2; k >= 0; --k)   // the first frontier neighbour in head order
+                    if (h[k] != NONE && ((fw[j][1 + k] >> (h[k] & 31)) & 1u)) {
                         found[j] = true;
                         par[j] = h[k];
-                        ex = k + 3;
+                        ex = k + 2;
                     }
             } else if (found[j]) {
-                ex = par[j] == r[j].head.x ? 1 : 2;
+                ex = 1;
             }
             if (act[j]) { exam += ex; ++myact; }
         }
