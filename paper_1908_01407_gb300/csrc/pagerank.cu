@@ -569,7 +569,13 @@ static gb_info pagerank_run(gb_context *ctx, const gb_matrix *A, float damping, 
     const uint32_t wpb = (uint32_t)block / 32;
     const uint32_t need = (ntiles + wpb - 1) / wpb;
     if (G > need) G = need > 0 ? need : 1;
-    const uint32_t UB = 1024;   // blocks of the update pass (fixed: the reduction order does not depend on the GPU)
+    // blocks of the update pass (fixed: the reduction order does not depend on
+    // the GPU). Its cost is mostly per block (the FP64 partial sums and the
+    // completion count): on R-MAT s22, 512 blocks took 24.9 us, 1,024 took
+    // 30.6, 2,048 took 39.5, and 256 to 608 took 25-27.
+    const uint32_t UB = 512;
+    // blocks of the final normalisation's FP64 sum (its partials share pres)
+    const uint32_t NB = 1024;
     Scratch p0(ctx), p1(ctx), x0(ctx), x1(ctx), yb(ctx), fl(ctx), tr(ctx), pf(ctx), pl(ctx), rl(ctx), tf(ctx),
         pres(ctx), pdang(ctx), scal(ctx), resid(ctx), outb(ctx), lsp(ctx);
     GB_CHECK(p0.alloc((size_t)n * 4 + 16));
@@ -585,7 +591,7 @@ static gb_info pagerank_run(gb_context *ctx, const gb_matrix *A, float damping, 
     GB_CHECK(tf.alloc((size_t)ntiles * 4 + 16));
     // each long row takes more than SPAN_SHORT tiles of its own
     GB_CHECK(lsp.alloc(((size_t)ntiles / SPAN_SHORT + 1) * sizeof(uint2)));
-    GB_CHECK(pres.alloc((size_t)UB * 8));
+    GB_CHECK(pres.alloc((size_t)(UB > NB ? UB : NB) * 8));
     GB_CHECK(pdang.alloc((size_t)UB * 8));
     GB_CHECK(scal.alloc(64));
     GB_CHECK(resid.alloc(((size_t)iters + 1) * 8));
@@ -666,8 +672,8 @@ static gb_info pagerank_run(gb_context *ctx, const gb_matrix *A, float damping, 
         t = xc; xc = xn; xn = t;
     }
     // final normalisation in FP64, back to A's vertex names
-    k_pr_sum<<<1024, PR_BLOCK, 0, ctx->stream>>>(n, pc, pres.as<double>());
-    k_pr_norm<<<1024, PR_BLOCK, 0, ctx->stream>>>(n, pc, pres.as<double>(), 1024, new_id, out);
+    k_pr_sum<<<NB, PR_BLOCK, 0, ctx->stream>>>(n, pc, pres.as<double>());
+    k_pr_norm<<<NB, PR_BLOCK, 0, ctx->stream>>>(n, pc, pres.as<double>(), NB, new_id, out);
     GB_LAUNCH_CHECK();
     if (residuals && iters) GB_CUDA(cudaMemcpyAsync(residuals, resid.p, (size_t)iters * 8, cudaMemcpyDeviceToHost, ctx->stream));
     if (mem == GB_HOST) GB_CUDA(cudaMemcpyAsync(rank, out, (size_t)n * 4, cudaMemcpyDeviceToHost, ctx->stream));
