@@ -511,9 +511,15 @@ gb_info gb_cc(gb_context *ctx, const gb_matrix *A, uint32_t *labels, gb_mem mem,
  * gb_cc, so labels[v] = smallest vertex id in v's component, bit-identical
  * to gb_cc): every vertex starts as a work item (label, vertex), and a
  * persistent launch relaxes items through a ring that warps poll until none
- * is in flight. Uses the out-edges (CSR): for a symmetric A these are the
- * components. stats (may be NULL) as for gb_sssp with GB_SCHED_ASYNC. */
-gb_info gb_cc_async(gb_context *ctx, const gb_matrix *A, uint32_t *labels, gb_mem mem, gb_bfs_stats *stats);
+ * is in flight. Labels are taken in buckets of label_bucket values (the
+ * near-far discipline of SSSP applied to label values: labels below the
+ * bound spread first, larger ones wait, one grid-barrier triple per bucket),
+ * so a vertex is relabelled fewer times; 0 = automatic (n / 1024, at
+ * least 1,024), nrows or more = one bucket. Uses the out-edges (CSR): for a
+ * symmetric A these are the components. stats (may be NULL) as for gb_sssp
+ * with GB_SCHED_ASYNC. */
+gb_info gb_cc_async(gb_context *ctx, const gb_matrix *A, uint32_t *labels, gb_mem mem, uint32_t label_bucket,
+                    gb_bfs_stats *stats);
 /* Connected components by FastSV (Section 7.4: the paper's CC algorithm):
  * per iteration mngf = A min.second gf, stochastic hooking
  * f(f(u)) = min(f(f(u)), mngf(u)), aggressive hooking and shortcut

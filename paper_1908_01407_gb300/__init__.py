@@ -133,7 +133,7 @@ _SIGS = {
     "gb_bfs_batch": [_P, _P, _P, _U32, _P, _P, _I, _P],
     "gb_sssp": [_P, _P, _U32, _P, _I, _P, _P, _P], "gb_pagerank": [_P, _P, ctypes.c_float, _U32, _P, _P, _I],
     "gb_cc": [_P, _P, _P, _I, _P, _P], "gb_tc": [_P, _P, _P, _P],
-    "gb_cc_fastsv": [_P, _P, _P, _I, _P], "gb_cc_async": [_P, _P, _P, _I, _P],
+    "gb_cc_fastsv": [_P, _P, _P, _I, _P], "gb_cc_async": [_P, _P, _P, _I, _U32, _P],
     "gb_pagerank_delta": [_P, _P, ctypes.c_float, ctypes.c_float, _U32, _P, _I, _P, _P, _P],
     "gb_pagerank_autotune": [_P, _P, _P, _P, _P, _P], "gb_pagerank_set_tile": [_P, _U32],
     "gb_pagerank_set_order": [_P, _I, _U32],
@@ -734,16 +734,18 @@ def cc(ctx, A, labels=None):
     return labels, it.value
 
 
-def cc_async(ctx, A, labels=None, stats=False):
+def cc_async(ctx, A, labels=None, stats=False, bucket=0):
     """Connected components by min-label propagation without level
-    barriers; returns labels, or (labels, stats-dict) with stats=True."""
+    barriers, labels taken in buckets of `bucket` values (0 = automatic,
+    nrows or more = one bucket); returns labels, or (labels, stats-dict)
+    with stats=True."""
     n = A.nrows
     if labels is None:
         torch = _torch()
         labels = torch.empty(n, dtype=torch.int32, device=f"cuda:{ctx.device}")
     pl, ml = _out_mem(labels)
     st = BfsStats()
-    check(lib().gb_cc_async(ctx.h, A.h, pl, ml, ctypes.byref(st) if stats else None))
+    check(lib().gb_cc_async(ctx.h, A.h, pl, ml, bucket, ctypes.byref(st) if stats else None))
     return (labels, st.as_dict()) if stats else labels
 
 

@@ -224,7 +224,7 @@ __device__ void relax_entries(const AArgs &a, unsigned long long e, uint64_t bou
         for (int k = 0; k < KS; ++k) {
             if (!ok[k]) continue;
             cn.updates++;
-            if (KIND == K_SSSP && a.delta && (uint64_t)c[k] >= bound) {
+            if (KIND != K_BFS && a.delta && (uint64_t)c[k] >= bound) {
                 mark_far(a, u[k]);
                 ok[k] = false;
             }
@@ -249,7 +249,7 @@ __device__ void relax_entries(const AArgs &a, unsigned long long e, uint64_t bou
                 ok[0] = c[0] < __ldcg(&a.val[u[0]]) && c[0] < atomicMin(&a.val[u[0]], c[0]);
                 if (ok[0]) {
                     cn.updates++;
-                    if (KIND == K_SSSP && a.delta && (uint64_t)c[0] >= bound) {
+                    if (KIND != K_BFS && a.delta && (uint64_t)c[0] >= bound) {
                         mark_far(a, u[0]);
                         ok[0] = false;
                     }
@@ -332,24 +332,35 @@ __global__ void __launch_bounds__(ABLOCK, 4) k_async(AArgs a) {
     AState *st = a.st;
     const uint64_t nth = (uint64_t)gridDim.x * ABLOCK;
     const uint64_t tid = (uint64_t)blockIdx.x * ABLOCK + threadIdx.x;
-    // start: values, far bitmap, ring (CC: every vertex is an entry)
+    // start: values, far bitmap, ring. Components: every vertex is an entry
+    // (label = id); with label buckets the vertices whose id is at or beyond
+    // the first bound start in the far set instead.
+    const uint64_t ncc = KIND == K_CC ? (a.delta && a.delta < a.n ? a.delta : (uint64_t)a.n) : 0;
     for (uint64_t i = tid; i < a.n; i += nth)
         a.val[i] = KIND == K_CC ? (uint32_t)i : (i == a.src ? 0u : UINT32_MAX);
     if (a.far)
-        for (uint64_t w = tid; w < a.nwords; w += nth) a.far[w] = 0u;
+        for (uint64_t w = tid; w < a.nwords; w += nth) {
+            uint32_t f = 0u;
+            if (KIND == K_CC) {   // bits of the ids in [ncc, n)
+                const uint64_t lo = w * 32, hi = lo + 32;
+                for (uint64_t v = lo < ncc ? ncc : lo; v < hi && v < a.n; ++v) f |= 1u << (v - lo);
+            }
+            a.far[w] = f;
+        }
     for (uint64_t s = tid; s <= a.mask; s += nth) {
         unsigned long long e = EMPTY;
         if (KIND == K_CC) {
-            if (s < a.n) e = pack((uint32_t)s, (uint32_t)s);
+            if (s < ncc) e = pack((uint32_t)s, (uint32_t)s);
         } else if (s == 0) {
             e = pack(0u, a.src);
         }
         a.ring[s] = e;
     }
     if (tid == 0) {
-        st->tail = KIND == K_CC ? a.n : 1ull;
+        st->tail = KIND == K_CC ? ncc : 1ull;
         st->done = 0;
         st->far_min = UINT32_MAX;
+        st->far_cnt = KIND == K_CC ? (unsigned int)(a.n - ncc) : 0u;
     }
     bool ok = dev::grid_sync(&st->bar, gridDim.x, &st->err, a.wait_ns);
     const uint64_t t_start = dev::globaltimer_ns();
@@ -516,7 +527,7 @@ gb_info async_relax_run(gb_context *ctx, const gb_matrix *A, int kind, uint32_t 
     a.nwords = (n + 31) / 32;
     a.src = src;
     a.val = out;
-    a.delta = kind == K_SSSP ? delta : 0;
+    a.delta = kind == K_BFS ? 0 : delta;
     a.local = 1;
     a.wait_ns = 4000000000ull;
     a.total_limit_ns = 60000000000ull;

@@ -90,12 +90,16 @@ def test_async_bfs_levels_and_parents(ctx, case):
 
 @pytest.mark.parametrize("case", ["grid", "rmat12", "path", "star", "pieces", "single", "pair"])
 def test_async_cc_matches_union_find(ctx, case):
+    """Barrier-free min-label components equal union-find's canonical labels
+    for every label-bucket width: the automatic one, narrow buckets (many
+    phases), a width that leaves a ragged last bucket, and one bucket."""
     g, A, n, _ = graphs(ctx, case)
     want = oracle.cc(g)
     lab = np.empty(n, np.uint32)
-    _, st = gb.cc_async(ctx, A, lab, stats=True)
-    assert np.array_equal(lab, want), case
-    assert st["status"] == 0 and st["schedule"] == gb.SCHED_ASYNC
+    for bucket in (0, 5, 333, 2**32 - 1):
+        _, st = gb.cc_async(ctx, A, lab, stats=True, bucket=bucket)
+        assert np.array_equal(lab, want), (case, bucket)
+        assert st["status"] == 0 and st["schedule"] == gb.SCHED_ASYNC
     # twice in a row on device memory: the launch leaves nothing behind
     dl = torch.empty(n, dtype=torch.int32, device="cuda")
     for _ in range(2):
