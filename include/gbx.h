@@ -456,7 +456,9 @@ gb_info gb_sssp(gb_context *ctx, const gb_matrix *A, uint32_t src, uint32_t *dis
  * sum|p'-p| and the dangling mass are reduced in FP64 over FP32 sums of 4
  * consecutive vertices, the final normalisation in FP64. The result is
  * bit-reproducible run to run (fixed summation orders, no float atomics).
- * rank[n] in `mem`; residuals[iters] (host, may be NULL). */
+ * rank[n] in `mem`; residuals[iters] (host, may be NULL). The call waits for
+ * the result; GB_TIMEOUT if a bounded device wait ran out (the staging copy
+ * of the most-referenced ranks into shared memory). */
 gb_info gb_pagerank(gb_context *ctx, const gb_matrix *A, float damping, uint32_t iters, float *rank,
                     double *residuals, gb_mem mem);
 /* Autotuner of the PageRank SpMV layout (the paper has no counterpart; its

@@ -65,6 +65,7 @@ struct TileArgs {
     const float *x;           // p(j)/deg(j)
     uint32_t nhub;            // x[0, nhub) is staged in shared memory (a multiple of 4; 0 = none)
     float *y;                 // row sums (rows never written stay 0)
+    int *err;                 // set to GB_TIMEOUT when the staging copy did not complete in time
     float *pfirst;            // per tile: partial of the row open at its start (the whole tile without starts)
     float *plast;             // per tile with a start: partial of the row open at its end
     uint32_t *rlast;          // its rank
@@ -98,11 +99,33 @@ __global__ void __launch_bounds__(HUB ? PR_HUB_BLOCK : PR_BLOCK) k_pr_tiles(Tile
     constexpr uint32_t PR_TILE = PR_SUB * PR_NSUB;   // nonzeros per warp tile
     constexpr uint32_t WARPS = (HUB ? PR_HUB_BLOCK : PR_BLOCK) / 32;
     extern __shared__ float4 s_hub4[];
+    __shared__ uint64_t s_bar;
     const float *s_hub = reinterpret_cast<const float *>(s_hub4);
     if (HUB) {
-        // x of the first nhub vertices, once per block (x is padded past n to a multiple of 4)
-        const float4 *x4 = reinterpret_cast<const float4 *>(a.x);
-        for (uint32_t i = threadIdx.x; i < a.nhub / 4; i += blockDim.x) s_hub4[i] = __ldg(&x4[i]);
+        // x of the first nhub vertices, once per block: one thread hands the
+        // copy to the TMA unit (cp.async.bulk into shared memory, completion
+        // counted on an mbarrier) and the block waits on the barrier. x is
+        // padded past n to a multiple of 4 and nhub is a multiple of 4, so
+        // the copy is whole 16-byte units from a 256-byte aligned start.
+        const uint32_t bytes = a.nhub * 4u;
+        if (threadIdx.x == 0) {
+            dev::mbar_init(&s_bar, 1);
+            dev::mbar_arrive_expect_tx(&s_bar, bytes);
+            constexpr uint32_t CHUNK = 32768;   // bytes per bulk copy
+            for (uint32_t off = 0; off < bytes; off += CHUNK)
+                dev::bulk_copy_g2s(reinterpret_cast<char *>(s_hub4) + off, reinterpret_cast<const char *>(a.x) + off,
+                                   bytes - off < CHUNK ? bytes - off : CHUNK, &s_bar);
+        }
+        __syncthreads();   // the barrier is initialised before anyone waits on it
+        if (!dev::mbar_wait_bounded(&s_bar, 0, 1000000000ull)) {
+            // never expected: record it, wait once more for the copy in flight,
+            // then stage with plain loads so the block's result stays defined
+            if (threadIdx.x == 0) atomicExch(a.err, (int)GB_TIMEOUT);
+            (void)dev::mbar_wait_bounded(&s_bar, 0, 1000000000ull);
+            __syncthreads();
+            const float4 *x4 = reinterpret_cast<const float4 *>(a.x);
+            for (uint32_t i = threadIdx.x; i < a.nhub / 4; i += blockDim.x) s_hub4[i] = __ldg(&x4[i]);
+        }
         __syncthreads();
     }
     const uint32_t full = 0xffffffffu;
@@ -633,6 +656,7 @@ static gb_info pagerank_run(gb_context *ctx, const gb_matrix *A, float damping, 
     // edges come first, so the k-th nonempty row is row k
     ta.live = (order && M->csc_alias) ? nullptr : M->live_list;
     ta.nhub = nhub;
+    ta.err = reinterpret_cast<int *>(scal.as<char>());   // bytes 0-3 of the scalar block
     ta.y = yb.as<float>();
     ta.pfirst = pf.as<float>();
     ta.plast = pl.as<float>();
@@ -677,7 +701,10 @@ static gb_info pagerank_run(gb_context *ctx, const gb_matrix *A, float damping, 
     GB_LAUNCH_CHECK();
     if (residuals && iters) GB_CUDA(cudaMemcpyAsync(residuals, resid.p, (size_t)iters * 8, cudaMemcpyDeviceToHost, ctx->stream));
     if (mem == GB_HOST) GB_CUDA(cudaMemcpyAsync(rank, out, (size_t)n * 4, cudaMemcpyDeviceToHost, ctx->stream));
-    if (residuals || mem == GB_HOST) GB_CHECK(sync(ctx));
+    int herr = 0;
+    GB_CUDA(cudaMemcpyAsync(&herr, scal.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    GB_CHECK(sync(ctx));
+    if (herr) return fail(GB_TIMEOUT, "gb_pagerank: a bounded wait for a shared-memory staging copy ran out");
     return GB_SUCCESS;
 }
 
