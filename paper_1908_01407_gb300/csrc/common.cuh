@@ -240,6 +240,17 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialization attribute may start while the kernel before it in
+// the stream drains. grid_dep_wait blocks until that kernel has completed
+// and its writes are visible, so a kernel calls it before it reads anything
+// the previous one wrote; grid_dep_launch lets the next kernel start
+// launching once every block of this one has called it (or exited), so no
+// block of this kernel is ever left without an SM. Both are no-ops in a
+// kernel launched without the attribute.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // one arrival expected (the thread that posts the transaction count)
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");

@@ -101,6 +101,9 @@ __global__ void __launch_bounds__(HUB ? PR_HUB_BLOCK : PR_BLOCK) k_pr_tiles(Tile
     extern __shared__ float4 s_hub4[];
     __shared__ uint64_t s_bar;
     const float *s_hub = reinterpret_cast<const float *>(s_hub4);
+    // x was written by the update kernel before this one in the stream
+    dev::grid_dep_wait();
+    dev::grid_dep_launch();
     if (HUB) {
         // x of the first nhub vertices, once per block: one thread hands the
         // copy to the TMA unit (cp.async.bulk into shared memory, completion
@@ -109,6 +112,8 @@ __global__ void __launch_bounds__(HUB ? PR_HUB_BLOCK : PR_BLOCK) k_pr_tiles(Tile
         // the copy is whole 16-byte units from a 256-byte aligned start.
         const uint32_t bytes = a.nhub * 4u;
         if (threadIdx.x == 0) {
+            // x's writes (generic proxy) before the copy that reads them (async proxy)
+            asm volatile("fence.proxy.async.global;" ::: "memory");
             dev::mbar_init(&s_bar, 1);
             dev::mbar_arrive_expect_tx(&s_bar, bytes);
             constexpr uint32_t CHUNK = 32768;   // bytes per bulk copy
@@ -281,6 +286,8 @@ __global__ void k_pr_long_spans(const uint32_t *trank, uint32_t ntiles, uint2 *l
 
 __global__ void __launch_bounds__(PR_BLOCK) k_pr_span(TileArgs a, uint32_t short_blocks, const uint2 *long_list,
                                                      const uint32_t *long_count) {
+    dev::grid_dep_wait();   // the partial sums of the SpMV kernel before it
+    dev::grid_dep_launch();
     if (blockIdx.x < short_blocks) {
         for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < a.ntiles; t += short_blocks * blockDim.x) {
             if (!a.tflag[t]) continue;
@@ -369,6 +376,8 @@ __global__ void __launch_bounds__(PR_BLOCK) k_pr_update(UpdArgs a) {
     // and the row offsets start 256-byte aligned), and loads G groups
     // before it computes any
     constexpr int G = 2;
+    dev::grid_dep_wait();   // y of the SpMV and span kernels before it
+    dev::grid_dep_launch();
     const uint64_t per = (((uint64_t)a.n + gridDim.x - 1) / gridDim.x + 3) & ~3ull;
     const uint64_t b0 = per * blockIdx.x < a.n ? per * blockIdx.x : a.n;
     const uint64_t b1 = b0 + per < a.n ? b0 + per : a.n;
@@ -549,6 +558,26 @@ static gb_info pagerank_view(const gb_matrix *Ac) {
     return GB_SUCCESS;
 }
 
+// Launches kernel k on the context stream with programmatic stream
+// serialization: its blocks may be scheduled while the kernel before it
+// drains (k calls dev::grid_dep_wait before reading that kernel's output),
+// which hides most of the launch gap between the three kernels of an
+// iteration.
+static gb_info launch_overlapped(gb_context *ctx, const void *k, dim3 grid, dim3 block, size_t smem, void **args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    GB_CUDA(cudaLaunchKernelExC(&cfg, k, args));
+    return GB_SUCCESS;
+}
+
 // One PageRank of `iters` iterations with warp tiles of nsub sub-tiles, on A
 // as stored (order 0) or on its degree-ordered copy with staged ranks (1).
 static gb_info pagerank_run(gb_context *ctx, const gb_matrix *A, float damping, uint32_t iters, float *rank,
@@ -682,14 +711,17 @@ static gb_info pagerank_run(gb_context *ctx, const gb_matrix *A, float damping, 
         if (ntiles) {
             int span = prof_begin(ctx, "pagerank_spmv");
             void *args[] = {&ta};
-            GB_CUDA(cudaLaunchKernel(kern, dim3(G), dim3(block), args, smem, ctx->stream));
+            GB_CHECK(launch_overlapped(ctx, kern, dim3(G), dim3(block), smem, args));
             prof_end(ctx, span);
             int sspan = prof_begin(ctx, "pagerank_span");
-            k_pr_span<<<SB + LB, PR_BLOCK, 0, ctx->stream>>>(ta, SB, lsp.as<uint2>(), nlong);
+            const uint2 *lsp_p = lsp.as<uint2>();
+            void *sargs[] = {&ta, (void *)&SB, (void *)&lsp_p, (void *)&nlong};
+            GB_CHECK(launch_overlapped(ctx, (const void *)k_pr_span, dim3(SB + LB), dim3(PR_BLOCK), 0, sargs));
             prof_end(ctx, sspan);
         }
         int span = prof_begin(ctx, "pagerank_update");
-        k_pr_update<<<UB, PR_BLOCK, 0, ctx->stream>>>(ua);
+        void *uargs[] = {&ua};
+        GB_CHECK(launch_overlapped(ctx, (const void *)k_pr_update, dim3(UB), dim3(PR_BLOCK), 0, uargs));
         prof_end(ctx, span);
         GB_LAUNCH_CHECK();
         float *t = pc; pc = pn; pn = t;
