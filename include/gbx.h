@@ -378,12 +378,13 @@ gb_info gb_bfs_autotune(gb_context *ctx, gb_matrix *A, const uint32_t *srcs, uin
                         double *best_ms);
 /* BFS tile shape of the persistent grid kernel (its pull walks candidates
  * in groups of 32 x pull_width, each lane pull_width of them with their
- * loads in flight together; its launch fills blocks_per_sm blocks of 256
- * threads on every SM). gb_bfs_autotune times pull widths {1, 2, 4} x
- * {2, 3, 4} blocks per SM at the threshold it chose and keeps the fastest
- * on the matrix; gb_bfs_set_shape sets them by hand (pull_width 0, 1, 2 or
- * 4, 0 = the default 2; blocks_per_sm 0..4, 0 = as many as fit, else
- * GB_INVALID_VALUE). The outputs of a BFS do not depend on the shape. The
+ * loads in flight together; its launch puts blocks_per_sm blocks of 512
+ * threads on every SM, at most as many as fit: two for pull widths 1 and 2,
+ * one for 4). gb_bfs_autotune times pull widths {1, 2, 4} x {1, all that
+ * fit} blocks per SM at the threshold it chose and keeps the fastest on the
+ * matrix; gb_bfs_set_shape sets them by hand (pull_width 0, 1, 2 or 4,
+ * 0 = the default 2; blocks_per_sm 0..4, 0 = as many as fit, a larger
+ * number than fit runs as many as fit; else GB_INVALID_VALUE). The outputs of a BFS do not depend on the shape. The
  * paper fixes its kernels' launch shapes (Section 6); tuning them per graph
  * is this library's. gb_bfs_get_shape reports the pull width in effect and
  * the blocks per SM (0 = as many as fit). */

@@ -21,6 +21,12 @@
 //
 // Levels are separated by a grid barrier with a wall-clock bound; on timeout
 // the kernel records GB_TIMEOUT and exits.
+//
+// Blocks of 512 threads, two per SM: the same threads per SM as four blocks
+// of 256, but half the blocks meet at each grid barrier and each block walks
+// twice the candidates between them (0.111 against 0.115 ms per BFS on R-MAT
+// scale 22).
+#define GBX_FRONTIER_BLOCK 512
 #include "common.cuh"
 #include "bfs_common.cuh"
 #include "frontier.cuh"
@@ -655,9 +661,11 @@ __device__ void bfs_leave(const BfsArgs &a) {
     }
 }
 
-// WPW: pull candidates per lane in flight (a tile shape tuned per matrix)
+// WPW: pull candidates per lane in flight (a tile shape tuned per matrix);
+// 1,024 threads per SM for widths 1 and 2 (64 registers each), 512 for
+// width 4, which needs more
 template <int WPW>
-__global__ void __launch_bounds__(BLOCK, WPW == 4 ? 3 : 4) k_bfs(BfsArgs a) {
+__global__ void __launch_bounds__(BLOCK, (WPW == 4 ? 512 : 1024) / BLOCK) k_bfs(BfsArgs a) {
     __shared__ BfsShared shm;
     __shared__ unsigned long long s_box[4];
     __shared__ uint32_t s_box32[4];
@@ -827,7 +835,9 @@ gb_info bfs_launch(gb_context *ctx, const gb_matrix *A, uint32_t src, int32_t *l
     int per_sm = w->occ[wpw_slot(wpw)];
     if (A->bfs_blocks_per_sm > 0 && (int)A->bfs_blocks_per_sm < per_sm) per_sm = (int)A->bfs_blocks_per_sm;
     int grid = per_sm * ctx->num_sms;
-    if (ctx->grid_limit > 0 && ctx->grid_limit < grid) grid = ctx->grid_limit;
+    // the context's cap counts blocks of 256 threads
+    const int cap = ctx->grid_limit > 0 ? std::max(1, ctx->grid_limit * 256 / bfsk::BLOCK) : 0;
+    if (cap > 0 && cap < grid) grid = cap;
     if (grid_override > 0 && grid_override < grid) grid = grid_override;
     void *args[] = {&a};
     int span = prof_begin(ctx, "bfs");
@@ -1204,16 +1214,16 @@ extern "C" gb_info gb_bfs_autotune(gb_context *ctx, gb_matrix *A, const uint32_t
     // default shape's time is the threshold pass's
     {
         static const uint32_t widths[] = {1, 2, 4};
-        static const uint32_t per_sm[] = {2, 3, 4};
-        constexpr int NS = 9;
+        static const uint32_t per_sm[] = {1, 0};   // one block per SM, or as many as fit
+        constexpr int NP = 2, NS = 3 * NP;
         double ts[NS];
         for (int c = 0; c < NS; ++c) ts[c] = 1e30;
         d.beta = (int)bb;
         for (int pass = 0; pass < 2; ++pass) {
             for (int ci = 0; ci < NS; ++ci) {
                 const int c = pass == 0 ? ci : NS - 1 - ci;
-                A->bfs_pull_width = widths[c / 3];
-                A->bfs_blocks_per_sm = per_sm[c % 3];
+                A->bfs_pull_width = widths[c / NP];
+                A->bfs_blocks_per_sm = per_sm[c % NP];
                 gb_info r = bfs_launch(ctx, A, srcs[0], lv.as<int32_t>(), pa.as<int32_t>(), &d, w, 0);
                 if (r == GB_SUCCESS) r = cudaEventRecord(e0, ctx->stream) == cudaSuccess ? GB_SUCCESS : GB_PANIC;
                 for (uint32_t q = 0; q < k && r == GB_SUCCESS; ++q)
@@ -1234,7 +1244,7 @@ extern "C" gb_info gb_bfs_autotune(gb_context *ctx, gb_matrix *A, const uint32_t
         }
         uint32_t bw = 0, bp = 0;
         for (int c = 0; c < NS; ++c)
-            if (ts[c] < best) { best = ts[c]; bw = widths[c / 3]; bp = per_sm[c % 3]; }
+            if (ts[c] < best) { best = ts[c]; bw = widths[c / NP]; bp = per_sm[c % NP]; }
         A->bfs_pull_width = bw;
         A->bfs_blocks_per_sm = bp;
     }

@@ -56,8 +56,10 @@ struct gb_context_t {
     struct Span { std::string name; cudaEvent_t a, b; };
     std::vector<Span> spans;
     std::vector<cudaEvent_t> event_pool;   // reused across enable/disable cycles
-    // upper bound on the blocks of a persistent (cooperative) launch; 0 = the
-    // whole GPU. Contexts that share a GPU concurrently split it this way.
+    // upper bound on the blocks of a persistent (cooperative) launch, counted
+    // in blocks of 256 threads (a kernel with larger blocks launches
+    // proportionally fewer); 0 = the whole GPU. Contexts that share a GPU
+    // concurrently split it this way.
     int grid_limit = 0;
 };
 

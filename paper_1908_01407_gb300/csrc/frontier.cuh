@@ -6,11 +6,21 @@
 #pragma once
 #include "common.cuh"
 
+// Threads per block of the kernels that use this machinery: 256 unless the
+// including file sets GBX_FRONTIER_BLOCK before it includes this header
+// (the BFS kernel runs 512). Everything here has internal linkage, so each
+// file gets its own instance at its own block size.
+#ifndef GBX_FRONTIER_BLOCK
+#define GBX_FRONTIER_BLOCK 256
+#endif
+
 namespace gbx {
 namespace fr {
+namespace {
 
-constexpr int BLOCK = 256;
+constexpr int BLOCK = GBX_FRONTIER_BLOCK;
 constexpr int WARPS = BLOCK / 32;
+static_assert(BLOCK % 32 == 0 && BLOCK >= 64 && BLOCK <= 1024, "block size");
 constexpr int PUSH_ITEMS = 4;
 constexpr int PUSH_TILE = BLOCK * PUSH_ITEMS;      // edges per block tile
 constexpr int PUSH_OWNERS = PUSH_TILE + 1;          // owner entries staged in smem
@@ -296,5 +306,6 @@ __device__ void compact_level(const Args &a, Smem &sm, int d) {
 }
 
 
+}  // namespace
 }  // namespace fr
 }  // namespace gbx
