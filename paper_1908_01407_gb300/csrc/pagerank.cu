@@ -562,7 +562,9 @@ static gb_info pagerank_view(const gb_matrix *Ac) {
 // serialization: its blocks may be scheduled while the kernel before it
 // drains (k calls dev::grid_dep_wait before reading that kernel's output),
 // which hides most of the launch gap between the three kernels of an
-// iteration.
+// iteration. Not while the context shares the GPU (a capped context, as in
+// the serving loop): blocks placed early wait on the SMs, holding slots that
+// concurrent jobs could run in.
 static gb_info launch_overlapped(gb_context *ctx, const void *k, dim3 grid, dim3 block, size_t smem, void **args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
@@ -573,7 +575,7 @@ static gb_info launch_overlapped(gb_context *ctx, const void *k, dim3 grid, dim3
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = ctx->grid_limit > 0 ? 0 : 1;
     GB_CUDA(cudaLaunchKernelExC(&cfg, k, args));
     return GB_SUCCESS;
 }
