@@ -104,3 +104,15 @@ def test_traffic_record_of_a_sample_scales_by_algorithmic_bytes(tmp_path):
         assert bench.recorded_traffic("p.md", ["k.cu"], 16, "2,0", 110.0) is None
     finally:
         bench.ROOT = old_root
+
+
+def test_committed_bfs_traffic_records_match_the_committed_kernel():
+    """The DRAM traffic the bench reports beside k_bfs comes from records in
+    the kernel's profile summary that were captured on the same kernel code
+    (their digest equals that of the BFS sources as committed) at the tile
+    shape the autotuner picks on the benchmark graph, for each threshold it
+    picks there; a kernel change without a new capture fails here."""
+    for beta in (16, 20, 24):
+        t = bench.recorded_traffic(bench.BFS_PROFILE, bench.BFS_KERNEL_SOURCES, beta, "1,0", 101.3e6)
+        assert t is not None, beta
+        assert 1.3 < t / 101.3e6 < 1.7      # the 32-byte pull records: ~1.5x the algorithmic bytes
